@@ -1,0 +1,222 @@
+"""Seeded synthetic densities for the vdW-DF nonlocal-correlation path.
+
+This module holds no arithmetic of the vdW-DF method: it only makes inputs
+(a density n on a periodic grid and sigma = |grad n|^2) with the shapes and
+structure of the paper's workloads.  Both the CUDA path and the FP64 oracle
+are fed from here; nothing here depends on either.
+
+Density model: a floor plus periodic atom-like exponentials
+    n(r) = floor + sum_a sum_R Z_a zeta_a^3 / (8 pi) exp(-zeta_a |r - R_a - R|)
+(each term integrates to Z_a electrons).  Periodic images R are summed while
+zeta_a |r - R_a - R| <= 30 can occur (exp(-30) ~ 1e-13 of the peak, below the
+floor).  sigma is |grad n|^2 from a spectral
+gradient with the Nyquist component of each axis zeroed.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import List, Sequence, Tuple
+
+import numpy as np
+import torch
+
+Atom = Tuple[float, float, Tuple[float, float, float]]   # (Z, zeta, centre)
+
+
+@dataclass
+class System:
+    """One synthetic evaluation: grid shape, cell (rows = lattice vectors,
+    bohr), functional id (1 = vdW-DF1, 2 = vdW-DF2), n and sigma (float64)."""
+    shape: Tuple[int, int, int]
+    cell: np.ndarray
+    functional: int
+    n: torch.Tensor
+    sigma: torch.Tensor
+    atoms: List[Atom] = field(default_factory=list)
+    name: str = ""
+
+    @property
+    def npts(self) -> int:
+        return int(self.shape[0] * self.shape[1] * self.shape[2])
+
+
+def _grid_coords(shape, cell, device):
+    cell_t = torch.as_tensor(np.asarray(cell, dtype=np.float64), device=device)
+    fr = [torch.arange(s, dtype=torch.float64, device=device) / s for s in shape]
+    fx, fy, fz = torch.meshgrid(*fr, indexing="ij")
+    frac = torch.stack([fx, fy, fz], dim=-1)            # (nx, ny, nz, 3)
+    return frac @ cell_t                                 # cartesian
+
+
+def density(shape, cell, atoms: Sequence[Atom], floor: float = 1e-10,
+            device="cpu", cutoff: float = 30.0) -> torch.Tensor:
+    """n(r) on the grid (float64, [nx][ny][nz], z contiguous)."""
+    cell = np.asarray(cell, dtype=np.float64)
+    r = _grid_coords(shape, cell, device)
+    n = torch.full(tuple(shape), float(floor), dtype=torch.float64, device=device)
+    # shortest distance between opposite faces, for the image range
+    vol = abs(np.linalg.det(cell))
+    heights = [vol / np.linalg.norm(np.cross(cell[(i + 1) % 3], cell[(i + 2) % 3])) for i in range(3)]
+    cell_t = torch.as_tensor(cell, device=device)
+    mid = 0.5 * cell.sum(axis=0)
+    half_diag = 0.5 * max(np.linalg.norm(cell[0] * sx + cell[1] * sy + cell[2] * sz)
+                          for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1))
+    for Z, zeta, centre in atoms:
+        reach = cutoff / zeta
+        nimg = [int(math.ceil(reach / h)) + 1 for h in heights]
+        pref = Z * zeta ** 3 / (8.0 * math.pi)
+        c = torch.as_tensor(np.asarray(centre, dtype=np.float64), device=device)
+        for i in range(-nimg[0], nimg[0] + 1):
+            for j in range(-nimg[1], nimg[1] + 1):
+                for k in range(-nimg[2], nimg[2] + 1):
+                    shift_np = np.asarray(centre) + i * cell[0] + j * cell[1] + k * cell[2]
+                    if (np.linalg.norm(shift_np - mid) - half_diag) * zeta > cutoff:
+                        continue          # this image cannot reach the cell
+                    shift = c + i * cell_t[0] + j * cell_t[1] + k * cell_t[2]
+                    d = torch.linalg.vector_norm(r - shift, dim=-1)
+                    n += pref * torch.exp(-zeta * d)
+    return n
+
+
+def spectral_sigma(n: torch.Tensor, cell) -> torch.Tensor:
+    """sigma = |grad n|^2 with the gradient taken spectrally (Nyquist zeroed)."""
+    shape = n.shape
+    dev = n.device
+    cell = np.asarray(cell, dtype=np.float64)
+    B = torch.as_tensor(2.0 * np.pi * np.linalg.inv(cell).T, device=dev)   # rows b_j
+    nk = torch.fft.fftn(n)
+    ms = []
+    for s in shape:
+        m = torch.fft.fftfreq(s, 1.0 / s, dtype=torch.float64, device=dev)
+        if s % 2 == 0:
+            m[s // 2] = 0.0
+        ms.append(m)
+    mx, my, mz = torch.meshgrid(*ms, indexing="ij")
+    sig = torch.zeros(shape, dtype=torch.float64, device=dev)
+    for c in range(3):
+        kc = mx * B[0, c] + my * B[1, c] + mz * B[2, c]
+        g = torch.fft.ifftn(1j * kc * nk).real
+        sig += g * g
+    return sig
+
+
+def make_system(shape, cell, atoms, functional=1, floor=1e-10, device="cpu", name="") -> System:
+    n = density(shape, cell, atoms, floor, device)
+    s = spectral_sigma(n, cell)
+    return System(tuple(int(v) for v in shape), np.asarray(cell, dtype=np.float64),
+                  int(functional), n, s, list(atoms), name)
+
+
+# ---------------------------------------------------------------------------
+# Workloads (sizes and structure of the paper's use cases, all synthetic).
+# ---------------------------------------------------------------------------
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+def small_cubic(seed=0, ngrid=24, L=10.0, natoms=4, functional=1, device="cpu") -> System:
+    """24^3 grid in a cubic 10 bohr cell, 4 exponentials with Z in [1, 8],
+    zeta in [1, 3] and uniform centres, floor 1e-10."""
+    g = _rng(seed)
+    atoms = [(float(g.uniform(1, 8)), float(g.uniform(1, 3)), tuple(g.uniform(0, L, 3)))
+             for _ in range(natoms)]
+    cell = np.diag([L, L, L])
+    return make_system((ngrid,) * 3, cell, atoms, functional, 1e-10, device,
+                       "cubic%d_L%g_s%d" % (ngrid, L, seed))
+
+
+def dimer(seed=0, shape=(96, 96, 96), cell_lengths=(18.0, 18.0, 24.0), per_cluster=12,
+          functional=1, device="cpu") -> System:
+    """Dimer-like density: two clusters of 12 exponentials each (offsets
+    N(0, 1.5 bohr) around centres separated by d in [3, 8] bohr along z),
+    orthorhombic 18 x 18 x 24 bohr cell on a 96^3 grid."""
+    g = _rng(seed)
+    Lx, Ly, Lz = cell_lengths
+    d = g.uniform(3.0, 8.0)
+    atoms = []
+    for cz in (0.5 * Lz - 0.5 * d, 0.5 * Lz + 0.5 * d):
+        for _ in range(per_cluster):
+            off = g.normal(0.0, 1.5, 3)
+            c = (0.5 * Lx + off[0], 0.5 * Ly + off[1], cz + off[2])
+            atoms.append((float(g.uniform(1, 6)), float(g.uniform(1.2, 3.0)), c))
+    return make_system(shape, np.diag(cell_lengths), atoms, functional, 1e-10, device,
+                       "dimer%dx%dx%d_s%d_df%d" % (shape + (seed, functional)))
+
+
+def ligand_shell(seed=0, ngrid=192, L=36.0, functional=1, device="cpu") -> System:
+    """Ligand-shell-like sparse density: a core of 40 exponentials within
+    5 bohr of the centre (Z in [6, 8], zeta in [2, 3]) and 160 on 20 radial
+    chains out to about 14 bohr (Z in [1, 6], zeta in [1, 2.5]); floor 1e-10,
+    vacuum near 1e-8."""
+    g = _rng(seed)
+    c0 = np.array([L / 2] * 3)
+    atoms = []
+    for _ in range(40):
+        v = g.normal(size=3)
+        v *= g.uniform(0, 5.0) / np.linalg.norm(v)
+        atoms.append((float(g.uniform(6, 8)), float(g.uniform(2, 3)), tuple(c0 + v)))
+    for _ in range(20):
+        u = g.normal(size=3)
+        u /= np.linalg.norm(u)
+        for s in range(8):
+            rad = 6.0 + s * 1.1 + g.normal(0, 0.2)
+            atoms.append((float(g.uniform(1, 6)), float(g.uniform(1, 2.5)), tuple(c0 + rad * u)))
+    return make_system((ngrid,) * 3, np.diag([L, L, L]), atoms, functional, 1e-10, device,
+                       "shell%d_s%d" % (ngrid, seed))
+
+
+def uneven_batch(seed=0, count=64, sizes=(32, 48, 64, 80, 96, 128), functional_mix=True,
+                 device="cpu") -> List[System]:
+    """Independent systems with grids drawn per axis from ``sizes`` (non-cubic
+    mixes), spacing h in [0.15, 0.30] bohr and 4-60 exponentials each."""
+    g = _rng(seed)
+    out = []
+    for i in range(count):
+        shape = tuple(int(v) for v in g.choice(sizes, 3))
+        h = g.uniform(0.15, 0.30)
+        lengths = [s * h for s in shape]
+        na = int(g.integers(4, 61))
+        atoms = [(float(g.uniform(1, 8)), float(g.uniform(1, 3)),
+                  tuple(g.uniform(0, 1, 3) * lengths)) for _ in range(na)]
+        fn = int(g.integers(1, 3)) if functional_mix else 1
+        out.append(make_system(shape, np.diag(lengths), atoms, fn, 1e-10, device,
+                               "batch%d_%dx%dx%d" % ((i,) + shape)))
+    return out
+
+
+def serving_requests(seed=0, count=2000, rate=200.0,
+                     sizes=(48, 64, 80, 96, 112, 128, 160, 192, 224),
+                     cap=(160, 192, 224)):
+    """Poisson arrival times (mean ``rate`` per second) and request specs
+    (grid shape sorted and capped at 160 x 192 x 224, 10-400 exponentials).
+    Densities are built lazily by :func:`realise`."""
+    g = _rng(seed)
+    t = np.cumsum(g.exponential(1.0 / rate, count))
+    reqs = []
+    for i in range(count):
+        shape = sorted(int(v) for v in g.choice(sizes, 3))
+        shape = tuple(min(s, c) for s, c in zip(shape, cap))
+        h = g.uniform(0.15, 0.30)
+        na = int(g.integers(10, 401))
+        reqs.append({"id": i, "arrival": float(t[i]), "shape": shape, "h": float(h),
+                     "natoms": na, "seed": int(g.integers(0, 2 ** 31)),
+                     "functional": int(g.integers(1, 3))})
+    return reqs
+
+
+def realise(req, device="cpu") -> System:
+    g = _rng(req["seed"])
+    lengths = [s * req["h"] for s in req["shape"]]
+    atoms = [(float(g.uniform(1, 8)), float(g.uniform(1, 3)),
+              tuple(g.uniform(0, 1, 3) * lengths)) for _ in range(req["natoms"])]
+    return make_system(req["shape"], np.diag(lengths), atoms, req["functional"], 1e-10, device,
+                       "req%d" % req["id"])
+
+
+def hello_example():
+    """The 1 x 2 x 2 example of the library section: rho = 1..4,
+    sigma = 0.5..3.5, cell diag(1, 2, 2), vdW-DF1."""
+    n = torch.tensor([1.0, 2.0, 3.0, 4.0], dtype=torch.float64).reshape(1, 2, 2)
+    s = torch.tensor([0.5, 1.5, 2.5, 3.5], dtype=torch.float64).reshape(1, 2, 2)
+    return System((1, 2, 2), np.diag([1.0, 2.0, 2.0]), 1, n, s, [], "hello")
