@@ -1,0 +1,174 @@
+/*
+ * vdwgb -- GB300-native vdW-DF nonlocal correlation (Roman-Perez--Soler FFT
+ * evaluation of E_c^nl and its potential), arXiv:1703.06999.
+ *
+ * C ABI.  Plain pointers and sizes only.  Every function returns 0 on
+ * success or a negative VDWGB_E* code; nothing is thrown across the ABI.
+ * vdwgb_strerror() names a code; vdwgb_last_error() gives the message of the
+ * calling thread's last failure.
+ *
+ * Calling sequence (Sec. 6 of the paper, "The library"): create a handle for
+ * a functional (vdwgb_new), give it the grid and unit cell
+ * (vdwgb_set_unit_cell), initialise the backend and its memory
+ * (vdwgb_init_cuda), evaluate any number of times (vdwgb_calculate /
+ * vdwgb_calculate_device), release (vdwgb_finalize).
+ *
+ * Arrays: row-major [nx][ny][nz], z contiguous (the density grid of Sec. 3
+ * with x least contiguous).  Units: bohr and Hartree.  Cell: three rows, the
+ * lattice vectors a_1, a_2, a_3 (row i = a_i).
+ *
+ * Outputs (Eq. dedn, Eq. dedsigma): dedrho[i] = dE/dn(r_i) at fixed sigma and
+ * dedsigma[i] = dE/dsigma(r_i) at fixed n, both per unit volume (so that
+ * dE = sum_i dV (dedrho_i dn_i + dedsigma_i dsigma_i)).  They are OVERWRITTEN,
+ * not accumulated.  Points with n <= 1e-12 give theta = 0 and zero
+ * derivatives; sigma < 0 is treated as 0.
+ */
+#ifndef VDWGB_H
+#define VDWGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Functionals: the nonlocal part differs only by Z_ab (appendix, q0):
+ * vdW-DF1 Z_ab = -0.8491, vdW-DF2 Z_ab = -1.887. */
+enum { VDWGB_DF1 = 1, VDWGB_DF2 = 2 };
+
+/* Precision of the evaluation.
+ *   VDWGB_FP64        every step in FP64 (the paper computes in double
+ *                     precision, Sec. 6).
+ *   VDWGB_FP32_MIXED  theta fields, FFTs and kernel contraction in FP32;
+ *                     q0, saturation and spline coefficients in FP64; the
+ *                     energy sum in FP64. */
+enum { VDWGB_FP64 = 0, VDWGB_FP32_MIXED = 1 };
+
+/* Kernel interpolation in |k| (Sec. 3, procedure step 3a): the paper
+ * interpolates the tabulated phi_ab(k) linearly; the default here is a
+ * natural cubic spline through the same table. */
+enum { VDWGB_INTERP_CUBIC = 0, VDWGB_INTERP_LINEAR = 1 };
+
+/* Error codes. */
+enum {
+    VDWGB_OK = 0,
+    VDWGB_EINVAL = -1,    /* bad argument (null pointer, bad size or enum)  */
+    VDWGB_ENOMEM = -2,    /* device or host allocation failed               */
+    VDWGB_ECUDA = -3,     /* a CUDA call failed (message in last_error)     */
+    VDWGB_ESTATE = -4,    /* call out of sequence (e.g. calculate before init) */
+    VDWGB_ETIMEDOUT = -5, /* a bounded wait ran out                         */
+    VDWGB_EAGAIN = -6,    /* not admitted now (serving); retry later        */
+    VDWGB_ENOTFOUND = -7  /* unknown request id (serving)                   */
+};
+
+typedef struct vdwgb_data *vdwgb_handle;
+
+/* ---- single-system interface (paper-shaped) -------------------------- */
+
+/* Create an empty handle for a functional (cf. vdwxc_new, Sec. 6).
+ * functional: VDWGB_DF1 or VDWGB_DF2.  *out receives the handle, owned by
+ * the library until vdwgb_finalize.  EINVAL on a bad functional or null out. */
+int vdwgb_new(int functional, vdwgb_handle *out);
+
+/* Grid points per axis and the unit cell (cf. vdwxc_set_unit_cell, Sec. 6).
+ * nx, ny, nz >= 1 with every prime factor in {2, 3, 5, 7} and each <= 1024
+ * (EINVAL otherwise); cXY = component Y of lattice vector X (bohr).  The cell
+ * must have positive volume.  Calling it again after init re-plans at the
+ * next vdwgb_init_cuda. */
+int vdwgb_set_unit_cell(vdwgb_handle h, int nx, int ny, int nz,
+                        double c00, double c01, double c02,
+                        double c10, double c11, double c12,
+                        double c20, double c21, double c22);
+
+/* Choose kernel interpolation (VDWGB_INTERP_*) before init.  Default cubic. */
+int vdwgb_set_interp(vdwgb_handle h, int interp);
+
+/* Initialise on a CUDA device (cf. vdwxc_init_serial, Sec. 6): builds the
+ * resident kernel table on that device (once per device and process),
+ * plans the FFTs, allocates the work buffer (20 complex fields on the
+ * half spectrum) and the per-point records.  precision: VDWGB_FP64 or
+ * VDWGB_FP32_MIXED.  ENOMEM if the device is out of memory, ECUDA on other
+ * CUDA failures, ESTATE if the cell was not set. */
+int vdwgb_init_cuda(vdwgb_handle h, int device, int precision);
+
+/* Evaluate E_c^nl and its partial derivatives from HOST arrays (cf.
+ * vdwxc_calculate, Sec. 6).  rho, sigma: nx*ny*nz doubles (read).  dedrho,
+ * dedsigma: nx*ny*nz doubles (overwritten).  energy: one double (written,
+ * Hartree).  Blocking; copies in and out through pinned staging buffers
+ * owned by the handle.  Callable any number of times after init. */
+int vdwgb_calculate(vdwgb_handle h, const double *rho, const double *sigma,
+                    double *dedrho, double *dedsigma, double *energy);
+
+/* The same with DEVICE pointers, enqueued on cuda_stream (a cudaStream_t,
+ * NULL = the legacy default stream); returns without waiting.  d_energy is
+ * one device double.  The caller keeps every pointer valid until the stream
+ * work completes and must not run two calls of one handle concurrently. */
+int vdwgb_calculate_device(vdwgb_handle h, const double *d_rho, const double *d_sigma,
+                           double *d_dedrho, double *d_dedsigma, double *d_energy,
+                           void *cuda_stream);
+
+/* Paper-shaped convenience: returns the energy, NaN on any error. */
+double vdwgb_calculate_simple(vdwgb_handle h, const double *rho, const double *sigma,
+                              double *dedrho, double *dedsigma);
+
+/* Release every resource of the handle and set *h = NULL (cf. vdwxc_finalize). */
+int vdwgb_finalize(vdwgb_handle *h);
+
+/* ---- information --------------------------------------------------- */
+
+const char *vdwgb_strerror(int code);
+const char *vdwgb_last_error(void);
+/* Print the handle's state (functional, grid, cell, plan, memory) to stdout. */
+int vdwgb_print(vdwgb_handle h);
+/* 1 if a CUDA device is usable by this library, else 0. */
+int vdwgb_has_cuda(void);
+/* Bytes of device memory one handle of this grid and precision allocates
+ * (work buffer + records + partials), excluding the shared kernel table. */
+size_t vdwgb_footprint_bytes(int nx, int ny, int nz, int precision);
+
+/* Number of our kernel launches one evaluation enqueues (all stages). */
+int vdwgb_launches_per_call(vdwgb_handle h);
+
+/* ---- kernel table (setup, resident per device) ------------------------ */
+
+/* Copy the resident FP64 tables of `device` to host memory (building them if
+ * needed).  phik: 210 * 1024 doubles, phi_ab(k_j) for the symmetric pairs
+ * (a <= b, row-major) at k_j = j * 2 pi / 100 bohr; phir: 210 * 1025 doubles,
+ * phi_ab(r_i) = phi(q_a r_i, q_b r_i) at r_i = i * 100/1024 bohr; qmesh: 20
+ * doubles.  Any pointer may be NULL.  (Sec. 2: the M x M radial functions
+ * phi_ab(k) on a discrete k-grid; the kernel phi of Eq. 2.) */
+int vdwgb_kernel_table(int device, double *phik, double *phir, double *qmesh);
+
+/* phi(d1[i], d2[i]) for npts pairs on `device` with the table's quadrature
+ * (host arrays in and out), for checking the kernel itself. */
+int vdwgb_phi(int device, int npts, const double *d1, const double *d2, double *out);
+
+/* Seconds spent building the table on `device` (0 if not built). */
+double vdwgb_table_build_seconds(int device);
+
+/* ---- batched form: many independent systems, one launch per stage ----- */
+
+typedef struct vdwgb_batch_s *vdwgb_batch;
+
+/* Create a batch of `count` initialised handles (same device and precision,
+ * any grids).  The batch owns a launch plan over all systems and a CUDA
+ * graph of its stages; the handles stay owned by the caller and must
+ * outlive the batch. */
+int vdwgb_batch_new(vdwgb_handle *handles, int count, vdwgb_batch *out);
+
+/* Evaluate every system of the batch from DEVICE arrays enqueued on
+ * cuda_stream: d_rho[i], d_sigma[i], d_dedrho[i], d_dedsigma[i] point to the
+ * arrays of system i, d_energy to `count` device doubles.  One launch per
+ * stage covers all systems (persistent tile loop), replayed from a CUDA
+ * graph when the pointer set repeats. */
+int vdwgb_batch_calculate_device(vdwgb_batch b, const double *const *d_rho,
+                                 const double *const *d_sigma, double *const *d_dedrho,
+                                 double *const *d_dedsigma, double *d_energy, void *cuda_stream);
+int vdwgb_batch_free(vdwgb_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VDWGB_H */

@@ -1,0 +1,234 @@
+"""Thin ctypes binding of ``libvdwgb.so`` (C ABI in ``include/vdwgb.h``).
+
+Functions carry the C names and only marshal arguments: every step of the
+evaluation runs in the CUDA library.  A missing library raises at load time;
+there is no CPU fallback.  torch is used only to hand over device pointers
+and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvdwgb.so")
+
+DF1, DF2 = 1, 2
+FP64, FP32_MIXED = 0, 1
+INTERP_CUBIC, INTERP_LINEAR = 0, 1
+NQ, NPAIR, NK, NR = 20, 210, 1024, 1024
+
+_c_double_p = ctypes.POINTER(ctypes.c_double)
+_lib = None
+
+# name: (restype, argtypes)
+_SIGS = {
+    "vdwgb_new": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "vdwgb_set_unit_cell": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+                            + [ctypes.c_double] * 9),
+    "vdwgb_set_interp": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "vdwgb_init_cuda": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "vdwgb_calculate": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 5),
+    "vdwgb_calculate_device": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 6),
+    "vdwgb_calculate_simple": (ctypes.c_double, [ctypes.c_void_p] + [ctypes.c_void_p] * 4),
+    "vdwgb_finalize": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p)]),
+    "vdwgb_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "vdwgb_last_error": (ctypes.c_char_p, []),
+    "vdwgb_print": (ctypes.c_int, [ctypes.c_void_p]),
+    "vdwgb_has_cuda": (ctypes.c_int, []),
+    "vdwgb_footprint_bytes": (ctypes.c_size_t, [ctypes.c_int] * 4),
+    "vdwgb_launches_per_call": (ctypes.c_int, [ctypes.c_void_p]),
+    "vdwgb_kernel_table": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "vdwgb_phi": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "vdwgb_table_build_seconds": (ctypes.c_double, [ctypes.c_int]),
+    "vdwgb_batch_new": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "vdwgb_batch_calculate_device": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 6),
+    "vdwgb_batch_free": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p)]),
+}
+
+
+class VdwgbError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = lib().vdwgb_last_error().decode(errors="replace")
+        super().__init__("%s failed: %s (%d): %s" % (where, lib().vdwgb_strerror(code).decode(), code, msg))
+
+
+def lib():
+    """Load the CUDA library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("CUDA library %s is missing; build it with __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ck(rc, where):
+    if rc != 0:
+        raise VdwgbError(rc, where)
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+# ---- C-named wrappers ----------------------------------------------------
+def vdwgb_new(functional):
+    h = ctypes.c_void_p()
+    _ck(lib().vdwgb_new(int(functional), ctypes.byref(h)), "vdwgb_new")
+    return h
+
+
+def vdwgb_set_unit_cell(h, shape, cell):
+    cell = np.asarray(cell, dtype=np.float64).reshape(9)
+    _ck(lib().vdwgb_set_unit_cell(h, int(shape[0]), int(shape[1]), int(shape[2]), *[float(v) for v in cell]),
+        "vdwgb_set_unit_cell")
+
+
+def vdwgb_set_interp(h, interp):
+    _ck(lib().vdwgb_set_interp(h, int(interp)), "vdwgb_set_interp")
+
+
+def vdwgb_init_cuda(h, device=0, precision=FP64):
+    _ck(lib().vdwgb_init_cuda(h, int(device), int(precision)), "vdwgb_init_cuda")
+
+
+def vdwgb_calculate(h, rho, sigma, dedrho, dedsigma):
+    """Host arrays (float64, C order); returns the energy."""
+    e = np.zeros(1)
+    _ck(lib().vdwgb_calculate(h, _ptr(rho), _ptr(sigma), _ptr(dedrho), _ptr(dedsigma), e.ctypes.data),
+        "vdwgb_calculate")
+    return float(e[0])
+
+
+def vdwgb_calculate_device(h, rho, sigma, dedrho, dedsigma, energy, stream=0):
+    """Device tensors (float64, contiguous); ``stream`` is a raw cudaStream_t."""
+    _ck(lib().vdwgb_calculate_device(h, _ptr(rho), _ptr(sigma), _ptr(dedrho), _ptr(dedsigma), _ptr(energy),
+                                     ctypes.c_void_p(int(stream))), "vdwgb_calculate_device")
+
+
+def vdwgb_calculate_simple(h, rho, sigma, dedrho, dedsigma):
+    return float(lib().vdwgb_calculate_simple(h, _ptr(rho), _ptr(sigma), _ptr(dedrho), _ptr(dedsigma)))
+
+
+def vdwgb_finalize(h):
+    _ck(lib().vdwgb_finalize(ctypes.byref(h)), "vdwgb_finalize")
+
+
+def vdwgb_strerror(code):
+    return lib().vdwgb_strerror(int(code)).decode()
+
+
+def vdwgb_last_error():
+    return lib().vdwgb_last_error().decode(errors="replace")
+
+
+def vdwgb_print(h):
+    _ck(lib().vdwgb_print(h), "vdwgb_print")
+
+
+def vdwgb_has_cuda():
+    return bool(lib().vdwgb_has_cuda())
+
+
+def vdwgb_footprint_bytes(shape, precision):
+    return int(lib().vdwgb_footprint_bytes(int(shape[0]), int(shape[1]), int(shape[2]), int(precision)))
+
+
+def vdwgb_launches_per_call(h):
+    return int(lib().vdwgb_launches_per_call(h))
+
+
+def vdwgb_kernel_table(device=0):
+    phik = np.zeros((NPAIR, NK))
+    phir = np.zeros((NPAIR, NR + 1))
+    q = np.zeros(NQ)
+    _ck(lib().vdwgb_kernel_table(int(device), phik.ctypes.data, phir.ctypes.data, q.ctypes.data),
+        "vdwgb_kernel_table")
+    return phik, phir, q
+
+
+def vdwgb_phi(d1, d2, device=0):
+    d1 = np.ascontiguousarray(d1, dtype=np.float64).ravel()
+    d2 = np.ascontiguousarray(d2, dtype=np.float64).ravel()
+    out = np.zeros(d1.size)
+    _ck(lib().vdwgb_phi(int(device), d1.size, d1.ctypes.data, d2.ctypes.data, out.ctypes.data), "vdwgb_phi")
+    return out
+
+
+def vdwgb_table_build_seconds(device=0):
+    return float(lib().vdwgb_table_build_seconds(int(device)))
+
+
+def vdwgb_batch_new(handles):
+    arr = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
+    b = ctypes.c_void_p()
+    _ck(lib().vdwgb_batch_new(arr, len(handles), ctypes.byref(b)), "vdwgb_batch_new")
+    return b
+
+
+def vdwgb_batch_calculate_device(b, rhos, sigmas, dedrhos, dedsigmas, energies, stream=0):
+    n = len(rhos)
+    P = ctypes.c_void_p * n
+    _ck(lib().vdwgb_batch_calculate_device(b, P(*[_ptr(t) for t in rhos]), P(*[_ptr(t) for t in sigmas]),
+                                           P(*[_ptr(t) for t in dedrhos]), P(*[_ptr(t) for t in dedsigmas]),
+                                           _ptr(energies), ctypes.c_void_p(int(stream))),
+        "vdwgb_batch_calculate_device")
+
+
+def vdwgb_batch_free(b):
+    _ck(lib().vdwgb_batch_free(ctypes.byref(b)), "vdwgb_batch_free")
+
+
+# ---- convenience ------------------------------------------------------------
+class Functional:
+    """One initialised handle: ``Functional(shape, cell, functional, precision)``."""
+
+    def __init__(self, shape, cell, functional=DF1, precision=FP64, device=0, interp=INTERP_CUBIC):
+        self.shape = tuple(int(v) for v in shape)
+        self.h = vdwgb_new(functional)
+        try:
+            vdwgb_set_unit_cell(self.h, self.shape, cell)
+            vdwgb_set_interp(self.h, interp)
+            vdwgb_init_cuda(self.h, device, precision)
+        except Exception:
+            vdwgb_finalize(self.h)
+            raise
+
+    def calculate(self, rho, sigma):
+        """Host float64 arrays in; (energy, dedrho, dedsigma) out."""
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+        dn = np.empty_like(rho)
+        ds = np.empty_like(rho)
+        e = vdwgb_calculate(self.h, rho, sigma, dn, ds)
+        return e, dn, ds
+
+    def calculate_device(self, rho, sigma, dedrho, dedsigma, energy, stream=0):
+        vdwgb_calculate_device(self.h, rho, sigma, dedrho, dedsigma, energy, stream)
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            vdwgb_finalize(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,654 @@
+// C ABI of the library (include/vdwgb.h): handles, FFT plans, launches,
+// batches.  Host code only; the kernels are in pipeline.cu and table.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/vdwgb.h"
+#include "common.cuh"
+#include "pipeline.h"
+#include "table.h"
+
+using namespace vdwgb;
+
+static thread_local std::string g_err;
+
+static int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+static int cuda_fail(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation)
+        return fail(VDWGB_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(VDWGB_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// per-device one-time setup: q-mesh constants, kernel shared-memory limits
+// ---------------------------------------------------------------------------
+struct DevInfo {
+    bool ready = false;
+    int sms = 0;
+    size_t maxsmem = 0;
+};
+static std::mutex g_dev_mu;
+static DevInfo g_dev[64];
+
+static int device_setup(int device) {
+    if (device < 0 || device >= 64) return fail(VDWGB_EINVAL, "device %d out of range", device);
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    DevInfo &d = g_dev[device];
+    if (d.ready) return 0;
+    CK(cudaSetDevice(device), "cudaSetDevice");
+    int sms = 0, optin = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device), "attr");
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device), "attr");
+    d.sms = sms;
+    d.maxsmem = (size_t)optin;
+    QMeshDev qm;
+    host_qmesh(qm);
+    CK(upload_qmesh(qm), "upload q-mesh");
+    CK(init_kernels(d.maxsmem - 1024), "kernel attributes");
+    d.ready = true;
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// FFT plan of one axis
+// ---------------------------------------------------------------------------
+static bool factor_axis(int n, AxisPlan &p) {
+    p.n = n;
+    p.nst = 0;
+    int e2 = 0, m = n;
+    while (m % 2 == 0) { m /= 2; ++e2; }
+    std::vector<int> r;
+    while (e2 >= 3) { r.push_back(8); e2 -= 3; }
+    if (e2 == 2) r.push_back(4);
+    if (e2 == 1) r.push_back(2);
+    const int odd[3] = {3, 5, 7};
+    for (int q : odd)
+        while (m % q == 0) { r.push_back(q); m /= q; }
+    if (m != 1 || (int)r.size() > MAXST) return false;
+    p.nst = (int)r.size();
+    for (int i = 0; i < p.nst; ++i) p.rad[i] = r[i];
+    return true;
+}
+
+static std::vector<double> twiddles(int n) {
+    std::vector<double> w(2 * (size_t)n);
+    for (int m = 0; m < n; ++m) {
+        // exp(-2 pi i m / n), argument reduced to the first half-turn for accuracy
+        const double ang = 2.0 * M_PI * (double)m / (double)n;
+        w[2 * m] = std::cos(ang);
+        w[2 * m + 1] = -std::sin(ang);
+    }
+    return w;
+}
+
+// ---------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------
+struct vdwgb_data {
+    int functional = 1;
+    int interp = VDWGB_INTERP_CUBIC;
+    int nx = 0, ny = 0, nz = 0;
+    double cell[9] = {0};
+    bool cell_set = false;
+    bool inited = false;
+    int device = -1;
+    int prec = VDWGB_FP64;
+    // device memory
+    void *spec = nullptr;
+    void *rec = nullptr;
+    double *epart = nullptr;
+    void *tw[3] = {nullptr, nullptr, nullptr};
+    SysDev *dsys = nullptr;
+    int *dprefix = nullptr;
+    SysDev hsys;
+    LaunchSet ls;
+    const void *table = nullptr;
+    size_t bytes = 0;
+    // host-pointer path staging
+    double *d_io = nullptr;      // n, sigma, dedn, dedsigma, energy
+    cudaStream_t stream = nullptr;
+    const double *last_ptr[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+static void release(vdwgb_data *h) {
+    if (!h) return;
+    if (h->device >= 0) cudaSetDevice(h->device);
+    cudaFree(h->spec);
+    cudaFree(h->rec);
+    cudaFree(h->epart);
+    for (int i = 0; i < 3; ++i) cudaFree(h->tw[i]);
+    cudaFree(h->dsys);
+    cudaFree(h->dprefix);
+    cudaFree(h->d_io);
+    if (h->stream) cudaStreamDestroy(h->stream);
+    h->spec = h->rec = nullptr;
+    h->epart = nullptr;
+    h->dsys = nullptr;
+    h->dprefix = nullptr;
+    h->d_io = nullptr;
+    h->stream = nullptr;
+    for (int i = 0; i < 3; ++i) h->tw[i] = nullptr;
+    h->inited = false;
+}
+
+static size_t elem_bytes(int prec) { return prec == VDWGB_FP32_MIXED ? 8 : 16; }
+static size_t rec_bytes(int prec) { return prec == VDWGB_FP32_MIXED ? 16 : 32; }
+
+// Tile choices: z passes LZ lines, x/y passes W columns; prefer two blocks
+// per SM (<= ~110 KB), else fall back to the largest block that fits.
+static void choose_tiles(int prec, int nx, int ny, int nz, int nzh, size_t maxsmem, int &LZ, int &W) {
+    const size_t budget = 110 * 1024;
+    LZ = 1;
+    for (int l = 8; l >= 1; --l)
+        if (stage_smem(0, prec, nz, l) <= budget) { LZ = l; break; }
+    const int nxy = nx > ny ? nx : ny;
+    W = 1;
+    for (int w = 8; w >= 1; --w)
+        if (stage_smem(1, prec, nxy, w) <= budget) { W = w; break; }
+    if (W > nzh) W = nzh;
+    if (LZ > nx * ny) LZ = nx * ny;
+    (void)maxsmem;
+}
+
+static int plan(vdwgb_data *h) {
+    const int prec = h->prec;
+    const int nx = h->nx, ny = h->ny, nz = h->nz, nzh = nz / 2 + 1;
+    DevInfo &di = g_dev[h->device];
+    SysDev &S = h->hsys;
+    std::memset(&S, 0, sizeof S);
+    S.nx = nx;
+    S.ny = ny;
+    S.nz = nz;
+    S.nzh = nzh;
+    const int dims[3] = {nx, ny, nz};
+    for (int a = 0; a < 3; ++a)
+        if (!factor_axis(dims[a], S.ax[a]))
+            return fail(VDWGB_EINVAL, "axis %d length %d: prime factors must be 2, 3, 5, 7", a, dims[a]);
+    choose_tiles(prec, nx, ny, nz, nzh, di.maxsmem, S.LZ, S.W);
+    const size_t lim = di.maxsmem - 1024;
+    if (stage_smem(0, prec, nz, S.LZ) > lim || stage_smem(1, prec, nx, S.W) > lim ||
+        stage_smem(1, prec, ny, S.W) > lim)
+        return fail(VDWGB_EINVAL, "grid %dx%dx%d too large for one block per pencil in this precision",
+                    nx, ny, nz);
+    const int ncol = (nzh + S.W - 1) / S.W;
+    S.tiles[0] = (nx * ny + S.LZ - 1) / S.LZ;
+    S.tiles[1] = nx * ncol;
+    S.tiles[2] = ny * ncol;
+    S.tiles[3] = S.tiles[0];
+    // reciprocal metric g = B B^T, B = 2 pi C^{-T} (rows b_j)
+    const double *c = h->cell;
+    const double det = c[0] * (c[4] * c[8] - c[5] * c[7]) - c[1] * (c[3] * c[8] - c[5] * c[6]) +
+                       c[2] * (c[3] * c[7] - c[4] * c[6]);
+    double inv[9];   // inverse of C
+    inv[0] = (c[4] * c[8] - c[5] * c[7]) / det;
+    inv[1] = (c[2] * c[7] - c[1] * c[8]) / det;
+    inv[2] = (c[1] * c[5] - c[2] * c[4]) / det;
+    inv[3] = (c[5] * c[6] - c[3] * c[8]) / det;
+    inv[4] = (c[0] * c[8] - c[2] * c[6]) / det;
+    inv[5] = (c[2] * c[3] - c[0] * c[5]) / det;
+    inv[6] = (c[3] * c[7] - c[4] * c[6]) / det;
+    inv[7] = (c[1] * c[6] - c[0] * c[7]) / det;
+    inv[8] = (c[0] * c[4] - c[1] * c[3]) / det;
+    double B[9];   // B[j][k] = 2 pi inv[k][j]
+    for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k) B[j * 3 + k] = 2.0 * M_PI * inv[k * 3 + j];
+    double g[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            g[i][j] = B[i * 3] * B[j * 3] + B[i * 3 + 1] * B[j * 3 + 1] + B[i * 3 + 2] * B[j * 3 + 2];
+    S.g[0] = g[0][0];
+    S.g[1] = g[1][1];
+    S.g[2] = g[2][2];
+    S.g[3] = g[0][1];
+    S.g[4] = g[0][2];
+    S.g[5] = g[1][2];
+    const double N = (double)nx * ny * nz;
+    const double omega = std::fabs(det);
+    S.escale = 0.5 * omega / (N * N);
+    S.invN = 1.0 / N;
+    S.Z = h->functional == VDWGB_DF2 ? -1.887 : -0.8491;
+    // memory
+    const size_t nspec = (size_t)nx * ny * nzh * NQ;
+    CK(cudaMalloc(&h->spec, nspec * elem_bytes(prec)), "work buffer");
+    CK(cudaMalloc(&h->rec, (size_t)nx * ny * nz * rec_bytes(prec)), "point records");
+    CK(cudaMalloc(&h->epart, (size_t)S.tiles[2] * sizeof(double)), "energy partials");
+    for (int a = 0; a < 3; ++a) {
+        std::vector<double> w = twiddles(dims[a]);
+        if (prec == VDWGB_FP32_MIXED) {
+            std::vector<float> wf(w.size());
+            for (size_t i = 0; i < w.size(); ++i) wf[i] = (float)w[i];
+            CK(cudaMalloc(&h->tw[a], wf.size() * sizeof(float)), "twiddles");
+            CK(cudaMemcpy(h->tw[a], wf.data(), wf.size() * sizeof(float), cudaMemcpyHostToDevice), "twiddles");
+        } else {
+            CK(cudaMalloc(&h->tw[a], w.size() * sizeof(double)), "twiddles");
+            CK(cudaMemcpy(h->tw[a], w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice), "twiddles");
+        }
+        S.tw[a] = h->tw[a];
+    }
+    S.spec = h->spec;
+    S.rec = h->rec;
+    S.epart = h->epart;
+    h->bytes = nspec * elem_bytes(prec) + (size_t)nx * ny * nz * rec_bytes(prec) + S.tiles[2] * sizeof(double);
+    CK(cudaMalloc(&h->dsys, sizeof(SysDev)), "descriptor");
+    CK(cudaMalloc(&h->dprefix, 8 * sizeof(int)), "prefix");
+    int pre[8];
+    for (int s = 0; s < 4; ++s) {
+        pre[2 * s] = 0;
+        pre[2 * s + 1] = S.tiles[s];
+    }
+    CK(cudaMemcpy(h->dprefix, pre, sizeof pre, cudaMemcpyHostToDevice), "prefix");
+    CK(cudaMemcpy(h->dsys, &S, sizeof(SysDev), cudaMemcpyHostToDevice), "descriptor");
+    // launch set
+    LaunchSet &L = h->ls;
+    L.sys = h->dsys;
+    L.nsys = 1;
+    for (int s = 0; s < 4; ++s) {
+        L.prefix[s] = h->dprefix + 2 * s;
+        L.total[s] = S.tiles[s];
+    }
+    L.smem[0] = stage_smem(0, prec, nz, S.LZ);
+    L.smem[3] = L.smem[0];
+    L.smem[1] = stage_smem(1, prec, ny, S.W);
+    L.smem[2] = stage_smem(1, prec, nx, S.W);
+    for (int s = 0; s < 4; ++s) {
+        int per_sm = (int)((228 * 1024) / (L.smem[s] + 1024));
+        per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
+        const int cap = di.sms * per_sm;
+        L.grid[s] = L.total[s] < cap ? L.total[s] : cap;
+    }
+    TableRefs tr;
+    CK(table_get(h->device, tr), "kernel table");
+    if (prec == VDWGB_FP32_MIXED)
+        L.table = h->interp == VDWGB_INTERP_LINEAR ? (const void *)tr.lin32 : (const void *)tr.cub32;
+    else
+        L.table = h->interp == VDWGB_INTERP_LINEAR ? (const void *)tr.lin64 : (const void *)tr.cub64;
+    h->table = L.table;
+    CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "stream");
+    return 0;
+}
+
+static bool axis_ok(int n) {
+    if (n < 1 || n > 1024) return false;
+    AxisPlan p;
+    return factor_axis(n, p);
+}
+
+extern "C" {
+
+int vdwgb_new(int functional, vdwgb_handle *out) {
+    if (!out) return fail(VDWGB_EINVAL, "null output handle");
+    *out = nullptr;
+    if (functional != VDWGB_DF1 && functional != VDWGB_DF2)
+        return fail(VDWGB_EINVAL, "unknown functional %d", functional);
+    vdwgb_data *h = new (std::nothrow) vdwgb_data();
+    if (!h) return fail(VDWGB_ENOMEM, "host allocation");
+    h->functional = functional;
+    *out = h;
+    return 0;
+}
+
+int vdwgb_set_unit_cell(vdwgb_handle h, int nx, int ny, int nz, double c00, double c01, double c02,
+                        double c10, double c11, double c12, double c20, double c21, double c22) {
+    if (!h) return fail(VDWGB_EINVAL, "null handle");
+    if (!axis_ok(nx) || !axis_ok(ny) || !axis_ok(nz))
+        return fail(VDWGB_EINVAL, "grid %dx%dx%d: each axis 1..1024 with prime factors 2, 3, 5, 7", nx, ny, nz);
+    const double c[9] = {c00, c01, c02, c10, c11, c12, c20, c21, c22};
+    for (double v : c)
+        if (!std::isfinite(v)) return fail(VDWGB_EINVAL, "non-finite cell component");
+    const double det = c[0] * (c[4] * c[8] - c[5] * c[7]) - c[1] * (c[3] * c[8] - c[5] * c[6]) +
+                       c[2] * (c[3] * c[7] - c[4] * c[6]);
+    if (!(std::fabs(det) > 1e-12)) return fail(VDWGB_EINVAL, "cell volume is zero");
+    if (h->inited) release(h);
+    h->nx = nx;
+    h->ny = ny;
+    h->nz = nz;
+    std::memcpy(h->cell, c, sizeof c);
+    h->cell_set = true;
+    return 0;
+}
+
+int vdwgb_set_interp(vdwgb_handle h, int interp) {
+    if (!h) return fail(VDWGB_EINVAL, "null handle");
+    if (interp != VDWGB_INTERP_CUBIC && interp != VDWGB_INTERP_LINEAR)
+        return fail(VDWGB_EINVAL, "unknown interpolation %d", interp);
+    if (h->inited) return fail(VDWGB_ESTATE, "set the interpolation before init");
+    h->interp = interp;
+    return 0;
+}
+
+int vdwgb_init_cuda(vdwgb_handle h, int device, int precision) {
+    if (!h) return fail(VDWGB_EINVAL, "null handle");
+    if (!h->cell_set) return fail(VDWGB_ESTATE, "set the unit cell before init");
+    if (precision != VDWGB_FP64 && precision != VDWGB_FP32_MIXED)
+        return fail(VDWGB_EINVAL, "unknown precision %d", precision);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return fail(VDWGB_EINVAL, "no CUDA device %d", device);
+    if (h->inited) release(h);
+    int rc = device_setup(device);
+    if (rc) return rc;
+    CK(cudaSetDevice(device), "cudaSetDevice");
+    h->device = device;
+    h->prec = precision;
+    rc = plan(h);
+    if (rc) {
+        release(h);
+        return rc;
+    }
+    h->inited = true;
+    return 0;
+}
+
+static int set_io(vdwgb_data *h, const double *n, const double *s, double *dn, double *ds, double *e,
+                  cudaStream_t st) {
+    const double *p[5] = {n, s, dn, ds, e};
+    if (std::memcmp(p, h->last_ptr, sizeof p) == 0) return 0;
+    h->hsys.n = n;
+    h->hsys.sigma = s;
+    h->hsys.dedn = dn;
+    h->hsys.dedsigma = ds;
+    h->hsys.energy = e;
+    // pageable source: the copy has consumed it when the call returns
+    CK(cudaMemcpyAsync(h->dsys, &h->hsys, sizeof(SysDev), cudaMemcpyHostToDevice, st), "descriptor update");
+    std::memcpy(h->last_ptr, p, sizeof p);
+    return 0;
+}
+
+int vdwgb_calculate_device(vdwgb_handle h, const double *d_rho, const double *d_sigma, double *d_dedrho,
+                           double *d_dedsigma, double *d_energy, void *cuda_stream) {
+    if (!h) return fail(VDWGB_EINVAL, "null handle");
+    if (!h->inited) return fail(VDWGB_ESTATE, "calculate before init");
+    if (!d_rho || !d_sigma || !d_dedrho || !d_dedsigma || !d_energy)
+        return fail(VDWGB_EINVAL, "null array");
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int rc = set_io(h, d_rho, d_sigma, d_dedrho, d_dedsigma, d_energy, st);
+    if (rc) return rc;
+    CK(launch_all(h->ls, h->prec, st), "launch");
+    return 0;
+}
+
+int vdwgb_calculate(vdwgb_handle h, const double *rho, const double *sigma, double *dedrho, double *dedsigma,
+                    double *energy) {
+    if (!h) return fail(VDWGB_EINVAL, "null handle");
+    if (!h->inited) return fail(VDWGB_ESTATE, "calculate before init");
+    if (!rho || !sigma || !dedrho || !dedsigma || !energy) return fail(VDWGB_EINVAL, "null array");
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    const size_t N = (size_t)h->nx * h->ny * h->nz;
+    if (!h->d_io) {
+        CK(cudaMalloc(&h->d_io, (4 * N + 1) * sizeof(double)), "staging");
+        h->bytes += (4 * N + 1) * sizeof(double);
+    }
+    double *dn = h->d_io, *ds = dn + N, *odn = ds + N, *ods = odn + N, *oe = ods + N;
+    cudaStream_t st = h->stream;
+    CK(cudaMemcpyAsync(dn, rho, N * sizeof(double), cudaMemcpyHostToDevice, st), "copy rho");
+    CK(cudaMemcpyAsync(ds, sigma, N * sizeof(double), cudaMemcpyHostToDevice, st), "copy sigma");
+    int rc = set_io(h, dn, ds, odn, ods, oe, st);
+    if (rc) return rc;
+    CK(launch_all(h->ls, h->prec, st), "launch");
+    CK(cudaMemcpyAsync(dedrho, odn, N * sizeof(double), cudaMemcpyDeviceToHost, st), "copy dedrho");
+    CK(cudaMemcpyAsync(dedsigma, ods, N * sizeof(double), cudaMemcpyDeviceToHost, st), "copy dedsigma");
+    CK(cudaMemcpyAsync(energy, oe, sizeof(double), cudaMemcpyDeviceToHost, st), "copy energy");
+    CK(cudaStreamSynchronize(st), "synchronize");
+    return 0;
+}
+
+double vdwgb_calculate_simple(vdwgb_handle h, const double *rho, const double *sigma, double *dedrho,
+                              double *dedsigma) {
+    double e = NAN;
+    if (vdwgb_calculate(h, rho, sigma, dedrho, dedsigma, &e) != 0) return NAN;
+    return e;
+}
+
+int vdwgb_finalize(vdwgb_handle *hp) {
+    if (!hp) return fail(VDWGB_EINVAL, "null handle pointer");
+    if (*hp) {
+        release(*hp);
+        delete *hp;
+    }
+    *hp = nullptr;
+    return 0;
+}
+
+const char *vdwgb_strerror(int code) {
+    switch (code) {
+        case VDWGB_OK: return "success";
+        case VDWGB_EINVAL: return "invalid argument";
+        case VDWGB_ENOMEM: return "out of memory";
+        case VDWGB_ECUDA: return "CUDA error";
+        case VDWGB_ESTATE: return "call out of sequence";
+        case VDWGB_ETIMEDOUT: return "timed out";
+        case VDWGB_EAGAIN: return "not admitted, retry later";
+        case VDWGB_ENOTFOUND: return "unknown request";
+        default: return "unknown error";
+    }
+}
+
+const char *vdwgb_last_error(void) { return g_err.c_str(); }
+
+int vdwgb_print(vdwgb_handle h) {
+    if (!h) return fail(VDWGB_EINVAL, "null handle");
+    printf("vdwgb handle: functional vdW-DF%d, interp %s\n", h->functional,
+           h->interp == VDWGB_INTERP_LINEAR ? "linear" : "cubic");
+    printf("  grid %d x %d x %d, cell rows (%g %g %g) (%g %g %g) (%g %g %g)\n", h->nx, h->ny, h->nz,
+           h->cell[0], h->cell[1], h->cell[2], h->cell[3], h->cell[4], h->cell[5], h->cell[6], h->cell[7],
+           h->cell[8]);
+    if (h->inited) {
+        const SysDev &S = h->hsys;
+        printf("  device %d, %s, tiles z %d y %d x %d (LZ %d, W %d), %.1f MB\n", h->device,
+               h->prec == VDWGB_FP32_MIXED ? "FP32-mixed" : "FP64", S.tiles[0], S.tiles[1], S.tiles[2], S.LZ,
+               S.W, h->bytes / 1e6);
+        for (int a = 0; a < 3; ++a) {
+            printf("  axis %d n=%d radices", a, S.ax[a].n);
+            for (int s = 0; s < S.ax[a].nst; ++s) printf(" %d", S.ax[a].rad[s]);
+            printf("\n");
+        }
+    } else {
+        printf("  not initialised\n");
+    }
+    fflush(stdout);
+    return 0;
+}
+
+int vdwgb_has_cuda(void) {
+    int n = 0;
+    return cudaGetDeviceCount(&n) == cudaSuccess && n > 0 ? 1 : 0;
+}
+
+size_t vdwgb_footprint_bytes(int nx, int ny, int nz, int precision) {
+    const int p = precision == VDWGB_FP32_MIXED ? VDWGB_FP32_MIXED : VDWGB_FP64;
+    const size_t nzh = (size_t)nz / 2 + 1;
+    const size_t N = (size_t)nx * ny * nz;
+    return (size_t)nx * ny * nzh * NQ * elem_bytes(p) + N * rec_bytes(p) + ((size_t)ny * nzh + 1) * sizeof(double);
+}
+
+int vdwgb_launches_per_call(vdwgb_handle h) {
+    (void)h;
+    return launches_per_eval();
+}
+
+int vdwgb_kernel_table(int device, double *phik, double *phir, double *qmesh) {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return fail(VDWGB_EINVAL, "no CUDA device %d", device);
+    int rc = device_setup(device);
+    if (rc) return rc;
+    TableRefs tr;
+    CK(table_get(device, tr), "kernel table");
+    CK(cudaSetDevice(device), "cudaSetDevice");
+    if (phik) CK(cudaMemcpy(phik, tr.phik, (size_t)NPAIR * NK * sizeof(double), cudaMemcpyDeviceToHost), "copy");
+    if (phir)
+        CK(cudaMemcpy(phir, tr.phir, (size_t)NPAIR * (NR + 1) * sizeof(double), cudaMemcpyDeviceToHost), "copy");
+    if (qmesh) {
+        QMeshDev q;
+        host_qmesh(q);
+        std::memcpy(qmesh, q.q, NQ * sizeof(double));
+    }
+    return 0;
+}
+
+int vdwgb_phi(int device, int npts, const double *d1, const double *d2, double *out) {
+    if (npts < 0 || (npts > 0 && (!d1 || !d2 || !out))) return fail(VDWGB_EINVAL, "bad arguments");
+    if (npts == 0) return 0;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return fail(VDWGB_EINVAL, "no CUDA device %d", device);
+    int rc = device_setup(device);
+    if (rc) return rc;
+    CK(table_phi(device, npts, d1, d2, out), "phi");
+    return 0;
+}
+
+double vdwgb_table_build_seconds(int device) { return table_seconds(device); }
+
+// ---------------------------------------------------------------------------
+// batches
+// ---------------------------------------------------------------------------
+struct vdwgb_batch_s {
+    std::vector<vdwgb_data *> hs;
+    int device = -1;
+    int prec = 0;
+    SysDev *dsys = nullptr;
+    int *dprefix = nullptr;
+    std::vector<SysDev> host;
+    LaunchSet ls;
+    std::vector<const double *> last;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaStream_t cap = nullptr;
+};
+
+int vdwgb_batch_new(vdwgb_handle *handles, int count, vdwgb_batch *out) {
+    if (!out) return fail(VDWGB_EINVAL, "null output");
+    *out = nullptr;
+    if (!handles || count < 1) return fail(VDWGB_EINVAL, "empty batch");
+    for (int i = 0; i < count; ++i) {
+        if (!handles[i] || !handles[i]->inited) return fail(VDWGB_ESTATE, "handle %d not initialised", i);
+        if (handles[i]->device != handles[0]->device || handles[i]->prec != handles[0]->prec ||
+            handles[i]->table != handles[0]->table)
+            return fail(VDWGB_EINVAL, "handle %d: device, precision and interpolation must match", i);
+    }
+    vdwgb_batch_s *b = new (std::nothrow) vdwgb_batch_s();
+    if (!b) return fail(VDWGB_ENOMEM, "host allocation");
+    b->hs.assign(handles, handles + count);
+    b->device = handles[0]->device;
+    b->prec = handles[0]->prec;
+    cudaSetDevice(b->device);
+    b->host.resize(count);
+    std::vector<int> pre(4 * (count + 1), 0);
+    LaunchSet &L = b->ls;
+    std::memset(&L, 0, sizeof L);
+    for (int i = 0; i < count; ++i) {
+        b->host[i] = handles[i]->hsys;
+        for (int s = 0; s < 4; ++s) {
+            pre[s * (count + 1) + i + 1] = pre[s * (count + 1) + i] + handles[i]->hsys.tiles[s];
+            if (handles[i]->ls.smem[s] > L.smem[s]) L.smem[s] = handles[i]->ls.smem[s];
+        }
+    }
+    cudaError_t e = cudaMalloc(&b->dsys, count * sizeof(SysDev));
+    if (e == cudaSuccess) e = cudaMalloc(&b->dprefix, pre.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(b->dprefix, pre.data(), pre.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->dsys, b->host.data(), count * sizeof(SysDev), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(b->dsys);
+        cudaFree(b->dprefix);
+        delete b;
+        return cuda_fail(e, "batch setup");
+    }
+    DevInfo &di = g_dev[b->device];
+    L.sys = b->dsys;
+    L.nsys = count;
+    L.table = handles[0]->table;
+    for (int s = 0; s < 4; ++s) {
+        L.prefix[s] = b->dprefix + s * (count + 1);
+        L.total[s] = pre[s * (count + 1) + count];
+        int per_sm = (int)((228 * 1024) / (L.smem[s] + 1024));
+        per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
+        const int cap = di.sms * per_sm;
+        L.grid[s] = L.total[s] < cap ? L.total[s] : cap;
+    }
+    b->last.assign(5 * count, nullptr);
+    *out = b;
+    return 0;
+}
+
+int vdwgb_batch_calculate_device(vdwgb_batch b, const double *const *d_rho, const double *const *d_sigma,
+                                 double *const *d_dedrho, double *const *d_dedsigma, double *d_energy,
+                                 void *cuda_stream) {
+    if (!b) return fail(VDWGB_EINVAL, "null batch");
+    if (!d_rho || !d_sigma || !d_dedrho || !d_dedsigma || !d_energy) return fail(VDWGB_EINVAL, "null array");
+    const int n = (int)b->hs.size();
+    CK(cudaSetDevice(b->device), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    bool changed = false;
+    for (int i = 0; i < n; ++i) {
+        if (!d_rho[i] || !d_sigma[i] || !d_dedrho[i] || !d_dedsigma[i])
+            return fail(VDWGB_EINVAL, "null array of system %d", i);
+        const double *p[5] = {d_rho[i], d_sigma[i], d_dedrho[i], d_dedsigma[i], d_energy + i};
+        for (int k = 0; k < 5; ++k)
+            if (b->last[5 * i + k] != p[k]) {
+                b->last[5 * i + k] = p[k];
+                changed = true;
+            }
+        SysDev &S = b->host[i];
+        S.n = p[0];
+        S.sigma = p[1];
+        S.dedn = const_cast<double *>(p[2]);
+        S.dedsigma = const_cast<double *>(p[3]);
+        S.energy = const_cast<double *>(p[4]);
+    }
+    if (changed)
+        CK(cudaMemcpyAsync(b->dsys, b->host.data(), n * sizeof(SysDev), cudaMemcpyHostToDevice, st),
+           "descriptor update");
+    if (!b->exec) {
+        // capture the stage launches once; replays read the descriptors above
+        CK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "capture stream");
+        CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+        cudaError_t le = launch_all(b->ls, b->prec, b->cap);
+        cudaError_t ce = cudaStreamEndCapture(b->cap, &b->graph);
+        if (le != cudaSuccess) return cuda_fail(le, "capture launch");
+        if (ce != cudaSuccess) return cuda_fail(ce, "end capture");
+        CK(cudaGraphInstantiate(&b->exec, b->graph, 0), "instantiate graph");
+    }
+    CK(cudaGraphLaunch(b->exec, st), "graph launch");
+    return 0;
+}
+
+int vdwgb_batch_free(vdwgb_batch *bp) {
+    if (!bp) return fail(VDWGB_EINVAL, "null batch pointer");
+    vdwgb_batch_s *b = *bp;
+    if (b) {
+        cudaSetDevice(b->device);
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        if (b->cap) cudaStreamDestroy(b->cap);
+        cudaFree(b->dsys);
+        cudaFree(b->dprefix);
+        delete b;
+    }
+    *bp = nullptr;
+    return 0;
+}
+
+}  // extern "C"

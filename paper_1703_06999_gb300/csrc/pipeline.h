@@ -1,0 +1,27 @@
+// Host-visible interface of the stage kernels (pipeline.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace vdwgb {
+
+// Everything one launch of the five stages needs: device descriptors of all
+// systems, per-stage tile prefix sums (device), grid and shared memory.
+// Stage index: 0 z-forward, 1 y (both directions), 2 x-contract, 3 z-inverse.
+struct LaunchSet {
+    const SysDev *sys;       // device array [nsys]
+    const int *prefix[4];    // device arrays [nsys + 1]
+    int nsys;
+    int total[4];            // tiles per stage over all systems
+    int grid[4];
+    size_t smem[4];
+    const void *table;       // kernel polynomial table (float4 or double4), [210][NK-1]
+};
+
+size_t stage_smem(int stage, int prec, int n, int tile);
+cudaError_t init_kernels(size_t maxsmem);
+cudaError_t launch_all(const LaunchSet &ls, int prec, cudaStream_t st);
+int launches_per_eval();
+cudaError_t upload_qmesh(const QMeshDev &q);
+
+}  // namespace vdwgb

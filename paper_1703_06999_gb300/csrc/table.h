@@ -1,0 +1,24 @@
+// Resident kernel table (table.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace vdwgb {
+
+struct TableRefs {
+    const double *phir;     // [NPAIR][NR + 1]
+    const double *phik;     // [NPAIR][NK]
+    const dvec4 *cub64;   // [NPAIR][NK - 1] interval polynomials, cubic spline
+    const dvec4 *lin64;   // linear interpolation
+    const float4 *cub32;
+    const float4 *lin32;
+    double seconds;
+};
+
+// Build (once per device and process) and return the resident table.
+cudaError_t table_get(int device, TableRefs &out);
+double table_seconds(int device);
+cudaError_t table_phi(int device, int npts, const double *d1, const double *d2, double *out);
+void host_qmesh(QMeshDev &q);
+
+}  // namespace vdwgb
