@@ -1,0 +1,354 @@
+"""Benchmark: grid points per second of the vdW-DF nonlocal-correlation
+evaluation (E_c^nl and its potential), FP32-mixed batched form against the
+FP64 plain form, with latency, roofline and a CPU (oracle) baseline.
+
+Workload (default): a batch of 8 dimer-like systems on 96^3 grids in an
+18 x 18 x 24 bohr cell (seeds 0-3, vdW-DF1 and vdW-DF2), synthetic densities.
+One step = the whole hot path (q0/theta, forward FFTs, kernel contraction and
+energy, inverse FFTs, potential) over the batch, one launch per stage.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1: run under torch.distributed.run; each rank evaluates its own batch
+(independent systems, no data-path collective), weak scaling.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "dimer96_batch8"
+SHAPE = (96, 96, 96)
+CELL = (18.0, 18.0, 24.0)
+METRIC = "grid pts/s for E_c^nl+potential, FP32 batched vs FP64 plain; p50/p99 latency"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def stage_bytes(shape, prec_bytes):
+    """Algorithmic DRAM bytes per launch of each stage for one system.
+    c = complex element size; the half spectrum holds 20 * nx * ny * (nz/2+1)
+    complex values; records are 16 B (FP32-mixed) or 32 B (FP64) per point."""
+    nx, ny, nz = shape
+    N = nx * ny * nz
+    c = 2 * prec_bytes
+    rec = 16 if prec_bytes == 4 else 32
+    spec = 20 * nx * ny * (nz // 2 + 1) * c
+    return {
+        "zfwd": 16 * N + rec * N + spec,          # n, sigma in; records, spectrum out
+        "yfwd": 2 * spec,
+        "xcontract": 2 * spec,
+        "yinv": 2 * spec,
+        "zinv": spec + rec * N + 16 * N,          # spectrum, records in; dedn, dedsigma out
+        "efinish": 0,
+    }
+
+
+def run_reference(args, rank):
+    """The oracle (FP64 CPU, test infrastructure) timed on the host cores on a
+    bounded sample of the workload: one 48^3 grid of the same dimer density
+    per step (the full 96^3 batch would take minutes per step)."""
+    if rank != 0:
+        return
+    from paper_1703_06999_gb300 import inputs
+    from oracle import vdw
+    o = vdw.Oracle()
+    s = inputs.dimer(0, shape=(48, 48, 48), cell_lengths=CELL, functional=1)
+    n, sg = s.n.numpy(), s.sigma.numpy()
+    for _ in range(args.warmup):
+        o.energy_potential(n, sg, s.cell, 1)
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        o.energy_potential(n, sg, s.cell, 1)
+        t.append(time.perf_counter() - t0)
+    tot = sum(t)
+    val = s.npts * args.steps / tot
+    sample = "oracle on one 48^3 grid of the 96^3 dimer workload's density (18x18x24 bohr, seed 0, vdW-DF1) per step"
+    out = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "grid pts/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD + " (oracle sample: 48^3)", "grid": [48, 48, 48]},
+        "cpu_baseline": {"value": val, "unit": "grid pts/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "grid pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def cpu_baseline():
+    """Oracle (as it stands) on one 96^3 system of the workload, on the host."""
+    from paper_1703_06999_gb300 import inputs
+    from oracle import vdw
+    o = vdw.Oracle()                      # table setup not timed
+    s = inputs.dimer(0, shape=SHAPE, cell_lengths=CELL, functional=1)
+    n, sg = s.n.numpy(), s.sigma.numpy()
+    t0 = time.perf_counter()
+    o.energy_potential(n, sg, s.cell, 1)
+    dt = time.perf_counter() - t0
+    return {"value": s.npts / dt, "unit": "grid pts/s", "cores": 1, "kind": "oracle",
+            "sample": "one 96^3 dimer system (seed 0, vdW-DF1), %.1f s" % dt}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import torch
+    from paper_1703_06999_gb300 import binding as B
+    from paper_1703_06999_gb300 import inputs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    B.lib()   # fails loudly if the CUDA library is missing
+
+    nb = args.batch
+    systems = [inputs.dimer(rank * 1000 + i // 2, shape=SHAPE, cell_lengths=CELL, functional=1 + i % 2,
+                            device=dev) for i in range(nb)]
+    pts = sum(s.npts for s in systems)
+
+    def make(prec):
+        return [B.Functional(s.shape, s.cell, s.functional, prec, device=local) for s in systems]
+
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    dn = [torch.empty_like(s.n) for s in systems]
+    ds = [torch.empty_like(s.n) for s in systems]
+    en = torch.zeros(nb, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 2x L2
+
+    f32 = make(B.FP32_MIXED)
+    bt = B.vdwgb_batch_new([f.h for f in f32])
+    ns = [s.n for s in systems]
+    ss = [s.sigma for s in systems]
+    for _ in range(args.warmup):
+        B.vdwgb_batch_calculate_device(bt, ns, ss, dn, ds, en, sp)
+    torch.cuda.synchronize()
+
+    # ---- timed region: FP32-mixed batched ------------------------------------
+    B.vdwgb_batch_set_timing(bt, True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    for k in range(args.steps):
+        flush.zero_()                       # L2 flushed between timed steps (outside the events)
+        evs[k][0].record(stream)
+        B.vdwgb_batch_calculate_device(bt, ns, ss, dn, ds, en, sp)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = np.array([a.elapsed_time(b) for a, b in evs])
+    stage_ms, ncalls = B.vdwgb_batch_stage_ms(bt)
+    B.vdwgb_batch_set_timing(bt, False)
+    tot_ms = float(step_ms.sum())
+    if world > 1:
+        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = pts * world * args.steps / (tot_ms / 1000.0)
+    e32 = en.cpu().numpy().copy()
+    dn32 = [x.clone() for x in dn]
+    ds32 = [x.clone() for x in ds]
+
+    # ---- latency of single FP32 evaluations (one system at a time) -----------
+    lat = []
+    e1 = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    for i in range(220):
+        f = f32[i % nb]
+        e1[0].record(stream)
+        f.calculate_device(ns[i % nb], ss[i % nb], dn[i % nb], ds[i % nb], en[i % nb:i % nb + 1], sp)
+        e1[1].record(stream)
+        e1[1].synchronize()
+        if i >= 20:
+            lat.append(e1[0].elapsed_time(e1[1]))
+    lat = np.array(lat)
+
+    # ---- FP64 plain, one system at a time, same inputs ------------------------
+    f64 = make(B.FP64)
+    k64 = max(2, args.steps // 4)
+    for i, f in enumerate(f64):
+        f.calculate_device(ns[i], ss[i], dn[i], ds[i], en[i:i + 1], sp)
+    torch.cuda.synchronize()
+    t64 = 0.0
+    for _ in range(k64):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for i, f in enumerate(f64):
+            f.calculate_device(ns[i], ss[i], dn[i], ds[i], en[i:i + 1], sp)
+        b.record(stream)
+        b.synchronize()
+        t64 += a.elapsed_time(b)
+    fp64_value = pts * k64 / (t64 / 1000.0)
+    e64 = en.cpu().numpy().copy()
+    err_e = float(np.max(np.abs(e32 - e64)))
+    err_n = max(float((dn32[i] - dn[i]).abs().max() / dn[i].abs().max()) for i in range(nb))
+    err_s = max(float((ds32[i] - ds[i]).abs().max() / ds[i].abs().max()) for i in range(nb))
+    for f in f64:
+        f.close()
+
+    # ---- end to end through the host-pointer batch API ------------------------
+    hn = [s.n.cpu().pin_memory().numpy() for s in systems]
+    hs = [s.sigma.cpu().pin_memory().numpy() for s in systems]
+    hdn = [torch.empty(s.shape, dtype=torch.float64).pin_memory().numpy() for s in systems]
+    hds = [torch.empty(s.shape, dtype=torch.float64).pin_memory().numpy() for s in systems]
+    B.vdwgb_batch_calculate(bt, hn, hs, hdn, hds)
+    ke = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        B.vdwgb_batch_calculate(bt, hn, hs, hdn, hds)
+    e2e_s = time.perf_counter() - t0
+    e2e_val = pts * ke / e2e_s
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_val = pts * world * ke / float(t.item())
+    h2d = sum(2 * s.npts * 8 for s in systems)
+    d2h = sum(2 * s.npts * 8 for s in systems) + 8 * nb
+
+    # ---- roofline of the dominant stage --------------------------------------
+    names = [B.vdwgb_stage_name(i) for i in range(B.vdwgb_num_stages())]
+    per_launch_ms = stage_ms / max(ncalls, 1)
+    dom = int(np.argmax(per_launch_ms))
+    sb = {k: 0 for k in names}
+    for s in systems:
+        for k, v in stage_bytes(s.shape, 4).items():
+            sb[k] += v
+    pk, pk_kind = peaks()
+    achieved = sb[names[dom]] / (per_launch_ms[dom] / 1000.0) / 1e9
+    traffic = None
+    roof = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": pk["hbm_gbs"],
+            "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
+            "peak_source": pk_kind,
+            "stages": {n: {"ms_per_launch": float(m), "alg_bytes": int(sb[n]),
+                           "GBps": (sb[n] / (m / 1000.0) / 1e9) if m > 0 else None}
+                       for n, m in zip(names, per_launch_ms)}}
+
+    for f in f32:
+        f.close()
+    B.vdwgb_batch_free(bt)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "grid pts/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32-mixed (f64 q0 and energy sum)",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": list(SHAPE), "cell_bohr": list(CELL), "systems": nb,
+                       "functionals": "DF1+DF2", "precision": "fp32_mixed", "parallelism": "replicas",
+                       "l2": "flushed between timed steps (256 MB write); working set %.0f MB"
+                             % (nb * (SHAPE[0] * SHAPE[1] * (SHAPE[2] // 2 + 1) * 160 + 48 * np.prod(SHAPE)) / 1e6)},
+            "fp64_plain": {"value": fp64_value, "unit": "grid pts/s", "steps": k64,
+                           "ms_per_step": t64 / k64, "form": "one system at a time"},
+            "speedup_fp32_batched_vs_fp64_plain": value / (fp64_value * world),
+            "latency_ms": {"single_system_fp32": {"p50": float(np.percentile(lat, 50)),
+                                                  "p99": float(np.percentile(lat, 99)), "n": int(lat.size)},
+                           "batch_step": {"p50": float(np.percentile(step_ms, 50)),
+                                          "p99": float(np.percentile(step_ms, 99))}},
+            "error_fp32_vs_fp64": {"max_abs_dE_Ha": err_e, "dedn_maxnorm_rel": err_n,
+                                   "dedsigma_maxnorm_rel": err_s},
+            "roofline": roof,
+            "e2e": {"value": e2e_val, "unit": "grid pts/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "api": "vdwgb_batch_calculate (host arrays, pinned)"},
+            "gpu_launches": int(args.steps * B.vdwgb_num_stages()),
+            "clocks": clocks,
+            "table_build_s": B.vdwgb_table_build_seconds(local),
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

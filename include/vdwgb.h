@@ -95,8 +95,9 @@ int vdwgb_init_cuda(vdwgb_handle h, int device, int precision);
 /* Evaluate E_c^nl and its partial derivatives from HOST arrays (cf.
  * vdwxc_calculate, Sec. 6).  rho, sigma: nx*ny*nz doubles (read).  dedrho,
  * dedsigma: nx*ny*nz doubles (overwritten).  energy: one double (written,
- * Hartree).  Blocking; copies in and out through pinned staging buffers
- * owned by the handle.  Callable any number of times after init. */
+ * Hartree).  Blocking; the arrays are copied to and from device staging
+ * buffers owned by the handle (page-locked caller memory copies fastest).
+ * Callable any number of times after init. */
 int vdwgb_calculate(vdwgb_handle h, const double *rho, const double *sigma,
                     double *dedrho, double *dedsigma, double *energy);
 
@@ -165,6 +166,22 @@ int vdwgb_batch_new(vdwgb_handle *handles, int count, vdwgb_batch *out);
 int vdwgb_batch_calculate_device(vdwgb_batch b, const double *const *d_rho,
                                  const double *const *d_sigma, double *const *d_dedrho,
                                  double *const *d_dedsigma, double *d_energy, void *cuda_stream);
+/* The same from HOST arrays: copies in through per-handle device staging,
+ * evaluates, copies dedrho, dedsigma and the `count` energies back, and waits.
+ * Blocking. */
+int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double *const *sigma,
+                          double *const *dedrho, double *const *dedsigma, double *energy);
+
+/* Stage timing: with timing enabled, each batch evaluation records CUDA
+ * events between its kernel launches (launched directly, not from the
+ * graph).  vdwgb_batch_stage_ms waits for the recorded calls, writes the
+ * summed milliseconds per stage to ms[vdwgb_num_stages()], the number of
+ * calls to *ncalls, and starts a new accumulation. */
+int vdwgb_batch_set_timing(vdwgb_batch b, int enable);
+int vdwgb_batch_stage_ms(vdwgb_batch b, double *ms, int *ncalls);
+int vdwgb_num_stages(void);
+const char *vdwgb_stage_name(int i);
+
 int vdwgb_batch_free(vdwgb_batch *b);
 
 #ifdef __cplusplus

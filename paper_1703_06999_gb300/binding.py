@@ -46,6 +46,11 @@ _SIGS = {
     "vdwgb_batch_new": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "vdwgb_batch_calculate_device": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 6),
     "vdwgb_batch_free": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p)]),
+    "vdwgb_batch_calculate": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 5),
+    "vdwgb_batch_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "vdwgb_batch_stage_ms": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "vdwgb_num_stages": (ctypes.c_int, []),
+    "vdwgb_stage_name": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
 
@@ -189,6 +194,37 @@ def vdwgb_batch_calculate_device(b, rhos, sigmas, dedrhos, dedsigmas, energies, 
                                            P(*[_ptr(t) for t in dedrhos]), P(*[_ptr(t) for t in dedsigmas]),
                                            _ptr(energies), ctypes.c_void_p(int(stream))),
         "vdwgb_batch_calculate_device")
+
+
+def vdwgb_batch_calculate(b, rhos, sigmas, dedrhos, dedsigmas):
+    """Host arrays (numpy float64, C order, pinned or pageable); returns energies."""
+    n = len(rhos)
+    P = ctypes.c_void_p * n
+    e = np.zeros(n)
+    _ck(lib().vdwgb_batch_calculate(b, P(*[_ptr(t) for t in rhos]), P(*[_ptr(t) for t in sigmas]),
+                                    P(*[_ptr(t) for t in dedrhos]), P(*[_ptr(t) for t in dedsigmas]),
+                                    e.ctypes.data), "vdwgb_batch_calculate")
+    return e
+
+
+def vdwgb_batch_set_timing(b, enable):
+    _ck(lib().vdwgb_batch_set_timing(b, int(bool(enable))), "vdwgb_batch_set_timing")
+
+
+def vdwgb_num_stages():
+    return int(lib().vdwgb_num_stages())
+
+
+def vdwgb_stage_name(i):
+    return lib().vdwgb_stage_name(int(i)).decode()
+
+
+def vdwgb_batch_stage_ms(b):
+    """(per-stage summed milliseconds, number of timed calls)."""
+    ms = np.zeros(vdwgb_num_stages())
+    nc = ctypes.c_int(0)
+    _ck(lib().vdwgb_batch_stage_ms(b, ms.ctypes.data, ctypes.byref(nc)), "vdwgb_batch_stage_ms")
+    return ms, int(nc.value)
 
 
 def vdwgb_batch_free(b):

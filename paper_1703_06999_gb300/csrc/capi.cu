@@ -485,7 +485,7 @@ size_t vdwgb_footprint_bytes(int nx, int ny, int nz, int precision) {
 
 int vdwgb_launches_per_call(vdwgb_handle h) {
     (void)h;
-    return launches_per_eval();
+    return NSTAGE;
 }
 
 int vdwgb_kernel_table(int device, double *phik, double *phir, double *qmesh) {
@@ -537,6 +537,11 @@ struct vdwgb_batch_s {
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     cudaStream_t cap = nullptr;
+    bool timing = false;
+    std::vector<std::vector<cudaEvent_t>> pending;   // NSTAGE + 1 events per timed call
+    std::vector<std::vector<cudaEvent_t>> spare;
+    double *d_energy = nullptr;                        // host-pointer path
+    cudaStream_t own = nullptr;
 };
 
 int vdwgb_batch_new(vdwgb_handle *handles, int count, vdwgb_batch *out) {
@@ -621,6 +626,20 @@ int vdwgb_batch_calculate_device(vdwgb_batch b, const double *const *d_rho, cons
     if (changed)
         CK(cudaMemcpyAsync(b->dsys, b->host.data(), n * sizeof(SysDev), cudaMemcpyHostToDevice, st),
            "descriptor update");
+    if (b->timing) {
+        // stages launched directly with events between them (no graph)
+        std::vector<cudaEvent_t> ev;
+        if (!b->spare.empty()) {
+            ev = b->spare.back();
+            b->spare.pop_back();
+        } else {
+            ev.resize(NSTAGE + 1);
+            for (auto &x : ev) CK(cudaEventCreate(&x), "event");
+        }
+        CK(launch_all(b->ls, b->prec, st, ev.data()), "launch");
+        b->pending.push_back(ev);
+        return 0;
+    }
     if (!b->exec) {
         // capture the stage launches once; replays read the descriptors above
         CK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "capture stream");
@@ -635,12 +654,86 @@ int vdwgb_batch_calculate_device(vdwgb_batch b, const double *const *d_rho, cons
     return 0;
 }
 
+int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double *const *sigma,
+                          double *const *dedrho, double *const *dedsigma, double *energy) {
+    if (!b) return fail(VDWGB_EINVAL, "null batch");
+    if (!rho || !sigma || !dedrho || !dedsigma || !energy) return fail(VDWGB_EINVAL, "null array");
+    const int n = (int)b->hs.size();
+    CK(cudaSetDevice(b->device), "cudaSetDevice");
+    if (!b->own) CK(cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking), "stream");
+    if (!b->d_energy) CK(cudaMalloc(&b->d_energy, n * sizeof(double)), "energies");
+    std::vector<const double *> dr(n), dsg(n);
+    std::vector<double *> odn(n), ods(n);
+    for (int i = 0; i < n; ++i) {
+        vdwgb_data *h = b->hs[i];
+        if (!rho[i] || !sigma[i] || !dedrho[i] || !dedsigma[i]) return fail(VDWGB_EINVAL, "null array %d", i);
+        const size_t N = (size_t)h->nx * h->ny * h->nz;
+        if (!h->d_io) {
+            CK(cudaMalloc(&h->d_io, (4 * N + 1) * sizeof(double)), "staging");
+            h->bytes += (4 * N + 1) * sizeof(double);
+        }
+        double *d = h->d_io;
+        dr[i] = d;
+        dsg[i] = d + N;
+        odn[i] = d + 2 * N;
+        ods[i] = d + 3 * N;
+        CK(cudaMemcpyAsync(d, rho[i], N * sizeof(double), cudaMemcpyHostToDevice, b->own), "copy rho");
+        CK(cudaMemcpyAsync(d + N, sigma[i], N * sizeof(double), cudaMemcpyHostToDevice, b->own), "copy sigma");
+    }
+    int rc = vdwgb_batch_calculate_device(b, dr.data(), dsg.data(), odn.data(), ods.data(), b->d_energy, b->own);
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i) {
+        vdwgb_data *h = b->hs[i];
+        const size_t N = (size_t)h->nx * h->ny * h->nz;
+        CK(cudaMemcpyAsync(dedrho[i], odn[i], N * sizeof(double), cudaMemcpyDeviceToHost, b->own), "copy dedrho");
+        CK(cudaMemcpyAsync(dedsigma[i], ods[i], N * sizeof(double), cudaMemcpyDeviceToHost, b->own),
+           "copy dedsigma");
+    }
+    CK(cudaMemcpyAsync(energy, b->d_energy, n * sizeof(double), cudaMemcpyDeviceToHost, b->own), "copy energy");
+    CK(cudaStreamSynchronize(b->own), "synchronize");
+    return 0;
+}
+
+int vdwgb_batch_set_timing(vdwgb_batch b, int enable) {
+    if (!b) return fail(VDWGB_EINVAL, "null batch");
+    b->timing = enable != 0;
+    return 0;
+}
+
+int vdwgb_batch_stage_ms(vdwgb_batch b, double *ms, int *ncalls) {
+    if (!b || !ms) return fail(VDWGB_EINVAL, "null argument");
+    CK(cudaSetDevice(b->device), "cudaSetDevice");
+    for (int k = 0; k < NSTAGE; ++k) ms[k] = 0.0;
+    for (auto &ev : b->pending) {
+        CK(cudaEventSynchronize(ev[NSTAGE]), "event sync");
+        for (int k = 0; k < NSTAGE; ++k) {
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, ev[k], ev[k + 1]), "elapsed");
+            ms[k] += t;
+        }
+        b->spare.push_back(ev);
+    }
+    if (ncalls) *ncalls = (int)b->pending.size();
+    b->pending.clear();
+    return 0;
+}
+
+const char *vdwgb_stage_name(int i) { return stage_name(i); }
+
+int vdwgb_num_stages(void) { return NSTAGE; }
+
 int vdwgb_batch_free(vdwgb_batch *bp) {
     if (!bp) return fail(VDWGB_EINVAL, "null batch pointer");
     vdwgb_batch_s *b = *bp;
     if (b) {
         cudaSetDevice(b->device);
         if (b->exec) cudaGraphExecDestroy(b->exec);
+        for (auto &v : b->pending)
+            for (auto e : v) cudaEventDestroy(e);
+        for (auto &v : b->spare)
+            for (auto e : v) cudaEventDestroy(e);
+        if (b->own) cudaStreamDestroy(b->own);
+        cudaFree(b->d_energy);
         if (b->graph) cudaGraphDestroy(b->graph);
         if (b->cap) cudaStreamDestroy(b->cap);
         cudaFree(b->dsys);

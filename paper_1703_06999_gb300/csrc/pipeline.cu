@@ -573,22 +573,33 @@ cudaError_t init_kernels(size_t maxsmem) {
 }
 
 template <typename T>
-static cudaError_t launch_all_t(const LaunchSet &ls, cudaStream_t st) {
+static cudaError_t launch_all_t(const LaunchSet &ls, cudaStream_t st, cudaEvent_t *ev) {
     const typename KTab<T>::V *tab = reinterpret_cast<const typename KTab<T>::V *>(ls.table);
+    if (ev) cudaEventRecord(ev[0], st);
     k_zfwd<T><<<ls.grid[0], 256, ls.smem[0], st>>>(ls.sys, ls.prefix[0], ls.nsys, ls.total[0]);
+    if (ev) cudaEventRecord(ev[1], st);
     k_yfft<T, false><<<ls.grid[1], 256, ls.smem[1], st>>>(ls.sys, ls.prefix[1], ls.nsys, ls.total[1]);
+    if (ev) cudaEventRecord(ev[2], st);
     k_xcontract<T><<<ls.grid[2], 256, ls.smem[2], st>>>(ls.sys, ls.prefix[2], ls.nsys, ls.total[2], tab);
+    if (ev) cudaEventRecord(ev[3], st);
     k_yfft<T, true><<<ls.grid[1], 256, ls.smem[1], st>>>(ls.sys, ls.prefix[1], ls.nsys, ls.total[1]);
+    if (ev) cudaEventRecord(ev[4], st);
     k_zinv<T><<<ls.grid[3], 256, ls.smem[3], st>>>(ls.sys, ls.prefix[3], ls.nsys, ls.total[3]);
+    if (ev) cudaEventRecord(ev[5], st);
     k_efinish<<<ls.nsys < 1024 ? ls.nsys : 1024, 256, 0, st>>>(ls.sys, ls.nsys);
+    if (ev) cudaEventRecord(ev[6], st);
     return cudaGetLastError();
 }
 
-cudaError_t launch_all(const LaunchSet &ls, int prec, cudaStream_t st) {
-    return prec == 1 ? launch_all_t<float>(ls, st) : launch_all_t<double>(ls, st);
+cudaError_t launch_all(const LaunchSet &ls, int prec, cudaStream_t st, cudaEvent_t *ev) {
+    return prec == 1 ? launch_all_t<float>(ls, st, ev) : launch_all_t<double>(ls, st, ev);
 }
 
-int launches_per_eval() { return 6; }
+const char *stage_name(int i) {
+    static const char *names[NSTAGE] = {"zfwd", "yfwd", "xcontract", "yinv", "zinv", "efinish"};
+    return (i >= 0 && i < NSTAGE) ? names[i] : "";
+}
+
 
 cudaError_t upload_qmesh(const QMeshDev &q) { return cudaMemcpyToSymbol(c_qm, &q, sizeof(QMeshDev)); }
 

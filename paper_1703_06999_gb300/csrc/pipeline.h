@@ -20,8 +20,10 @@ struct LaunchSet {
 
 size_t stage_smem(int stage, int prec, int n, int tile);
 cudaError_t init_kernels(size_t maxsmem);
-cudaError_t launch_all(const LaunchSet &ls, int prec, cudaStream_t st);
-int launches_per_eval();
+constexpr int NSTAGE = 6;   // kernel launches per evaluation
+// Enqueue all stages; if ev != nullptr, record ev[0..NSTAGE] around them.
+cudaError_t launch_all(const LaunchSet &ls, int prec, cudaStream_t st, cudaEvent_t *ev = nullptr);
+const char *stage_name(int i);
 cudaError_t upload_qmesh(const QMeshDev &q);
 
 }  // namespace vdwgb
