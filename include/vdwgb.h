@@ -128,6 +128,12 @@ int vdwgb_has_cuda(void);
  * (work buffer + records + partials), excluding the shared kernel table. */
 size_t vdwgb_footprint_bytes(int nx, int ny, int nz, int precision);
 
+/* 0, or VDWGB_ETIMEDOUT if a kernel on `device` gave up a bounded wait for
+ * its staged data since the last call (its results are then invalid); the
+ * flag is cleared.  The host-array calls check it themselves; callers of the
+ * device-pointer calls check it after synchronising. */
+int vdwgb_device_status(int device);
+
 /* Number of our kernel launches one evaluation enqueues (all stages). */
 int vdwgb_launches_per_call(vdwgb_handle h);
 
@@ -144,6 +150,14 @@ int vdwgb_kernel_table(int device, double *phik, double *phir, double *qmesh);
 /* phi(d1[i], d2[i]) for npts pairs on `device` with the table's quadrature
  * (host arrays in and out), for checking the kernel itself. */
 int vdwgb_phi(int device, int npts, const double *d1, const double *d2, double *out);
+
+/* q0(n, sigma) and its partial derivatives (appendix, q0 with PW92
+ * correlation and the saturation h_5) exactly as the given precision form
+ * evaluates them inside vdwgb_calculate (FP64 values either way; the
+ * FP32-mixed form reaches them with FP32-seeded FP64 iterations and forms
+ * the derivatives in FP32).  Host arrays of npts doubles. */
+int vdwgb_q0(int device, int precision, int functional, int npts, const double *n, const double *sigma,
+             double *q0, double *dq0dn, double *dq0dsigma);
 
 /* Seconds spent building the table on `device` (0 if not built). */
 double vdwgb_table_build_seconds(int device);

@@ -40,9 +40,11 @@ _SIGS = {
     "vdwgb_has_cuda": (ctypes.c_int, []),
     "vdwgb_footprint_bytes": (ctypes.c_size_t, [ctypes.c_int] * 4),
     "vdwgb_launches_per_call": (ctypes.c_int, [ctypes.c_void_p]),
+    "vdwgb_device_status": (ctypes.c_int, [ctypes.c_int]),
     "vdwgb_kernel_table": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "vdwgb_phi": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "vdwgb_table_build_seconds": (ctypes.c_double, [ctypes.c_int]),
+    "vdwgb_q0": (ctypes.c_int, [ctypes.c_int] * 4 + [ctypes.c_void_p] * 5),
     "vdwgb_batch_new": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "vdwgb_batch_calculate_device": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 6),
     "vdwgb_batch_free": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p)]),
@@ -155,6 +157,10 @@ def vdwgb_footprint_bytes(shape, precision):
     return int(lib().vdwgb_footprint_bytes(int(shape[0]), int(shape[1]), int(shape[2]), int(precision)))
 
 
+def vdwgb_device_status(device=0):
+    _ck(lib().vdwgb_device_status(int(device)), "vdwgb_device_status")
+
+
 def vdwgb_launches_per_call(h):
     return int(lib().vdwgb_launches_per_call(h))
 
@@ -174,6 +180,16 @@ def vdwgb_phi(d1, d2, device=0):
     out = np.zeros(d1.size)
     _ck(lib().vdwgb_phi(int(device), d1.size, d1.ctypes.data, d2.ctypes.data, out.ctypes.data), "vdwgb_phi")
     return out
+
+
+def vdwgb_q0(n, sigma, functional=DF1, precision=FP64, device=0):
+    """(q0, dq0/dn, dq0/dsigma) as the given precision form computes them."""
+    n = np.ascontiguousarray(n, dtype=np.float64).ravel()
+    sigma = np.ascontiguousarray(sigma, dtype=np.float64).ravel()
+    q0, dn, ds = np.zeros(n.size), np.zeros(n.size), np.zeros(n.size)
+    _ck(lib().vdwgb_q0(int(device), int(precision), int(functional), n.size, n.ctypes.data, sigma.ctypes.data,
+                       q0.ctypes.data, dn.ctypes.data, ds.ctypes.data), "vdwgb_q0")
+    return q0, dn, ds
 
 
 def vdwgb_table_build_seconds(device=0):

@@ -47,6 +47,7 @@ struct DevInfo {
     bool ready = false;
     int sms = 0;
     size_t maxsmem = 0;
+    int *err = nullptr;      // device flag written by kernels whose bounded wait ran out
 };
 static std::mutex g_dev_mu;
 static DevInfo g_dev[64];
@@ -66,6 +67,8 @@ static int device_setup(int device) {
     host_qmesh(qm);
     CK(upload_qmesh(qm), "upload q-mesh");
     CK(init_kernels(d.maxsmem - 1024), "kernel attributes");
+    CK(cudaMalloc(&d.err, sizeof(int)), "error flag");
+    CK(cudaMemset(d.err, 0, sizeof(int)), "error flag");
     d.ready = true;
     return 0;
 }
@@ -155,20 +158,22 @@ static void release(vdwgb_data *h) {
 static size_t elem_bytes(int prec) { return prec == VDWGB_FP32_MIXED ? 8 : 16; }
 static size_t rec_bytes(int prec) { return prec == VDWGB_FP32_MIXED ? 16 : 32; }
 
-// Tile choices: z passes LZ lines, x/y passes W columns; prefer two blocks
-// per SM (<= ~110 KB), else fall back to the largest block that fits.
-static void choose_tiles(int prec, int nx, int ny, int nz, int nzh, size_t maxsmem, int &LZ, int &W) {
+// Tile choices: z passes LZ lines, x/y passes W columns with three row
+// buffers (prefetch); prefer two blocks per SM (<= ~110 KB).  Axes too long
+// for three buffers of one column use two (no prefetch).
+static void choose_tiles(int prec, int nx, int ny, int nz, int nzh, size_t lim, int &LZ, int &W, int &nbuf) {
     const size_t budget = 110 * 1024;
     LZ = 1;
     for (int l = 8; l >= 1; --l)
         if (stage_smem(0, prec, nz, l) <= budget) { LZ = l; break; }
     const int nxy = nx > ny ? nx : ny;
     W = 1;
+    nbuf = 3;
     for (int w = 8; w >= 1; --w)
-        if (stage_smem(1, prec, nxy, w) <= budget) { W = w; break; }
+        if (stage_smem(1, prec, nxy, w, 3) <= budget) { W = w; break; }
+    if (stage_smem(1, prec, nxy, 1, 3) > lim) nbuf = 2;
     if (W > nzh) W = nzh;
     if (LZ > nx * ny) LZ = nx * ny;
-    (void)maxsmem;
 }
 
 static int plan(vdwgb_data *h) {
@@ -185,10 +190,11 @@ static int plan(vdwgb_data *h) {
     for (int a = 0; a < 3; ++a)
         if (!factor_axis(dims[a], S.ax[a]))
             return fail(VDWGB_EINVAL, "axis %d length %d: prime factors must be 2, 3, 5, 7", a, dims[a]);
-    choose_tiles(prec, nx, ny, nz, nzh, di.maxsmem, S.LZ, S.W);
     const size_t lim = di.maxsmem - 1024;
-    if (stage_smem(0, prec, nz, S.LZ) > lim || stage_smem(1, prec, nx, S.W) > lim ||
-        stage_smem(1, prec, ny, S.W) > lim)
+    int nbuf = 3;
+    choose_tiles(prec, nx, ny, nz, nzh, lim, S.LZ, S.W, nbuf);
+    if (stage_smem(0, prec, nz, S.LZ) > lim || stage_smem(1, prec, nx, S.W, nbuf) > lim ||
+        stage_smem(1, prec, ny, S.W, nbuf) > lim)
         return fail(VDWGB_EINVAL, "grid %dx%dx%d too large for one block per pencil in this precision",
                     nx, ny, nz);
     const int ncol = (nzh + S.W - 1) / S.W;
@@ -267,10 +273,19 @@ static int plan(vdwgb_data *h) {
         L.prefix[s] = h->dprefix + 2 * s;
         L.total[s] = S.tiles[s];
     }
+    L.err = di.err;
+    L.twmax[0] = L.twmax[3] = nz;
+    L.twmax[1] = ny;
+    L.twmax[2] = nx;
+    L.bufelems[0] = L.bufelems[3] = 0;
+    L.bufelems[1] = ny * S.W * NQ;
+    L.bufelems[2] = nx * S.W * NQ;
     L.smem[0] = stage_smem(0, prec, nz, S.LZ);
     L.smem[3] = L.smem[0];
-    L.smem[1] = stage_smem(1, prec, ny, S.W);
-    L.smem[2] = stage_smem(1, prec, nx, S.W);
+    L.nbuf[0] = L.nbuf[3] = 0;
+    L.nbuf[1] = L.nbuf[2] = nbuf;
+    L.smem[1] = stage_smem(1, prec, ny, S.W, nbuf);
+    L.smem[2] = stage_smem(1, prec, nx, S.W, nbuf);
     for (int s = 0; s < 4; ++s) {
         int per_sm = (int)((228 * 1024) / (L.smem[s] + 1024));
         per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
@@ -411,6 +426,18 @@ int vdwgb_calculate(vdwgb_handle h, const double *rho, const double *sigma, doub
     CK(cudaMemcpyAsync(dedsigma, ods, N * sizeof(double), cudaMemcpyDeviceToHost, st), "copy dedsigma");
     CK(cudaMemcpyAsync(energy, oe, sizeof(double), cudaMemcpyDeviceToHost, st), "copy energy");
     CK(cudaStreamSynchronize(st), "synchronize");
+    return vdwgb_device_status(h->device);
+}
+
+int vdwgb_device_status(int device) {
+    if (device < 0 || device >= 64 || !g_dev[device].ready) return 0;
+    int v = 0;
+    CK(cudaSetDevice(device), "cudaSetDevice");
+    CK(cudaMemcpy(&v, g_dev[device].err, sizeof(int), cudaMemcpyDeviceToHost), "status");
+    if (v) {
+        CK(cudaMemset(g_dev[device].err, 0, sizeof(int)), "status");
+        return fail(VDWGB_ETIMEDOUT, "a kernel's bounded wait for its staged tile ran out");
+    }
     return 0;
 }
 
@@ -522,6 +549,33 @@ int vdwgb_phi(int device, int npts, const double *d1, const double *d2, double *
 
 double vdwgb_table_build_seconds(int device) { return table_seconds(device); }
 
+int vdwgb_q0(int device, int precision, int functional, int npts, const double *n, const double *sigma,
+             double *q0, double *dq0dn, double *dq0dsigma) {
+    if (npts < 0 || (npts > 0 && (!n || !sigma || !q0 || !dq0dn || !dq0dsigma)))
+        return fail(VDWGB_EINVAL, "bad arguments");
+    if (functional != VDWGB_DF1 && functional != VDWGB_DF2) return fail(VDWGB_EINVAL, "unknown functional");
+    if (precision != VDWGB_FP64 && precision != VDWGB_FP32_MIXED) return fail(VDWGB_EINVAL, "unknown precision");
+    if (npts == 0) return 0;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return fail(VDWGB_EINVAL, "no CUDA device %d", device);
+    int rc = device_setup(device);
+    if (rc) return rc;
+    CK(cudaSetDevice(device), "cudaSetDevice");
+    double *b = nullptr;
+    CK(cudaMalloc(&b, 5 * (size_t)npts * sizeof(double)), "q0 buffers");
+    cudaError_t e = cudaMemcpy(b, n, npts * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b + npts, sigma, npts * sizeof(double), cudaMemcpyHostToDevice);
+    const double Z = functional == VDWGB_DF2 ? -1.887 : -0.8491;
+    if (e == cudaSuccess) e = launch_q0(precision, npts, b, b + npts, Z, b + 2 * npts, b + 3 * npts, b + 4 * npts);
+    if (e == cudaSuccess) e = cudaMemcpy(q0, b + 2 * npts, npts * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(dq0dn, b + 3 * npts, npts * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(dq0dsigma, b + 4 * npts, npts * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(b);
+    if (e != cudaSuccess) return cuda_fail(e, "q0");
+    return 0;
+}
+
 // ---------------------------------------------------------------------------
 // batches
 // ---------------------------------------------------------------------------
@@ -569,6 +623,9 @@ int vdwgb_batch_new(vdwgb_handle *handles, int count, vdwgb_batch *out) {
         for (int s = 0; s < 4; ++s) {
             pre[s * (count + 1) + i + 1] = pre[s * (count + 1) + i] + handles[i]->hsys.tiles[s];
             if (handles[i]->ls.smem[s] > L.smem[s]) L.smem[s] = handles[i]->ls.smem[s];
+            if (handles[i]->ls.twmax[s] > L.twmax[s]) L.twmax[s] = handles[i]->ls.twmax[s];
+            if (handles[i]->ls.bufelems[s] > L.bufelems[s]) L.bufelems[s] = handles[i]->ls.bufelems[s];
+            if (i == 0 || handles[i]->ls.nbuf[s] < L.nbuf[s]) L.nbuf[s] = handles[i]->ls.nbuf[s];
         }
     }
     cudaError_t e = cudaMalloc(&b->dsys, count * sizeof(SysDev));
@@ -584,6 +641,20 @@ int vdwgb_batch_new(vdwgb_handle *handles, int count, vdwgb_batch *out) {
     DevInfo &di = g_dev[b->device];
     L.sys = b->dsys;
     L.nsys = count;
+    L.err = handles[0]->ls.err;
+    {
+        // x / y stages: shared memory from the largest row tile and twiddle table of the batch
+        const size_t c = b->prec == VDWGB_FP32_MIXED ? 8 : 16;
+        for (int s = 1; s <= 2; ++s)
+            L.smem[s] = 16 + c * ((size_t)((L.twmax[s] + 7) & ~7) + (size_t)L.nbuf[s] * L.bufelems[s]);
+        const size_t lim = g_dev[b->device].maxsmem - 1024;
+        if (L.smem[1] > lim || L.smem[2] > lim) {
+            cudaFree(b->dsys);
+            cudaFree(b->dprefix);
+            delete b;
+            return fail(VDWGB_EINVAL, "batch: combined row tiles exceed shared memory");
+        }
+    }
     L.table = handles[0]->table;
     for (int s = 0; s < 4; ++s) {
         L.prefix[s] = b->dprefix + s * (count + 1);
@@ -691,7 +762,7 @@ int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double 
     }
     CK(cudaMemcpyAsync(energy, b->d_energy, n * sizeof(double), cudaMemcpyDeviceToHost, b->own), "copy energy");
     CK(cudaStreamSynchronize(b->own), "synchronize");
-    return 0;
+    return vdwgb_device_status(b->device);
 }
 
 int vdwgb_batch_set_timing(vdwgb_batch b, int enable) {

@@ -221,30 +221,22 @@ __device__ __forceinline__ void dft(cx<T> *v) {
 }
 
 // One Stockham stage (radix R) over `nlines` lines held in shared memory:
-// element i of line l sits at buf[i * es + l * ls].  Ns = product of the
-// radices already applied.  All threads of the block take part.
+// element i of line l sits at buf[i * nlines + l].  Thread tid works on line
+// tid % nlines and butterflies j = tid / nlines, + jstep, ... (jstep =
+// blockDim / nlines; the last blockDim % nlines threads idle), so the loop
+// needs no division; q = j / Ns and jm = j % Ns are carried along.
+// Ns = product of the radices already applied.
 template <int R, bool INV, typename T>
-__device__ __forceinline__ void fft_stage(const cx<T> *__restrict__ in, cx<T> *__restrict__ out,
-                                          int n, int Ns, int nlines, int es, int ls,
-                                          const cx<T> *__restrict__ tw, bool line_fast) {
+__device__ __forceinline__ void fft_stage(const cx<T> *in, cx<T> *out, int n, int Ns, int nlines, int line,
+                                          int j0, int jstep, const cx<T> *tw) {
     const int nb = n / R;
-    const int total = nb * nlines;
     const int tws = n / (Ns * R);
-    for (int b = threadIdx.x; b < total; b += blockDim.x) {
-        int line, j;
-        if (line_fast) {
-            j = b / nlines;
-            line = b - j * nlines;
-        } else {
-            line = b / nb;
-            j = b - line * nb;
-        }
-        const cx<T> *src = in + line * ls;
-        cx<T> *dst = out + line * ls;
-        const int jm = j % Ns;
+    int q = j0 / Ns;
+    int jm = j0 - q * Ns;
+    for (int j = j0; j < nb; j += jstep) {
         cx<T> v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[(j + r * nb) * es];
+        for (int r = 0; r < R; ++r) v[r] = in[(j + r * nb) * nlines + line];
         if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
@@ -254,27 +246,38 @@ __device__ __forceinline__ void fft_stage(const cx<T> *__restrict__ in, cx<T> *_
             }
         }
         dft<R, INV>(v);
-        const int base = (j - jm) * R + jm;
+        const int base = q * Ns * R + jm;
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[(base + r * Ns) * es] = v[r];
+        for (int r = 0; r < R; ++r) out[(base + r * Ns) * nlines + line] = v[r];
+        jm += jstep;
+        while (jm >= Ns) {
+            jm -= Ns;
+            ++q;
+        }
     }
 }
 
-// Full 1-D transforms of `nlines` lines (unnormalised).  Ping-pongs between
-// a and b; returns the buffer that holds the result.  Ends with a barrier.
+// Full 1-D transforms of `nlines` lines (unnormalised), layout [i][line].
+// Ping-pongs between a and b; returns the buffer that holds the result.
+// Ends with a barrier.  Requires nlines <= blockDim.x.
 template <bool INV, typename T>
-__device__ cx<T> *fft_lines(cx<T> *a, cx<T> *b, const AxisPlan &p, int nlines, int es, int ls,
-                            const cx<T> *tw, bool line_fast) {
+__device__ cx<T> *fft_lines(cx<T> *a, cx<T> *b, const AxisPlan &p, int nlines, const cx<T> *tw) {
+    const int jstep = blockDim.x / nlines;
+    const int j0 = threadIdx.x / nlines;
+    const int line = threadIdx.x - j0 * nlines;
+    const bool active = j0 < jstep;
     int Ns = 1;
     for (int s = 0; s < p.nst; ++s) {
         const int R = p.rad[s];
-        switch (R) {
-            case 2: fft_stage<2, INV>(a, b, p.n, Ns, nlines, es, ls, tw, line_fast); break;
-            case 3: fft_stage<3, INV>(a, b, p.n, Ns, nlines, es, ls, tw, line_fast); break;
-            case 4: fft_stage<4, INV>(a, b, p.n, Ns, nlines, es, ls, tw, line_fast); break;
-            case 5: fft_stage<5, INV>(a, b, p.n, Ns, nlines, es, ls, tw, line_fast); break;
-            case 7: fft_stage<7, INV>(a, b, p.n, Ns, nlines, es, ls, tw, line_fast); break;
-            default: fft_stage<8, INV>(a, b, p.n, Ns, nlines, es, ls, tw, line_fast); break;
+        if (active) {
+            switch (R) {
+                case 2: fft_stage<2, INV>(a, b, p.n, Ns, nlines, line, j0, jstep, tw); break;
+                case 3: fft_stage<3, INV>(a, b, p.n, Ns, nlines, line, j0, jstep, tw); break;
+                case 4: fft_stage<4, INV>(a, b, p.n, Ns, nlines, line, j0, jstep, tw); break;
+                case 5: fft_stage<5, INV>(a, b, p.n, Ns, nlines, line, j0, jstep, tw); break;
+                case 7: fft_stage<7, INV>(a, b, p.n, Ns, nlines, line, j0, jstep, tw); break;
+                default: fft_stage<8, INV>(a, b, p.n, Ns, nlines, line, j0, jstep, tw); break;
+            }
         }
         __syncthreads();
         cx<T> *t = a;

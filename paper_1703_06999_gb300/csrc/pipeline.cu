@@ -13,6 +13,7 @@
 // Every kernel walks a global tile list spanning all systems of a launch.
 #include "common.cuh"
 #include "pipeline.h"
+#include "tma.cuh"
 
 namespace vdwgb {
 
@@ -76,6 +77,155 @@ __device__ __forceinline__ Q0 q0_point(double n, double s, double Z) {
     r.q0 = q0;
     r.dqdn = dh * dq_dn;
     r.dqds = dh * dq_ds;
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// q0 for the FP32-mixed form: the same FP64 quantity with fewer FP64
+// operations (GB300's FP64 rate is a small fraction of its FP32 rate).
+//  * 1/x, sqrt(x), cbrt(x): FP32 seed, one FP64 Newton step (error ~ seed^2).
+//  * ln(x): x = m 2^e with m in [1/sqrt2, sqrt2), ln m = 2 atanh((m-1)/(m+1)),
+//    atanh by its Taylor series to s^19 (|s| <= 0.172: truncation < 1e-16).
+//  * exp(-S), S >= 0: S = k ln2 + r, |r| <= ln2/2, exp(-r) by its Taylor
+//    series to r^13, times 2^-k; exp(-S) = 0 for S > 40 (h_a saturated).
+//  * The derivatives dq0/dn, dq0/dsigma only enter the potential (stored in
+//    FP32) and are formed in FP32 from the FP64 intermediates.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double rcp_nr(double v) {
+    const double r = (double)(1.0f / (float)v);
+    return fma(r, fma(-v, r, 1.0), r);
+}
+
+__device__ __forceinline__ double sqrt_nr(double x) {
+    const double y = (double)sqrtf((float)x);
+    const double r = (double)(0.5f / (float)y);
+    return fma(fma(-y, y, x), r, y);
+}
+
+__device__ __forceinline__ double cbrt_nr(double x) {
+    const double y = (double)cbrtf((float)x);
+    const double y2 = y * y;
+    const double r = (double)(1.0f / (3.0f * (float)y2));
+    return fma(fma(-y2, y, x), r, y);
+}
+
+// 2 atanh(s) = 2 (s + s^3/3 + ... + s^19/19)
+__device__ __forceinline__ double two_atanh_series(double s) {
+    const double z = s * s;
+    double p = 1.0 / 19.0;
+    p = fma(p, z, 1.0 / 17.0);
+    p = fma(p, z, 1.0 / 15.0);
+    p = fma(p, z, 1.0 / 13.0);
+    p = fma(p, z, 1.0 / 11.0);
+    p = fma(p, z, 1.0 / 9.0);
+    p = fma(p, z, 1.0 / 7.0);
+    p = fma(p, z, 1.0 / 5.0);
+    p = fma(p, z, 1.0 / 3.0);
+    p = fma(p, z, 1.0);
+    return 2.0 * s * p;
+}
+
+__device__ __forceinline__ double ln_series(double x) {
+    long long b = __double_as_longlong(x);
+    int e = (int)((b >> 52) & 0x7ff) - 1023;
+    double m = __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);   // [1, 2)
+    if (m > 1.4142135623730951) {
+        m *= 0.5;
+        e += 1;
+    }
+    const double s = (m - 1.0) * rcp_nr(m + 1.0);
+    return fma((double)e, 0.69314718055994530942, two_atanh_series(s));
+}
+
+// ln(1 + u), u > 0
+__device__ __forceinline__ double ln1p_series(double u) {
+    if (u < 0.41421356237309505) return two_atanh_series(u * rcp_nr(2.0 + u));
+    return ln_series(1.0 + u);
+}
+
+__device__ __forceinline__ double exp_neg(double S) {
+    if (S > 40.0) return 0.0;
+    const double k = rint(S * 1.4426950408889634074);
+    const double r = fma(-k, 0.69314718055994530942, S);     // S - k ln2
+    const double x = -r;
+    double p = 1.0 / 6227020800.0;                 // 1/13!
+    p = fma(p, x, 1.0 / 479001600.0);
+    p = fma(p, x, 1.0 / 39916800.0);
+    p = fma(p, x, 1.0 / 3628800.0);
+    p = fma(p, x, 1.0 / 362880.0);
+    p = fma(p, x, 1.0 / 40320.0);
+    p = fma(p, x, 1.0 / 5040.0);
+    p = fma(p, x, 1.0 / 720.0);
+    p = fma(p, x, 1.0 / 120.0);
+    p = fma(p, x, 1.0 / 24.0);
+    p = fma(p, x, 1.0 / 6.0);
+    p = fma(p, x, 0.5);
+    p = fma(p, x, 1.0);
+    p = fma(p, x, 1.0);
+    const long long ki = (long long)k;
+    return p * __longlong_as_double((1023LL - ki) << 52);   // 2^-k, 0 <= k <= 58
+}
+
+__device__ __forceinline__ Q0 q0_point_mixed(double n, double s, double Z) {
+    Q0 r;
+    r.live = n > c_qm.n_min;
+    if (!r.live) {
+        r.q0 = c_qm.q_min;
+        r.dqdn = 0.0;
+        r.dqds = 0.0;
+        return r;
+    }
+    s = s > 0.0 ? s : 0.0;
+    const double A = 0.031091, a1 = 0.2137;
+    const double b1 = 7.5957, b2 = 3.5876, b3 = 1.6382, b4 = 0.49294;
+    const double PI = 3.14159265358979323846;
+    const double kF = cbrt_nr(3.0 * PI * PI * n);
+    const double ikF = rcp_nr(kF);
+    const double rs = 1.9191582926775128 * ikF;             // (9 pi / 4)^(1/3) / k_F
+    const double srs = sqrt_nr(rs);
+    const double D = 2.0 * A * (b1 * srs + b2 * rs + b3 * rs * srs + b4 * rs * rs);
+    const double L = ln1p_series(rcp_nr(D));
+    const double eps = -2.0 * A * (1.0 + a1 * rs) * L;
+    const double in2 = rcp_nr(n * n);
+    const double G = -(Z / 36.0) * s * ikF * in2;
+    const double qraw = kF - (4.0 * PI / 3.0) * eps + G;
+    const double a = c_qm.q_cut;
+    const double t = qraw * (1.0 / a);
+    double S = 1.0 / 12.0;
+#pragma unroll
+    for (int m = 11; m >= 1; --m) S = fma(S, t, 1.0 / (double)m);
+    S *= t;
+    const double e = exp_neg(S);
+    const double q0 = a * (1.0 - e);
+    if (q0 < c_qm.q_min) {
+        r.q0 = c_qm.q_min;
+        r.dqdn = 0.0;
+        r.dqds = 0.0;
+        return r;
+    }
+    r.q0 = q0;
+    // derivatives in FP32
+    float dh = 0.f;
+    if (S <= 40.0) {
+        const float tf = (float)t;
+        float dS = 1.f;
+#pragma unroll
+        for (int m = 0; m < 11; ++m) dS = fmaf(dS, tf, 1.f);    // sum_{m=0}^{11} t^m
+        dh = (float)e * dS;
+    }
+    const float Df = (float)D, rsf = (float)rs, srsf = (float)srs, Lf = (float)L;
+    const float dD = 2.f * (float)A * (0.5f * (float)b1 / srsf + (float)b2 + 1.5f * (float)b3 * srsf +
+                                       2.f * (float)b4 * rsf);
+    const float deps = -2.f * (float)A * (float)a1 * Lf +
+                       2.f * (float)A * (1.f + (float)a1 * rsf) * dD / (Df * Df + Df);
+    const float inv_n = 1.f / (float)n;
+    const float kFf = (float)kF;
+    const float Gf = (float)G;
+    const float dq_dn = kFf * inv_n * (1.f / 3.f) + (float)(4.0 * PI / 9.0) * deps * rsf * inv_n -
+                        (7.f / 3.f) * Gf * inv_n;
+    const float dq_ds = -(float)(Z / 36.0) * (float)ikF * (float)in2;
+    r.dqdn = (double)(dh * dq_dn);
+    r.dqds = (double)(dh * dq_ds);
     return r;
 }
 
@@ -179,7 +329,7 @@ __global__ void __launch_bounds__(256) k_zfwd(const SysDev *__restrict__ sys, co
             const int li = i / nz, z = i - li * nz;
             const double n = S.n[p0 + i];
             const double sg = S.sigma[p0 + i];
-            const Q0 q = q0_point(n, sg, S.Z);
+            const Q0 q = sizeof(T) == 4 ? q0_point_mixed(n, sg, S.Z) : q0_point(n, sg, S.Z);
             Rec<T> r;
             T th[NQ];
             if (q.live) {
@@ -209,7 +359,7 @@ __global__ void __launch_bounds__(256) k_zfwd(const SysDev *__restrict__ sys, co
             for (int c = 0; c < 10; ++c) dst[c] = cx<T>{th[2 * c], th[2 * c + 1]};
         }
         __syncthreads();
-        cx<T> *R = fft_lines<false>(bufA, bufB, S.ax[2], L, L, 1, tw, true);
+        cx<T> *R = fft_lines<false>(bufA, bufB, S.ax[2], L, tw);
         // unpack the two real transforms and store the half spectrum
         cx<T> *spec = reinterpret_cast<cx<T> *>(S.spec) + (size_t)l0 * nzh * NQ;
         const int nout = nl * nzh * NQ;
@@ -237,48 +387,13 @@ __global__ void __launch_bounds__(256) k_zfwd(const SysDev *__restrict__ sys, co
 }
 
 // ---------------------------------------------------------------------------
-// y transform of a tile (x, kz0 .. kz0 + W - 1), all 20 fields.
-// ---------------------------------------------------------------------------
-template <typename T, bool INV>
-__global__ void __launch_bounds__(256) k_yfft(const SysDev *__restrict__ sys, const int *__restrict__ prefix,
-                                              int nsys, int total) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    for (int t = blockIdx.x; t < total; t += gridDim.x) {
-        const int si = find_sys(prefix, nsys, t);
-        const SysDev &S = sys[si];
-        const int lt = t - prefix[si];
-        const int ny = S.ny, nzh = S.nzh, W = S.W;
-        const int ncol = (nzh + W - 1) / W;
-        const int x = lt / ncol;
-        const int kz0 = (lt - x * ncol) * W;
-        const int wt = min(W, nzh - kz0);
-        const int L = wt * NQ;
-        cx<T> *tw = reinterpret_cast<cx<T> *>(smem);
-        cx<T> *bufA = tw + ny;
-        cx<T> *bufB = bufA + (size_t)ny * L;
-        const cx<T> *twg = reinterpret_cast<const cx<T> *>(S.tw[1]);
-        for (int i = threadIdx.x; i < ny; i += blockDim.x) tw[i] = twg[i];
-        cx<T> *spec = reinterpret_cast<cx<T> *>(S.spec);
-        const size_t rowstride = (size_t)nzh * NQ;
-        const size_t g0 = ((size_t)x * ny * nzh + kz0) * NQ;
-        for (int i = threadIdx.x; i < ny * L; i += blockDim.x) {
-            const int y = i / L, e = i - y * L;
-            bufA[i] = spec[g0 + y * rowstride + e];
-        }
-        __syncthreads();
-        cx<T> *R = fft_lines<INV>(bufA, bufB, S.ax[1], L, L, 1, tw, true);
-        for (int i = threadIdx.x; i < ny * L; i += blockDim.x) {
-            const int y = i / L, e = i - y * L;
-            spec[g0 + y * rowstride + e] = R[i];
-        }
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------------------
-// x transform + kernel contraction + energy + inverse x transform.
-// Tile (ky, kz0 .. kz0 + W - 1); after the forward x transform every k-point
-// of the tile has its 20 theta_a(k) in shared memory.
+// Transforms along y and x.  A tile is (outer index, kz0 .. kz0 + W - 1):
+// for the y pass outer = x and the tile's rows run over y; for the x pass
+// outer = ky and the rows run over x.  Each row is W * 20 contiguous complex
+// values (the [x][y][kz][a] layout), fetched by bulk copies into a double-
+// buffered shared-memory stage while the previous tile is transformed.
+// The x pass adds the kernel contraction and energy between the forward and
+// inverse transforms (procedure step 3).
 // ---------------------------------------------------------------------------
 template <typename T>
 struct KTab;
@@ -354,69 +469,153 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
     return s;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_xcontract(const SysDev *__restrict__ sys, const int *__restrict__ prefix,
-                                                   int nsys, int total,
-                                                   const typename KTab<T>::V *__restrict__ tab) {
-    extern __shared__ __align__(16) unsigned char smem[];
+struct XYTile {
+    int si, lt, nrows, wt, L, outer, kz0;
+    size_t g0, rowstride;
+};
+
+template <bool XPASS>
+__device__ __forceinline__ XYTile xy_tile(const SysDev *__restrict__ sys, const int *__restrict__ prefix, int nsys,
+                                          int t) {
+    XYTile g;
+    g.si = find_sys(prefix, nsys, t);
+    const SysDev &S = sys[g.si];
+    g.lt = t - prefix[g.si];
+    const int ncol = (S.nzh + S.W - 1) / S.W;
+    g.outer = g.lt / ncol;
+    g.kz0 = (g.lt - g.outer * ncol) * S.W;
+    g.wt = min(S.W, S.nzh - g.kz0);
+    g.L = g.wt * NQ;
+    if (XPASS) {
+        g.nrows = S.nx;
+        g.g0 = ((size_t)g.outer * S.nzh + g.kz0) * NQ;
+        g.rowstride = (size_t)S.ny * S.nzh * NQ;
+    } else {
+        g.nrows = S.ny;
+        g.g0 = ((size_t)g.outer * S.ny * S.nzh + g.kz0) * NQ;
+        g.rowstride = (size_t)S.nzh * NQ;
+    }
+    return g;
+}
+
+// warp 0 issues the bulk copies of tile t into buf (completion on bar)
+template <typename T, bool XPASS>
+__device__ __forceinline__ void xy_issue(const SysDev *__restrict__ sys, const int *__restrict__ prefix, int nsys,
+                                         int t, cx<T> *buf, unsigned long long *bar) {
+    const XYTile g = xy_tile<XPASS>(sys, prefix, nsys, t);
+    const cx<T> *spec = reinterpret_cast<const cx<T> *>(sys[g.si].spec);
+    const unsigned rowbytes = (unsigned)(g.L * sizeof(cx<T>));
+    const int lane = threadIdx.x & 31;
+    fence_proxy_async();
+    if (lane == 0) mbar_expect_tx(bar, rowbytes * (unsigned)g.nrows);
+    __syncwarp();
+    for (int r = lane; r < g.nrows; r += 32) bulk_g2s(buf + (size_t)r * g.L, spec + g.g0 + r * g.rowstride, rowbytes, bar);
+}
+
+// MODE 0: forward y, 1: inverse y, 2: forward x + contraction + inverse x
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_xy(const SysDev *__restrict__ sys, const int *__restrict__ prefix,
+                                               int nsys, int total, int twmax, int bufelems, int nbuf,
+                                               const typename KTab<T>::V *__restrict__ tab, int *__restrict__ err) {
+    constexpr bool XPASS = MODE == 2;
+    extern __shared__ __align__(128) unsigned char smem[];
     __shared__ double red[32];
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem);
+    cx<T> *tw = reinterpret_cast<cx<T> *>(smem + 16);
+    cx<T> *in0 = tw + ((twmax + 7) & ~7);
+    // nbuf 3: two input stages (prefetch of the next tile) + transform scratch;
+    // nbuf 2: one input stage, loaded after the previous tile is stored.
+    cx<T> *bufs[2] = {in0, nbuf == 3 ? in0 + bufelems : in0};
+    cx<T> *work = in0 + (size_t)(nbuf - 1) * bufelems;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    unsigned ph[2] = {0u, 0u};
+    int t = blockIdx.x;
+    if (t < total && threadIdx.x < 32) xy_issue<T, XPASS>(sys, prefix, nsys, t, bufs[0], &bar[0]);
+    int cur_sys = -1;
     const T inv_dk = (T)(RMAX / (2.0 * 3.14159265358979323846));
-    for (int t = blockIdx.x; t < total; t += gridDim.x) {
-        const int si = find_sys(prefix, nsys, t);
-        const SysDev &S = sys[si];
-        const int lt = t - prefix[si];
-        const int nx = S.nx, ny = S.ny, nz = S.nz, nzh = S.nzh, W = S.W;
-        const int ncol = (nzh + W - 1) / W;
-        const int ky = lt / ncol;
-        const int kz0 = (lt - ky * ncol) * W;
-        const int wt = min(W, nzh - kz0);
-        const int L = wt * NQ;
-        cx<T> *tw = reinterpret_cast<cx<T> *>(smem);
-        cx<T> *bufA = tw + nx;
-        cx<T> *bufB = bufA + (size_t)nx * L;
-        const cx<T> *twg = reinterpret_cast<const cx<T> *>(S.tw[0]);
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) tw[i] = twg[i];
+    for (int i = 0; t < total; ++i, t += gridDim.x) {
+        const int cur = i & 1;
+        const int tn = t + gridDim.x;
+        if (nbuf == 3 && tn < total && threadIdx.x < 32)
+            xy_issue<T, XPASS>(sys, prefix, nsys, tn, bufs[cur ^ 1], &bar[cur ^ 1]);
+        const XYTile g = xy_tile<XPASS>(sys, prefix, nsys, t);
+        const SysDev &S = sys[g.si];
+        const AxisPlan &ap = S.ax[XPASS ? 0 : 1];
+        if (g.si != cur_sys) {
+            const cx<T> *twg = reinterpret_cast<const cx<T> *>(S.tw[XPASS ? 0 : 1]);
+            for (int k = threadIdx.x; k < ap.n; k += blockDim.x) tw[k] = twg[k];
+            cur_sys = g.si;
+        }
+        bool ok = mbar_wait(&bar[cur], ph[cur]);
+        ph[cur] ^= 1u;
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) atomicExch(err, 1);
+            if (nbuf == 3 && tn < total) mbar_wait(&bar[cur ^ 1], ph[cur ^ 1]);
+            return;
+        }
+        cx<T> *in = bufs[cur];
+        cx<T> *R;
+        if (MODE == 1) R = fft_lines<true>(in, work, ap, g.L, tw);
+        else R = fft_lines<false>(in, work, ap, g.L, tw);
+        if (MODE == 2) {
+            cx<T> *O = R == in ? work : in;
+            double eacc = 0.0;
+            const int nx = S.nx, ny = S.ny, nz = S.nz;
+            const int ky = g.outer;
+            const int my = fold(ky, ny);
+            const bool nyq_y = (ny % 2 == 0) && (ky == ny / 2);
+            const T g00 = (T)S.g[0], g11 = (T)S.g[1], g22 = (T)S.g[2];
+            const T g01 = (T)S.g[3], g02 = (T)S.g[4], g12 = (T)S.g[5];
+            for (int k = threadIdx.x; k < nx * g.wt; k += blockDim.x) {
+                const int x = k / g.wt, w = k - x * g.wt;
+                const int kz = g.kz0 + w;
+                const int mx = fold(x, nx);
+                const bool nyq_x = (nx % 2 == 0) && (x == nx / 2);
+                const bool nyq_z = (nz % 2 == 0) && (kz == nz / 2);
+                const int mz = nyq_z ? -kz : kz;
+                const T fx = (T)mx, fy = (T)my, fz = (T)mz;
+                const T cxv = nyq_x ? (T)0 : fx, cyv = nyq_y ? (T)0 : fy, czv = nyq_z ? (T)0 : fz;
+                T k2 = g00 * fx * fx + g11 * fy * fy + g22 * fz * fz +
+                       (T)2 * (g01 * cxv * cyv + g02 * cxv * czv + g12 * cyv * czv);
+                k2 = k2 > (T)0 ? k2 : (T)0;
+                const T kabs = sqrt(k2);
+                const T weight = (kz == 0 || nyq_z) ? (T)1 : (T)2;
+                contract_point<T>(R + (size_t)x * g.L + w * NQ, kabs, tab, inv_dk, weight, eacc);
+            }
+            const double es = block_sum<T>(eacc, red);
+            if (threadIdx.x == 0) S.epart[g.lt] = es;
+            __syncthreads();
+            R = fft_lines<true>(R, O, ap, g.L, tw);
+        }
+        // store the rows back (16-byte vectors)
         cx<T> *spec = reinterpret_cast<cx<T> *>(S.spec);
-        const size_t rowstride = (size_t)ny * nzh * NQ;
-        const size_t g0 = ((size_t)ky * nzh + kz0) * NQ;
-        for (int i = threadIdx.x; i < nx * L; i += blockDim.x) {
-            const int x = i / L, e = i - x * L;
-            bufA[i] = spec[g0 + x * rowstride + e];
+        if (sizeof(cx<T>) == 8) {
+            const int h = g.L >> 1;   // L = 20 W is even
+            for (int k = threadIdx.x; k < g.nrows * h; k += blockDim.x) {
+                const int r = k / h, e = k - r * h;
+                const float4 v = *reinterpret_cast<const float4 *>(R + (size_t)r * g.L + 2 * e);
+                *reinterpret_cast<float4 *>(spec + g.g0 + r * g.rowstride + 2 * e) = v;
+            }
+        } else {
+            for (int k = threadIdx.x; k < g.nrows * g.L; k += blockDim.x) {
+                const int r = k / g.L, e = k - r * g.L;
+                spec[g.g0 + r * g.rowstride + e] = R[(size_t)r * g.L + e];
+            }
         }
+        fence_proxy_async();   // this tile's generic accesses before the next bulk writes
         __syncthreads();
-        cx<T> *R = fft_lines<false>(bufA, bufB, S.ax[0], L, L, 1, tw, true);
-        cx<T> *O = R == bufA ? bufB : bufA;
-        // contraction, one thread per k-point
-        double eacc = 0.0;
-        const int my = fold(ky, ny);
-        const bool nyq_y = (ny % 2 == 0) && (ky == ny / 2);
-        const T g00 = (T)S.g[0], g11 = (T)S.g[1], g22 = (T)S.g[2];
-        const T g01 = (T)S.g[3], g02 = (T)S.g[4], g12 = (T)S.g[5];
-        for (int i = threadIdx.x; i < nx * wt; i += blockDim.x) {
-            const int x = i / wt, w = i - x * wt;
-            const int kz = kz0 + w;
-            const int mx = fold(x, nx);
-            const bool nyq_x = (nx % 2 == 0) && (x == nx / 2);
-            const bool nyq_z = (nz % 2 == 0) && (kz == nz / 2);
-            const int mz = nyq_z ? -kz : kz;
-            const T fx = (T)mx, fy = (T)my, fz = (T)mz;
-            const T cxv = nyq_x ? (T)0 : fx, cyv = nyq_y ? (T)0 : fy, czv = nyq_z ? (T)0 : fz;
-            T k2 = g00 * fx * fx + g11 * fy * fy + g22 * fz * fz +
-                   (T)2 * (g01 * cxv * cyv + g02 * cxv * czv + g12 * cyv * czv);
-            k2 = k2 > (T)0 ? k2 : (T)0;
-            const T kabs = sqrt(k2);
-            const T weight = (kz == 0 || nyq_z) ? (T)1 : (T)2;
-            contract_point<T>(R + (size_t)x * L + w * NQ, kabs, tab, inv_dk, weight, eacc);
-        }
-        const double es = block_sum<T>(eacc, red);
-        if (threadIdx.x == 0) S.epart[lt] = es;
-        __syncthreads();
-        cx<T> *R2 = fft_lines<true>(R, O, S.ax[0], L, L, 1, tw, true);
-        for (int i = threadIdx.x; i < nx * L; i += blockDim.x) {
-            const int x = i / L, e = i - x * L;
-            spec[g0 + x * rowstride + e] = R2[i];
-        }
-        __syncthreads();
+        if (nbuf == 2 && tn < total && threadIdx.x < 32)
+            xy_issue<T, XPASS>(sys, prefix, nsys, tn, bufs[cur ^ 1], &bar[cur ^ 1]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_inval(&bar[0]);
+        mbar_inval(&bar[1]);
     }
 }
 
@@ -464,7 +663,7 @@ __global__ void __launch_bounds__(256) k_zinv(const SysDev *__restrict__ sys, co
                 bufA[(size_t)km * L + li * 10 + c] = cx<T>{a.x + b.y, b.x - a.y};
         }
         __syncthreads();
-        cx<T> *R = fft_lines<true>(bufA, bufB, S.ax[2], L, L, 1, tw, true);
+        cx<T> *R = fft_lines<true>(bufA, bufB, S.ax[2], L, tw);
         const Rec<T> *rec = reinterpret_cast<const Rec<T> *>(S.rec);
         const size_t p0 = (size_t)l0 * nz;
         const T invN = (T)S.invN;
@@ -530,6 +729,27 @@ __global__ void k_efinish(const SysDev *__restrict__ sys, int nsys) {
     }
 }
 
+// q0, dq0/dn, dq0/dsigma of the chosen form at given points (checks of the
+// q0 step on its own).
+template <typename T>
+__global__ void k_q0(int npts, const double *__restrict__ n, const double *__restrict__ s, double Z,
+                     double *__restrict__ q0, double *__restrict__ dqdn, double *__restrict__ dqds) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npts) return;
+    const Q0 q = sizeof(T) == 4 ? q0_point_mixed(n[i], s[i], Z) : q0_point(n[i], s[i], Z);
+    q0[i] = q.q0;
+    dqdn[i] = q.dqdn;
+    dqds[i] = q.dqds;
+}
+
+cudaError_t launch_q0(int prec, int npts, const double *n, const double *s, double Z, double *q0, double *dqdn,
+                      double *dqds) {
+    const int blocks = (npts + 255) / 256;
+    if (prec == 1) k_q0<float><<<blocks, 256>>>(npts, n, s, Z, q0, dqdn, dqds);
+    else k_q0<double><<<blocks, 256>>>(npts, n, s, Z, q0, dqdn, dqds);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Host-side launchers
 // ---------------------------------------------------------------------------
@@ -538,30 +758,32 @@ size_t smem_z(int nz, int LZ) {
     return ((sizeof(QShared<T>) + 15) / 16) * 16 + sizeof(cx<T>) * ((size_t)nz + 2ull * nz * 10 * LZ);
 }
 template <typename T>
-size_t smem_xy(int n, int W) {
-    return sizeof(cx<T>) * ((size_t)n + 2ull * n * NQ * W);
+size_t smem_xy(int n, int W, int nbuf) {
+    return 16 + sizeof(cx<T>) * ((size_t)((n + 7) & ~7) + (size_t)nbuf * n * NQ * W);
 }
 
-size_t stage_smem(int stage, int prec, int n, int tile) {
+size_t stage_smem(int stage, int prec, int n, int tile, int nbuf) {
     const bool f = prec == 1;
     switch (stage) {
         case 0:
         case 3: return f ? smem_z<float>(n, tile) : smem_z<double>(n, tile);
-        default: return f ? smem_xy<float>(n, tile) : smem_xy<double>(n, tile);
+        default: return f ? smem_xy<float>(n, tile, nbuf) : smem_xy<double>(n, tile, nbuf);
     }
 }
 
 static cudaError_t set_smem(const void *fn, size_t bytes) {
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
 template <typename T>
 static cudaError_t init_kernels_t(size_t maxsmem) {
     cudaError_t e;
     if ((e = set_smem((const void *)k_zfwd<T>, maxsmem)) != cudaSuccess) return e;
-    if ((e = set_smem((const void *)k_yfft<T, false>, maxsmem)) != cudaSuccess) return e;
-    if ((e = set_smem((const void *)k_yfft<T, true>, maxsmem)) != cudaSuccess) return e;
-    if ((e = set_smem((const void *)k_xcontract<T>, maxsmem - 32 * sizeof(double))) != cudaSuccess) return e;
+    if ((e = set_smem((const void *)k_xy<T, 0>, maxsmem - 32 * sizeof(double))) != cudaSuccess) return e;
+    if ((e = set_smem((const void *)k_xy<T, 1>, maxsmem - 32 * sizeof(double))) != cudaSuccess) return e;
+    if ((e = set_smem((const void *)k_xy<T, 2>, maxsmem - 32 * sizeof(double))) != cudaSuccess) return e;
     if ((e = set_smem((const void *)k_zinv<T>, maxsmem)) != cudaSuccess) return e;
     return cudaSuccess;
 }
@@ -578,11 +800,14 @@ static cudaError_t launch_all_t(const LaunchSet &ls, cudaStream_t st, cudaEvent_
     if (ev) cudaEventRecord(ev[0], st);
     k_zfwd<T><<<ls.grid[0], 256, ls.smem[0], st>>>(ls.sys, ls.prefix[0], ls.nsys, ls.total[0]);
     if (ev) cudaEventRecord(ev[1], st);
-    k_yfft<T, false><<<ls.grid[1], 256, ls.smem[1], st>>>(ls.sys, ls.prefix[1], ls.nsys, ls.total[1]);
+    k_xy<T, 0><<<ls.grid[1], 256, ls.smem[1], st>>>(ls.sys, ls.prefix[1], ls.nsys, ls.total[1], ls.twmax[1],
+                                                     ls.bufelems[1], ls.nbuf[1], tab, ls.err);
     if (ev) cudaEventRecord(ev[2], st);
-    k_xcontract<T><<<ls.grid[2], 256, ls.smem[2], st>>>(ls.sys, ls.prefix[2], ls.nsys, ls.total[2], tab);
+    k_xy<T, 2><<<ls.grid[2], 256, ls.smem[2], st>>>(ls.sys, ls.prefix[2], ls.nsys, ls.total[2], ls.twmax[2],
+                                                     ls.bufelems[2], ls.nbuf[2], tab, ls.err);
     if (ev) cudaEventRecord(ev[3], st);
-    k_yfft<T, true><<<ls.grid[1], 256, ls.smem[1], st>>>(ls.sys, ls.prefix[1], ls.nsys, ls.total[1]);
+    k_xy<T, 1><<<ls.grid[1], 256, ls.smem[1], st>>>(ls.sys, ls.prefix[1], ls.nsys, ls.total[1], ls.twmax[1],
+                                                     ls.bufelems[1], ls.nbuf[1], tab, ls.err);
     if (ev) cudaEventRecord(ev[4], st);
     k_zinv<T><<<ls.grid[3], 256, ls.smem[3], st>>>(ls.sys, ls.prefix[3], ls.nsys, ls.total[3]);
     if (ev) cudaEventRecord(ev[5], st);

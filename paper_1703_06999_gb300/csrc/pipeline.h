@@ -15,15 +15,21 @@ struct LaunchSet {
     int total[4];            // tiles per stage over all systems
     int grid[4];
     size_t smem[4];
-    const void *table;       // kernel polynomial table (float4 or double4), [210][NK-1]
+    const void *table;       // kernel polynomial table (float4 or dvec4), [210][NK-1]
+    int twmax[4];            // longest axis of the stage over all systems (twiddle slots)
+    int bufelems[4];         // complex elements of one row-tile buffer (x / y stages)
+    int nbuf[4];             // row-tile buffers of the x / y stages: 3 (prefetching) or 2
+    int *err;                // device flag set by a stage whose bounded wait ran out
 };
 
-size_t stage_smem(int stage, int prec, int n, int tile);
+size_t stage_smem(int stage, int prec, int n, int tile, int nbuf = 3);
 cudaError_t init_kernels(size_t maxsmem);
 constexpr int NSTAGE = 6;   // kernel launches per evaluation
 // Enqueue all stages; if ev != nullptr, record ev[0..NSTAGE] around them.
 cudaError_t launch_all(const LaunchSet &ls, int prec, cudaStream_t st, cudaEvent_t *ev = nullptr);
 const char *stage_name(int i);
 cudaError_t upload_qmesh(const QMeshDev &q);
+cudaError_t launch_q0(int prec, int npts, const double *n, const double *s, double Z, double *q0, double *dqdn,
+                      double *dqds);
 
 }  // namespace vdwgb
