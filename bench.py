@@ -109,16 +109,20 @@ def peaks():
 def stage_bytes(shape, prec_bytes):
     """Algorithmic DRAM bytes per launch of each stage for one system.
     c = complex element size; the half spectrum holds 20 * nx * ny * (nz/2+1)
-    complex values; records are 16 B (FP32-mixed) or 32 B (FP64) per point."""
+    complex values; records are 16 B (FP32-mixed) or 32 B (FP64) per point;
+    the contraction also reads one 4-byte k-point index per k-point."""
     nx, ny, nz = shape
     N = nx * ny * nz
+    nk = nx * ny * (nz // 2 + 1)
     c = 2 * prec_bytes
     rec = 16 if prec_bytes == 4 else 32
-    spec = 20 * nx * ny * (nz // 2 + 1) * c
+    spec = 20 * nk * c
     return {
         "zfwd": 16 * N + rec * N + spec,          # n, sigma in; records, spectrum out
         "yfwd": 2 * spec,
-        "xcontract": 2 * spec,
+        "xfwd": 2 * spec,
+        "contract": 2 * spec + 4 * nk,
+        "xinv": 2 * spec,
         "yinv": 2 * spec,
         "zinv": spec + rec * N + 16 * N,          # spectrum, records in; dedn, dedsigma out
         "efinish": 0,

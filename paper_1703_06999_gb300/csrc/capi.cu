@@ -122,6 +122,8 @@ struct vdwgb_data {
     void *rec = nullptr;
     double *epart = nullptr;
     void *tw[3] = {nullptr, nullptr, nullptr};
+    unsigned *kidx = nullptr;
+    int4 *chunks = nullptr;
     SysDev *dsys = nullptr;
     int *dprefix = nullptr;
     SysDev hsys;
@@ -141,6 +143,10 @@ static void release(vdwgb_data *h) {
     cudaFree(h->rec);
     cudaFree(h->epart);
     for (int i = 0; i < 3; ++i) cudaFree(h->tw[i]);
+    cudaFree(h->kidx);
+    cudaFree(h->chunks);
+    h->kidx = nullptr;
+    h->chunks = nullptr;
     cudaFree(h->dsys);
     cudaFree(h->dprefix);
     cudaFree(h->d_io);
@@ -161,11 +167,16 @@ static size_t rec_bytes(int prec) { return prec == VDWGB_FP32_MIXED ? 16 : 32; }
 // Tile choices: z passes LZ lines, x/y passes W columns with three row
 // buffers (prefetch); prefer two blocks per SM (<= ~110 KB).  Axes too long
 // for three buffers of one column use two (no prefetch).
-static void choose_tiles(int prec, int nx, int ny, int nz, int nzh, size_t lim, int &LZ, int &W, int &nbuf) {
+static void choose_tiles(int prec, int nx, int ny, int nz, int nzh, size_t lim, int &LZ, int &LZi, int &W,
+                         int &nbuf) {
     const size_t budget = 110 * 1024;
     LZ = 1;
     for (int l = 8; l >= 1; --l)
         if (stage_smem(0, prec, nz, l) <= budget) { LZ = l; break; }
+    LZi = 1;
+    for (int l = 8; l >= 1; --l)
+        if (stage_smem(3, prec, nz, l) <= budget) { LZi = l; break; }
+    if (LZi > nx * ny) LZi = nx * ny;
     const int nxy = nx > ny ? nx : ny;
     W = 1;
     nbuf = 3;
@@ -174,6 +185,66 @@ static void choose_tiles(int prec, int nx, int ny, int nz, int nzh, size_t lim, 
     if (stage_smem(1, prec, nxy, 1, 3) > lim) nbuf = 2;
     if (W > nzh) W = nzh;
     if (LZ > nx * ny) LZ = nx * ny;
+}
+
+// Sort the half-spectrum k-points of a system by kernel-table interval
+// j = floor(|k| / dk) (|k| with the same Nyquist convention as the kernels;
+// intervals beyond the table form their own group) and cut the order into
+// chunks of at most 256 k-points spanning at most `maxspan` intervals.
+// chunk = {first index into kidx, count, first interval, intervals (0 beyond)}.
+static void build_chunks(const SysDev &S, int maxspan, std::vector<unsigned> &kidx, std::vector<int4> &chunks) {
+    const int nx = S.nx, ny = S.ny, nz = S.nz, nzh = S.nzh;
+    const size_t nk = (size_t)nx * ny * nzh;
+    const double dk = 2.0 * M_PI / RMAX;
+    std::vector<int> bin(nk);
+    std::vector<size_t> count(NK + 1, 0);
+    auto fold = [](int i, int n) { return i <= (n - 1) / 2 ? i : i - n; };
+    for (int x = 0; x < nx; ++x) {
+        const int mx = fold(x, nx);
+        const bool qx = (nx % 2 == 0) && (x == nx / 2);
+        for (int y = 0; y < ny; ++y) {
+            const int my = fold(y, ny);
+            const bool qy = (ny % 2 == 0) && (y == ny / 2);
+            for (int kz = 0; kz < nzh; ++kz) {
+                const bool qz = (nz % 2 == 0) && (kz == nz / 2);
+                const int mz = qz ? -kz : kz;
+                const double cx = qx ? 0.0 : mx, cy = qy ? 0.0 : my, cz = qz ? 0.0 : mz;
+                double k2 = S.g[0] * mx * mx + S.g[1] * (double)my * my + S.g[2] * (double)mz * mz +
+                            2.0 * (S.g[3] * cx * cy + S.g[4] * cx * cz + S.g[5] * cy * cz);
+                if (k2 < 0) k2 = 0;
+                long j = (long)(std::sqrt(k2) / dk);
+                if (j > NK - 1) j = NK - 1;
+                const size_t idx = ((size_t)x * ny + y) * nzh + kz;
+                bin[idx] = (int)j;
+                ++count[j];
+            }
+        }
+    }
+    std::vector<size_t> start(NK + 1, 0);
+    for (int j = 1; j <= NK; ++j) start[j] = start[j - 1] + count[j - 1];
+    kidx.assign(nk, 0);
+    std::vector<size_t> pos(start.begin(), start.end());
+    for (size_t i = 0; i < nk; ++i) kidx[pos[bin[i]]++] = (unsigned)i;
+    chunks.clear();
+    size_t i = 0;
+    while (i < nk) {
+        const int j0 = bin[kidx[i]];
+        int4 c;
+        c.x = (int)i;
+        c.z = j0;
+        size_t n = 0;
+        int jl = j0;
+        while (i + n < nk && n < 256) {
+            const int jb = bin[kidx[i + n]];
+            if (j0 == NK - 1 ? jb != NK - 1 : (jb == NK - 1 || jb - j0 >= maxspan)) break;
+            jl = jb;
+            ++n;
+        }
+        c.y = (int)n;
+        c.w = j0 == NK - 1 ? 0 : jl - j0 + 1;
+        chunks.push_back(c);
+        i += n;
+    }
 }
 
 static int plan(vdwgb_data *h) {
@@ -192,16 +263,16 @@ static int plan(vdwgb_data *h) {
             return fail(VDWGB_EINVAL, "axis %d length %d: prime factors must be 2, 3, 5, 7", a, dims[a]);
     const size_t lim = di.maxsmem - 1024;
     int nbuf = 3;
-    choose_tiles(prec, nx, ny, nz, nzh, lim, S.LZ, S.W, nbuf);
+    choose_tiles(prec, nx, ny, nz, nzh, lim, S.LZ, S.LZi, S.W, nbuf);
     if (stage_smem(0, prec, nz, S.LZ) > lim || stage_smem(1, prec, nx, S.W, nbuf) > lim ||
-        stage_smem(1, prec, ny, S.W, nbuf) > lim)
+        stage_smem(1, prec, ny, S.W, nbuf) > lim || stage_smem(3, prec, nz, S.LZi) > lim)
         return fail(VDWGB_EINVAL, "grid %dx%dx%d too large for one block per pencil in this precision",
                     nx, ny, nz);
     const int ncol = (nzh + S.W - 1) / S.W;
     S.tiles[0] = (nx * ny + S.LZ - 1) / S.LZ;
     S.tiles[1] = nx * ncol;
     S.tiles[2] = ny * ncol;
-    S.tiles[3] = S.tiles[0];
+    S.tiles[3] = (nx * ny + S.LZi - 1) / S.LZi;
     // reciprocal metric g = B B^T, B = 2 pi C^{-T} (rows b_j)
     const double *c = h->cell;
     const double det = c[0] * (c[4] * c[8] - c[5] * c[7]) - c[1] * (c[3] * c[8] - c[5] * c[6]) +
@@ -234,11 +305,23 @@ static int plan(vdwgb_data *h) {
     S.escale = 0.5 * omega / (N * N);
     S.invN = 1.0 / N;
     S.Z = h->functional == VDWGB_DF2 ? -1.887 : -0.8491;
+    // half-spectrum k-points sorted by kernel-table interval, cut into chunks
+    const int maxspan = prec == VDWGB_FP32_MIXED ? 16 : 8;
+    std::vector<unsigned> kidx;
+    std::vector<int4> chunks;
+    build_chunks(S, maxspan, kidx, chunks);
+    S.tiles[4] = (int)chunks.size();
     // memory
     const size_t nspec = (size_t)nx * ny * nzh * NQ;
     CK(cudaMalloc(&h->spec, nspec * elem_bytes(prec)), "work buffer");
     CK(cudaMalloc(&h->rec, (size_t)nx * ny * nz * rec_bytes(prec)), "point records");
-    CK(cudaMalloc(&h->epart, (size_t)S.tiles[2] * sizeof(double)), "energy partials");
+    CK(cudaMalloc(&h->epart, (size_t)S.tiles[4] * sizeof(double)), "energy partials");
+    CK(cudaMalloc(&h->kidx, kidx.size() * sizeof(unsigned)), "k-point order");
+    CK(cudaMemcpy(h->kidx, kidx.data(), kidx.size() * sizeof(unsigned), cudaMemcpyHostToDevice), "k-point order");
+    CK(cudaMalloc(&h->chunks, chunks.size() * sizeof(int4)), "chunks");
+    CK(cudaMemcpy(h->chunks, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice), "chunks");
+    S.kidx = h->kidx;
+    S.chunks = h->chunks;
     for (int a = 0; a < 3; ++a) {
         std::vector<double> w = twiddles(dims[a]);
         if (prec == VDWGB_FP32_MIXED) {
@@ -255,11 +338,12 @@ static int plan(vdwgb_data *h) {
     S.spec = h->spec;
     S.rec = h->rec;
     S.epart = h->epart;
-    h->bytes = nspec * elem_bytes(prec) + (size_t)nx * ny * nz * rec_bytes(prec) + S.tiles[2] * sizeof(double);
+    h->bytes = nspec * elem_bytes(prec) + (size_t)nx * ny * nz * rec_bytes(prec) + S.tiles[4] * sizeof(double) +
+               kidx.size() * sizeof(unsigned) + chunks.size() * sizeof(int4);
     CK(cudaMalloc(&h->dsys, sizeof(SysDev)), "descriptor");
-    CK(cudaMalloc(&h->dprefix, 8 * sizeof(int)), "prefix");
-    int pre[8];
-    for (int s = 0; s < 4; ++s) {
+    CK(cudaMalloc(&h->dprefix, 2 * NKIND * sizeof(int)), "prefix");
+    int pre[2 * NKIND];
+    for (int s = 0; s < NKIND; ++s) {
         pre[2 * s] = 0;
         pre[2 * s + 1] = S.tiles[s];
     }
@@ -269,7 +353,8 @@ static int plan(vdwgb_data *h) {
     LaunchSet &L = h->ls;
     L.sys = h->dsys;
     L.nsys = 1;
-    for (int s = 0; s < 4; ++s) {
+    L.maxspan = maxspan;
+    for (int s = 0; s < NKIND; ++s) {
         L.prefix[s] = h->dprefix + 2 * s;
         L.total[s] = S.tiles[s];
     }
@@ -277,16 +362,23 @@ static int plan(vdwgb_data *h) {
     L.twmax[0] = L.twmax[3] = nz;
     L.twmax[1] = ny;
     L.twmax[2] = nx;
-    L.bufelems[0] = L.bufelems[3] = 0;
+    L.bufelems[0] = 0;
+    L.bufelems[3] = S.LZi * nzh * NQ;
+    L.recelems = S.LZi * nz;
+    L.abelems = nz * 10 * S.LZi;
     L.bufelems[1] = ny * S.W * NQ;
     L.bufelems[2] = nx * S.W * NQ;
+    L.twmax[4] = 0;
+    L.bufelems[4] = 0;
+    L.nbuf[4] = 0;
     L.smem[0] = stage_smem(0, prec, nz, S.LZ);
-    L.smem[3] = L.smem[0];
+    L.smem[3] = stage_smem(3, prec, nz, S.LZi);
     L.nbuf[0] = L.nbuf[3] = 0;
     L.nbuf[1] = L.nbuf[2] = nbuf;
     L.smem[1] = stage_smem(1, prec, ny, S.W, nbuf);
     L.smem[2] = stage_smem(1, prec, nx, S.W, nbuf);
-    for (int s = 0; s < 4; ++s) {
+    L.smem[4] = contract_smem(prec, maxspan);
+    for (int s = 0; s < NKIND; ++s) {
         int per_sm = (int)((228 * 1024) / (L.smem[s] + 1024));
         per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
         const int cap = di.sms * per_sm;
@@ -483,9 +575,9 @@ int vdwgb_print(vdwgb_handle h) {
            h->cell[8]);
     if (h->inited) {
         const SysDev &S = h->hsys;
-        printf("  device %d, %s, tiles z %d y %d x %d (LZ %d, W %d), %.1f MB\n", h->device,
-               h->prec == VDWGB_FP32_MIXED ? "FP32-mixed" : "FP64", S.tiles[0], S.tiles[1], S.tiles[2], S.LZ,
-               S.W, h->bytes / 1e6);
+        printf("  device %d, %s, tiles zf %d y %d x %d zi %d chunks %d (LZ %d, LZi %d, W %d, nbuf %d), %.1f MB\n",
+               h->device, h->prec == VDWGB_FP32_MIXED ? "FP32-mixed" : "FP64", S.tiles[0], S.tiles[1], S.tiles[2],
+               S.tiles[3], S.tiles[4], S.LZ, S.LZi, S.W, h->ls.nbuf[1], h->bytes / 1e6);
         for (int a = 0; a < 3; ++a) {
             printf("  axis %d n=%d radices", a, S.ax[a].n);
             for (int s = 0; s < S.ax[a].nst; ++s) printf(" %d", S.ax[a].rad[s]);
@@ -507,7 +599,8 @@ size_t vdwgb_footprint_bytes(int nx, int ny, int nz, int precision) {
     const int p = precision == VDWGB_FP32_MIXED ? VDWGB_FP32_MIXED : VDWGB_FP64;
     const size_t nzh = (size_t)nz / 2 + 1;
     const size_t N = (size_t)nx * ny * nz;
-    return (size_t)nx * ny * nzh * NQ * elem_bytes(p) + N * rec_bytes(p) + ((size_t)ny * nzh + 1) * sizeof(double);
+    const size_t nk = (size_t)nx * ny * nzh;
+    return nk * NQ * elem_bytes(p) + N * rec_bytes(p) + nk * sizeof(unsigned) + (nk / 64 + NK) * (sizeof(int4) + sizeof(double));
 }
 
 int vdwgb_launches_per_call(vdwgb_handle h) {
@@ -615,18 +708,20 @@ int vdwgb_batch_new(vdwgb_handle *handles, int count, vdwgb_batch *out) {
     b->prec = handles[0]->prec;
     cudaSetDevice(b->device);
     b->host.resize(count);
-    std::vector<int> pre(4 * (count + 1), 0);
+    std::vector<int> pre(NKIND * (count + 1), 0);
     LaunchSet &L = b->ls;
     std::memset(&L, 0, sizeof L);
     for (int i = 0; i < count; ++i) {
         b->host[i] = handles[i]->hsys;
-        for (int s = 0; s < 4; ++s) {
+        for (int s = 0; s < NKIND; ++s) {
             pre[s * (count + 1) + i + 1] = pre[s * (count + 1) + i] + handles[i]->hsys.tiles[s];
             if (handles[i]->ls.smem[s] > L.smem[s]) L.smem[s] = handles[i]->ls.smem[s];
             if (handles[i]->ls.twmax[s] > L.twmax[s]) L.twmax[s] = handles[i]->ls.twmax[s];
             if (handles[i]->ls.bufelems[s] > L.bufelems[s]) L.bufelems[s] = handles[i]->ls.bufelems[s];
             if (i == 0 || handles[i]->ls.nbuf[s] < L.nbuf[s]) L.nbuf[s] = handles[i]->ls.nbuf[s];
         }
+        if (handles[i]->ls.recelems > L.recelems) L.recelems = handles[i]->ls.recelems;
+        if (handles[i]->ls.abelems > L.abelems) L.abelems = handles[i]->ls.abelems;
     }
     cudaError_t e = cudaMalloc(&b->dsys, count * sizeof(SysDev));
     if (e == cudaSuccess) e = cudaMalloc(&b->dprefix, pre.size() * sizeof(int));
@@ -642,13 +737,15 @@ int vdwgb_batch_new(vdwgb_handle *handles, int count, vdwgb_batch *out) {
     L.sys = b->dsys;
     L.nsys = count;
     L.err = handles[0]->ls.err;
+    L.maxspan = handles[0]->ls.maxspan;
     {
         // x / y stages: shared memory from the largest row tile and twiddle table of the batch
         const size_t c = b->prec == VDWGB_FP32_MIXED ? 8 : 16;
         for (int s = 1; s <= 2; ++s)
             L.smem[s] = 16 + c * ((size_t)((L.twmax[s] + 7) & ~7) + (size_t)L.nbuf[s] * L.bufelems[s]);
+        L.smem[3] = zinv_smem(b->prec, L.twmax[3], L.bufelems[3], L.recelems, L.abelems);
         const size_t lim = g_dev[b->device].maxsmem - 1024;
-        if (L.smem[1] > lim || L.smem[2] > lim) {
+        if (L.smem[1] > lim || L.smem[2] > lim || L.smem[3] > lim) {
             cudaFree(b->dsys);
             cudaFree(b->dprefix);
             delete b;
@@ -656,7 +753,7 @@ int vdwgb_batch_new(vdwgb_handle *handles, int count, vdwgb_batch *out) {
         }
     }
     L.table = handles[0]->table;
-    for (int s = 0; s < 4; ++s) {
+    for (int s = 0; s < NKIND; ++s) {
         L.prefix[s] = b->dprefix + s * (count + 1);
         L.total[s] = pre[s * (count + 1) + count];
         int per_sm = (int)((228 * 1024) / (L.smem[s] + 1024));

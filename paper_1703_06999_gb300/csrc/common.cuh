@@ -75,9 +75,10 @@ struct __align__(16) Rec<double> {
 // Device descriptor of one system of a launch (one handle).
 struct SysDev {
     int nx, ny, nz, nzh;
-    int LZ;          // z-lines per tile of the z passes
+    int LZ;          // z-lines per tile of the z-forward pass
+    int LZi;         // z-lines per tile of the z-inverse pass
     int W;           // k_z columns per tile of the x / y passes
-    int tiles[4];    // tiles of: z-forward, y, x-contract, z-inverse
+    int tiles[5];    // tiles of: z-forward, y, x, z-inverse, contraction chunks
     AxisPlan ax[3];  // x, y, z
     const void *tw[3];   // twiddles exp(-2 pi i m / n), m < n, per axis (T complex)
     double g[6];     // reciprocal metric g00 g11 g22 g01 g02 g12 (|k|^2 = m^T g m)
@@ -90,7 +91,9 @@ struct SysDev {
     double *dedsigma;
     void *spec;      // [nx][ny][nzh][20] complex (T)
     void *rec;       // [nx*ny*nz] Rec<T>
-    double *epart;   // one partial per x-contract tile
+    const unsigned *kidx;   // half-spectrum k-points sorted by kernel-table interval
+    const int4 *chunks;     // contraction chunks: {first, count, first interval, intervals}
+    double *epart;   // one energy partial per contraction chunk
     double *energy;  // output (device)
 };
 

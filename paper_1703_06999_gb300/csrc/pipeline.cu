@@ -392,8 +392,6 @@ __global__ void __launch_bounds__(256) k_zfwd(const SysDev *__restrict__ sys, co
 // outer = ky and the rows run over x.  Each row is W * 20 contiguous complex
 // values (the [x][y][kz][a] layout), fetched by bulk copies into a double-
 // buffered shared-memory stage while the previous tile is transformed.
-// The x pass adds the kernel contraction and energy between the forward and
-// inverse transforms (procedure step 3).
 // ---------------------------------------------------------------------------
 template <typename T>
 struct KTab;
@@ -413,46 +411,14 @@ __device__ __forceinline__ dvec4 ld_tab(const dvec4 *p) {
     return make_dvec4(a.x, a.y, b.x, b.y);
 }
 
-__device__ __forceinline__ int fold(int i, int n) { return i <= (n - 1) / 2 ? i : i - n; }
-
-template <typename T>
-__device__ __forceinline__ void contract_point(cx<T> *v, T kabs, const typename KTab<T>::V *__restrict__ tab,
-                                               T inv_dk, T weight, double &eacc) {
-    cx<T> th[NQ];
-#pragma unroll
-    for (int a = 0; a < NQ; ++a) th[a] = v[a];
-    cx<T> F[NQ];
-#pragma unroll
-    for (int a = 0; a < NQ; ++a) F[a] = cx<T>{(T)0, (T)0};
-    const T xk = kabs * inv_dk;
-    int j = (int)xk;                         // kabs >= 0
-    if (j < NK - 1) {
-        const T tt = xk - (T)j;
-        const typename KTab<T>::V *row = tab + j;
-        int pidx = 0;
-#pragma unroll
-        for (int a = 0; a < NQ; ++a) {
-#pragma unroll
-            for (int b = a; b < NQ; ++b) {
-                const typename KTab<T>::V c = ld_tab(row + (size_t)pidx * (NK - 1));
-                const T phi = c.x + tt * (c.y + tt * (c.z + tt * c.w));
-                F[a].x += phi * th[b].x;
-                F[a].y += phi * th[b].y;
-                if (b != a) {
-                    F[b].x += phi * th[a].x;
-                    F[b].y += phi * th[a].y;
-                }
-                ++pidx;
-            }
-        }
-    }
-    T e = (T)0;
-#pragma unroll
-    for (int a = 0; a < NQ; ++a) e += th[a].x * F[a].x + th[a].y * F[a].y;
-    eacc += (double)(weight * e);
-#pragma unroll
-    for (int a = 0; a < NQ; ++a) v[a] = F[a];
+__device__ __forceinline__ float4 ld_row(const float4 *p) { return *p; }
+__device__ __forceinline__ dvec4 ld_row(const dvec4 *p) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0];
+    const double2 b = reinterpret_cast<const double2 *>(p)[1];
+    return make_dvec4(a.x, a.y, b.x, b.y);
 }
+
+__device__ __forceinline__ int fold(int i, int n) { return i <= (n - 1) / 2 ? i : i - n; }
 
 template <typename T>
 __device__ __forceinline__ double block_sum(double v, double *red) {
@@ -509,17 +475,19 @@ __device__ __forceinline__ void xy_issue(const SysDev *__restrict__ sys, const i
     fence_proxy_async();
     if (lane == 0) mbar_expect_tx(bar, rowbytes * (unsigned)g.nrows);
     __syncwarp();
-    for (int r = lane; r < g.nrows; r += 32) bulk_g2s(buf + (size_t)r * g.L, spec + g.g0 + r * g.rowstride, rowbytes, bar);
+    for (int r = lane; r < g.nrows; r += 32)
+        bulk_g2s(buf + (size_t)r * g.L, spec + g.g0 + r * g.rowstride, rowbytes, bar);
 }
 
-// MODE 0: forward y, 1: inverse y, 2: forward x + contraction + inverse x
+// MODE 0: forward y, 1: inverse y, 2: forward x, 3: inverse x
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_xy(const SysDev *__restrict__ sys, const int *__restrict__ prefix,
-                                               int nsys, int total, int twmax, int bufelems, int nbuf,
-                                               const typename KTab<T>::V *__restrict__ tab, int *__restrict__ err) {
-    constexpr bool XPASS = MODE == 2;
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ double red[32];
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_xy(const SysDev *__restrict__ sys,
+                                                                   const int *__restrict__ prefix, int nsys,
+                                                                   int total, int twmax, int bufelems, int nbuf,
+                                                                   int *__restrict__ err) {
+    constexpr bool XPASS = MODE >= 2;
+    constexpr bool INV = (MODE & 1) != 0;
+    extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem);
     cx<T> *tw = reinterpret_cast<cx<T> *>(smem + 16);
     cx<T> *in0 = tw + ((twmax + 7) & ~7);
@@ -537,7 +505,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_xy(const SysDev
     int t = blockIdx.x;
     if (t < total && threadIdx.x < 32) xy_issue<T, XPASS>(sys, prefix, nsys, t, bufs[0], &bar[0]);
     int cur_sys = -1;
-    const T inv_dk = (T)(RMAX / (2.0 * 3.14159265358979323846));
     for (int i = 0; t < total; ++i, t += gridDim.x) {
         const int cur = i & 1;
         const int tn = t + gridDim.x;
@@ -558,40 +525,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_xy(const SysDev
             if (nbuf == 3 && tn < total) mbar_wait(&bar[cur ^ 1], ph[cur ^ 1]);
             return;
         }
-        cx<T> *in = bufs[cur];
-        cx<T> *R;
-        if (MODE == 1) R = fft_lines<true>(in, work, ap, g.L, tw);
-        else R = fft_lines<false>(in, work, ap, g.L, tw);
-        if (MODE == 2) {
-            cx<T> *O = R == in ? work : in;
-            double eacc = 0.0;
-            const int nx = S.nx, ny = S.ny, nz = S.nz;
-            const int ky = g.outer;
-            const int my = fold(ky, ny);
-            const bool nyq_y = (ny % 2 == 0) && (ky == ny / 2);
-            const T g00 = (T)S.g[0], g11 = (T)S.g[1], g22 = (T)S.g[2];
-            const T g01 = (T)S.g[3], g02 = (T)S.g[4], g12 = (T)S.g[5];
-            for (int k = threadIdx.x; k < nx * g.wt; k += blockDim.x) {
-                const int x = k / g.wt, w = k - x * g.wt;
-                const int kz = g.kz0 + w;
-                const int mx = fold(x, nx);
-                const bool nyq_x = (nx % 2 == 0) && (x == nx / 2);
-                const bool nyq_z = (nz % 2 == 0) && (kz == nz / 2);
-                const int mz = nyq_z ? -kz : kz;
-                const T fx = (T)mx, fy = (T)my, fz = (T)mz;
-                const T cxv = nyq_x ? (T)0 : fx, cyv = nyq_y ? (T)0 : fy, czv = nyq_z ? (T)0 : fz;
-                T k2 = g00 * fx * fx + g11 * fy * fy + g22 * fz * fz +
-                       (T)2 * (g01 * cxv * cyv + g02 * cxv * czv + g12 * cyv * czv);
-                k2 = k2 > (T)0 ? k2 : (T)0;
-                const T kabs = sqrt(k2);
-                const T weight = (kz == 0 || nyq_z) ? (T)1 : (T)2;
-                contract_point<T>(R + (size_t)x * g.L + w * NQ, kabs, tab, inv_dk, weight, eacc);
-            }
-            const double es = block_sum<T>(eacc, red);
-            if (threadIdx.x == 0) S.epart[g.lt] = es;
-            __syncthreads();
-            R = fft_lines<true>(R, O, ap, g.L, tw);
-        }
+        cx<T> *R = fft_lines<INV>(bufs[cur], work, ap, g.L, tw);
         // store the rows back (16-byte vectors)
         cx<T> *spec = reinterpret_cast<cx<T> *>(S.spec);
         if (sizeof(cx<T>) == 8) {
@@ -620,30 +554,210 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_xy(const SysDev
 }
 
 // ---------------------------------------------------------------------------
-// z-inverse: complex-to-real along z, then the potential.
+// Kernel contraction and energy (procedure step 3): for every half-spectrum
+// k-point F_a(k) = sum_b phi_ab(|k|) theta_b(k), written over theta, and the
+// energy increment w_k sum_a Re(theta_a^* F_a).  The k-points of a system
+// are sorted by kernel-table interval; a chunk (<= 256 k-points, one per
+// thread) covers a few consecutive intervals, whose rows [interval][pair]
+// are one contiguous block staged in shared memory by one bulk copy.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_zinv(const SysDev *__restrict__ sys, const int *__restrict__ prefix,
-                                              int nsys, int total) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_contract(const SysDev *__restrict__ sys, const int *__restrict__ prefix,
+                                                     int nsys, int total, int maxspan,
+                                                     const typename KTab<T>::V *__restrict__ tab,
+                                                     int *__restrict__ err) {
+    using V = typename KTab<T>::V;
     extern __shared__ __align__(16) unsigned char smem[];
-    QShared<T> *qs = reinterpret_cast<QShared<T> *>(smem);
-    unsigned char *base = smem + align_up(sizeof(QShared<T>), 16);
-    load_qshared(qs);
+    __shared__ double red[32];
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem);
+    V *rows = reinterpret_cast<V *>(smem + 32);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    unsigned ph = 0u;
+    const T inv_dk = (T)(RMAX / (2.0 * 3.14159265358979323846));
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
         const int si = find_sys(prefix, nsys, t);
         const SysDev &S = sys[si];
         const int lt = t - prefix[si];
-        const int nz = S.nz, nzh = S.nzh, LZ = S.LZ;
-        const int nlines_tot = S.nx * S.ny;
-        const int l0 = lt * LZ;
-        const int nl = min(LZ, nlines_tot - l0);
+        const int4 c = S.chunks[lt];     // first, count, first interval, intervals
+        const int span = min(c.w, maxspan);
+        if (span > 0 && threadIdx.x == 0) {
+            const unsigned bytes = (unsigned)((size_t)span * NPAIR * sizeof(V));
+            fence_proxy_async();
+            mbar_expect_tx(&bar[0], bytes);
+            bulk_g2s(rows, tab + (size_t)c.z * NPAIR, bytes, &bar[0]);
+        }
+        // this thread's k-point: index, theta_a(k)
+        const bool have = threadIdx.x < c.y;
+        unsigned idx = 0;
+        cx<T> th[NQ];
+        cx<T> *v = nullptr;
+        if (have) {
+            idx = S.kidx[c.x + threadIdx.x];
+            v = reinterpret_cast<cx<T> *>(S.spec) + (size_t)idx * NQ;
+            if (sizeof(cx<T>) == 8) {   // 160-byte record, 16-byte aligned: ten 16-byte loads
+                const float4 *v4 = reinterpret_cast<const float4 *>(v);
+#pragma unroll
+                for (int a = 0; a < NQ / 2; ++a) {
+                    const float4 q = v4[a];
+                    th[2 * a] = cx<T>{(T)q.x, (T)q.y};
+                    th[2 * a + 1] = cx<T>{(T)q.z, (T)q.w};
+                }
+            } else {
+#pragma unroll
+                for (int a = 0; a < NQ; ++a) th[a] = v[a];
+            }
+        }
+        if (span > 0) {
+            const bool ok = mbar_wait(&bar[0], ph);
+            ph ^= 1u;
+            if (!__syncthreads_and(ok)) {
+                if (threadIdx.x == 0) atomicExch(err, 1);
+                return;
+            }
+        }
+        double eacc = 0.0;
+        if (have) {
+            const int nx = S.nx, ny = S.ny, nz = S.nz, nzh = S.nzh;
+            const int kz = (int)(idx % (unsigned)nzh);
+            const int rest = (int)(idx / (unsigned)nzh);
+            const int y = rest % ny, x = rest / ny;
+            const int mx = fold(x, nx), my = fold(y, ny);
+            const bool nyq_x = (nx % 2 == 0) && (x == nx / 2);
+            const bool nyq_y = (ny % 2 == 0) && (y == ny / 2);
+            const bool nyq_z = (nz % 2 == 0) && (kz == nz / 2);
+            const int mz = nyq_z ? -kz : kz;
+            const T fx = (T)mx, fy = (T)my, fz = (T)mz;
+            const T cxv = nyq_x ? (T)0 : fx, cyv = nyq_y ? (T)0 : fy, czv = nyq_z ? (T)0 : fz;
+            T k2 = (T)S.g[0] * fx * fx + (T)S.g[1] * fy * fy + (T)S.g[2] * fz * fz +
+                   (T)2 * ((T)S.g[3] * cxv * cyv + (T)S.g[4] * cxv * czv + (T)S.g[5] * cyv * czv);
+            k2 = k2 > (T)0 ? k2 : (T)0;
+            const T xk = sqrt(k2) * inv_dk;
+            const int j = (int)xk;
+            const T tt = xk - (T)j;
+            cx<T> F[NQ];
+#pragma unroll
+            for (int a = 0; a < NQ; ++a) F[a] = cx<T>{(T)0, (T)0};
+            if (j < NK - 1) {
+                // the interval's row: staged in shared memory, else (rounding at a
+                // chunk edge) read from the global table
+                const bool staged = span > 0 && j >= c.z && j < c.z + span;
+                const V *row = staged ? rows + (size_t)(j - c.z) * NPAIR : tab + (size_t)j * NPAIR;
+                int pidx = 0;
+#pragma unroll
+                for (int a = 0; a < NQ; ++a) {
+#pragma unroll
+                    for (int b = a; b < NQ; ++b) {
+                        const V cf = staged ? ld_row(row + pidx) : ld_tab(row + pidx);
+                        const T phi = cf.x + tt * (cf.y + tt * (cf.z + tt * cf.w));
+                        F[a].x += phi * th[b].x;
+                        F[a].y += phi * th[b].y;
+                        if (b != a) {
+                            F[b].x += phi * th[a].x;
+                            F[b].y += phi * th[a].y;
+                        }
+                        ++pidx;
+                    }
+                }
+            }
+            T e = (T)0;
+#pragma unroll
+            for (int a = 0; a < NQ; ++a) e += th[a].x * F[a].x + th[a].y * F[a].y;
+            const T weight = (kz == 0 || nyq_z) ? (T)1 : (T)2;
+            eacc = (double)(weight * e);
+            if (sizeof(cx<T>) == 8) {
+                float4 *v4 = reinterpret_cast<float4 *>(v);
+#pragma unroll
+                for (int a = 0; a < NQ / 2; ++a)
+                    v4[a] = make_float4((float)F[2 * a].x, (float)F[2 * a].y, (float)F[2 * a + 1].x, (float)F[2 * a + 1].y);
+            } else {
+#pragma unroll
+                for (int a = 0; a < NQ; ++a) v[a] = F[a];
+            }
+        }
+        const double es = block_sum<T>(eacc, red);
+        if (threadIdx.x == 0) S.epart[lt] = es;
+        fence_proxy_async();
+        __syncthreads();   // rows free for the next chunk's copy
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_inval(&bar[0]);
+}
+
+// ---------------------------------------------------------------------------
+// z-inverse: complex-to-real along z, then the potential.  A tile is LZi
+// consecutive (x, y) lines; their half spectra and point records are one
+// contiguous range each, fetched by two bulk copies into a double-buffered
+// stage while the previous tile is transformed.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void zinv_issue(const SysDev *__restrict__ sys, const int *__restrict__ prefix, int nsys,
+                                           int t, cx<T> *ibuf, Rec<T> *rbuf, unsigned long long *bar) {
+    const int si = find_sys(prefix, nsys, t);
+    const SysDev &S = sys[si];
+    const int lt = t - prefix[si];
+    const int l0 = lt * S.LZi;
+    const int nl = min(S.LZi, S.nx * S.ny - l0);
+    const unsigned sb = (unsigned)((size_t)nl * S.nzh * NQ * sizeof(cx<T>));
+    const unsigned rb = (unsigned)((size_t)nl * S.nz * sizeof(Rec<T>));
+    fence_proxy_async();
+    mbar_expect_tx(bar, sb + rb);
+    bulk_g2s(ibuf, reinterpret_cast<const cx<T> *>(S.spec) + (size_t)l0 * S.nzh * NQ, sb, bar);
+    bulk_g2s(rbuf, reinterpret_cast<const Rec<T> *>(S.rec) + (size_t)l0 * S.nz, rb, bar);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_zinv(const SysDev *__restrict__ sys, const int *__restrict__ prefix,
+                                              int nsys, int total, int nzmax, int inelems, int recelems,
+                                              int abelems, int *__restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem);
+    QShared<T> *qs = reinterpret_cast<QShared<T> *>(smem + 16);
+    cx<T> *tw = reinterpret_cast<cx<T> *>(smem + 16 + align_up(sizeof(QShared<T>), 16));
+    cx<T> *in0 = tw + ((nzmax + 7) & ~7);
+    cx<T> *ins[2] = {in0, in0 + inelems};
+    Rec<T> *rec0 = reinterpret_cast<Rec<T> *>(in0 + 2 * (size_t)inelems);
+    Rec<T> *recs[2] = {rec0, rec0 + recelems};
+    cx<T> *bufA = reinterpret_cast<cx<T> *>(rec0 + 2 * (size_t)recelems);
+    cx<T> *bufB = bufA + abelems;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    load_qshared(qs);
+    __syncthreads();
+    unsigned ph[2] = {0u, 0u};
+    int t = blockIdx.x;
+    if (t < total && threadIdx.x == 0) zinv_issue<T>(sys, prefix, nsys, t, ins[0], recs[0], &bar[0]);
+    int cur_sys = -1;
+    for (int it = 0; t < total; ++it, t += gridDim.x) {
+        const int cur = it & 1;
+        const int tn = t + gridDim.x;
+        if (tn < total && threadIdx.x == 0) zinv_issue<T>(sys, prefix, nsys, tn, ins[cur ^ 1], recs[cur ^ 1], &bar[cur ^ 1]);
+        const int si = find_sys(prefix, nsys, t);
+        const SysDev &S = sys[si];
+        const int lt = t - prefix[si];
+        const int nz = S.nz, nzh = S.nzh;
+        const int l0 = lt * S.LZi;
+        const int nl = min(S.LZi, S.nx * S.ny - l0);
         const int L = 10 * nl;
-        cx<T> *tw = reinterpret_cast<cx<T> *>(base);
-        cx<T> *bufA = tw + nz;
-        cx<T> *bufB = bufA + (size_t)nz * L;
-        const cx<T> *twg = reinterpret_cast<const cx<T> *>(S.tw[2]);
-        for (int i = threadIdx.x; i < nz; i += blockDim.x) tw[i] = twg[i];
-        const cx<T> *spec = reinterpret_cast<const cx<T> *>(S.spec) + (size_t)l0 * nzh * NQ;
+        if (si != cur_sys) {
+            const cx<T> *twg = reinterpret_cast<const cx<T> *>(S.tw[2]);
+            for (int i = threadIdx.x; i < nz; i += blockDim.x) tw[i] = twg[i];
+            cur_sys = si;
+        }
+        const bool ok = mbar_wait(&bar[cur], ph[cur]);
+        ph[cur] ^= 1u;
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) atomicExch(err, 1);
+            if (tn < total) mbar_wait(&bar[cur ^ 1], ph[cur ^ 1]);
+            return;
+        }
+        const cx<T> *spec = ins[cur];
         const bool even = (nz % 2) == 0;
         // Z_c[kz] = X_{2c}[kz] + i X_{2c+1}[kz]; Z_c[nz-kz] = conj(X_{2c}) + i conj(X_{2c+1})
         for (int i = threadIdx.x; i < nl * nzh * 10; i += blockDim.x) {
@@ -664,12 +778,12 @@ __global__ void __launch_bounds__(256) k_zinv(const SysDev *__restrict__ sys, co
         }
         __syncthreads();
         cx<T> *R = fft_lines<true>(bufA, bufB, S.ax[2], L, tw);
-        const Rec<T> *rec = reinterpret_cast<const Rec<T> *>(S.rec);
+        const Rec<T> *rec = recs[cur];
         const size_t p0 = (size_t)l0 * nz;
         const T invN = (T)S.invN;
         for (int i = threadIdx.x; i < nl * nz; i += blockDim.x) {
             const int li = i / nz, z = i - li * nz;
-            const Rec<T> r = rec[p0 + i];
+            const Rec<T> r = rec[i];
             double dn = 0.0, ds = 0.0;
             if (r.j >= 0) {
                 T p[NQ], dp[NQ];
@@ -691,7 +805,13 @@ __global__ void __launch_bounds__(256) k_zinv(const SysDev *__restrict__ sys, co
             S.dedn[p0 + i] = dn;
             S.dedsigma[p0 + i] = ds;
         }
+        fence_proxy_async();
         __syncthreads();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_inval(&bar[0]);
+        mbar_inval(&bar[1]);
     }
 }
 
@@ -703,7 +823,7 @@ __global__ void k_efinish(const SysDev *__restrict__ sys, int nsys) {
     __shared__ double ssum[256], scmp[256];
     for (int si = blockIdx.x; si < nsys; si += gridDim.x) {
         const SysDev &S = sys[si];
-        const int n = S.tiles[2];
+        const int n = S.tiles[4];
         double s = 0.0, c = 0.0;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             const double v = S.epart[i];
@@ -762,11 +882,28 @@ size_t smem_xy(int n, int W, int nbuf) {
     return 16 + sizeof(cx<T>) * ((size_t)((n + 7) & ~7) + (size_t)nbuf * n * NQ * W);
 }
 
+template <typename T>
+size_t smem_zinv(int nz, int LZ) {
+    const size_t nzh = nz / 2 + 1;
+    return 16 + ((sizeof(QShared<T>) + 15) / 16) * 16 +
+           sizeof(cx<T>) * ((size_t)((nz + 7) & ~7) + 2 * (size_t)LZ * nzh * NQ + 2ull * nz * 10 * LZ) +
+           2 * (size_t)LZ * nz * sizeof(Rec<T>);
+}
+
+size_t zinv_smem(int prec, int nzmax, int inelems, int recelems, int abelems) {
+    const bool f = prec == 1;
+    const size_t c = f ? sizeof(cx<float>) : sizeof(cx<double>);
+    const size_t rs = f ? sizeof(Rec<float>) : sizeof(Rec<double>);
+    const size_t qsz = f ? ((sizeof(QShared<float>) + 15) / 16) * 16 : ((sizeof(QShared<double>) + 15) / 16) * 16;
+    return 16 + qsz + c * ((size_t)((nzmax + 7) & ~7) + 2 * (size_t)inelems + 2 * (size_t)abelems) +
+           2 * (size_t)recelems * rs;
+}
+
 size_t stage_smem(int stage, int prec, int n, int tile, int nbuf) {
     const bool f = prec == 1;
     switch (stage) {
-        case 0:
-        case 3: return f ? smem_z<float>(n, tile) : smem_z<double>(n, tile);
+        case 0: return f ? smem_z<float>(n, tile) : smem_z<double>(n, tile);
+        case 3: return f ? smem_zinv<float>(n, tile) : smem_zinv<double>(n, tile);
         default: return f ? smem_xy<float>(n, tile, nbuf) : smem_xy<double>(n, tile, nbuf);
     }
 }
@@ -781,9 +918,11 @@ template <typename T>
 static cudaError_t init_kernels_t(size_t maxsmem) {
     cudaError_t e;
     if ((e = set_smem((const void *)k_zfwd<T>, maxsmem)) != cudaSuccess) return e;
-    if ((e = set_smem((const void *)k_xy<T, 0>, maxsmem - 32 * sizeof(double))) != cudaSuccess) return e;
-    if ((e = set_smem((const void *)k_xy<T, 1>, maxsmem - 32 * sizeof(double))) != cudaSuccess) return e;
-    if ((e = set_smem((const void *)k_xy<T, 2>, maxsmem - 32 * sizeof(double))) != cudaSuccess) return e;
+    if ((e = set_smem((const void *)k_xy<T, 0>, maxsmem)) != cudaSuccess) return e;
+    if ((e = set_smem((const void *)k_xy<T, 1>, maxsmem)) != cudaSuccess) return e;
+    if ((e = set_smem((const void *)k_xy<T, 2>, maxsmem)) != cudaSuccess) return e;
+    if ((e = set_smem((const void *)k_xy<T, 3>, maxsmem)) != cudaSuccess) return e;
+    if ((e = set_smem((const void *)k_contract<T>, maxsmem - 32 * sizeof(double))) != cudaSuccess) return e;
     if ((e = set_smem((const void *)k_zinv<T>, maxsmem)) != cudaSuccess) return e;
     return cudaSuccess;
 }
@@ -797,22 +936,30 @@ cudaError_t init_kernels(size_t maxsmem) {
 template <typename T>
 static cudaError_t launch_all_t(const LaunchSet &ls, cudaStream_t st, cudaEvent_t *ev) {
     const typename KTab<T>::V *tab = reinterpret_cast<const typename KTab<T>::V *>(ls.table);
-    if (ev) cudaEventRecord(ev[0], st);
+    int k = 0;
+    if (ev) cudaEventRecord(ev[k++], st);
     k_zfwd<T><<<ls.grid[0], 256, ls.smem[0], st>>>(ls.sys, ls.prefix[0], ls.nsys, ls.total[0]);
-    if (ev) cudaEventRecord(ev[1], st);
+    if (ev) cudaEventRecord(ev[k++], st);
     k_xy<T, 0><<<ls.grid[1], 256, ls.smem[1], st>>>(ls.sys, ls.prefix[1], ls.nsys, ls.total[1], ls.twmax[1],
-                                                     ls.bufelems[1], ls.nbuf[1], tab, ls.err);
-    if (ev) cudaEventRecord(ev[2], st);
+                                                     ls.bufelems[1], ls.nbuf[1], ls.err);
+    if (ev) cudaEventRecord(ev[k++], st);
     k_xy<T, 2><<<ls.grid[2], 256, ls.smem[2], st>>>(ls.sys, ls.prefix[2], ls.nsys, ls.total[2], ls.twmax[2],
-                                                     ls.bufelems[2], ls.nbuf[2], tab, ls.err);
-    if (ev) cudaEventRecord(ev[3], st);
+                                                     ls.bufelems[2], ls.nbuf[2], ls.err);
+    if (ev) cudaEventRecord(ev[k++], st);
+    k_contract<T><<<ls.grid[4], 256, ls.smem[4], st>>>(ls.sys, ls.prefix[4], ls.nsys, ls.total[4], ls.maxspan,
+                                                        tab, ls.err);
+    if (ev) cudaEventRecord(ev[k++], st);
+    k_xy<T, 3><<<ls.grid[2], 256, ls.smem[2], st>>>(ls.sys, ls.prefix[2], ls.nsys, ls.total[2], ls.twmax[2],
+                                                     ls.bufelems[2], ls.nbuf[2], ls.err);
+    if (ev) cudaEventRecord(ev[k++], st);
     k_xy<T, 1><<<ls.grid[1], 256, ls.smem[1], st>>>(ls.sys, ls.prefix[1], ls.nsys, ls.total[1], ls.twmax[1],
-                                                     ls.bufelems[1], ls.nbuf[1], tab, ls.err);
-    if (ev) cudaEventRecord(ev[4], st);
-    k_zinv<T><<<ls.grid[3], 256, ls.smem[3], st>>>(ls.sys, ls.prefix[3], ls.nsys, ls.total[3]);
-    if (ev) cudaEventRecord(ev[5], st);
+                                                     ls.bufelems[1], ls.nbuf[1], ls.err);
+    if (ev) cudaEventRecord(ev[k++], st);
+    k_zinv<T><<<ls.grid[3], 256, ls.smem[3], st>>>(ls.sys, ls.prefix[3], ls.nsys, ls.total[3], ls.twmax[3],
+                                                    ls.bufelems[3], ls.recelems, ls.abelems, ls.err);
+    if (ev) cudaEventRecord(ev[k++], st);
     k_efinish<<<ls.nsys < 1024 ? ls.nsys : 1024, 256, 0, st>>>(ls.sys, ls.nsys);
-    if (ev) cudaEventRecord(ev[6], st);
+    if (ev) cudaEventRecord(ev[k++], st);
     return cudaGetLastError();
 }
 
@@ -820,8 +967,12 @@ cudaError_t launch_all(const LaunchSet &ls, int prec, cudaStream_t st, cudaEvent
     return prec == 1 ? launch_all_t<float>(ls, st, ev) : launch_all_t<double>(ls, st, ev);
 }
 
+size_t contract_smem(int prec, int maxspan) {
+    return 32 + (size_t)maxspan * NPAIR * (prec == 1 ? sizeof(float4) : sizeof(dvec4));
+}
+
 const char *stage_name(int i) {
-    static const char *names[NSTAGE] = {"zfwd", "yfwd", "xcontract", "yinv", "zinv", "efinish"};
+    static const char *names[NSTAGE] = {"zfwd", "yfwd", "xfwd", "contract", "xinv", "yinv", "zinv", "efinish"};
     return (i >= 0 && i < NSTAGE) ? names[i] : "";
 }
 

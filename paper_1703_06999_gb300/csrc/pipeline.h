@@ -7,24 +7,31 @@ namespace vdwgb {
 
 // Everything one launch of the five stages needs: device descriptors of all
 // systems, per-stage tile prefix sums (device), grid and shared memory.
-// Stage index: 0 z-forward, 1 y (both directions), 2 x-contract, 3 z-inverse.
+// Tile kinds: 0 z-forward, 1 y (both directions), 2 x (both directions),
+// 3 z-inverse, 4 contraction chunks.
 struct LaunchSet {
     const SysDev *sys;       // device array [nsys]
-    const int *prefix[4];    // device arrays [nsys + 1]
+    const int *prefix[5];    // device arrays [nsys + 1]
     int nsys;
-    int total[4];            // tiles per stage over all systems
-    int grid[4];
-    size_t smem[4];
+    int total[5];            // tiles per kind over all systems
+    int grid[5];
+    size_t smem[5];
+    int maxspan;             // contraction: kernel-table intervals staged per chunk
     const void *table;       // kernel polynomial table (float4 or dvec4), [210][NK-1]
-    int twmax[4];            // longest axis of the stage over all systems (twiddle slots)
-    int bufelems[4];         // complex elements of one row-tile buffer (x / y stages)
-    int nbuf[4];             // row-tile buffers of the x / y stages: 3 (prefetching) or 2
+    int twmax[5];            // longest axis of the stage over all systems (twiddle slots)
+    int bufelems[5];         // complex elements of one row-tile buffer (x / y stages)
+    int nbuf[5];             // row-tile buffers of the x / y stages: 3 (prefetching) or 2
+    int recelems;            // z-inverse: point records per staged tile
+    int abelems;             // z-inverse: complex elements of one transform buffer
     int *err;                // device flag set by a stage whose bounded wait ran out
 };
 
 size_t stage_smem(int stage, int prec, int n, int tile, int nbuf = 3);
+size_t zinv_smem(int prec, int nzmax, int inelems, int recelems, int abelems);
+size_t contract_smem(int prec, int maxspan);
 cudaError_t init_kernels(size_t maxsmem);
-constexpr int NSTAGE = 6;   // kernel launches per evaluation
+constexpr int NSTAGE = 8;   // kernel launches per evaluation
+constexpr int NKIND = 5;    // tile kinds
 // Enqueue all stages; if ev != nullptr, record ev[0..NSTAGE] around them.
 cudaError_t launch_all(const LaunchSet &ls, int prec, cudaStream_t st, cudaEvent_t *ev = nullptr);
 const char *stage_name(int i);

@@ -14,7 +14,8 @@
 //    k_j = j * 2 pi / 100 bohr, j = 0..1023 (Sec. 2: the M x M radial
 //    functions on a discrete k-grid).
 //  Interpolation in k (Sec. 3, procedure step 3a): per interval a cubic in
-//    t = k/dk - j, from a natural cubic spline (default) or linear.
+//    t = k/dk - j, from a natural cubic spline (default) or linear; stored
+//    [interval][pair] so that the rows of a |k| range are one contiguous block.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -251,7 +252,7 @@ __global__ void k_kspline(const double *__restrict__ phik, double *__restrict__ 
         const double c1 = (y[j + 1] - y[j]) - h26 * (2.0 * s0 + s1);
         const double c2 = 3.0 * h26 * s0;
         const double c3 = h26 * (s1 - s0);
-        const size_t o = (size_t)pair * (NK - 1) + j;
+        const size_t o = (size_t)j * NPAIR + pair;     // [interval][pair]
         cub64[o] = make_dvec4(c0, c1, c2, c3);
         cub32[o] = make_float4((float)c0, (float)c1, (float)c2, (float)c3);
         lin64[o] = make_dvec4(y[j], y[j + 1] - y[j], 0.0, 0.0);

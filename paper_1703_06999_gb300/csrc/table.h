@@ -8,7 +8,7 @@ namespace vdwgb {
 struct TableRefs {
     const double *phir;     // [NPAIR][NR + 1]
     const double *phik;     // [NPAIR][NK]
-    const dvec4 *cub64;   // [NPAIR][NK - 1] interval polynomials, cubic spline
+    const dvec4 *cub64;   // [NK - 1][NPAIR] interval polynomials, cubic spline
     const dvec4 *lin64;   // linear interpolation
     const float4 *cub32;
     const float4 *lin32;
