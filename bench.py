@@ -40,9 +40,25 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-stream measurement")
     ap.add_argument("--only-timed", action="store_true",
                     help="stop after the timed batched steps (for profiler launch lists)")
     return ap.parse_args()
+
+
+def rank_seeds(rank, nb):
+    """Seeds of the systems rank `rank` evaluates: independent systems per
+    rank (weak scaling, no data exchange between ranks)."""
+    return [rank * 1000 + i // 2 for i in range(nb)]
+
+
+def reduce_max(x, device):
+    """Max of a float over the ranks of the default process group."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def dist_env():
@@ -162,6 +178,72 @@ def run_reference(args, rank):
     print(json.dumps(out), flush=True)
 
 
+def serve_bench(B, inputs, torch, dev, local, seconds=3.0, rate=200.0, pool_entries=16):
+    """Served form: Poisson arrivals (mean `rate` per second) of evaluations
+    with grids from 48^3 to 160x192x224 (10-400 exponentials), FP32-mixed,
+    admitted by footprint into an 8 GiB pool, continuous batching; against
+    the same evaluations one at a time in FP64.  Inputs come from a pool of
+    `pool_entries` distinct requests reused across arrivals (host arrays,
+    page-locked)."""
+    reqs = inputs.serving_requests(seed=0, count=pool_entries, rate=rate)
+    pool = []
+    for r in reqs:
+        sy = inputs.realise(r, device=dev)
+        hn = sy.n.cpu().pin_memory().numpy()
+        hs = sy.sigma.cpu().pin_memory().numpy()
+        dn = torch.empty(sy.shape, dtype=torch.float64).pin_memory().numpy()
+        ds = torch.empty(sy.shape, dtype=torch.float64).pin_memory().numpy()
+        pool.append((sy, hn, hs, dn, ds))
+    # FP64 one at a time (plain form), device-resident inputs
+    lat64, pts64 = [], 0
+    for sy, *_ in pool:
+        f = B.Functional(sy.shape, sy.cell, sy.functional, B.FP64, device=local)
+        o1, o2 = torch.empty_like(sy.n), torch.empty_like(sy.n)
+        en = torch.zeros(1, dtype=torch.float64, device=dev)
+        f.calculate_device(sy.n, sy.sigma, o1, o2, en)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        f.calculate_device(sy.n, sy.sigma, o1, o2, en)
+        b.record()
+        b.synchronize()
+        lat64.append(a.elapsed_time(b) / 1000.0)
+        pts64 += sy.npts
+        f.close()
+    fp64_rate = pts64 / sum(lat64)
+    sv = B.vdwgb_server_new(local, B.FP32_MIXED, pool_bytes=8 << 30, max_batch=16, max_inflight=3)
+    try:
+        # warm-up: every pool entry once
+        for sy, hn, hs, dn, ds in pool:
+            B.vdwgb_server_wait(sv, B.vdwgb_server_submit(sv, sy.functional, sy.shape, sy.cell, hn, hs, dn, ds), 120)
+        B.vdwgb_server_free(sv)
+        sv = B.vdwgb_server_new(local, B.FP32_MIXED, pool_bytes=8 << 30, max_batch=16, max_inflight=3)
+        g = np.random.default_rng(1)
+        arrivals = np.cumsum(g.exponential(1.0 / rate, int(rate * seconds * 1.5)))
+        arrivals = arrivals[arrivals < seconds]
+        ids = []
+        t0 = time.perf_counter()
+        for k, ta in enumerate(arrivals):
+            while time.perf_counter() - t0 < ta:
+                time.sleep(0.0002)
+            sy, hn, hs, dn, ds = pool[k % len(pool)]
+            ids.append(B.vdwgb_server_submit(sv, sy.functional, sy.shape, sy.cell, hn, hs, dn, ds))
+        for rid in ids:
+            B.vdwgb_server_wait(sv, rid, 300.0)
+        wall = time.perf_counter() - t0
+        st = B.vdwgb_server_stats(sv)
+    finally:
+        B.vdwgb_server_free(sv)
+    return {"requests": len(ids), "rate_req_s": rate, "seconds": seconds, "value": st["pts_per_s"],
+            "unit": "grid pts/s", "p50_ms": 1000 * st["p50_s"], "p99_ms": 1000 * st["p99_s"],
+            "mean_batch": st["mean_batch"], "batches": st["batches"], "failed": st["failed"],
+            "wall_s": wall, "pool_peak_GB": st["pool_used_peak"] / 1e9,
+            "fp64_one_at_a_time": {"value": fp64_rate, "unit": "grid pts/s",
+                                   "p50_ms": 1000 * float(np.median(lat64)),
+                                   "p99_ms": 1000 * float(np.percentile(lat64, 99))},
+            "grids": sorted({tuple(p[0].shape) for p in pool})}
+
+
 def cpu_baseline():
     """Oracle (as it stands) on one 96^3 system of the workload, on the host."""
     from paper_1703_06999_gb300 import inputs
@@ -192,9 +274,11 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     B.lib()   # fails loudly if the CUDA library is missing
+    B.vdwgb_set_autotune(True)   # tile shapes measured once per grid at init (outside the timed region)
 
     nb = args.batch
-    systems = [inputs.dimer(rank * 1000 + i // 2, shape=SHAPE, cell_lengths=CELL, functional=1 + i % 2,
+    seeds = rank_seeds(rank, nb)
+    systems = [inputs.dimer(seeds[i], shape=SHAPE, cell_lengths=CELL, functional=1 + i % 2,
                             device=dev) for i in range(nb)]
     pts = sum(s.npts for s in systems)
 
@@ -209,6 +293,7 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 2x L2
 
     f32 = make(B.FP32_MIXED)
+    plan_info = B.vdwgb_plan_info(f32[0].h)
     bt = B.vdwgb_batch_new([f.h for f in f32])
     ns = [s.n for s in systems]
     ss = [s.sigma for s in systems]
@@ -237,9 +322,7 @@ def main():
     B.vdwgb_batch_set_timing(bt, False)
     tot_ms = float(step_ms.sum())
     if world > 1:
-        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
+        tot_ms = reduce_max(tot_ms, dev)
     value = pts * world * args.steps / (tot_ms / 1000.0)
     if args.only_timed:
         if rank == 0:
@@ -302,9 +385,7 @@ def main():
     e2e_s = time.perf_counter() - t0
     e2e_val = pts * ke / e2e_s
     if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_val = pts * world * ke / float(t.item())
+        e2e_val = pts * world * ke / reduce_max(e2e_s, dev)
     h2d = sum(2 * s.npts * 8 for s in systems)
     d2h = sum(2 * s.npts * 8 for s in systems) + 8 * nb
 
@@ -329,6 +410,7 @@ def main():
     for f in f32:
         f.close()
     B.vdwgb_batch_free(bt)
+    serving = None if args.no_serve else serve_bench(B, inputs, torch, dev, local)
 
     if rank == 0:
         out = {
@@ -338,6 +420,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": list(SHAPE), "cell_bohr": list(CELL), "systems": nb,
                        "functionals": "DF1+DF2", "precision": "fp32_mixed", "parallelism": "replicas",
+                       "plan": plan_info,
                        "l2": "flushed between timed steps (256 MB write); working set %.0f MB"
                              % (nb * (SHAPE[0] * SHAPE[1] * (SHAPE[2] // 2 + 1) * 160 + 48 * np.prod(SHAPE)) / 1e6)},
             "fp64_plain": {"value": fp64_value, "unit": "grid pts/s", "steps": k64,
@@ -356,6 +439,8 @@ def main():
             "clocks": clocks,
             "table_build_s": B.vdwgb_table_build_seconds(local),
         }
+        if serving is not None:
+            out["serving"] = serving
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()
         print(json.dumps(out), flush=True)

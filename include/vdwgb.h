@@ -159,6 +159,22 @@ int vdwgb_phi(int device, int npts, const double *d1, const double *d2, double *
 int vdwgb_q0(int device, int precision, int functional, int npts, const double *n, const double *sigma,
              double *q0, double *dq0dn, double *dq0dsigma);
 
+/* Autotuning of tile shapes: when enabled (here or by the environment
+ * variable VDWGB_AUTOTUNE=1), vdwgb_init_cuda times every stage kernel for
+ * each candidate tile shape that fits shared memory (z-forward lines, y / x
+ * kz-columns with 2 or 3 row buffers, z-inverse lines) on the handle's
+ * own buffers and keeps the
+ * fastest; the choice is cached per (grid, precision) for the process and
+ * reused by later handles, batches and the server.  Default off. */
+int vdwgb_set_autotune(int enable);
+
+/* Plan of an initialised handle: info[0..7] = z-forward lines per tile,
+ * z-inverse lines per tile, y-pass kz-columns, x-pass kz-columns, row
+ * buffers of the y and x passes as 10 * y + x (3 prefetching, 2 not),
+ * contraction chunks,
+ * kernel launches per evaluation, 1 if the tile shapes were autotuned. */
+int vdwgb_plan_info(vdwgb_handle h, int *info);
+
 /* Seconds spent building the table on `device` (0 if not built). */
 double vdwgb_table_build_seconds(int device);
 
@@ -197,6 +213,54 @@ int vdwgb_num_stages(void);
 const char *vdwgb_stage_name(int i);
 
 int vdwgb_batch_free(vdwgb_batch *b);
+
+/* ---- served form: requests of different grids arriving over time -------- */
+
+typedef struct vdwgb_server_s *vdwgb_server;
+
+typedef struct {
+    long long submitted, completed, failed, batches;
+    double mean_batch;       /* requests per batched launch */
+    double pts_per_s;        /* grid points of completed requests / (last completion - first submit) */
+    double p50_s, p99_s;     /* latency quantiles (completion - submission) of completed requests */
+    size_t pool_bytes, pool_used_peak;
+} vdwgb_server_stats_t;
+
+/* Create a server on `device` for `precision`.  pool_bytes: device-memory
+ * budget for admitted requests (work buffer, records, staging of each); a
+ * request is admitted, in arrival order, when its footprint fits what is
+ * left.  max_batch (1..256): most requests per batched launch (one launch per
+ * stage over all of them); max_inflight (1..8): batches on the GPU at once,
+ * each on its own stream, so later requests are admitted and planned while
+ * earlier ones run.  Worker threads plan requests (FFT plans, k-point order),
+ * upload inputs with stream-ordered allocations, launch batches and collect
+ * results.  The kernel table is built and stays resident. */
+int vdwgb_server_new(int device, int precision, size_t pool_bytes, int max_batch, int max_inflight,
+                     vdwgb_server *out);
+
+/* Queue one evaluation (grid nx*ny*nz, cell9 = 9 cell doubles as in
+ * vdwgb_set_unit_cell).  rho, sigma (read) and dedrho, dedsigma (written)
+ * are HOST arrays owned by the caller, valid until the request is reported
+ * done.  *id receives the request id.  Never waits for the GPU.  EAGAIN if
+ * the request alone exceeds the pool; EINVAL on bad arguments (a grid the
+ * planner rejects fails the request, reported by poll/wait). */
+int vdwgb_server_submit(vdwgb_server s, int functional, int nx, int ny, int nz, const double *cell9,
+                        const double *rho, const double *sigma, double *dedrho, double *dedsigma,
+                        long long *id);
+
+/* 1 and energy / latency written if request id is done (the id is then
+ * forgotten), 0 if still pending, a negative code if it failed (also
+ * forgotten) or is unknown (ENOTFOUND). */
+int vdwgb_server_poll(vdwgb_server s, long long id, double *energy, double *latency_s);
+
+/* As poll, but waits up to timeout_s seconds; ETIMEDOUT if still pending. */
+int vdwgb_server_wait(vdwgb_server s, long long id, double timeout_s, double *energy, double *latency_s);
+
+int vdwgb_server_stats(vdwgb_server s, vdwgb_server_stats_t *out);
+
+/* Wait (at most 60 s) for batches on the GPU, stop the workers, free
+ * everything, set *s = NULL.  Requests not yet reported are dropped. */
+int vdwgb_server_free(vdwgb_server *s);
 
 #ifdef __cplusplus
 }

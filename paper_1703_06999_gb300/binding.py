@@ -45,6 +45,8 @@ _SIGS = {
     "vdwgb_phi": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "vdwgb_table_build_seconds": (ctypes.c_double, [ctypes.c_int]),
     "vdwgb_q0": (ctypes.c_int, [ctypes.c_int] * 4 + [ctypes.c_void_p] * 5),
+    "vdwgb_set_autotune": (ctypes.c_int, [ctypes.c_int]),
+    "vdwgb_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "vdwgb_batch_new": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "vdwgb_batch_calculate_device": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 6),
     "vdwgb_batch_free": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p)]),
@@ -54,6 +56,32 @@ _SIGS = {
     "vdwgb_num_stages": (ctypes.c_int, []),
     "vdwgb_stage_name": (ctypes.c_char_p, [ctypes.c_int]),
 }
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("failed", ctypes.c_longlong), ("batches", ctypes.c_longlong),
+                ("mean_batch", ctypes.c_double), ("pts_per_s", ctypes.c_double),
+                ("p50_s", ctypes.c_double), ("p99_s", ctypes.c_double),
+                ("pool_bytes", ctypes.c_size_t), ("pool_used_peak", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_SIGS.update({
+    "vdwgb_server_new": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "vdwgb_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
+    "vdwgb_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double)]),
+    "vdwgb_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_double,
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "vdwgb_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerStats)]),
+    "vdwgb_server_free": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p)]),
+})
 
 
 class VdwgbError(RuntimeError):
@@ -192,6 +220,17 @@ def vdwgb_q0(n, sigma, functional=DF1, precision=FP64, device=0):
     return q0, dn, ds
 
 
+def vdwgb_set_autotune(enable):
+    _ck(lib().vdwgb_set_autotune(int(bool(enable))), "vdwgb_set_autotune")
+
+
+def vdwgb_plan_info(h):
+    info = np.zeros(8, dtype=np.int32)
+    _ck(lib().vdwgb_plan_info(h, info.ctypes.data), "vdwgb_plan_info")
+    keys = ["LZ", "LZi", "Wy", "Wx", "nbuf_yx", "chunks", "launches", "autotuned"]
+    return {k: int(v) for k, v in zip(keys, info)}
+
+
 def vdwgb_table_build_seconds(device=0):
     return float(lib().vdwgb_table_build_seconds(int(device)))
 
@@ -245,6 +284,52 @@ def vdwgb_batch_stage_ms(b):
 
 def vdwgb_batch_free(b):
     _ck(lib().vdwgb_batch_free(ctypes.byref(b)), "vdwgb_batch_free")
+
+
+def vdwgb_server_new(device=0, precision=FP32_MIXED, pool_bytes=8 << 30, max_batch=16, max_inflight=2):
+    sv = ctypes.c_void_p()
+    _ck(lib().vdwgb_server_new(int(device), int(precision), int(pool_bytes), int(max_batch), int(max_inflight),
+                               ctypes.byref(sv)), "vdwgb_server_new")
+    return sv
+
+
+def vdwgb_server_submit(sv, functional, shape, cell, rho, sigma, dedrho, dedsigma):
+    """Host arrays (numpy float64, C order) owned by the caller until done; returns the id."""
+    cell = np.ascontiguousarray(np.asarray(cell, dtype=np.float64).reshape(9))
+    rid = ctypes.c_longlong()
+    _ck(lib().vdwgb_server_submit(sv, int(functional), int(shape[0]), int(shape[1]), int(shape[2]),
+                                  cell.ctypes.data, _ptr(rho), _ptr(sigma), _ptr(dedrho), _ptr(dedsigma),
+                                  ctypes.byref(rid)), "vdwgb_server_submit")
+    return int(rid.value)
+
+
+def vdwgb_server_poll(sv, rid):
+    """None if pending, else (energy, latency_s)."""
+    e, t = ctypes.c_double(), ctypes.c_double()
+    rc = lib().vdwgb_server_poll(sv, int(rid), ctypes.byref(e), ctypes.byref(t))
+    if rc == 0:
+        return None
+    if rc < 0:
+        raise VdwgbError(rc, "vdwgb_server_poll")
+    return e.value, t.value
+
+
+def vdwgb_server_wait(sv, rid, timeout_s=60.0):
+    e, t = ctypes.c_double(), ctypes.c_double()
+    rc = lib().vdwgb_server_wait(sv, int(rid), float(timeout_s), ctypes.byref(e), ctypes.byref(t))
+    if rc < 0:
+        raise VdwgbError(rc, "vdwgb_server_wait")
+    return e.value, t.value
+
+
+def vdwgb_server_stats(sv):
+    st = ServerStats()
+    _ck(lib().vdwgb_server_stats(sv, ctypes.byref(st)), "vdwgb_server_stats")
+    return st.as_dict()
+
+
+def vdwgb_server_free(sv):
+    _ck(lib().vdwgb_server_free(ctypes.byref(sv)), "vdwgb_server_free")
 
 
 # ---- convenience ------------------------------------------------------------

@@ -8,17 +8,19 @@
 #include <new>
 #include <string>
 #include <vector>
+#include <map>
+#include <tuple>
+#include <cstdlib>
 
-#include "../../include/vdwgb.h"
-#include "common.cuh"
-#include "pipeline.h"
+#include "internal.h"
 #include "table.h"
 
 using namespace vdwgb;
 
 static thread_local std::string g_err;
 
-static int fail(int code, const char *fmt, ...) {
+namespace vdwgb {
+int fail(int code, const char *fmt, ...) {
     char buf[512];
     va_list ap;
     va_start(ap, fmt);
@@ -28,11 +30,12 @@ static int fail(int code, const char *fmt, ...) {
     return code;
 }
 
-static int cuda_fail(cudaError_t e, const char *what) {
+int cuda_fail(cudaError_t e, const char *what) {
     if (e == cudaErrorMemoryAllocation)
         return fail(VDWGB_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
     return fail(VDWGB_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
+}  // namespace vdwgb
 
 #define CK(call, what)                                  \
     do {                                                \
@@ -52,7 +55,7 @@ struct DevInfo {
 static std::mutex g_dev_mu;
 static DevInfo g_dev[64];
 
-static int device_setup(int device) {
+int vdwgb::device_setup(int device) {
     if (device < 0 || device >= 64) return fail(VDWGB_EINVAL, "device %d out of range", device);
     std::lock_guard<std::mutex> lk(g_dev_mu);
     DevInfo &d = g_dev[device];
@@ -106,50 +109,41 @@ static std::vector<double> twiddles(int n) {
 }
 
 // ---------------------------------------------------------------------------
-// handle
+// handle (struct vdwgb_data in internal.h)
 // ---------------------------------------------------------------------------
-struct vdwgb_data {
-    int functional = 1;
-    int interp = VDWGB_INTERP_CUBIC;
-    int nx = 0, ny = 0, nz = 0;
-    double cell[9] = {0};
-    bool cell_set = false;
-    bool inited = false;
-    int device = -1;
-    int prec = VDWGB_FP64;
-    // device memory
-    void *spec = nullptr;
-    void *rec = nullptr;
-    double *epart = nullptr;
-    void *tw[3] = {nullptr, nullptr, nullptr};
-    unsigned *kidx = nullptr;
-    int4 *chunks = nullptr;
-    SysDev *dsys = nullptr;
-    int *dprefix = nullptr;
-    SysDev hsys;
-    LaunchSet ls;
-    const void *table = nullptr;
-    size_t bytes = 0;
-    // host-pointer path staging
-    double *d_io = nullptr;      // n, sigma, dedn, dedsigma, energy
-    cudaStream_t stream = nullptr;
-    const double *last_ptr[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-};
+
+static cudaError_t dalloc(vdwgb_data *h, void **p, size_t bytes) {
+    if (h->alloc_stream) return cudaMallocAsync(p, bytes, h->alloc_stream);
+    return cudaMalloc(p, bytes);
+}
+template <typename P>
+static cudaError_t dalloc(vdwgb_data *h, P **p, size_t bytes) {
+    return dalloc(h, reinterpret_cast<void **>(p), bytes);
+}
+static cudaError_t dupload(vdwgb_data *h, void *dst, const void *src, size_t bytes) {
+    if (h->alloc_stream) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->alloc_stream);
+    return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+}
+static void dfree(vdwgb_data *h, void *p) {
+    if (!p) return;
+    if (h->alloc_stream) cudaFreeAsync(p, h->alloc_stream);
+    else cudaFree(p);
+}
 
 static void release(vdwgb_data *h) {
     if (!h) return;
     if (h->device >= 0) cudaSetDevice(h->device);
-    cudaFree(h->spec);
-    cudaFree(h->rec);
-    cudaFree(h->epart);
-    for (int i = 0; i < 3; ++i) cudaFree(h->tw[i]);
-    cudaFree(h->kidx);
-    cudaFree(h->chunks);
+    dfree(h, h->spec);
+    dfree(h, h->rec);
+    dfree(h, h->epart);
+    for (int i = 0; i < 3; ++i) dfree(h, h->tw[i]);
+    dfree(h, h->kidx);
+    dfree(h, h->chunks);
     h->kidx = nullptr;
     h->chunks = nullptr;
-    cudaFree(h->dsys);
-    cudaFree(h->dprefix);
-    cudaFree(h->d_io);
+    dfree(h, h->dsys);
+    dfree(h, h->dprefix);
+    dfree(h, h->d_io);
     if (h->stream) cudaStreamDestroy(h->stream);
     h->spec = h->rec = nullptr;
     h->epart = nullptr;
@@ -164,27 +158,34 @@ static void release(vdwgb_data *h) {
 static size_t elem_bytes(int prec) { return prec == VDWGB_FP32_MIXED ? 8 : 16; }
 static size_t rec_bytes(int prec) { return prec == VDWGB_FP32_MIXED ? 16 : 32; }
 
-// Tile choices: z passes LZ lines, x/y passes W columns with three row
-// buffers (prefetch); prefer two blocks per SM (<= ~110 KB).  Axes too long
-// for three buffers of one column use two (no prefetch).
-static void choose_tiles(int prec, int nx, int ny, int nz, int nzh, size_t lim, int &LZ, int &LZi, int &W,
+// Default tile choices (heuristic): z passes LZ / LZi lines, y / x passes Wy /
+// Wx kz-columns with three row buffers (prefetch); prefer two blocks per SM
+// (<= ~110 KB).  Axes too long for three buffers of one column use two (no
+// prefetch).  The autotuner below replaces them by measured choices.
+static const size_t TILE_BUDGET = 110 * 1024;
+
+static int best_w(int prec, int n, int nzh) {
+    int W = 1;
+    for (int w = 8; w >= 1; --w)
+        if (stage_smem(1, prec, n, w, 3) <= TILE_BUDGET) { W = w; break; }
+    return W > nzh ? nzh : W;
+}
+
+static void choose_tiles(int prec, int nx, int ny, int nz, int nzh, size_t lim, int &LZ, int &LZi, int &Wy, int &Wx,
                          int &nbuf) {
-    const size_t budget = 110 * 1024;
     LZ = 1;
     for (int l = 8; l >= 1; --l)
-        if (stage_smem(0, prec, nz, l) <= budget) { LZ = l; break; }
+        if (stage_smem(0, prec, nz, l) <= TILE_BUDGET) { LZ = l; break; }
     LZi = 1;
     for (int l = 8; l >= 1; --l)
-        if (stage_smem(3, prec, nz, l) <= budget) { LZi = l; break; }
+        if (stage_smem(3, prec, nz, l) <= TILE_BUDGET) { LZi = l; break; }
     if (LZi > nx * ny) LZi = nx * ny;
-    const int nxy = nx > ny ? nx : ny;
-    W = 1;
-    nbuf = 3;
-    for (int w = 8; w >= 1; --w)
-        if (stage_smem(1, prec, nxy, w, 3) <= budget) { W = w; break; }
-    if (stage_smem(1, prec, nxy, 1, 3) > lim) nbuf = 2;
-    if (W > nzh) W = nzh;
     if (LZ > nx * ny) LZ = nx * ny;
+    Wy = best_w(prec, ny, nzh);
+    Wx = best_w(prec, nx, nzh);
+    nbuf = 3;
+    const int nxy = nx > ny ? nx : ny;
+    if (stage_smem(1, prec, nxy, 1, 3) > lim) nbuf = 2;
 }
 
 // Sort the half-spectrum k-points of a system by kernel-table interval
@@ -247,6 +248,190 @@ static void build_chunks(const SysDev &S, int maxspan, std::vector<unsigned> &ki
     }
 }
 
+// Tile-dependent parts of a handle's plan: tile counts of the z, y, x passes
+// and the matching launch-set fields.
+static void set_tiles(vdwgb_data *h, int LZ, int LZi, int Wy, int Wx, int nby, int nbx) {
+    SysDev &S = h->hsys;
+    LaunchSet &L = h->ls;
+    const int prec = h->prec;
+    const int nx = S.nx, ny = S.ny, nz = S.nz, nzh = S.nzh;
+    DevInfo &di = g_dev[h->device];
+    S.LZ = LZ;
+    S.LZi = LZi;
+    S.Wy = Wy;
+    S.Wx = Wx;
+    S.tiles[0] = (nx * ny + LZ - 1) / LZ;
+    S.tiles[1] = nx * ((nzh + Wy - 1) / Wy);
+    S.tiles[2] = ny * ((nzh + Wx - 1) / Wx);
+    S.tiles[3] = (nx * ny + LZi - 1) / LZi;
+    for (int s = 0; s < 4; ++s) {
+        L.prefix[s] = h->dprefix + 2 * s;
+        L.total[s] = S.tiles[s];
+    }
+    L.twmax[0] = L.twmax[3] = nz;
+    L.twmax[1] = ny;
+    L.twmax[2] = nx;
+    L.bufelems[0] = 0;
+    L.bufelems[3] = LZi * nzh * NQ;
+    L.recelems = LZi * nz;
+    L.abelems = nz * 10 * LZi;
+    L.bufelems[1] = ny * Wy * NQ;
+    L.bufelems[2] = nx * Wx * NQ;
+    L.nbuf[0] = L.nbuf[3] = 0;
+    L.nbuf[1] = nby;
+    L.nbuf[2] = nbx;
+    L.smem[0] = stage_smem(0, prec, nz, LZ);
+    L.smem[3] = stage_smem(3, prec, nz, LZi);
+    L.smem[1] = stage_smem(1, prec, ny, Wy, nby);
+    L.smem[2] = stage_smem(1, prec, nx, Wx, nbx);
+    for (int s = 0; s < 4; ++s) {
+        int per_sm = (int)((228 * 1024) / (L.smem[s] + 1024));
+        per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
+        const int cap = di.sms * per_sm;
+        L.grid[s] = L.total[s] < cap ? L.total[s] : cap;
+    }
+}
+
+static int upload_plan(vdwgb_data *h) {
+    int pre[2 * NKIND];
+    for (int s = 0; s < NKIND; ++s) {
+        pre[2 * s] = 0;
+        pre[2 * s + 1] = h->hsys.tiles[s];
+    }
+    CK(dupload(h, h->dprefix, pre, sizeof pre), "prefix");
+    CK(dupload(h, h->dsys, &h->hsys, sizeof(SysDev)), "descriptor");
+    h->last_ptr[0] = nullptr;   // descriptor rewritten: refresh I/O pointers next call
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: per (grid, precision) the tile shapes LZ (z forward), Wy, Wx
+// (y, x passes) and LZi (z inverse) are chosen by timing each stage on the
+// device for every candidate that fits shared memory; results are cached for
+// the process.  Enabled by vdwgb_set_autotune(1) or VDWGB_AUTOTUNE=1.
+// ---------------------------------------------------------------------------
+struct TuneKey {
+    int nx, ny, nz, prec;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(nx, ny, nz, prec) < std::tie(o.nx, o.ny, o.nz, o.prec);
+    }
+};
+struct TuneVal {
+    int LZ, LZi, Wy, Wx, nby, nbx;
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, TuneVal> g_tune;
+static int g_autotune = -1;   // -1: read VDWGB_AUTOTUNE once
+
+static bool autotune_on() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (g_autotune < 0) {
+        const char *e = std::getenv("VDWGB_AUTOTUNE");
+        g_autotune = (e && e[0] == '1') ? 1 : 0;
+    }
+    return g_autotune == 1;
+}
+
+static int time_stage(vdwgb_data *h, int stage, float &ms) {
+    int pre[2 * NKIND];
+    for (int s = 0; s < NKIND; ++s) {
+        pre[2 * s] = 0;
+        pre[2 * s + 1] = h->hsys.tiles[s];
+    }
+    CK(cudaMemcpy(h->dprefix, pre, sizeof pre, cudaMemcpyHostToDevice), "prefix");
+    CK(cudaMemcpy(h->dsys, &h->hsys, sizeof(SysDev), cudaMemcpyHostToDevice), "descriptor");
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a), "event");
+    CK(cudaEventCreate(&b), "event");
+    CK(launch_stage(h->ls, h->prec, stage, h->stream), "tune launch");
+    CK(cudaEventRecord(a, h->stream), "event");
+    for (int r = 0; r < 3; ++r) CK(launch_stage(h->ls, h->prec, stage, h->stream), "tune launch");
+    CK(cudaEventRecord(b, h->stream), "event");
+    CK(cudaEventSynchronize(b), "event");
+    CK(cudaEventElapsedTime(&ms, a, b), "event");
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return vdwgb_device_status(h->device);
+}
+
+static int apply_tuned(vdwgb_data *h) {
+    SysDev &S = h->hsys;
+    const TuneKey key{S.nx, S.ny, S.nz, h->prec};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            set_tiles(h, it->second.LZ, it->second.LZi, it->second.Wy, it->second.Wx, it->second.nby, it->second.nbx);
+            return 0;
+        }
+    }
+    if (h->alloc_stream || !autotune_on()) return 0;
+    // measure on this handle's buffers with a constant density (every point live)
+    const int prec = h->prec;
+    const size_t N = (size_t)S.nx * S.ny * S.nz;
+    const size_t lim = g_dev[h->device].maxsmem - 1024;
+    std::vector<double> host(2 * N, 0.0);
+    for (size_t i = 0; i < N; ++i) host[i] = 0.01;
+    double *tmp = nullptr;
+    CK(cudaMalloc(&tmp, (4 * N + 1) * sizeof(double)), "tune buffers");
+    int rc = 0;
+    TuneVal best{S.LZ, S.LZi, S.Wy, S.Wx, h->ls.nbuf[1], h->ls.nbuf[2]};
+    auto set_io_dev = [&]() {
+        S.n = tmp;
+        S.sigma = tmp + N;
+        S.dedn = tmp + 2 * N;
+        S.dedsigma = tmp + 3 * N;
+        S.energy = tmp + 4 * N;
+    };
+    if (cudaMemcpy(tmp, host.data(), 2 * N * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = fail(VDWGB_ECUDA, "tune upload");
+    set_io_dev();
+    const int cand[6] = {1, 2, 3, 4, 6, 8};
+    // z forward first (it writes the records and spectrum the other stages read)
+    for (int pass = 0; pass < 4 && !rc; ++pass) {
+        float best_ms = 1e30f;
+        for (int ci = 0; ci < 12; ++ci) {
+            const int c = cand[ci % 6];
+            const int nb = ci < 6 ? 3 : 2;          // x / y passes: prefetching or not
+            if ((pass == 0 || pass == 3) && ci >= 6) break;
+            TuneVal v = best;
+            if (pass == 0) {
+                if (c > S.nx * S.ny || stage_smem(0, prec, S.nz, c) > lim) continue;
+                v.LZ = c;
+            } else if (pass == 1) {
+                if (c > S.nzh || stage_smem(1, prec, S.ny, c, nb) > lim) continue;
+                v.Wy = c;
+                v.nby = nb;
+            } else if (pass == 2) {
+                if (c > S.nzh || stage_smem(1, prec, S.nx, c, nb) > lim) continue;
+                v.Wx = c;
+                v.nbx = nb;
+            } else {
+                if (c > S.nx * S.ny || stage_smem(3, prec, S.nz, c) > lim) continue;
+                v.LZi = c;
+            }
+            set_tiles(h, v.LZ, v.LZi, v.Wy, v.Wx, v.nby, v.nbx);
+            set_io_dev();
+            float ms = 0.f;
+            const int stage = pass == 0 ? 0 : (pass == 1 ? 1 : (pass == 2 ? 2 : 6));
+            rc = time_stage(h, stage, ms);
+            if (rc) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = v;
+            }
+        }
+    }
+    cudaFree(tmp);
+    S.n = S.sigma = nullptr;
+    S.dedn = S.dedsigma = S.energy = nullptr;
+    if (rc) return rc;
+    set_tiles(h, best.LZ, best.LZi, best.Wy, best.Wx, best.nby, best.nbx);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best;
+    return 0;
+}
+
 static int plan(vdwgb_data *h) {
     const int prec = h->prec;
     const int nx = h->nx, ny = h->ny, nz = h->nz, nzh = nz / 2 + 1;
@@ -263,16 +448,11 @@ static int plan(vdwgb_data *h) {
             return fail(VDWGB_EINVAL, "axis %d length %d: prime factors must be 2, 3, 5, 7", a, dims[a]);
     const size_t lim = di.maxsmem - 1024;
     int nbuf = 3;
-    choose_tiles(prec, nx, ny, nz, nzh, lim, S.LZ, S.LZi, S.W, nbuf);
-    if (stage_smem(0, prec, nz, S.LZ) > lim || stage_smem(1, prec, nx, S.W, nbuf) > lim ||
-        stage_smem(1, prec, ny, S.W, nbuf) > lim || stage_smem(3, prec, nz, S.LZi) > lim)
+    choose_tiles(prec, nx, ny, nz, nzh, lim, S.LZ, S.LZi, S.Wy, S.Wx, nbuf);
+    if (stage_smem(0, prec, nz, S.LZ) > lim || stage_smem(1, prec, nx, S.Wx, nbuf) > lim ||
+        stage_smem(1, prec, ny, S.Wy, nbuf) > lim || stage_smem(3, prec, nz, S.LZi) > lim)
         return fail(VDWGB_EINVAL, "grid %dx%dx%d too large for one block per pencil in this precision",
                     nx, ny, nz);
-    const int ncol = (nzh + S.W - 1) / S.W;
-    S.tiles[0] = (nx * ny + S.LZ - 1) / S.LZ;
-    S.tiles[1] = nx * ncol;
-    S.tiles[2] = ny * ncol;
-    S.tiles[3] = (nx * ny + S.LZi - 1) / S.LZi;
     // reciprocal metric g = B B^T, B = 2 pi C^{-T} (rows b_j)
     const double *c = h->cell;
     const double det = c[0] * (c[4] * c[8] - c[5] * c[7]) - c[1] * (c[3] * c[8] - c[5] * c[6]) +
@@ -313,13 +493,13 @@ static int plan(vdwgb_data *h) {
     S.tiles[4] = (int)chunks.size();
     // memory
     const size_t nspec = (size_t)nx * ny * nzh * NQ;
-    CK(cudaMalloc(&h->spec, nspec * elem_bytes(prec)), "work buffer");
-    CK(cudaMalloc(&h->rec, (size_t)nx * ny * nz * rec_bytes(prec)), "point records");
-    CK(cudaMalloc(&h->epart, (size_t)S.tiles[4] * sizeof(double)), "energy partials");
-    CK(cudaMalloc(&h->kidx, kidx.size() * sizeof(unsigned)), "k-point order");
-    CK(cudaMemcpy(h->kidx, kidx.data(), kidx.size() * sizeof(unsigned), cudaMemcpyHostToDevice), "k-point order");
-    CK(cudaMalloc(&h->chunks, chunks.size() * sizeof(int4)), "chunks");
-    CK(cudaMemcpy(h->chunks, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice), "chunks");
+    CK(dalloc(h, &h->spec, nspec * elem_bytes(prec)), "work buffer");
+    CK(dalloc(h, &h->rec, (size_t)nx * ny * nz * rec_bytes(prec)), "point records");
+    CK(dalloc(h, &h->epart, (size_t)S.tiles[4] * sizeof(double)), "energy partials");
+    CK(dalloc(h, &h->kidx, kidx.size() * sizeof(unsigned)), "k-point order");
+    CK(dupload(h, h->kidx, kidx.data(), kidx.size() * sizeof(unsigned)), "k-point order");
+    CK(dalloc(h, &h->chunks, chunks.size() * sizeof(int4)), "chunks");
+    CK(dupload(h, h->chunks, chunks.data(), chunks.size() * sizeof(int4)), "chunks");
     S.kidx = h->kidx;
     S.chunks = h->chunks;
     for (int a = 0; a < 3; ++a) {
@@ -327,11 +507,11 @@ static int plan(vdwgb_data *h) {
         if (prec == VDWGB_FP32_MIXED) {
             std::vector<float> wf(w.size());
             for (size_t i = 0; i < w.size(); ++i) wf[i] = (float)w[i];
-            CK(cudaMalloc(&h->tw[a], wf.size() * sizeof(float)), "twiddles");
-            CK(cudaMemcpy(h->tw[a], wf.data(), wf.size() * sizeof(float), cudaMemcpyHostToDevice), "twiddles");
+            CK(dalloc(h, &h->tw[a], wf.size() * sizeof(float)), "twiddles");
+            CK(dupload(h, h->tw[a], wf.data(), wf.size() * sizeof(float)), "twiddles");
         } else {
-            CK(cudaMalloc(&h->tw[a], w.size() * sizeof(double)), "twiddles");
-            CK(cudaMemcpy(h->tw[a], w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice), "twiddles");
+            CK(dalloc(h, &h->tw[a], w.size() * sizeof(double)), "twiddles");
+            CK(dupload(h, h->tw[a], w.data(), w.size() * sizeof(double)), "twiddles");
         }
         S.tw[a] = h->tw[a];
     }
@@ -340,50 +520,24 @@ static int plan(vdwgb_data *h) {
     S.epart = h->epart;
     h->bytes = nspec * elem_bytes(prec) + (size_t)nx * ny * nz * rec_bytes(prec) + S.tiles[4] * sizeof(double) +
                kidx.size() * sizeof(unsigned) + chunks.size() * sizeof(int4);
-    CK(cudaMalloc(&h->dsys, sizeof(SysDev)), "descriptor");
-    CK(cudaMalloc(&h->dprefix, 2 * NKIND * sizeof(int)), "prefix");
-    int pre[2 * NKIND];
-    for (int s = 0; s < NKIND; ++s) {
-        pre[2 * s] = 0;
-        pre[2 * s + 1] = S.tiles[s];
-    }
-    CK(cudaMemcpy(h->dprefix, pre, sizeof pre, cudaMemcpyHostToDevice), "prefix");
-    CK(cudaMemcpy(h->dsys, &S, sizeof(SysDev), cudaMemcpyHostToDevice), "descriptor");
+    CK(dalloc(h, &h->dsys, sizeof(SysDev)), "descriptor");
+    CK(dalloc(h, &h->dprefix, 2 * NKIND * sizeof(int)), "prefix");
     // launch set
     LaunchSet &L = h->ls;
     L.sys = h->dsys;
     L.nsys = 1;
     L.maxspan = maxspan;
-    for (int s = 0; s < NKIND; ++s) {
-        L.prefix[s] = h->dprefix + 2 * s;
-        L.total[s] = S.tiles[s];
-    }
     L.err = di.err;
-    L.twmax[0] = L.twmax[3] = nz;
-    L.twmax[1] = ny;
-    L.twmax[2] = nx;
-    L.bufelems[0] = 0;
-    L.bufelems[3] = S.LZi * nzh * NQ;
-    L.recelems = S.LZi * nz;
-    L.abelems = nz * 10 * S.LZi;
-    L.bufelems[1] = ny * S.W * NQ;
-    L.bufelems[2] = nx * S.W * NQ;
-    L.twmax[4] = 0;
-    L.bufelems[4] = 0;
-    L.nbuf[4] = 0;
-    L.smem[0] = stage_smem(0, prec, nz, S.LZ);
-    L.smem[3] = stage_smem(3, prec, nz, S.LZi);
-    L.nbuf[0] = L.nbuf[3] = 0;
-    L.nbuf[1] = L.nbuf[2] = nbuf;
-    L.smem[1] = stage_smem(1, prec, ny, S.W, nbuf);
-    L.smem[2] = stage_smem(1, prec, nx, S.W, nbuf);
     L.smem[4] = contract_smem(prec, maxspan);
-    for (int s = 0; s < NKIND; ++s) {
-        int per_sm = (int)((228 * 1024) / (L.smem[s] + 1024));
+    L.twmax[4] = L.bufelems[4] = L.nbuf[4] = 0;
+    L.total[4] = S.tiles[4];
+    L.prefix[4] = h->dprefix + 8;
+    {
+        int per_sm = (int)((228 * 1024) / (L.smem[4] + 1024));
         per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
-        const int cap = di.sms * per_sm;
-        L.grid[s] = L.total[s] < cap ? L.total[s] : cap;
+        L.grid[4] = L.total[4] < di.sms * per_sm ? L.total[4] : di.sms * per_sm;
     }
+    set_tiles(h, S.LZ, S.LZi, S.Wy, S.Wx, nbuf, nbuf);
     TableRefs tr;
     CK(table_get(h->device, tr), "kernel table");
     if (prec == VDWGB_FP32_MIXED)
@@ -391,8 +545,12 @@ static int plan(vdwgb_data *h) {
     else
         L.table = h->interp == VDWGB_INTERP_LINEAR ? (const void *)tr.lin64 : (const void *)tr.cub64;
     h->table = L.table;
-    CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "stream");
-    return 0;
+    if (!h->alloc_stream) CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "stream");
+    {
+        int rc = apply_tuned(h);          // cached or measured tile choices
+        if (rc) return rc;
+    }
+    return upload_plan(h);
 }
 
 static bool axis_ok(int n) {
@@ -444,7 +602,9 @@ int vdwgb_set_interp(vdwgb_handle h, int interp) {
     return 0;
 }
 
-int vdwgb_init_cuda(vdwgb_handle h, int device, int precision) {
+}  // extern "C"
+
+int vdwgb::handle_init(vdwgb_data *h, int device, int precision, cudaStream_t alloc_stream) {
     if (!h) return fail(VDWGB_EINVAL, "null handle");
     if (!h->cell_set) return fail(VDWGB_ESTATE, "set the unit cell before init");
     if (precision != VDWGB_FP64 && precision != VDWGB_FP32_MIXED)
@@ -458,13 +618,29 @@ int vdwgb_init_cuda(vdwgb_handle h, int device, int precision) {
     CK(cudaSetDevice(device), "cudaSetDevice");
     h->device = device;
     h->prec = precision;
+    h->alloc_stream = alloc_stream;
     rc = plan(h);
     if (rc) {
         release(h);
         return rc;
     }
+    if (alloc_stream) {
+        const size_t N = (size_t)h->nx * h->ny * h->nz;
+        CK(dalloc(h, &h->d_io, (4 * N + 1) * sizeof(double)), "staging");
+        h->bytes += (4 * N + 1) * sizeof(double);
+    }
     h->inited = true;
     return 0;
+}
+
+void vdwgb::handle_release(vdwgb_data *h) { release(h); }
+
+size_t vdwgb::handle_io_bytes(const vdwgb_data *h) { return h->bytes; }
+
+extern "C" {
+
+int vdwgb_init_cuda(vdwgb_handle h, int device, int precision) {
+    return handle_init(h, device, precision, nullptr);
 }
 
 static int set_io(vdwgb_data *h, const double *n, const double *s, double *dn, double *ds, double *e,
@@ -575,9 +751,9 @@ int vdwgb_print(vdwgb_handle h) {
            h->cell[8]);
     if (h->inited) {
         const SysDev &S = h->hsys;
-        printf("  device %d, %s, tiles zf %d y %d x %d zi %d chunks %d (LZ %d, LZi %d, W %d, nbuf %d), %.1f MB\n",
+        printf("  device %d, %s, tiles zf %d y %d x %d zi %d chunks %d (LZ %d, LZi %d, Wy %d, Wx %d, nbuf %d), %.1f MB\n",
                h->device, h->prec == VDWGB_FP32_MIXED ? "FP32-mixed" : "FP64", S.tiles[0], S.tiles[1], S.tiles[2],
-               S.tiles[3], S.tiles[4], S.LZ, S.LZi, S.W, h->ls.nbuf[1], h->bytes / 1e6);
+               S.tiles[3], S.tiles[4], S.LZ, S.LZi, S.Wy, S.Wx, h->ls.nbuf[1], h->bytes / 1e6);
         for (int a = 0; a < 3; ++a) {
             printf("  axis %d n=%d radices", a, S.ax[a].n);
             for (int s = 0; s < S.ax[a].nst; ++s) printf(" %d", S.ax[a].rad[s]);
@@ -642,6 +818,28 @@ int vdwgb_phi(int device, int npts, const double *d1, const double *d2, double *
 
 double vdwgb_table_build_seconds(int device) { return table_seconds(device); }
 
+int vdwgb_set_autotune(int enable) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_autotune = enable ? 1 : 0;
+    return 0;
+}
+
+int vdwgb_plan_info(vdwgb_handle h, int *info) {
+    if (!h || !info) return fail(VDWGB_EINVAL, "null argument");
+    if (!h->inited) return fail(VDWGB_ESTATE, "handle not initialised");
+    const SysDev &S = h->hsys;
+    info[0] = S.LZ;
+    info[1] = S.LZi;
+    info[2] = S.Wy;
+    info[3] = S.Wx;
+    info[4] = h->ls.nbuf[1] * 10 + h->ls.nbuf[2];
+    info[5] = S.tiles[4];
+    info[6] = NSTAGE;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    info[7] = g_tune.count(TuneKey{S.nx, S.ny, S.nz, h->prec}) ? 1 : 0;
+    return 0;
+}
+
 int vdwgb_q0(int device, int precision, int functional, int npts, const double *n, const double *sigma,
              double *q0, double *dq0dn, double *dq0dsigma) {
     if (npts < 0 || (npts > 0 && (!n || !sigma || !q0 || !dq0dn || !dq0dsigma)))
@@ -691,6 +889,53 @@ struct vdwgb_batch_s {
     cudaStream_t own = nullptr;
 };
 
+}  // extern "C"
+
+int vdwgb::batch_launchset(vdwgb_data *const *hs, int count, SysDev *hdesc, int *pre, const SysDev *ddesc,
+                           const int *dprefix, LaunchSet &L) {
+    std::memset(&L, 0, sizeof L);
+    for (int s = 0; s < NKIND; ++s) pre[s * (count + 1)] = 0;
+    for (int i = 0; i < count; ++i) {
+        hdesc[i] = hs[i]->hsys;
+        for (int s = 0; s < NKIND; ++s) {
+            pre[s * (count + 1) + i + 1] = pre[s * (count + 1) + i] + hs[i]->hsys.tiles[s];
+            if (hs[i]->ls.smem[s] > L.smem[s]) L.smem[s] = hs[i]->ls.smem[s];
+            if (hs[i]->ls.twmax[s] > L.twmax[s]) L.twmax[s] = hs[i]->ls.twmax[s];
+            if (hs[i]->ls.bufelems[s] > L.bufelems[s]) L.bufelems[s] = hs[i]->ls.bufelems[s];
+            if (i == 0 || hs[i]->ls.nbuf[s] < L.nbuf[s]) L.nbuf[s] = hs[i]->ls.nbuf[s];
+        }
+        if (hs[i]->ls.recelems > L.recelems) L.recelems = hs[i]->ls.recelems;
+        if (hs[i]->ls.abelems > L.abelems) L.abelems = hs[i]->ls.abelems;
+    }
+    const int device = hs[0]->device;
+    const int prec = hs[0]->prec;
+    DevInfo &di = g_dev[device];
+    L.sys = ddesc;
+    L.nsys = count;
+    L.err = hs[0]->ls.err;
+    L.maxspan = hs[0]->ls.maxspan;
+    L.table = hs[0]->table;
+    // x / y stages: shared memory from the largest row tile and twiddle table of the batch
+    const size_t c = prec == VDWGB_FP32_MIXED ? 8 : 16;
+    for (int s = 1; s <= 2; ++s)
+        L.smem[s] = 16 + c * ((size_t)((L.twmax[s] + 7) & ~7) + (size_t)L.nbuf[s] * L.bufelems[s]);
+    L.smem[3] = zinv_smem(prec, L.twmax[3], L.bufelems[3], L.recelems, L.abelems);
+    const size_t lim = di.maxsmem - 1024;
+    if (L.smem[1] > lim || L.smem[2] > lim || L.smem[3] > lim)
+        return fail(VDWGB_EINVAL, "batch: combined row tiles exceed shared memory");
+    for (int s = 0; s < NKIND; ++s) {
+        L.prefix[s] = dprefix + s * (count + 1);
+        L.total[s] = pre[s * (count + 1) + count];
+        int per_sm = (int)((228 * 1024) / (L.smem[s] + 1024));
+        per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
+        const int cap = di.sms * per_sm;
+        L.grid[s] = L.total[s] < cap ? L.total[s] : cap;
+    }
+    return 0;
+}
+
+extern "C" {
+
 int vdwgb_batch_new(vdwgb_handle *handles, int count, vdwgb_batch *out) {
     if (!out) return fail(VDWGB_EINVAL, "null output");
     *out = nullptr;
@@ -709,57 +954,20 @@ int vdwgb_batch_new(vdwgb_handle *handles, int count, vdwgb_batch *out) {
     cudaSetDevice(b->device);
     b->host.resize(count);
     std::vector<int> pre(NKIND * (count + 1), 0);
-    LaunchSet &L = b->ls;
-    std::memset(&L, 0, sizeof L);
-    for (int i = 0; i < count; ++i) {
-        b->host[i] = handles[i]->hsys;
-        for (int s = 0; s < NKIND; ++s) {
-            pre[s * (count + 1) + i + 1] = pre[s * (count + 1) + i] + handles[i]->hsys.tiles[s];
-            if (handles[i]->ls.smem[s] > L.smem[s]) L.smem[s] = handles[i]->ls.smem[s];
-            if (handles[i]->ls.twmax[s] > L.twmax[s]) L.twmax[s] = handles[i]->ls.twmax[s];
-            if (handles[i]->ls.bufelems[s] > L.bufelems[s]) L.bufelems[s] = handles[i]->ls.bufelems[s];
-            if (i == 0 || handles[i]->ls.nbuf[s] < L.nbuf[s]) L.nbuf[s] = handles[i]->ls.nbuf[s];
-        }
-        if (handles[i]->ls.recelems > L.recelems) L.recelems = handles[i]->ls.recelems;
-        if (handles[i]->ls.abelems > L.abelems) L.abelems = handles[i]->ls.abelems;
-    }
     cudaError_t e = cudaMalloc(&b->dsys, count * sizeof(SysDev));
     if (e == cudaSuccess) e = cudaMalloc(&b->dprefix, pre.size() * sizeof(int));
-    if (e == cudaSuccess) e = cudaMemcpy(b->dprefix, pre.data(), pre.size() * sizeof(int), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b->dsys, b->host.data(), count * sizeof(SysDev), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
+    int rc = e == cudaSuccess ? batch_launchset(handles, count, b->host.data(), pre.data(), b->dsys, b->dprefix, b->ls)
+                              : cuda_fail(e, "batch setup");
+    if (rc == 0) {
+        e = cudaMemcpy(b->dprefix, pre.data(), pre.size() * sizeof(int), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(b->dsys, b->host.data(), count * sizeof(SysDev), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) rc = cuda_fail(e, "batch setup");
+    }
+    if (rc) {
         cudaFree(b->dsys);
         cudaFree(b->dprefix);
         delete b;
-        return cuda_fail(e, "batch setup");
-    }
-    DevInfo &di = g_dev[b->device];
-    L.sys = b->dsys;
-    L.nsys = count;
-    L.err = handles[0]->ls.err;
-    L.maxspan = handles[0]->ls.maxspan;
-    {
-        // x / y stages: shared memory from the largest row tile and twiddle table of the batch
-        const size_t c = b->prec == VDWGB_FP32_MIXED ? 8 : 16;
-        for (int s = 1; s <= 2; ++s)
-            L.smem[s] = 16 + c * ((size_t)((L.twmax[s] + 7) & ~7) + (size_t)L.nbuf[s] * L.bufelems[s]);
-        L.smem[3] = zinv_smem(b->prec, L.twmax[3], L.bufelems[3], L.recelems, L.abelems);
-        const size_t lim = g_dev[b->device].maxsmem - 1024;
-        if (L.smem[1] > lim || L.smem[2] > lim || L.smem[3] > lim) {
-            cudaFree(b->dsys);
-            cudaFree(b->dprefix);
-            delete b;
-            return fail(VDWGB_EINVAL, "batch: combined row tiles exceed shared memory");
-        }
-    }
-    L.table = handles[0]->table;
-    for (int s = 0; s < NKIND; ++s) {
-        L.prefix[s] = b->dprefix + s * (count + 1);
-        L.total[s] = pre[s * (count + 1) + count];
-        int per_sm = (int)((228 * 1024) / (L.smem[s] + 1024));
-        per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
-        const int cap = di.sms * per_sm;
-        L.grid[s] = L.total[s] < cap ? L.total[s] : cap;
+        return rc;
     }
     b->last.assign(5 * count, nullptr);
     *out = b;

@@ -77,7 +77,7 @@ struct SysDev {
     int nx, ny, nz, nzh;
     int LZ;          // z-lines per tile of the z-forward pass
     int LZi;         // z-lines per tile of the z-inverse pass
-    int W;           // k_z columns per tile of the x / y passes
+    int Wy, Wx;      // k_z columns per tile of the y and x passes
     int tiles[5];    // tiles of: z-forward, y, x, z-inverse, contraction chunks
     AxisPlan ax[3];  // x, y, z
     const void *tw[3];   // twiddles exp(-2 pi i m / n), m < n, per axis (T complex)

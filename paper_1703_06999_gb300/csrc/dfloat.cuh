@@ -1,0 +1,99 @@
+// Double-float arithmetic: a value is the unevaluated sum hi + lo of two
+// FP32 numbers (|lo| <= ulp(hi)/2), about 48 significant bits.  Built from
+// the error-free transformations two-sum (Knuth) and two-product (exact with
+// FMA), after Dekker (1971).  Used for the FP64-grade q0 of the FP32-mixed
+// form: GB300 issues 64 FP32 FMAs for every FP64 FMA.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace vdwgb {
+
+struct dfl {
+    float hi, lo;
+};
+
+// split a double constant into hi + lo (constant-folded for literals)
+__host__ __device__ constexpr dfl DF(double x) {
+    return dfl{(float)x, (float)(x - (double)(float)x)};
+}
+
+__device__ __forceinline__ dfl df_quick(float s, float e) {   // |s| >= |e|
+    const float h = s + e;
+    return dfl{h, e - (h - s)};
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ dfl df_from(double x) {
+    const float h = (float)x;
+    return dfl{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double df_to(dfl a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+    float s, e, t, f;
+    two_sum(a.hi, b.hi, s, e);
+    two_sum(a.lo, b.lo, t, f);
+    e += t;
+    dfl r = df_quick(s, e);
+    r.lo += f;
+    return df_quick(r.hi, r.lo);
+}
+
+__device__ __forceinline__ dfl df_neg(dfl a) { return dfl{-a.hi, -a.lo}; }
+__device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
+
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return df_quick(p, e);
+}
+
+__device__ __forceinline__ dfl df_mulf(dfl a, float b) {
+    const float p = a.hi * b;
+    float e = fmaf(a.hi, b, -p);
+    e = fmaf(a.lo, b, e);
+    return df_quick(p, e);
+}
+
+// a / b with two correction steps
+__device__ __forceinline__ dfl df_div(dfl a, dfl b) {
+    const float rb = 1.0f / b.hi;
+    const float q1 = a.hi * rb;
+    dfl r = df_sub(a, df_mulf(b, q1));
+    const float q2 = r.hi * rb;
+    r = df_sub(r, df_mulf(b, q2));
+    const float q3 = r.hi * rb;
+    dfl q = df_quick(q1, q2);
+    return df_add(q, dfl{q3, 0.f});
+}
+
+__device__ __forceinline__ dfl df_rcp(dfl b) { return df_div(dfl{1.f, 0.f}, b); }
+
+// Newton corrections from FP32 seeds (one step doubles the ~24 good bits)
+__device__ __forceinline__ dfl df_sqrt(dfl a) {
+    const float x = sqrtf(a.hi);
+    const float p = x * x;
+    const float e = fmaf(x, x, -p);
+    const dfl r = df_sub(a, dfl{p, e});
+    return df_quick(x, r.hi / (2.f * x));
+}
+
+__device__ __forceinline__ dfl df_cbrt(dfl a) {
+    const float y = cbrtf(a.hi);
+    const float p = y * y;
+    const float e = fmaf(y, y, -p);
+    const dfl y3 = df_mulf(dfl{p, e}, y);
+    const dfl r = df_sub(a, y3);
+    return df_quick(y, r.hi / (3.f * p));
+}
+
+__device__ __forceinline__ bool df_lt(dfl a, dfl b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+
+}  // namespace vdwgb

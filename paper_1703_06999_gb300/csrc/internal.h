@@ -1,0 +1,55 @@
+// Internal interfaces shared by the C ABI (capi.cu) and the serving loop
+// (serve.cu).  Not part of the public header.
+#pragma once
+#include <cstddef>
+#include <cuda_runtime.h>
+#include "../../include/vdwgb.h"
+#include "common.cuh"
+#include "pipeline.h"
+
+struct vdwgb_data {
+    int functional = 1;
+    int interp = VDWGB_INTERP_CUBIC;
+    int nx = 0, ny = 0, nz = 0;
+    double cell[9] = {0};
+    bool cell_set = false;
+    bool inited = false;
+    int device = -1;
+    int prec = VDWGB_FP64;
+    // device memory
+    void *spec = nullptr;
+    void *rec = nullptr;
+    double *epart = nullptr;
+    void *tw[3] = {nullptr, nullptr, nullptr};
+    unsigned *kidx = nullptr;
+    int4 *chunks = nullptr;
+    vdwgb::SysDev *dsys = nullptr;
+    int *dprefix = nullptr;
+    vdwgb::SysDev hsys;
+    vdwgb::LaunchSet ls;
+    const void *table = nullptr;
+    size_t bytes = 0;
+    // host-pointer path staging
+    double *d_io = nullptr;      // n, sigma, dedn, dedsigma, energy
+    cudaStream_t stream = nullptr;
+    cudaStream_t alloc_stream = nullptr;   // set: stream-ordered allocations (server handles)
+    const double *last_ptr[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace vdwgb {
+
+int fail(int code, const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+int device_setup(int device);
+// plan and allocate a handle (cell already set); alloc_stream != 0 makes
+// every allocation and upload stream-ordered on it
+int handle_init(vdwgb_data *h, int device, int precision, cudaStream_t alloc_stream);
+void handle_release(vdwgb_data *h);
+size_t handle_io_bytes(const vdwgb_data *h);
+// launch set over n handles: fills hdesc[n] (copies of the handles'
+// descriptors; the caller sets I/O pointers), hprefix[NKIND * (n + 1)] and L,
+// whose device pointers are ddesc / dprefix (filled by the caller's copy)
+int batch_launchset(vdwgb_data *const *hs, int n, SysDev *hdesc, int *hprefix, const SysDev *ddesc,
+                    const int *dprefix, LaunchSet &L);
+
+}  // namespace vdwgb

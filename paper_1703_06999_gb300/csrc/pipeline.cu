@@ -14,6 +14,7 @@
 #include "common.cuh"
 #include "pipeline.h"
 #include "tma.cuh"
+#include "dfloat.cuh"
 
 namespace vdwgb {
 
@@ -81,151 +82,155 @@ __device__ __forceinline__ Q0 q0_point(double n, double s, double Z) {
 }
 
 // ---------------------------------------------------------------------------
-// q0 for the FP32-mixed form: the same FP64 quantity with fewer FP64
-// operations (GB300's FP64 rate is a small fraction of its FP32 rate).
-//  * 1/x, sqrt(x), cbrt(x): FP32 seed, one FP64 Newton step (error ~ seed^2).
-//  * ln(x): x = m 2^e with m in [1/sqrt2, sqrt2), ln m = 2 atanh((m-1)/(m+1)),
-//    atanh by its Taylor series to s^19 (|s| <= 0.172: truncation < 1e-16).
-//  * exp(-S), S >= 0: S = k ln2 + r, |r| <= ln2/2, exp(-r) by its Taylor
-//    series to r^13, times 2^-k; exp(-S) = 0 for S > 40 (h_a saturated).
-//  * The derivatives dq0/dn, dq0/dsigma only enter the potential (stored in
-//    FP32) and are formed in FP32 from the FP64 intermediates.
+// q0 for the FP32-mixed form in double-float arithmetic (about 48 bits;
+// GB300's FP64 pipe is 1/64 of its FP32 rate).  Same formulas as q0_point:
+//  * ln(1 + u) = 2 atanh(s), s = u / (2 + u) for u < sqrt2 - 1, else
+//    x = 1 + u = m 2^e, m in [1/sqrt2, sqrt2), ln x = 2 atanh((m-1)/(m+1)) + e ln2;
+//    atanh by its Taylor series to s^19 (|s| <= 0.172).
+//  * exp(-S) = 2^-k exp(-r), S = k ln2 + r, |r| <= ln2/2, Taylor series to r^12.
+//  * Saturation: for t = q_raw/5 > 1.5, sum_{m<=12} t^m/m > 40 and
+//    q0 = 5 to FP64 precision.
+//  * The spline interval and coordinate B come from the double-float q0; the
+//    derivatives (they only enter the potential) are formed in FP32.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double rcp_nr(double v) {
-    const double r = (double)(1.0f / (float)v);
-    return fma(r, fma(-v, r, 1.0), r);
+struct Q0M {
+    bool live;
+    int j;
+    float B;
+    float dqdn, dqds;
+    double q0;
+};
+
+__device__ __forceinline__ dfl df_two_atanh(dfl s) {
+    const dfl z = df_mul(s, s);
+    dfl p = DF(1.0 / 19.0);
+    p = df_add(df_mul(p, z), DF(1.0 / 17.0));
+    p = df_add(df_mul(p, z), DF(1.0 / 15.0));
+    p = df_add(df_mul(p, z), DF(1.0 / 13.0));
+    p = df_add(df_mul(p, z), DF(1.0 / 11.0));
+    p = df_add(df_mul(p, z), DF(1.0 / 9.0));
+    p = df_add(df_mul(p, z), DF(1.0 / 7.0));
+    p = df_add(df_mul(p, z), DF(1.0 / 5.0));
+    p = df_add(df_mul(p, z), DF(1.0 / 3.0));
+    p = df_add(df_mul(p, z), DF(1.0));
+    const dfl r = df_mul(s, p);
+    return dfl{2.f * r.hi, 2.f * r.lo};
 }
 
-__device__ __forceinline__ double sqrt_nr(double x) {
-    const double y = (double)sqrtf((float)x);
-    const double r = (double)(0.5f / (float)y);
-    return fma(fma(-y, y, x), r, y);
-}
-
-__device__ __forceinline__ double cbrt_nr(double x) {
-    const double y = (double)cbrtf((float)x);
-    const double y2 = y * y;
-    const double r = (double)(1.0f / (3.0f * (float)y2));
-    return fma(fma(-y2, y, x), r, y);
-}
-
-// 2 atanh(s) = 2 (s + s^3/3 + ... + s^19/19)
-__device__ __forceinline__ double two_atanh_series(double s) {
-    const double z = s * s;
-    double p = 1.0 / 19.0;
-    p = fma(p, z, 1.0 / 17.0);
-    p = fma(p, z, 1.0 / 15.0);
-    p = fma(p, z, 1.0 / 13.0);
-    p = fma(p, z, 1.0 / 11.0);
-    p = fma(p, z, 1.0 / 9.0);
-    p = fma(p, z, 1.0 / 7.0);
-    p = fma(p, z, 1.0 / 5.0);
-    p = fma(p, z, 1.0 / 3.0);
-    p = fma(p, z, 1.0);
-    return 2.0 * s * p;
-}
-
-__device__ __forceinline__ double ln_series(double x) {
-    long long b = __double_as_longlong(x);
-    int e = (int)((b >> 52) & 0x7ff) - 1023;
-    double m = __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);   // [1, 2)
-    if (m > 1.4142135623730951) {
-        m *= 0.5;
-        e += 1;
+__device__ __forceinline__ dfl df_ln1p(dfl u) {
+    if (u.hi < 0.41421356f) return df_two_atanh(df_div(u, df_add(DF(2.0), u)));
+    dfl x = df_add(DF(1.0), u);
+    int e;
+    frexpf(x.hi, &e);                        // x.hi = m 2^e, m in [0.5, 1)
+    x = dfl{ldexpf(x.hi, -e), ldexpf(x.lo, -e)};
+    if (x.hi < 0.70710678f) {
+        x = dfl{2.f * x.hi, 2.f * x.lo};
+        --e;
     }
-    const double s = (m - 1.0) * rcp_nr(m + 1.0);
-    return fma((double)e, 0.69314718055994530942, two_atanh_series(s));
+    const dfl s = df_div(df_sub(x, DF(1.0)), df_add(x, DF(1.0)));
+    return df_add(df_two_atanh(s), df_mulf(DF(0.69314718055994530942), (float)e));
 }
 
-// ln(1 + u), u > 0
-__device__ __forceinline__ double ln1p_series(double u) {
-    if (u < 0.41421356237309505) return two_atanh_series(u * rcp_nr(2.0 + u));
-    return ln_series(1.0 + u);
+__device__ __forceinline__ dfl df_exp_neg(dfl S) {
+    const float k = rintf(S.hi * 1.44269504f);
+    const dfl x = df_neg(df_sub(S, df_mulf(DF(0.69314718055994530942), k)));   // -r
+    dfl p = DF(1.0 / 479001600.0);           // 1/12!
+    p = df_add(df_mul(p, x), DF(1.0 / 39916800.0));
+    p = df_add(df_mul(p, x), DF(1.0 / 3628800.0));
+    p = df_add(df_mul(p, x), DF(1.0 / 362880.0));
+    p = df_add(df_mul(p, x), DF(1.0 / 40320.0));
+    p = df_add(df_mul(p, x), DF(1.0 / 5040.0));
+    p = df_add(df_mul(p, x), DF(1.0 / 720.0));
+    p = df_add(df_mul(p, x), DF(1.0 / 120.0));
+    p = df_add(df_mul(p, x), DF(1.0 / 24.0));
+    p = df_add(df_mul(p, x), DF(1.0 / 6.0));
+    p = df_add(df_mul(p, x), DF(0.5));
+    p = df_add(df_mul(p, x), DF(1.0));
+    p = df_add(df_mul(p, x), DF(1.0));
+    const float sc = ldexpf(1.f, -(int)k);
+    return dfl{p.hi * sc, p.lo * sc};
 }
 
-__device__ __forceinline__ double exp_neg(double S) {
-    if (S > 40.0) return 0.0;
-    const double k = rint(S * 1.4426950408889634074);
-    const double r = fma(-k, 0.69314718055994530942, S);     // S - k ln2
-    const double x = -r;
-    double p = 1.0 / 6227020800.0;                 // 1/13!
-    p = fma(p, x, 1.0 / 479001600.0);
-    p = fma(p, x, 1.0 / 39916800.0);
-    p = fma(p, x, 1.0 / 3628800.0);
-    p = fma(p, x, 1.0 / 362880.0);
-    p = fma(p, x, 1.0 / 40320.0);
-    p = fma(p, x, 1.0 / 5040.0);
-    p = fma(p, x, 1.0 / 720.0);
-    p = fma(p, x, 1.0 / 120.0);
-    p = fma(p, x, 1.0 / 24.0);
-    p = fma(p, x, 1.0 / 6.0);
-    p = fma(p, x, 0.5);
-    p = fma(p, x, 1.0);
-    p = fma(p, x, 1.0);
-    const long long ki = (long long)k;
-    return p * __longlong_as_double((1023LL - ki) << 52);   // 2^-k, 0 <= k <= 58
-}
-
-__device__ __forceinline__ Q0 q0_point_mixed(double n, double s, double Z) {
-    Q0 r;
+__device__ __forceinline__ Q0M q0_point_df(double n, double s, double Z, const dfl *qd, const dfl *invhd) {
+    Q0M r;
     r.live = n > c_qm.n_min;
+    r.dqdn = 0.f;
+    r.dqds = 0.f;
     if (!r.live) {
+        r.j = -1;
+        r.B = 0.f;
         r.q0 = c_qm.q_min;
-        r.dqdn = 0.0;
-        r.dqds = 0.0;
         return r;
     }
     s = s > 0.0 ? s : 0.0;
     const double A = 0.031091, a1 = 0.2137;
     const double b1 = 7.5957, b2 = 3.5876, b3 = 1.6382, b4 = 0.49294;
     const double PI = 3.14159265358979323846;
-    const double kF = cbrt_nr(3.0 * PI * PI * n);
-    const double ikF = rcp_nr(kF);
-    const double rs = 1.9191582926775128 * ikF;             // (9 pi / 4)^(1/3) / k_F
-    const double srs = sqrt_nr(rs);
-    const double D = 2.0 * A * (b1 * srs + b2 * rs + b3 * rs * srs + b4 * rs * rs);
-    const double L = ln1p_series(rcp_nr(D));
-    const double eps = -2.0 * A * (1.0 + a1 * rs) * L;
-    const double in2 = rcp_nr(n * n);
-    const double G = -(Z / 36.0) * s * ikF * in2;
-    const double qraw = kF - (4.0 * PI / 3.0) * eps + G;
-    const double a = c_qm.q_cut;
-    const double t = qraw * (1.0 / a);
-    double S = 1.0 / 12.0;
+    const dfl nd = df_from(n), sd = df_from(s);
+    const dfl kF = df_cbrt(df_mul(nd, DF(3.0 * PI * PI)));
+    const dfl ikF = df_rcp(kF);
+    const dfl rs = df_mul(ikF, DF(1.9191582926775128));      // (9 pi / 4)^(1/3) / k_F
+    const dfl srs = df_sqrt(rs);
+    dfl poly = DF(b4);
+    poly = df_add(df_mul(poly, srs), DF(b3));
+    poly = df_add(df_mul(poly, srs), DF(b2));
+    poly = df_add(df_mul(poly, srs), DF(b1));
+    const dfl D = df_mul(df_mul(poly, srs), DF(2.0 * A));   // 2A (b1 rs^1/2 + b2 rs + b3 rs^3/2 + b4 rs^2)
+    const dfl L = df_ln1p(df_rcp(D));
+    const dfl eps = df_mul(df_mul(DF(-2.0 * A), df_add(DF(1.0), df_mul(DF(a1), rs))), L);
+    const dfl in2 = df_rcp(df_mul(nd, nd));
+    const dfl G = df_mul(df_mul(df_mul(DF(-Z / 36.0), sd), ikF), in2);
+    const dfl qraw = df_add(df_add(kF, df_mul(DF(-4.0 * PI / 3.0), eps)), G);
+    const dfl t = df_mul(qraw, DF(0.2));
+    dfl q0;
+    float e = 0.f, dS = 0.f;
+    if (t.hi > 1.5f) {
+        q0 = DF(5.0);
+    } else {
+        dfl S = DF(1.0 / 12.0);
 #pragma unroll
-    for (int m = 11; m >= 1; --m) S = fma(S, t, 1.0 / (double)m);
-    S *= t;
-    const double e = exp_neg(S);
-    const double q0 = a * (1.0 - e);
-    if (q0 < c_qm.q_min) {
+        for (int m = 11; m >= 1; --m) S = df_add(df_mul(S, t), DF(1.0 / (double)m));
+        S = df_mul(S, t);
+        const dfl ex = df_exp_neg(S);
+        q0 = df_mul(DF(5.0), df_sub(DF(1.0), ex));
+        e = ex.hi;
+        dS = 1.f;
+#pragma unroll
+        for (int m = 0; m < 11; ++m) dS = fmaf(dS, t.hi, 1.f);    // sum_{m=0}^{11} t^m
+    }
+    const dfl qmin = qd[0];
+    if (df_lt(q0, qmin)) {
+        r.j = 0;
+        r.B = 0.f;
         r.q0 = c_qm.q_min;
-        r.dqdn = 0.0;
-        r.dqds = 0.0;
         return r;
     }
-    r.q0 = q0;
-    // derivatives in FP32
-    float dh = 0.f;
-    if (S <= 40.0) {
-        const float tf = (float)t;
-        float dS = 1.f;
-#pragma unroll
-        for (int m = 0; m < 11; ++m) dS = fmaf(dS, tf, 1.f);    // sum_{m=0}^{11} t^m
-        dh = (float)e * dS;
+    r.q0 = df_to(q0);
+    int lo = 0, hi = NQ - 2;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (df_lt(q0, qd[mid])) hi = mid - 1;
+        else lo = mid;
     }
-    const float Df = (float)D, rsf = (float)rs, srsf = (float)srs, Lf = (float)L;
-    const float dD = 2.f * (float)A * (0.5f * (float)b1 / srsf + (float)b2 + 1.5f * (float)b3 * srsf +
-                                       2.f * (float)b4 * rsf);
-    const float deps = -2.f * (float)A * (float)a1 * Lf +
-                       2.f * (float)A * (1.f + (float)a1 * rsf) * dD / (Df * Df + Df);
-    const float inv_n = 1.f / (float)n;
-    const float kFf = (float)kF;
-    const float Gf = (float)G;
-    const float dq_dn = kFf * inv_n * (1.f / 3.f) + (float)(4.0 * PI / 9.0) * deps * rsf * inv_n -
-                        (7.f / 3.f) * Gf * inv_n;
-    const float dq_ds = -(float)(Z / 36.0) * (float)ikF * (float)in2;
-    r.dqdn = (double)(dh * dq_dn);
-    r.dqds = (double)(dh * dq_ds);
+    r.j = lo;
+    r.B = df_mul(df_sub(q0, qd[lo]), invhd[lo]).hi;
+    // derivatives: the sum in dq_raw/dn can cancel, so it is formed in
+    // double-float; the saturation factor and dq_raw/dsigma are plain products (FP32)
+    const float dh = e * dS;
+    const dfl dD = df_mul(DF(2.0 * A),
+                          df_add(df_add(df_div(DF(0.5 * b1), srs), DF(b2)),
+                                 df_add(df_mul(DF(1.5 * b3), srs), df_mul(DF(2.0 * b4), rs))));
+    const dfl deps = df_add(df_mul(DF(-2.0 * A * a1), L),
+                            df_div(df_mul(df_mul(DF(2.0 * A), df_add(DF(1.0), df_mul(DF(a1), rs))), dD),
+                                   df_add(df_mul(D, D), D)));
+    const dfl inv_n = df_rcp(nd);
+    const dfl dqn = df_mul(df_add(df_add(df_mul(kF, DF(1.0 / 3.0)), df_mul(df_mul(DF(4.0 * PI / 9.0), deps), rs)),
+                                  df_mul(DF(-7.0 / 3.0), G)),
+                           inv_n);
+    const float dq_dn = dqn.hi;
+    const float dq_ds = -(float)(Z / 36.0) * ikF.hi * in2.hi;
+    r.dqdn = dh * dq_dn;
+    r.dqds = dh * dq_ds;
     return r;
 }
 
@@ -281,6 +286,8 @@ template <typename T>
 struct QShared {
     double q[NQ];
     double invh[NQ];
+    dfl qd[NQ];      // the mesh and 1/h in double-float (FP32-mixed q0)
+    dfl invhd[NQ];
     T h[NQ];
     T d2[NQ * NQ];
 };
@@ -291,6 +298,8 @@ __device__ __forceinline__ void load_qshared(QShared<T> *qs) {
     for (int i = threadIdx.x; i < NQ; i += blockDim.x) {
         qs->q[i] = c_qm.q[i];
         qs->invh[i] = c_qm.invh[i];
+        qs->qd[i] = df_from(c_qm.q[i]);
+        qs->invhd[i] = df_from(c_qm.invh[i]);
         qs->h[i] = (T)c_qm.h[i];
     }
 }
@@ -329,30 +338,39 @@ __global__ void __launch_bounds__(256) k_zfwd(const SysDev *__restrict__ sys, co
             const int li = i / nz, z = i - li * nz;
             const double n = S.n[p0 + i];
             const double sg = S.sigma[p0 + i];
-            const Q0 q = sizeof(T) == 4 ? q0_point_mixed(n, sg, S.Z) : q0_point(n, sg, S.Z);
             Rec<T> r;
             T th[NQ];
-            if (q.live) {
-                const int j = q_interval(q.q0, qs->q);
-                const double Bd = (q.q0 - qs->q[j]) * qs->invh[j];
-                const T B = (T)Bd;
+            int j = -1;
+            T B = (T)0, ndqn = (T)0, ndqs = (T)0;
+            if (sizeof(T) == 4) {
+                const Q0M q = q0_point_df(n, sg, S.Z, qs->qd, qs->invhd);
+                j = q.j;
+                B = (T)q.B;
+                ndqn = (T)((float)n * q.dqdn);
+                ndqs = (T)((float)n * q.dqds);
+            } else {
+                const Q0 q = q0_point(n, sg, S.Z);
+                if (q.live) {
+                    j = q_interval(q.q0, qs->q);
+                    B = (T)((q.q0 - qs->q[j]) * qs->invh[j]);
+                    ndqn = (T)(n * q.dqdn);
+                    ndqs = (T)(n * q.dqds);
+                }
+            }
+            if (j >= 0) {
                 T p[NQ];
                 spline_p<T>(j, B, qs->h[j], qs->d2, p);
                 const T nn = (T)n;
 #pragma unroll
                 for (int a = 0; a < NQ; ++a) th[a] = nn * p[a];
-                r.B = B;
-                r.j = j;
-                r.ndqn = (T)(n * q.dqdn);
-                r.ndqs = (T)(n * q.dqds);
             } else {
 #pragma unroll
                 for (int a = 0; a < NQ; ++a) th[a] = (T)0;
-                r.B = (T)0;
-                r.j = -1;
-                r.ndqn = (T)0;
-                r.ndqs = (T)0;
             }
+            r.B = B;
+            r.j = j;
+            r.ndqn = ndqn;
+            r.ndqs = ndqs;
             rec[p0 + i] = r;
             cx<T> *dst = bufA + (size_t)z * L + li * 10;
 #pragma unroll
@@ -447,10 +465,11 @@ __device__ __forceinline__ XYTile xy_tile(const SysDev *__restrict__ sys, const 
     g.si = find_sys(prefix, nsys, t);
     const SysDev &S = sys[g.si];
     g.lt = t - prefix[g.si];
-    const int ncol = (S.nzh + S.W - 1) / S.W;
+    const int W = XPASS ? S.Wx : S.Wy;
+    const int ncol = (S.nzh + W - 1) / W;
     g.outer = g.lt / ncol;
-    g.kz0 = (g.lt - g.outer * ncol) * S.W;
-    g.wt = min(S.W, S.nzh - g.kz0);
+    g.kz0 = (g.lt - g.outer * ncol) * W;
+    g.wt = min(W, S.nzh - g.kz0);
     g.L = g.wt * NQ;
     if (XPASS) {
         g.nrows = S.nx;
@@ -854,12 +873,25 @@ __global__ void k_efinish(const SysDev *__restrict__ sys, int nsys) {
 template <typename T>
 __global__ void k_q0(int npts, const double *__restrict__ n, const double *__restrict__ s, double Z,
                      double *__restrict__ q0, double *__restrict__ dqdn, double *__restrict__ dqds) {
+    __shared__ dfl qd[NQ], ih[NQ];
+    if (threadIdx.x < NQ) {
+        qd[threadIdx.x] = df_from(c_qm.q[threadIdx.x]);
+        ih[threadIdx.x] = df_from(c_qm.invh[threadIdx.x]);
+    }
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npts) return;
-    const Q0 q = sizeof(T) == 4 ? q0_point_mixed(n[i], s[i], Z) : q0_point(n[i], s[i], Z);
-    q0[i] = q.q0;
-    dqdn[i] = q.dqdn;
-    dqds[i] = q.dqds;
+    if (sizeof(T) == 4) {
+        const Q0M q = q0_point_df(n[i], s[i], Z, qd, ih);
+        q0[i] = q.q0;
+        dqdn[i] = q.dqdn;
+        dqds[i] = q.dqds;
+    } else {
+        const Q0 q = q0_point(n[i], s[i], Z);
+        q0[i] = q.q0;
+        dqdn[i] = q.dqdn;
+        dqds[i] = q.dqds;
+    }
 }
 
 cudaError_t launch_q0(int prec, int npts, const double *n, const double *s, double Z, double *q0, double *dqdn,
@@ -934,37 +966,58 @@ cudaError_t init_kernels(size_t maxsmem) {
 }
 
 template <typename T>
-static cudaError_t launch_all_t(const LaunchSet &ls, cudaStream_t st, cudaEvent_t *ev) {
+static void launch_stage_t(const LaunchSet &ls, int stage, cudaStream_t st) {
     const typename KTab<T>::V *tab = reinterpret_cast<const typename KTab<T>::V *>(ls.table);
-    int k = 0;
-    if (ev) cudaEventRecord(ev[k++], st);
-    k_zfwd<T><<<ls.grid[0], 256, ls.smem[0], st>>>(ls.sys, ls.prefix[0], ls.nsys, ls.total[0]);
-    if (ev) cudaEventRecord(ev[k++], st);
-    k_xy<T, 0><<<ls.grid[1], 256, ls.smem[1], st>>>(ls.sys, ls.prefix[1], ls.nsys, ls.total[1], ls.twmax[1],
-                                                     ls.bufelems[1], ls.nbuf[1], ls.err);
-    if (ev) cudaEventRecord(ev[k++], st);
-    k_xy<T, 2><<<ls.grid[2], 256, ls.smem[2], st>>>(ls.sys, ls.prefix[2], ls.nsys, ls.total[2], ls.twmax[2],
-                                                     ls.bufelems[2], ls.nbuf[2], ls.err);
-    if (ev) cudaEventRecord(ev[k++], st);
-    k_contract<T><<<ls.grid[4], 256, ls.smem[4], st>>>(ls.sys, ls.prefix[4], ls.nsys, ls.total[4], ls.maxspan,
-                                                        tab, ls.err);
-    if (ev) cudaEventRecord(ev[k++], st);
-    k_xy<T, 3><<<ls.grid[2], 256, ls.smem[2], st>>>(ls.sys, ls.prefix[2], ls.nsys, ls.total[2], ls.twmax[2],
-                                                     ls.bufelems[2], ls.nbuf[2], ls.err);
-    if (ev) cudaEventRecord(ev[k++], st);
-    k_xy<T, 1><<<ls.grid[1], 256, ls.smem[1], st>>>(ls.sys, ls.prefix[1], ls.nsys, ls.total[1], ls.twmax[1],
-                                                     ls.bufelems[1], ls.nbuf[1], ls.err);
-    if (ev) cudaEventRecord(ev[k++], st);
-    k_zinv<T><<<ls.grid[3], 256, ls.smem[3], st>>>(ls.sys, ls.prefix[3], ls.nsys, ls.total[3], ls.twmax[3],
-                                                    ls.bufelems[3], ls.recelems, ls.abelems, ls.err);
-    if (ev) cudaEventRecord(ev[k++], st);
-    k_efinish<<<ls.nsys < 1024 ? ls.nsys : 1024, 256, 0, st>>>(ls.sys, ls.nsys);
-    if (ev) cudaEventRecord(ev[k++], st);
+    switch (stage) {
+        case 0:
+            k_zfwd<T><<<ls.grid[0], 256, ls.smem[0], st>>>(ls.sys, ls.prefix[0], ls.nsys, ls.total[0]);
+            break;
+        case 1:
+        case 5:
+            if (stage == 1)
+                k_xy<T, 0><<<ls.grid[1], 256, ls.smem[1], st>>>(ls.sys, ls.prefix[1], ls.nsys, ls.total[1],
+                                                                 ls.twmax[1], ls.bufelems[1], ls.nbuf[1], ls.err);
+            else
+                k_xy<T, 1><<<ls.grid[1], 256, ls.smem[1], st>>>(ls.sys, ls.prefix[1], ls.nsys, ls.total[1],
+                                                                 ls.twmax[1], ls.bufelems[1], ls.nbuf[1], ls.err);
+            break;
+        case 2:
+        case 4:
+            if (stage == 2)
+                k_xy<T, 2><<<ls.grid[2], 256, ls.smem[2], st>>>(ls.sys, ls.prefix[2], ls.nsys, ls.total[2],
+                                                                 ls.twmax[2], ls.bufelems[2], ls.nbuf[2], ls.err);
+            else
+                k_xy<T, 3><<<ls.grid[2], 256, ls.smem[2], st>>>(ls.sys, ls.prefix[2], ls.nsys, ls.total[2],
+                                                                 ls.twmax[2], ls.bufelems[2], ls.nbuf[2], ls.err);
+            break;
+        case 3:
+            k_contract<T><<<ls.grid[4], 256, ls.smem[4], st>>>(ls.sys, ls.prefix[4], ls.nsys, ls.total[4],
+                                                                ls.maxspan, tab, ls.err);
+            break;
+        case 6:
+            k_zinv<T><<<ls.grid[3], 256, ls.smem[3], st>>>(ls.sys, ls.prefix[3], ls.nsys, ls.total[3], ls.twmax[3],
+                                                            ls.bufelems[3], ls.recelems, ls.abelems, ls.err);
+            break;
+        default:
+            k_efinish<<<ls.nsys < 1024 ? ls.nsys : 1024, 256, 0, st>>>(ls.sys, ls.nsys);
+            break;
+    }
+}
+
+cudaError_t launch_stage(const LaunchSet &ls, int prec, int stage, cudaStream_t st) {
+    if (prec == 1) launch_stage_t<float>(ls, stage, st);
+    else launch_stage_t<double>(ls, stage, st);
     return cudaGetLastError();
 }
 
 cudaError_t launch_all(const LaunchSet &ls, int prec, cudaStream_t st, cudaEvent_t *ev) {
-    return prec == 1 ? launch_all_t<float>(ls, st, ev) : launch_all_t<double>(ls, st, ev);
+    if (ev) cudaEventRecord(ev[0], st);
+    for (int k = 0; k < NSTAGE; ++k) {
+        if (prec == 1) launch_stage_t<float>(ls, k, st);
+        else launch_stage_t<double>(ls, k, st);
+        if (ev) cudaEventRecord(ev[k + 1], st);
+    }
+    return cudaGetLastError();
 }
 
 size_t contract_smem(int prec, int maxspan) {

@@ -34,6 +34,8 @@ constexpr int NSTAGE = 8;   // kernel launches per evaluation
 constexpr int NKIND = 5;    // tile kinds
 // Enqueue all stages; if ev != nullptr, record ev[0..NSTAGE] around them.
 cudaError_t launch_all(const LaunchSet &ls, int prec, cudaStream_t st, cudaEvent_t *ev = nullptr);
+// one stage: 0 zfwd, 1 yfwd, 2 xfwd, 3 contract, 4 xinv, 5 yinv, 6 zinv, 7 efinish
+cudaError_t launch_stage(const LaunchSet &ls, int prec, int stage, cudaStream_t st);
 const char *stage_name(int i);
 cudaError_t upload_qmesh(const QMeshDev &q);
 cudaError_t launch_q0(int prec, int npts, const double *n, const double *s, double Z, double *q0, double *dqdn,

@@ -165,3 +165,43 @@ def test_errors_are_reported():
             B.vdwgb_init_cuda(h, 99, 0)
     finally:
         B.vdwgb_finalize(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_q0_step_matches_oracle(prec):
+    # q0 and its derivatives exactly as each form computes them inside the
+    # evaluation (FP32-mixed: double-float q0, FP32 derivatives).
+    rng = np.random.default_rng(5)
+    n = 10 ** rng.uniform(-11, 2, 4000)
+    s = 10 ** rng.uniform(-12, 3, 4000) * n ** (8 / 3) * rng.uniform(0, 50, 4000)
+    s[:50] = 0.0
+    for fn in (1, 2):
+        q, dn, ds = B.vdwgb_q0(n, s, fn, prec)
+        rq, rdn, rds = vdw.q0_of(n, s, fn)
+        assert np.max(np.abs(q - rq) / rq) < (1e-12 if prec == 0 else 1e-11)
+        tol = 1e-12 if prec == 0 else 1e-5
+        for got, ref in ((dn, rdn), (ds, rds)):
+            big = np.abs(ref) > 1e-6 * np.max(np.abs(ref))
+            assert np.max(np.abs(got[big] - ref[big]) / np.abs(ref[big])) < tol
+
+
+def test_autotuned_tiles_give_identical_results():
+    # Tile shapes only regroup independent lines and butterflies: the tuned
+    # plan must reproduce the default plan bit for bit.
+    s = inputs.make_system((40, 36, 30), np.diag([9.0, 8.0, 7.5]), [(3.0, 1.4, (4.0, 3.0, 3.0))], 1)
+    n, sg = s.n.numpy(), s.sigma.numpy()
+    for prec in (B.FP32_MIXED, B.FP64):
+        B.vdwgb_set_autotune(False)
+        f0 = B.Functional(s.shape, s.cell, 1, prec)
+        r0 = f0.calculate(n, sg)
+        f0.close()
+        B.vdwgb_set_autotune(True)
+        try:
+            f1 = B.Functional(s.shape, s.cell, 1, prec)
+            info = B.vdwgb_plan_info(f1.h)
+            r1 = f1.calculate(n, sg)
+            f1.close()
+        finally:
+            B.vdwgb_set_autotune(False)
+        assert info["autotuned"] == 1 and info["launches"] == 8
+        assert r1[0] == r0[0] and np.array_equal(r1[1], r0[1]) and np.array_equal(r1[2], r0[2])
