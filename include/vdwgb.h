@@ -262,6 +262,38 @@ int vdwgb_server_stats(vdwgb_server s, vdwgb_server_stats_t *out);
  * everything, set *s = NULL.  Requests not yet reported are dropped. */
 int vdwgb_server_free(vdwgb_server *s);
 
+/* ---- allocation-free evaluation ------------------------------------------
+ * The paper has no counterpart of this entry point; it serves host codes that
+ * must not allocate device memory where they evaluate (a code running inside
+ * its own memory pool or budget, or in a region where cudaMalloc is not
+ * allowed).  It computes what vdwgb_calculate_device computes for a handle of
+ * the same functional and cell in VDWGB_FP32_MIXED precision with cubic
+ * interpolation, without a handle and without allocating: every scratch
+ * array (work buffer, point records, k-point order, energy partials, plan
+ * descriptors) lives in one fixed device array of the library (about
+ * 3.4 MiB, held by every GPU that loads the library).
+ *
+ * Limits: each axis <= 64, nx*ny*nz <= 32768, nx*ny*(nz/2+1) <= 17408, axis
+ * lengths with prime factors 2, 3, 5, 7 only; beyond them EINVAL.
+ * ESTATE if the device has no resident kernel table yet: call
+ * vdwgb_kernel_table(device, NULL, NULL, NULL) once before (that call
+ * allocates).  The first call on a device looks up the device address of the
+ * fixed array, with the device made current; make that first call before any
+ * stream capture.
+ *
+ * Arguments: cell9 as in vdwgb_set_unit_cell (host, row-major lattice
+ * vectors, Bohr); d_rho, d_sigma (read), d_dedrho, d_dedsigma (written) are
+ * DEVICE arrays of nx*ny*nz doubles in C order, d_energy one device double;
+ * all enqueued on cuda_stream (NULL = legacy default stream), nothing waits.
+ * All calls on one device share its fixed array and leave their data in it
+ * (nothing needs clearing: each call overwrites what it reads).  Calls on one
+ * device whose GPU work overlaps (on two streams, say) race on the array and
+ * give wrong results: order them, e.g. on one stream.  Each device has its
+ * own array. */
+int vdwgb_calculate_noalloc(int device, int functional, int nx, int ny, int nz, const double *cell9,
+                            const double *d_rho, const double *d_sigma, double *d_dedrho,
+                            double *d_dedsigma, double *d_energy, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -81,6 +81,7 @@ _SIGS.update({
                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "vdwgb_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerStats)]),
     "vdwgb_server_free": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p)]),
+    "vdwgb_calculate_noalloc": (ctypes.c_int, [ctypes.c_int] * 5 + [ctypes.c_void_p] * 7),
 })
 
 
@@ -155,6 +156,16 @@ def vdwgb_calculate_device(h, rho, sigma, dedrho, dedsigma, energy, stream=0):
     """Device tensors (float64, contiguous); ``stream`` is a raw cudaStream_t."""
     _ck(lib().vdwgb_calculate_device(h, _ptr(rho), _ptr(sigma), _ptr(dedrho), _ptr(dedsigma), _ptr(energy),
                                      ctypes.c_void_p(int(stream))), "vdwgb_calculate_device")
+
+
+def vdwgb_calculate_noalloc(device, functional, shape, cell, rho, sigma, dedrho, dedsigma, energy, stream=0):
+    """Handle-free evaluation without device allocation (device tensors,
+    float64, contiguous; FP32-mixed, cubic).  The kernel table of ``device``
+    must be resident (``vdwgb_kernel_table``)."""
+    cell = np.ascontiguousarray(np.asarray(cell, dtype=np.float64).reshape(9))
+    _ck(lib().vdwgb_calculate_noalloc(int(device), int(functional), int(shape[0]), int(shape[1]), int(shape[2]),
+                                      cell.ctypes.data, _ptr(rho), _ptr(sigma), _ptr(dedrho), _ptr(dedsigma),
+                                      _ptr(energy), ctypes.c_void_p(int(stream))), "vdwgb_calculate_noalloc")
 
 
 def vdwgb_calculate_simple(h, rho, sigma, dedrho, dedsigma):

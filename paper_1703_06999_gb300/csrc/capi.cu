@@ -76,6 +76,19 @@ int vdwgb::device_setup(int device) {
     return 0;
 }
 
+// Set-up state of a device if vdwgb_* set it up earlier (never sets up or
+// allocates).
+bool vdwgb::device_peek(int device, int *sms, size_t *maxsmem, int **err) {
+    if (device < 0 || device >= 64) return false;
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    const DevInfo &d = g_dev[device];
+    if (!d.ready) return false;
+    *sms = d.sms;
+    *maxsmem = d.maxsmem;
+    *err = d.err;
+    return true;
+}
+
 // ---------------------------------------------------------------------------
 // FFT plan of one axis
 // ---------------------------------------------------------------------------

@@ -41,6 +41,7 @@ namespace vdwgb {
 int fail(int code, const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *what);
 int device_setup(int device);
+bool device_peek(int device, int *sms, size_t *maxsmem, int **err);
 // plan and allocate a handle (cell already set); alloc_stream != 0 makes
 // every allocation and upload stream-ordered on it
 int handle_init(vdwgb_data *h, int device, int precision, cudaStream_t alloc_stream);

@@ -389,6 +389,23 @@ cudaError_t table_get(int device, TableRefs &out) {
     return cudaSuccess;
 }
 
+// The resident table of `device` if it was already built (never builds or
+// allocates).
+bool table_peek(int device, TableRefs &out) {
+    if (device < 0 || device >= 64) return false;
+    std::lock_guard<std::mutex> lk(g_mu);
+    const DevTable &t = g_tab[device];
+    if (!t.built) return false;
+    out.phir = t.phir;
+    out.phik = t.phik;
+    out.cub64 = t.cub64;
+    out.lin64 = t.lin64;
+    out.cub32 = t.cub32;
+    out.lin32 = t.lin32;
+    out.seconds = t.seconds;
+    return true;
+}
+
 double table_seconds(int device) {
     if (device < 0 || device >= 64) return 0.0;
     std::lock_guard<std::mutex> lk(g_mu);

@@ -18,6 +18,7 @@ struct TableRefs {
 // Build (once per device and process) and return the resident table.
 cudaError_t table_get(int device, TableRefs &out);
 double table_seconds(int device);
+bool table_peek(int device, TableRefs &out);
 cudaError_t table_phi(int device, int npts, const double *d1, const double *d2, double *out);
 void host_qmesh(QMeshDev &q);
 
