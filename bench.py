@@ -308,12 +308,14 @@ def main():
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clk = ClockSampler(local)
+    torch.cuda.profiler.start()             # profilers started with capture off record the timed steps only
     for k in range(args.steps):
         flush.zero_()                       # L2 flushed between timed steps (outside the events)
         evs[k][0].record(stream)
         B.vdwgb_batch_calculate_device(bt, ns, ss, dn, ds, en, sp)
         evs[k][1].record(stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     clocks = clk.stop()
     if world > 1:
         torch.distributed.barrier()
