@@ -287,7 +287,7 @@ static void set_tiles(vdwgb_data *h, int LZ, int LZi, int Wy, int Wx, int nby, i
     L.bufelems[0] = 0;
     L.bufelems[3] = LZi * nzh * NQ;
     L.recelems = LZi * nz;
-    L.abelems = nz * 10 * LZi;
+    L.abelems = nz * z_ld(LZi);
     L.bufelems[1] = ny * Wy * NQ;
     L.bufelems[2] = nx * Wx * NQ;
     L.nbuf[0] = L.nbuf[3] = 0;

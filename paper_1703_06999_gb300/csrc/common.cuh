@@ -224,13 +224,13 @@ __device__ __forceinline__ void dft(cx<T> *v) {
 }
 
 // One Stockham stage (radix R) over `nlines` lines held in shared memory:
-// element i of line l sits at buf[i * nlines + l].  Thread tid works on line
+// element i of line l sits at buf[i * ld + l] (ld >= nlines).  Thread tid works on line
 // tid % nlines and butterflies j = tid / nlines, + jstep, ... (jstep =
 // blockDim / nlines; the last blockDim % nlines threads idle), so the loop
 // needs no division; q = j / Ns and jm = j % Ns are carried along.
 // Ns = product of the radices already applied.
 template <int R, bool INV, typename T>
-__device__ __forceinline__ void fft_stage(const cx<T> *in, cx<T> *out, int n, int Ns, int nlines, int line,
+__device__ __forceinline__ void fft_stage(const cx<T> *in, cx<T> *out, int n, int Ns, int ld, int line,
                                           int j0, int jstep, const cx<T> *tw) {
     const int nb = n / R;
     const int tws = n / (Ns * R);
@@ -239,7 +239,7 @@ __device__ __forceinline__ void fft_stage(const cx<T> *in, cx<T> *out, int n, in
     for (int j = j0; j < nb; j += jstep) {
         cx<T> v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = in[(j + r * nb) * nlines + line];
+        for (int r = 0; r < R; ++r) v[r] = in[(j + r * nb) * ld + line];
         if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
@@ -251,7 +251,7 @@ __device__ __forceinline__ void fft_stage(const cx<T> *in, cx<T> *out, int n, in
         dft<R, INV>(v);
         const int base = q * Ns * R + jm;
 #pragma unroll
-        for (int r = 0; r < R; ++r) out[(base + r * Ns) * nlines + line] = v[r];
+        for (int r = 0; r < R; ++r) out[(base + r * Ns) * ld + line] = v[r];
         jm += jstep;
         while (jm >= Ns) {
             jm -= Ns;
@@ -260,11 +260,11 @@ __device__ __forceinline__ void fft_stage(const cx<T> *in, cx<T> *out, int n, in
     }
 }
 
-// Full 1-D transforms of `nlines` lines (unnormalised), layout [i][line].
+// Full 1-D transforms of `nlines` lines (unnormalised), layout [i][ld].
 // Ping-pongs between a and b; returns the buffer that holds the result.
 // Ends with a barrier.  Requires nlines <= blockDim.x.
 template <bool INV, typename T>
-__device__ cx<T> *fft_lines(cx<T> *a, cx<T> *b, const AxisPlan &p, int nlines, const cx<T> *tw) {
+__device__ cx<T> *fft_lines(cx<T> *a, cx<T> *b, const AxisPlan &p, int nlines, int ld, const cx<T> *tw) {
     const int jstep = blockDim.x / nlines;
     const int j0 = threadIdx.x / nlines;
     const int line = threadIdx.x - j0 * nlines;
@@ -274,12 +274,12 @@ __device__ cx<T> *fft_lines(cx<T> *a, cx<T> *b, const AxisPlan &p, int nlines, c
         const int R = p.rad[s];
         if (active) {
             switch (R) {
-                case 2: fft_stage<2, INV>(a, b, p.n, Ns, nlines, line, j0, jstep, tw); break;
-                case 3: fft_stage<3, INV>(a, b, p.n, Ns, nlines, line, j0, jstep, tw); break;
-                case 4: fft_stage<4, INV>(a, b, p.n, Ns, nlines, line, j0, jstep, tw); break;
-                case 5: fft_stage<5, INV>(a, b, p.n, Ns, nlines, line, j0, jstep, tw); break;
-                case 7: fft_stage<7, INV>(a, b, p.n, Ns, nlines, line, j0, jstep, tw); break;
-                default: fft_stage<8, INV>(a, b, p.n, Ns, nlines, line, j0, jstep, tw); break;
+                case 2: fft_stage<2, INV>(a, b, p.n, Ns, ld, line, j0, jstep, tw); break;
+                case 3: fft_stage<3, INV>(a, b, p.n, Ns, ld, line, j0, jstep, tw); break;
+                case 4: fft_stage<4, INV>(a, b, p.n, Ns, ld, line, j0, jstep, tw); break;
+                case 5: fft_stage<5, INV>(a, b, p.n, Ns, ld, line, j0, jstep, tw); break;
+                case 7: fft_stage<7, INV>(a, b, p.n, Ns, ld, line, j0, jstep, tw); break;
+                default: fft_stage<8, INV>(a, b, p.n, Ns, ld, line, j0, jstep, tw); break;
             }
         }
         __syncthreads();

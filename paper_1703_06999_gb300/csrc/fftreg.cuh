@@ -1,0 +1,213 @@
+// Register-resident FFT codelets and a two-pass line transform for axis
+// lengths known at compile time.
+//
+// A length N = N1 * N2 transform of many lines held in shared memory (element
+// i of line l at buf[i * ld + l]) runs as two passes (Cooley-Tukey, Sec. 3
+// uses a library FFT; this is the GB300 replacement):
+//   pass A: for each (line, j2): the N1 elements j1 * N2 + j2 are loaded into
+//           registers, transformed by a length-N1 codelet, multiplied by the
+//           twiddles W_N^(j2 k1) and stored to scratch at (k1 * N2 + j2);
+//   pass B: for each (line, k1): the N2 scratch elements k1 * N2 + j2 are
+//           transformed by a length-N2 codelet and stored back at k1 + N1 k2.
+// Each pass is one barrier; codelet twiddles are compile-time constants.
+#pragma once
+#include "common.cuh"
+
+namespace vdwgb {
+
+// ---- compile-time cos and sin (Taylor series on an octant) ---------------
+constexpr double kPiC = 3.14159265358979323846264338327950288;
+
+constexpr double taylor_sin(double x) {   // |x| <= pi / 4
+    double x2 = x * x, term = x, sum = x;
+    for (int k = 1; k < 14; ++k) {
+        term *= -x2 / (double)((2 * k) * (2 * k + 1));
+        sum += term;
+    }
+    return sum;
+}
+
+constexpr double taylor_cos(double x) {   // |x| <= pi / 4
+    double x2 = x * x, term = 1.0, sum = 1.0;
+    for (int k = 1; k < 14; ++k) {
+        term *= -x2 / (double)((2 * k - 1) * (2 * k));
+        sum += term;
+    }
+    return sum;
+}
+
+constexpr double sin_oct(double a);
+constexpr double cos_oct(double a) {        // a in [0, 2 pi]
+    return a > kPiC           ? cos_oct(2.0 * kPiC - a)
+           : a > kPiC / 2     ? -cos_oct(kPiC - a)
+           : a > kPiC / 4     ? sin_oct(kPiC / 2 - a)
+                              : taylor_cos(a);
+}
+constexpr double sin_oct(double a) {
+    return a > kPiC           ? -sin_oct(2.0 * kPiC - a)
+           : a > kPiC / 2     ? sin_oct(kPiC - a)
+           : a > kPiC / 4     ? cos_oct(kPiC / 2 - a)
+                              : taylor_sin(a);
+}
+
+// exp(-2 pi i m / N) for m = 0..N-1 (the forward DFT's root powers)
+template <int N, typename T>
+struct RootTab {
+    T c[N], s[N];
+    constexpr RootTab() : c(), s() {
+        for (int m = 0; m < N; ++m) {
+            // exact zeros and ones at the quarter turns
+            if (4 * m == N || 4 * m == 3 * N) c[m] = (T)0;
+            else c[m] = (T)cos_oct(2.0 * kPiC * (double)m / (double)N);
+            if (2 * m == N || m == 0) s[m] = (T)0;
+            else s[m] = (T)-sin_oct(2.0 * kPiC * (double)m / (double)N);
+        }
+    }
+};
+
+// ---- codelets: in-place DFT of N registers, natural order in and out ------
+template <int N>
+__host__ __device__ constexpr int codelet_split() {     // first factor P of a composite N = P * Q
+    return N % 4 == 0 ? 4 : N % 2 == 0 ? 2 : N % 3 == 0 ? 3 : N % 5 == 0 ? 5 : 7;
+}
+
+template <int N>
+__host__ __device__ constexpr bool codelet_base() {
+    return N == 1 || N == 2 || N == 3 || N == 4 || N == 5 || N == 7 || N == 8;
+}
+
+template <int N, bool INV, typename T>
+__device__ __forceinline__ void dftr(cx<T> *v);
+
+template <int N, bool INV, typename T>
+__device__ __forceinline__ void dftr_composite(cx<T> *v) {
+    constexpr int P = codelet_split<N>();
+    constexpr int Q = N / P;
+    constexpr RootTab<N, T> W{};
+    cx<T> w[N];   // w[k1 * Q + q]: length-P transform of column q, twiddled
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        cx<T> u[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) u[p] = v[q + Q * p];
+        dftr<P, INV>(u);
+#pragma unroll
+        for (int k1 = 0; k1 < P; ++k1) {
+            const int m = q * k1;
+            if (m != 0) {
+                const T c = W.c[m], s = INV ? -W.s[m] : W.s[m];
+                u[k1] = cx<T>{u[k1].x * c - u[k1].y * s, u[k1].x * s + u[k1].y * c};
+            }
+            w[k1 * Q + q] = u[k1];
+        }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) {
+        cx<T> z[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) z[q] = w[k1 * Q + q];
+        dftr<Q, INV>(z);
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2) v[k1 + P * k2] = z[k2];
+    }
+}
+
+template <int N, bool INV, typename T>
+__device__ __forceinline__ void dftr(cx<T> *v) {
+    if constexpr (N == 1) {
+    } else if constexpr (codelet_base<N>()) {
+        dft<N, INV>(v);
+    } else {
+        dftr_composite<N, INV>(v);
+    }
+}
+
+// ---- two-pass transform of `nlines` lines in shared memory ---------------
+// a: data (element i of line l at a[i * ld + l]), overwritten by the result;
+// b: scratch of the same shape; tw: exp(-2 pi i m / N), m < N (forward).
+// All threads of the block must call; ends with a barrier.
+template <int N1, int N2, bool INV, typename T>
+__device__ __noinline__ void fft2p(cx<T> *a, cx<T> *b, int nlines, int ld, const cx<T> *tw) {
+    constexpr int N = N1 * N2;
+    const int nt = blockDim.x;
+    const int dl = nt % nlines, dj = nt / nlines;
+    {
+        int l = threadIdx.x % nlines, j2 = threadIdx.x / nlines;
+        for (; j2 < N2;) {
+            cx<T> v[N1];
+            const cx<T> *src = a + (size_t)j2 * ld + l;
+#pragma unroll
+            for (int j1 = 0; j1 < N1; ++j1) v[j1] = src[(size_t)j1 * N2 * ld];
+            dftr<N1, INV>(v);
+#pragma unroll
+            for (int k1 = 1; k1 < N1; ++k1) {
+                cx<T> w = tw[j2 * k1];
+                if (INV) w.y = -w.y;
+                v[k1] = cmul(v[k1], w);
+            }
+            cx<T> *dst = b + (size_t)j2 * ld + l;
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) dst[(size_t)k1 * N2 * ld] = v[k1];
+            l += dl;
+            j2 += dj;
+            if (l >= nlines) {
+                l -= nlines;
+                ++j2;
+            }
+        }
+    }
+    __syncthreads();
+    {
+        int l = threadIdx.x % nlines, k1 = threadIdx.x / nlines;
+        for (; k1 < N1;) {
+            cx<T> v[N2];
+            const cx<T> *src = b + (size_t)k1 * N2 * ld + l;
+#pragma unroll
+            for (int j2 = 0; j2 < N2; ++j2) v[j2] = src[(size_t)j2 * ld];
+            dftr<N2, INV>(v);
+            cx<T> *dst = a + (size_t)k1 * ld + l;
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) dst[(size_t)k2 * N1 * ld] = v[k2];
+            l += dl;
+            k1 += dj;
+            if (l >= nlines) {
+                l -= nlines;
+                ++k1;
+            }
+        }
+    }
+    __syncthreads();
+    (void)N;
+}
+
+// Transform `nlines` lines of length p.n (layout [i][ld]); returns the buffer
+// holding the result (a or b).  FP32 lengths with a compiled two-pass split
+// use fft2p, all others the generic Stockham stages.  Ends with a barrier.
+template <bool INV, typename T>
+__device__ __forceinline__ cx<T> *fft_auto(cx<T> *a, cx<T> *b, const AxisPlan &p, int nlines, int ld,
+                                           const cx<T> *tw) {
+    if constexpr (sizeof(T) == 4) {
+        switch (p.n) {
+            case 16: fft2p<4, 4, INV>(a, b, nlines, ld, tw); return a;
+            case 24: fft2p<8, 3, INV>(a, b, nlines, ld, tw); return a;
+            case 32: fft2p<8, 4, INV>(a, b, nlines, ld, tw); return a;
+            case 40: fft2p<8, 5, INV>(a, b, nlines, ld, tw); return a;
+            case 48: fft2p<8, 6, INV>(a, b, nlines, ld, tw); return a;
+            case 64: fft2p<8, 8, INV>(a, b, nlines, ld, tw); return a;
+            case 72: fft2p<8, 9, INV>(a, b, nlines, ld, tw); return a;
+            case 80: fft2p<10, 8, INV>(a, b, nlines, ld, tw); return a;
+            case 96: fft2p<12, 8, INV>(a, b, nlines, ld, tw); return a;
+            case 112: fft2p<14, 8, INV>(a, b, nlines, ld, tw); return a;
+            case 128: fft2p<16, 8, INV>(a, b, nlines, ld, tw); return a;
+            case 144: fft2p<12, 12, INV>(a, b, nlines, ld, tw); return a;
+            case 160: fft2p<16, 10, INV>(a, b, nlines, ld, tw); return a;
+            case 192: fft2p<16, 12, INV>(a, b, nlines, ld, tw); return a;
+            case 224: fft2p<16, 14, INV>(a, b, nlines, ld, tw); return a;
+            case 256: fft2p<16, 16, INV>(a, b, nlines, ld, tw); return a;
+            default: break;
+        }
+    }
+    return fft_lines<INV>(a, b, p, nlines, ld, tw);
+}
+
+}  // namespace vdwgb

@@ -261,7 +261,7 @@ extern "C" int vdwgb_calculate_noalloc(int device, int functional, int nx, int n
     L.twmax[2] = nx;
     L.bufelems[3] = S.LZi * nzh * NQ;
     L.recelems = S.LZi * nz;
-    L.abelems = nz * 10 * S.LZi;
+    L.abelems = nz * z_ld(S.LZi);
     L.bufelems[1] = ny * S.Wy * NQ;
     L.bufelems[2] = nx * S.Wx * NQ;
     L.nbuf[1] = L.nbuf[2] = 3;

@@ -15,6 +15,7 @@
 #include "pipeline.h"
 #include "tma.cuh"
 #include "dfloat.cuh"
+#include "fftreg.cuh"
 
 namespace vdwgb {
 
@@ -309,7 +310,33 @@ __device__ __forceinline__ size_t align_up(size_t v, size_t a) { return (v + a -
 // ---------------------------------------------------------------------------
 // z-forward: theta and the real-to-complex transform along z.
 // Two real fields share one complex line: c = theta_{2m} + i theta_{2m+1}.
+// A tile is LZ consecutive (x, y) lines; in shared memory element z of
+// complex line li * 10 + c sits at buf[z * ld + li * 10 + c], with an odd
+// row stride ld so that threads on consecutive z hit different banks.
 // ---------------------------------------------------------------------------
+
+// Rows j and j + 1 of the helper-spline second-derivative table.
+template <typename T>
+__device__ __forceinline__ void d2_rows(int j, const T *d2s, T *r0, T *r1) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 *a = reinterpret_cast<const float4 *>(d2s + j * NQ);
+#pragma unroll
+        for (int k = 0; k < NQ / 4; ++k) {
+            const float4 u = a[k], v = a[k + NQ / 4];
+            r0[4 * k] = u.x; r0[4 * k + 1] = u.y; r0[4 * k + 2] = u.z; r0[4 * k + 3] = u.w;
+            r1[4 * k] = v.x; r1[4 * k + 1] = v.y; r1[4 * k + 2] = v.z; r1[4 * k + 3] = v.w;
+        }
+    } else {
+        const double2 *a = reinterpret_cast<const double2 *>(d2s + j * NQ);
+#pragma unroll
+        for (int k = 0; k < NQ / 2; ++k) {
+            const double2 u = a[k], v = a[k + NQ / 2];
+            r0[2 * k] = u.x; r0[2 * k + 1] = u.y;
+            r1[2 * k] = v.x; r1[2 * k + 1] = v.y;
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_zfwd(const SysDev *__restrict__ sys, const int *__restrict__ prefix,
                                               int nsys, int total) {
@@ -317,6 +344,7 @@ __global__ void __launch_bounds__(256) k_zfwd(const SysDev *__restrict__ sys, co
     QShared<T> *qs = reinterpret_cast<QShared<T> *>(smem);
     unsigned char *base = smem + align_up(sizeof(QShared<T>), 16);
     load_qshared(qs);
+    const int nt = blockDim.x;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
         const int si = find_sys(prefix, nsys, t);
         const SysDev &S = sys[si];
@@ -326,79 +354,111 @@ __global__ void __launch_bounds__(256) k_zfwd(const SysDev *__restrict__ sys, co
         const int l0 = lt * LZ;
         const int nl = min(LZ, nlines_tot - l0);
         const int L = 10 * nl;              // complex lines in this tile
+        const int ld = z_ld(nl);
         cx<T> *tw = reinterpret_cast<cx<T> *>(base);
-        cx<T> *bufA = tw + nz;
-        cx<T> *bufB = bufA + (size_t)nz * L;
+        cx<T> *bufA = tw + ((nz + 1) & ~1);
+        cx<T> *bufB = bufA + (size_t)nz * ld;
         const cx<T> *twg = reinterpret_cast<const cx<T> *>(S.tw[2]);
-        for (int i = threadIdx.x; i < nz; i += blockDim.x) tw[i] = twg[i];
+        for (int i = threadIdx.x; i < nz; i += nt) tw[i] = twg[i];
         __syncthreads();   // q tables and twiddles ready
         Rec<T> *rec = reinterpret_cast<Rec<T> *>(S.rec);
         const size_t p0 = (size_t)l0 * nz;
-        for (int i = threadIdx.x; i < nl * nz; i += blockDim.x) {
-            const int li = i / nz, z = i - li * nz;
-            const double n = S.n[p0 + i];
-            const double sg = S.sigma[p0 + i];
-            Rec<T> r;
-            T th[NQ];
-            int j = -1;
-            T B = (T)0, ndqn = (T)0, ndqs = (T)0;
-            if (sizeof(T) == 4) {
-                const Q0M q = q0_point_df(n, sg, S.Z, qs->qd, qs->invhd);
-                j = q.j;
-                B = (T)q.B;
-                ndqn = (T)((float)n * q.dqdn);
-                ndqs = (T)((float)n * q.dqds);
-            } else {
-                const Q0 q = q0_point(n, sg, S.Z);
-                if (q.live) {
-                    j = q_interval(q.q0, qs->q);
-                    B = (T)((q.q0 - qs->q[j]) * qs->invh[j]);
-                    ndqn = (T)(n * q.dqdn);
-                    ndqs = (T)(n * q.dqds);
+        const double *gn = S.n + p0, *gs = S.sigma + p0;
+        {
+            // points i = li * nz + z, walked without division
+            const int dz = nt % nz, dli = nt / nz;
+            int z = threadIdx.x % nz, li = threadIdx.x / nz;
+            for (; li < nl;) {
+                const int i = li * nz + z;
+                const double n = gn[i];
+                const double sg = gs[i];
+                Rec<T> r;
+                int j = -1;
+                T B = (T)0, ndqn = (T)0, ndqs = (T)0;
+                if (sizeof(T) == 4) {
+                    const Q0M q = q0_point_df(n, sg, S.Z, qs->qd, qs->invhd);
+                    j = q.j;
+                    B = (T)q.B;
+                    ndqn = (T)((float)n * q.dqdn);
+                    ndqs = (T)((float)n * q.dqds);
+                } else {
+                    const Q0 q = q0_point(n, sg, S.Z);
+                    if (q.live) {
+                        j = q_interval(q.q0, qs->q);
+                        B = (T)((q.q0 - qs->q[j]) * qs->invh[j]);
+                        ndqn = (T)(n * q.dqdn);
+                        ndqs = (T)(n * q.dqds);
+                    }
+                }
+                cx<T> *dst = bufA + (size_t)z * ld + li * 10;
+                if (j >= 0) {
+                    // theta_a = n p_a: spline part for all a, then the node
+                    // terms A [a == j] + B [a == j + 1] at the two dynamic slots
+                    T r0[NQ], r1[NQ];
+                    d2_rows<T>(j, qs->d2, r0, r1);
+                    const T h = qs->h[j], A = (T)1 - B;
+                    const T nn = (T)n;
+                    const T cA = nn * (A * A * A - A) * h * h / (T)6;
+                    const T cB = nn * (B * B * B - B) * h * h / (T)6;
+#pragma unroll
+                    for (int c = 0; c < 10; ++c)
+                        dst[c] = cx<T>{cA * r0[2 * c] + cB * r1[2 * c], cA * r0[2 * c + 1] + cB * r1[2 * c + 1]};
+                    T *dt = reinterpret_cast<T *>(dst);
+                    const T *d0 = qs->d2 + j * NQ;
+                    dt[j] = nn * A + cA * d0[j] + cB * d0[NQ + j];
+                    dt[j + 1] = nn * B + cA * d0[j + 1] + cB * d0[NQ + j + 1];
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 10; ++c) dst[c] = cx<T>{(T)0, (T)0};
+                }
+                r.B = B;
+                r.j = j;
+                r.ndqn = ndqn;
+                r.ndqs = ndqs;
+                rec[p0 + i] = r;
+                z += dz;
+                li += dli;
+                if (z >= nz) {
+                    z -= nz;
+                    ++li;
                 }
             }
-            if (j >= 0) {
-                T p[NQ];
-                spline_p<T>(j, B, qs->h[j], qs->d2, p);
-                const T nn = (T)n;
-#pragma unroll
-                for (int a = 0; a < NQ; ++a) th[a] = nn * p[a];
-            } else {
-#pragma unroll
-                for (int a = 0; a < NQ; ++a) th[a] = (T)0;
-            }
-            r.B = B;
-            r.j = j;
-            r.ndqn = ndqn;
-            r.ndqs = ndqs;
-            rec[p0 + i] = r;
-            cx<T> *dst = bufA + (size_t)z * L + li * 10;
-#pragma unroll
-            for (int c = 0; c < 10; ++c) dst[c] = cx<T>{th[2 * c], th[2 * c + 1]};
         }
         __syncthreads();
-        cx<T> *R = fft_lines<false>(bufA, bufB, S.ax[2], L, tw);
-        // unpack the two real transforms and store the half spectrum
+        cx<T> *R = fft_auto<false>(bufA, bufB, S.ax[2], L, ld, tw);
+        // unpack the two real transforms: X_{2c}(kz) = (Z(kz) + conj Z(-kz)) / 2,
+        // X_{2c+1}(kz) = (Z(kz) - conj Z(-kz)) / 2i; one thread writes the 10
+        // outputs of half h (c = 5h .. 5h+4) of one (line, kz)
         cx<T> *spec = reinterpret_cast<cx<T> *>(S.spec) + (size_t)l0 * nzh * NQ;
-        const int nout = nl * nzh * NQ;
-        for (int i = threadIdx.x; i < nout; i += blockDim.x) {
-            const int a = i % NQ;
-            const int rest = i / NQ;
-            const int kz = rest % nzh;
-            const int li = rest / nzh;
-            const int c = a >> 1;
-            const cx<T> zk = R[(size_t)kz * L + li * 10 + c];
-            const int km = kz == 0 ? 0 : nz - kz;
-            const cx<T> zm = R[(size_t)km * L + li * 10 + c];
-            cx<T> X;
-            if ((a & 1) == 0) {
-                X = {(T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y)};
-            } else {
-                // (zk - conj(zm)) / (2 i)
-                const T dx = zk.x - zm.x, dy = zk.y + zm.y;
-                X = {(T)0.5 * dy, (T)-0.5 * dx};
+        {
+            const int half = threadIdx.x & 1;
+            const int step = nt >> 1;
+            const int dk = step % nzh, dli = step / nzh;
+            int kz = (threadIdx.x >> 1) % nzh, li = (threadIdx.x >> 1) / nzh;
+            for (; li < nl;) {
+                const int km = kz == 0 ? 0 : nz - kz;
+                const cx<T> *zk = R + (size_t)kz * ld + li * 10 + 5 * half;
+                const cx<T> *zm = R + (size_t)km * ld + li * 10 + 5 * half;
+                cx<T> *out = spec + ((size_t)li * nzh + kz) * NQ + 10 * half;
+#pragma unroll
+                for (int c = 0; c < 5; ++c) {
+                    const cx<T> a = zk[c], b = zm[c];
+                    const T ex = (T)0.5 * (a.x + b.x), ey = (T)0.5 * (a.y - b.y);
+                    const T ox = (T)0.5 * (a.y + b.y), oy = (T)-0.5 * (a.x - b.x);
+                    if constexpr (sizeof(T) == 4) {
+                        *reinterpret_cast<float4 *>(out + 2 * c) = make_float4(ex, ey, ox, oy);
+                    } else {
+                        out[2 * c] = cx<T>{ex, ey};
+                        out[2 * c + 1] = cx<T>{ox, oy};
+                    }
+                }
+                kz += dk;
+                li += dli;
+                if (kz >= nzh) {
+                    kz -= nzh;
+                    ++li;
+                }
             }
-            spec[i] = X;
         }
         __syncthreads();
     }
@@ -544,20 +604,23 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_xy(const SysDev
             if (nbuf == 3 && tn < total) mbar_wait(&bar[cur ^ 1], ph[cur ^ 1]);
             return;
         }
-        cx<T> *R = fft_lines<INV>(bufs[cur], work, ap, g.L, tw);
-        // store the rows back (16-byte vectors)
-        cx<T> *spec = reinterpret_cast<cx<T> *>(S.spec);
-        if (sizeof(cx<T>) == 8) {
-            const int h = g.L >> 1;   // L = 20 W is even
-            for (int k = threadIdx.x; k < g.nrows * h; k += blockDim.x) {
-                const int r = k / h, e = k - r * h;
-                const float4 v = *reinterpret_cast<const float4 *>(R + (size_t)r * g.L + 2 * e);
-                *reinterpret_cast<float4 *>(spec + g.g0 + r * g.rowstride + 2 * e) = v;
-            }
-        } else {
-            for (int k = threadIdx.x; k < g.nrows * g.L; k += blockDim.x) {
-                const int r = k / g.L, e = k - r * g.L;
-                spec[g.g0 + r * g.rowstride + e] = R[(size_t)r * g.L + e];
+        cx<T> *R = fft_auto<INV>(bufs[cur], work, ap, g.L, g.L, tw);
+        // store the rows back (16-byte vectors), walking (row, e) without division
+        cx<T> *spec = reinterpret_cast<cx<T> *>(S.spec) + g.g0;
+        {
+            constexpr int PER = 16 / (int)sizeof(cx<T>);   // complex values per vector
+            const int h = g.L / PER;                         // L = 20 W: even
+            const int de = blockDim.x % h, dr = blockDim.x / h;
+            int e = threadIdx.x % h, r = threadIdx.x / h;
+            for (; r < g.nrows;) {
+                const float4 v = *reinterpret_cast<const float4 *>(R + (size_t)r * g.L + PER * e);
+                *reinterpret_cast<float4 *>(spec + r * g.rowstride + PER * e) = v;
+                e += de;
+                r += dr;
+                if (e >= h) {
+                    e -= h;
+                    ++r;
+                }
             }
         }
         fence_proxy_async();   // this tile's generic accesses before the next bulk writes
@@ -778,51 +841,98 @@ __global__ void __launch_bounds__(256) k_zinv(const SysDev *__restrict__ sys, co
         }
         const cx<T> *spec = ins[cur];
         const bool even = (nz % 2) == 0;
-        // Z_c[kz] = X_{2c}[kz] + i X_{2c+1}[kz]; Z_c[nz-kz] = conj(X_{2c}) + i conj(X_{2c+1})
-        for (int i = threadIdx.x; i < nl * nzh * 10; i += blockDim.x) {
-            const int c = i % 10;
-            const int rest = i / 10;
-            const int kz = rest % nzh;
-            const int li = rest / nzh;
-            cx<T> a = spec[(size_t)rest * NQ + 2 * c];
-            cx<T> b = spec[(size_t)rest * NQ + 2 * c + 1];
-            if (kz == 0 || (even && kz == nz / 2)) {
-                a.y = (T)0;
-                b.y = (T)0;
+        const int ld = z_ld(nl);
+        // Z_c[kz] = X_{2c}[kz] + i X_{2c+1}[kz]; Z_c[nz-kz] = conj(X_{2c}) + i conj(X_{2c+1});
+        // one thread handles half h (c = 5h .. 5h+4) of one (line, kz)
+        {
+            const int half = threadIdx.x & 1;
+            const int step = blockDim.x >> 1;
+            const int dk = step % nzh, dli = step / nzh;
+            int kz = (threadIdx.x >> 1) % nzh, li = (threadIdx.x >> 1) / nzh;
+            for (; li < nl;) {
+                const cx<T> *in = spec + ((size_t)li * nzh + kz) * NQ + 10 * half;
+                cx<T> *o1 = bufA + (size_t)kz * ld + li * 10 + 5 * half;
+                const int km = nz - kz;
+                const bool mirror = kz > 0 && km >= nzh;
+                const bool realbin = kz == 0 || (even && kz == nz / 2);
+                cx<T> *o2 = bufA + (size_t)(mirror ? km : 0) * ld + li * 10 + 5 * half;
+#pragma unroll
+                for (int c = 0; c < 5; ++c) {
+                    cx<T> a, b;
+                    if constexpr (sizeof(T) == 4) {
+                        const float4 v = *reinterpret_cast<const float4 *>(in + 2 * c);
+                        a = cx<T>{v.x, v.y};
+                        b = cx<T>{v.z, v.w};
+                    } else {
+                        a = in[2 * c];
+                        b = in[2 * c + 1];
+                    }
+                    if (realbin) {
+                        a.y = (T)0;
+                        b.y = (T)0;
+                    }
+                    o1[c] = cx<T>{a.x - b.y, a.y + b.x};
+                    if (mirror) o2[c] = cx<T>{a.x + b.y, b.x - a.y};
+                }
+                kz += dk;
+                li += dli;
+                if (kz >= nzh) {
+                    kz -= nzh;
+                    ++li;
+                }
             }
-            bufA[(size_t)kz * L + li * 10 + c] = cx<T>{a.x - b.y, a.y + b.x};
-            const int km = nz - kz;
-            if (kz > 0 && km >= nzh)
-                bufA[(size_t)km * L + li * 10 + c] = cx<T>{a.x + b.y, b.x - a.y};
         }
         __syncthreads();
-        cx<T> *R = fft_lines<true>(bufA, bufB, S.ax[2], L, tw);
+        cx<T> *R = fft_auto<true>(bufA, bufB, S.ax[2], L, ld, tw);
         const Rec<T> *rec = recs[cur];
         const size_t p0 = (size_t)l0 * nz;
         const T invN = (T)S.invN;
-        for (int i = threadIdx.x; i < nl * nz; i += blockDim.x) {
-            const int li = i / nz, z = i - li * nz;
-            const Rec<T> r = rec[i];
-            double dn = 0.0, ds = 0.0;
-            if (r.j >= 0) {
-                T p[NQ], dp[NQ];
-                spline_p<T>(r.j, r.B, qs->h[r.j], qs->d2, p);
-                spline_dp<T>(r.j, r.B, qs->h[r.j], qs->d2, dp);
-                const cx<T> *src = R + (size_t)z * L + li * 10;
-                T s0 = (T)0, s1 = (T)0;
+        {
+            // dE/dtheta_a = dV F_a; dedn = sum_a F_a (p_a + n p_a' dq0/dn),
+            // dedsigma = sum_a F_a n p_a' dq0/dsigma (the 1/N of the inverse
+            // transform folded in).  With D_j = sum_a F_a d2_a[j]:
+            //   sum_a F_a p_a  = A F_j + B F_{j+1} + cA D_j + cB D_{j+1},
+            //   sum_a F_a p_a' = (F_{j+1} - F_j) / h + dA D_j + dB D_{j+1}.
+            const int dz = blockDim.x % nz, dli = blockDim.x / nz;
+            int z = threadIdx.x % nz, li = threadIdx.x / nz;
+            double *gdn = S.dedn + p0, *gds = S.dedsigma + p0;
+            for (; li < nl;) {
+                const int i = li * nz + z;
+                const Rec<T> r = rec[i];
+                double dn = 0.0, ds = 0.0;
+                if (r.j >= 0) {
+                    const int j = r.j;
+                    T r0[NQ], r1[NQ];
+                    d2_rows<T>(j, qs->d2, r0, r1);
+                    const cx<T> *src = R + (size_t)z * ld + li * 10;
+                    T D0 = (T)0, D1 = (T)0;
 #pragma unroll
-                for (int c = 0; c < 10; ++c) {
-                    const cx<T> v = src[c];
-                    s0 += v.x * p[2 * c] + v.y * p[2 * c + 1];
-                    s1 += v.x * dp[2 * c] + v.y * dp[2 * c + 1];
+                    for (int c = 0; c < 10; ++c) {
+                        const cx<T> v = src[c];
+                        D0 += v.x * r0[2 * c] + v.y * r0[2 * c + 1];
+                        D1 += v.x * r1[2 * c] + v.y * r1[2 * c + 1];
+                    }
+                    const T *ft = reinterpret_cast<const T *>(src);
+                    const T Fj = ft[j], Fj1 = ft[j + 1];
+                    const T h = qs->h[j], B = r.B, A = (T)1 - B;
+                    const T cA = (A * A * A - A) * h * h / (T)6;
+                    const T cB = (B * B * B - B) * h * h / (T)6;
+                    const T dA = -((T)3 * A * A - (T)1) * h / (T)6;
+                    const T dB = ((T)3 * B * B - (T)1) * h / (T)6;
+                    const T s0 = (A * Fj + B * Fj1 + cA * D0 + cB * D1) * invN;
+                    const T s1 = ((Fj1 - Fj) / h + dA * D0 + dB * D1) * invN;
+                    dn = (double)(s0 + r.ndqn * s1);
+                    ds = (double)(r.ndqs * s1);
                 }
-                s0 *= invN;
-                s1 *= invN;
-                dn = (double)(s0 + r.ndqn * s1);
-                ds = (double)(r.ndqs * s1);
+                gdn[i] = dn;
+                gds[i] = ds;
+                z += dz;
+                li += dli;
+                if (z >= nz) {
+                    z -= nz;
+                    ++li;
+                }
             }
-            S.dedn[p0 + i] = dn;
-            S.dedsigma[p0 + i] = ds;
         }
         fence_proxy_async();
         __syncthreads();
@@ -907,7 +1017,8 @@ cudaError_t launch_q0(int prec, int npts, const double *n, const double *s, doub
 // ---------------------------------------------------------------------------
 template <typename T>
 size_t smem_z(int nz, int LZ) {
-    return ((sizeof(QShared<T>) + 15) / 16) * 16 + sizeof(cx<T>) * ((size_t)nz + 2ull * nz * 10 * LZ);
+    return ((sizeof(QShared<T>) + 15) / 16) * 16 +
+           sizeof(cx<T>) * ((size_t)((nz + 1) & ~1) + 2ull * nz * z_ld(LZ));
 }
 template <typename T>
 size_t smem_xy(int n, int W, int nbuf) {
@@ -918,7 +1029,7 @@ template <typename T>
 size_t smem_zinv(int nz, int LZ) {
     const size_t nzh = nz / 2 + 1;
     return 16 + ((sizeof(QShared<T>) + 15) / 16) * 16 +
-           sizeof(cx<T>) * ((size_t)((nz + 7) & ~7) + 2 * (size_t)LZ * nzh * NQ + 2ull * nz * 10 * LZ) +
+           sizeof(cx<T>) * ((size_t)((nz + 7) & ~7) + 2 * (size_t)LZ * nzh * NQ + 2ull * nz * z_ld(LZ)) +
            2 * (size_t)LZ * nz * sizeof(Rec<T>);
 }
 

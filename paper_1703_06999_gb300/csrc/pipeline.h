@@ -26,6 +26,10 @@ struct LaunchSet {
     int *err;                // device flag set by a stage whose bounded wait ran out
 };
 
+// Row stride (complex elements) of the z-pass transform buffers for nl lines
+// (10 complex lines each); odd, so that consecutive rows start in different banks.
+__host__ __device__ inline int z_ld(int nl) { return 10 * nl + 1; }
+
 size_t stage_smem(int stage, int prec, int n, int tile, int nbuf = 3);
 size_t zinv_smem(int prec, int nzmax, int inelems, int recelems, int abelems);
 size_t contract_smem(int prec, int maxspan);
