@@ -83,16 +83,20 @@ __device__ __forceinline__ Q0 q0_point(double n, double s, double Z) {
 }
 
 // ---------------------------------------------------------------------------
-// q0 for the FP32-mixed form in double-float arithmetic (about 48 bits;
-// GB300's FP64 pipe is 1/64 of its FP32 rate).  Same formulas as q0_point:
-//  * ln(1 + u) = 2 atanh(s), s = u / (2 + u) for u < sqrt2 - 1, else
-//    x = 1 + u = m 2^e, m in [1/sqrt2, sqrt2), ln x = 2 atanh((m-1)/(m+1)) + e ln2;
-//    atanh by its Taylor series to s^19 (|s| <= 0.172).
-//  * exp(-S) = 2^-k exp(-r), S = k ln2 + r, |r| <= ln2/2, Taylor series to r^12.
-//  * Saturation: for t = q_raw/5 > 1.5, sum_{m<=12} t^m/m > 40 and
-//    q0 = 5 to FP64 precision.
-//  * The spline interval and coordinate B come from the double-float q0; the
-//    derivatives (they only enter the potential) are formed in FP32.
+// q0 for the FP32-mixed form in double-float arithmetic (about 46 bits;
+// GB300's FP64 pipe runs at 1/64 of its FP32 rate).  Same formulas as
+// q0_point, organised for few operations:
+//  * sums of positive terms use the sloppy double-float addition (exact
+//    two-sum of the high parts); sums that may cancel use the full one;
+//  * reciprocals: FP32 reciprocal plus one correction with the exact remainder;
+//  * ln x = e ln2 + ln c_i + ln(1 + r), x = 2^e m, m = c_i (1 + r), c_i from
+//    a 64-entry table (c_0 = 1), |r| <= 1/64, ln(1+r) to r^8;
+//  * exp(-S) = 2^(-k/64) exp(-r), |r| <= ln2/128, 2^(-j/64) from a table;
+//  * saturation (appendix): with t = q_raw / q_cut and S = sum_{m<=12} t^m/m,
+//    for t < 0.4 the identity S = -ln(1 - t) - R, R = sum_{m>=13} t^m/m, gives
+//    1 - e^-S = t - (1 - t) expm1(R) and h'(x) = e^R (1 - t^12) without
+//    cancellation; for 0.4 <= t <= 1.5 S and e^-S are formed directly; for
+//    t > 1.5, S > 40 and q0 = q_cut to double precision.
 // ---------------------------------------------------------------------------
 struct Q0M {
     bool live;
@@ -102,57 +106,118 @@ struct Q0M {
     double q0;
 };
 
-__device__ __forceinline__ dfl df_two_atanh(dfl s) {
-    const dfl z = df_mul(s, s);
-    dfl p = DF(1.0 / 19.0);
-    p = df_add(df_mul(p, z), DF(1.0 / 17.0));
-    p = df_add(df_mul(p, z), DF(1.0 / 15.0));
-    p = df_add(df_mul(p, z), DF(1.0 / 13.0));
-    p = df_add(df_mul(p, z), DF(1.0 / 11.0));
-    p = df_add(df_mul(p, z), DF(1.0 / 9.0));
-    p = df_add(df_mul(p, z), DF(1.0 / 7.0));
-    p = df_add(df_mul(p, z), DF(1.0 / 5.0));
-    p = df_add(df_mul(p, z), DF(1.0 / 3.0));
-    p = df_add(df_mul(p, z), DF(1.0));
-    const dfl r = df_mul(s, p);
-    return dfl{2.f * r.hi, 2.f * r.lo};
-}
+struct Q0Tab {
+    dfl qd[NQ];          // the q mesh and 1/h in double-float
+    dfl invhd[NQ];
+    float4 lnt[64];      // {1/c_i in FP32, ln c_i hi, ln c_i lo, 0}
+    float2 ex2[64];      // 2^(-j/64) hi, lo
+};
 
-__device__ __forceinline__ dfl df_ln1p(dfl u) {
-    if (u.hi < 0.41421356f) return df_two_atanh(df_div(u, df_add(DF(2.0), u)));
-    dfl x = df_add(DF(1.0), u);
-    int e;
-    frexpf(x.hi, &e);                        // x.hi = m 2^e, m in [0.5, 1)
-    x = dfl{ldexpf(x.hi, -e), ldexpf(x.lo, -e)};
-    if (x.hi < 0.70710678f) {
-        x = dfl{2.f * x.hi, 2.f * x.lo};
-        --e;
+__device__ __forceinline__ void load_q0tab(Q0Tab *t) {
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+        const double c = i == 0 ? 1.0 : 1.0 + (i + 0.5) / 64.0;
+        const float inv = (float)(1.0 / c);
+        const double lc = -log((double)inv);          // ln of 1 / inv exactly
+        const float lh = (float)lc;
+        t->lnt[i] = make_float4(inv, lh, (float)(lc - (double)lh), 0.f);
+        const double v = exp2(-(double)i / 64.0);
+        const float vh = (float)v;
+        t->ex2[i] = make_float2(vh, (float)(v - (double)vh));
     }
-    const dfl s = df_div(df_sub(x, DF(1.0)), df_add(x, DF(1.0)));
-    return df_add(df_two_atanh(s), df_mulf(DF(0.69314718055994530942), (float)e));
+    for (int i = threadIdx.x; i < NQ; i += blockDim.x) {
+        t->qd[i] = df_from(c_qm.q[i]);
+        t->invhd[i] = df_from(c_qm.invh[i]);
+    }
 }
 
-__device__ __forceinline__ dfl df_exp_neg(dfl S) {
-    const float k = rintf(S.hi * 1.44269504f);
-    const dfl x = df_neg(df_sub(S, df_mulf(DF(0.69314718055994530942), k)));   // -r
-    dfl p = DF(1.0 / 479001600.0);           // 1/12!
-    p = df_add(df_mul(p, x), DF(1.0 / 39916800.0));
-    p = df_add(df_mul(p, x), DF(1.0 / 3628800.0));
-    p = df_add(df_mul(p, x), DF(1.0 / 362880.0));
-    p = df_add(df_mul(p, x), DF(1.0 / 40320.0));
-    p = df_add(df_mul(p, x), DF(1.0 / 5040.0));
-    p = df_add(df_mul(p, x), DF(1.0 / 720.0));
-    p = df_add(df_mul(p, x), DF(1.0 / 120.0));
-    p = df_add(df_mul(p, x), DF(1.0 / 24.0));
-    p = df_add(df_mul(p, x), DF(1.0 / 6.0));
-    p = df_add(df_mul(p, x), DF(0.5));
-    p = df_add(df_mul(p, x), DF(1.0));
-    p = df_add(df_mul(p, x), DF(1.0));
-    const float sc = ldexpf(1.f, -(int)k);
-    return dfl{p.hi * sc, p.lo * sc};
+// a + b for a, b of one sign (sloppy addition: exact two-sum of the high parts)
+__device__ __forceinline__ dfl df_add_pos(dfl a, dfl b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e += a.lo + b.lo;
+    return df_quick(s, e);
 }
 
-__device__ __forceinline__ Q0M q0_point_df(double n, double s, double Z, const dfl *qd, const dfl *invhd) {
+__device__ __forceinline__ dfl df_rcp_fast(dfl b) {
+    const float r = __frcp_rn(b.hi);
+    float e = fmaf(-b.hi, r, 1.0f);      // exact remainder of the rounded reciprocal
+    e = fmaf(-b.lo, r, e);
+    return df_quick(r, r * e);
+}
+
+// ln(1 + r) for |r| <= 1/64 in double-float: r - r^2/2 + r^3/3 in
+// double-float plus the FP32 tail r^4 (-1/4 + r/5 - r^2/6 + r^3/7 - r^4/8)
+__device__ __forceinline__ dfl df_ln1p_small(float rh, float rl) {
+    const float p2 = rh * rh;
+    const float e2 = fmaf(rh, rh, -p2) + 2.f * rh * rl;
+    const float p3 = p2 * rh;
+    const float e3 = fmaf(p2, rh, -p3) + e2 * rh;
+    const dfl c3 = df_mul(dfl{p3, e3}, DF(1.0 / 3.0));
+    float tail = fmaf(rh, -0.125f, 0.14285715f);
+    tail = fmaf(rh, tail, -0.16666667f);
+    tail = fmaf(rh, tail, 0.2f);
+    tail = fmaf(rh, tail, -0.25f);
+    tail *= p2 * p2;
+    // |r^2/2| <= |r|/128 and |r^3/3| << |r - r^2/2|: fast two-sums
+    const float s = rh - 0.5f * p2;
+    float se = ((rh - s) - 0.5f * p2) + (rl - 0.5f * e2);
+    const float s2 = s + c3.hi;
+    se += ((s - s2) + c3.hi) + c3.lo + tail;
+    return df_quick(s2, se);
+}
+
+// ln(1 + u), u >= 0: the series on u itself below 1/64 (no rounding of 1 + u),
+// else x = 1 + u = 2^e m, m = c_i (1 + r), ln x = e ln2 + ln c_i + ln(1 + r)
+__device__ __forceinline__ dfl df_log1p(dfl u, const float4 *lnt) {
+    if (u.hi < 0.015625f) return df_ln1p_small(u.hi, u.lo);
+    const dfl x = df_add_pos(DF(1.0), u);
+    const int bits = __float_as_int(x.hi);
+    const int e = ((bits >> 23) & 0xff) - 127;
+    const int i = (bits >> 17) & 63;
+    const float sc = __int_as_float((127 - e) << 23);     // 2^-e
+    const float mh = x.hi * sc, ml = x.lo * sc;
+    const float4 T = lnt[i];
+    const float p = mh * T.x;
+    const float pe = fmaf(mh, T.x, -p);
+    float rh, rl;
+    two_sum(p - 1.0f, fmaf(ml, T.x, pe), rh, rl);         // r = m / c_i - 1 (p - 1 exact)
+    const dfl l1p = df_ln1p_small(rh, rl);
+    const dfl el = df_mulf(DF(0.69314718055994530942), (float)e);
+    return df_add(df_add_pos(el, dfl{T.y, T.z}), l1p);
+}
+
+// exp(-S), S >= 0
+__device__ __forceinline__ dfl df_exp_neg2(dfl S, const float2 *ex2) {
+    const float kf = rintf(S.hi * 92.332482616893656f);   // 64 / ln2
+    const int k = (int)kf;
+    // ln2/64 = C1 + C2 + C3, C1 with 11 significant bits (k * C1 exact for k < 8192)
+    const float C1 = 0.010833740234375f, C2 = -3.3155381516e-6f, C3 = 2.5727683872e-14f;
+    const float a = S.hi - kf * C1;
+    const float bh = kf * C2;
+    const float bl = fmaf(kf, C2, -bh);
+    float rh, rl;
+    two_sum(a, -bh, rh, rl);
+    rl += S.lo - bl - kf * C3;
+    const dfl r = df_quick(rh, rl);
+    // exp(-r) = 1 - r + r^2/2 - r^3/6 + r^4/24 - r^5/120
+    float oh, ol;
+    two_sum(1.0f, -r.hi, oh, ol);
+    ol -= r.lo;
+    const float p2 = r.hi * r.hi;
+    const float e2 = fmaf(r.hi, r.hi, -p2) + 2.f * r.hi * r.lo;
+    float tail = fmaf(r.hi, -8.3333333e-3f, 4.1666668e-2f);
+    tail = fmaf(r.hi, tail, -0.16666667f);
+    tail *= p2 * r.hi;
+    dfl E = df_add_pos(df_quick(oh, ol), dfl{0.5f * p2, 0.5f * e2});
+    E.lo += tail;
+    const float2 Tj = ex2[k & 63];
+    const dfl v = df_mul(dfl{Tj.x, Tj.y}, E);
+    const float sc = __int_as_float((127 - (k >> 6)) << 23);
+    return dfl{v.hi * sc, v.lo * sc};
+}
+
+// zc = -Z_ab / 36 in double-float (positive)
+__device__ __forceinline__ Q0M q0_point_df(double n, double s, dfl zc, const Q0Tab *tb) {
     Q0M r;
     r.live = n > c_qm.n_min;
     r.dqdn = 0.f;
@@ -169,37 +234,55 @@ __device__ __forceinline__ Q0M q0_point_df(double n, double s, double Z, const d
     const double PI = 3.14159265358979323846;
     const dfl nd = df_from(n), sd = df_from(s);
     const dfl kF = df_cbrt(df_mul(nd, DF(3.0 * PI * PI)));
-    const dfl ikF = df_rcp(kF);
+    const dfl ikF = df_rcp_fast(kF);
     const dfl rs = df_mul(ikF, DF(1.9191582926775128));      // (9 pi / 4)^(1/3) / k_F
     const dfl srs = df_sqrt(rs);
-    dfl poly = DF(b4);
-    poly = df_add(df_mul(poly, srs), DF(b3));
-    poly = df_add(df_mul(poly, srs), DF(b2));
-    poly = df_add(df_mul(poly, srs), DF(b1));
+    dfl poly = df_add_pos(df_mul(DF(b4), srs), DF(b3));
+    poly = df_add_pos(df_mul(poly, srs), DF(b2));
+    poly = df_add_pos(df_mul(poly, srs), DF(b1));
     const dfl D = df_mul(df_mul(poly, srs), DF(2.0 * A));   // 2A (b1 rs^1/2 + b2 rs + b3 rs^3/2 + b4 rs^2)
-    const dfl L = df_ln1p(df_rcp(D));
-    const dfl eps = df_mul(df_mul(DF(-2.0 * A), df_add(DF(1.0), df_mul(DF(a1), rs))), L);
-    const dfl in2 = df_rcp(df_mul(nd, nd));
-    const dfl G = df_mul(df_mul(df_mul(DF(-Z / 36.0), sd), ikF), in2);
-    const dfl qraw = df_add(df_add(kF, df_mul(DF(-4.0 * PI / 3.0), eps)), G);
+    const dfl L = df_log1p(df_rcp_fast(D), tb->lnt);
+    const dfl ar = df_add_pos(DF(1.0), df_mul(DF(a1), rs));
+    const dfl meps = df_mul(df_mul(DF(2.0 * A), ar), L);    // -eps_c > 0
+    const dfl in2 = df_rcp_fast(df_mul(nd, nd));
+    const dfl G = df_mul(df_mul(df_mul(zc, sd), ikF), in2);  // gradient term >= 0
+    const dfl qraw = df_add_pos(df_add_pos(kF, df_mul(DF(4.0 * PI / 3.0), meps)), G);
     const dfl t = df_mul(qraw, DF(0.2));
     dfl q0;
-    float e = 0.f, dS = 0.f;
+    float dh = 0.f;
     if (t.hi > 1.5f) {
         q0 = DF(5.0);
+    } else if (t.hi < 0.4f) {
+        const float th = t.hi;
+        float R = 1.f / 30.f;
+#pragma unroll
+        for (int m = 29; m >= 13; --m) R = fmaf(R, th, 1.f / (float)m);
+        const float t2 = th * th, t4 = t2 * t2, t12 = t4 * t4 * t4;
+        R *= t12 * th;
+        const float E = fmaf(0.5f * R, R, R);                 // expm1(R)
+        float omh, oml;
+        two_sum(1.0f, -t.hi, omh, oml);
+        oml -= t.lo;
+        const dfl w = df_mulf(df_quick(omh, oml), E);         // (1 - t) expm1(R)
+        const float h = t.hi - w.hi;                          // |w| << t: fast two-sum
+        const float he = ((t.hi - h) - w.hi) + t.lo - w.lo;
+        q0 = df_mulf(df_quick(h, he), 5.0f);
+        dh = (1.f + E) * (1.f - t12);
     } else {
         dfl S = DF(1.0 / 12.0);
 #pragma unroll
-        for (int m = 11; m >= 1; --m) S = df_add(df_mul(S, t), DF(1.0 / (double)m));
+        for (int m = 11; m >= 1; --m) S = df_add_pos(df_mul(S, t), DF(1.0 / (double)m));
         S = df_mul(S, t);
-        const dfl ex = df_exp_neg(S);
-        q0 = df_mul(DF(5.0), df_sub(DF(1.0), ex));
-        e = ex.hi;
-        dS = 1.f;
+        const dfl ex = df_exp_neg2(S, tb->ex2);
+        const float h = 1.0f - ex.hi;                         // ex <= e^-0.46: fast two-sum
+        const float he = ((1.0f - h) - ex.hi) - ex.lo;
+        q0 = df_mulf(df_quick(h, he), 5.0f);
+        float dS = 1.f;
 #pragma unroll
-        for (int m = 0; m < 11; ++m) dS = fmaf(dS, t.hi, 1.f);    // sum_{m=0}^{11} t^m
+        for (int m = 0; m < 11; ++m) dS = fmaf(dS, t.hi, 1.f);   // sum_{m=0}^{11} t^m
+        dh = ex.hi * dS;
     }
-    const dfl qmin = qd[0];
+    const dfl qmin = tb->qd[0];
     if (df_lt(q0, qmin)) {
         r.j = 0;
         r.B = 0.f;
@@ -210,28 +293,26 @@ __device__ __forceinline__ Q0M q0_point_df(double n, double s, double Z, const d
     int lo = 0, hi = NQ - 2;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (df_lt(q0, qd[mid])) hi = mid - 1;
+        if (df_lt(q0, tb->qd[mid])) hi = mid - 1;
         else lo = mid;
     }
     r.j = lo;
-    r.B = df_mul(df_sub(q0, qd[lo]), invhd[lo]).hi;
-    // derivatives: the sum in dq_raw/dn can cancel, so it is formed in
-    // double-float; the saturation factor and dq_raw/dsigma are plain products (FP32)
-    const float dh = e * dS;
-    const dfl dD = df_mul(DF(2.0 * A),
-                          df_add(df_add(df_div(DF(0.5 * b1), srs), DF(b2)),
-                                 df_add(df_mul(DF(1.5 * b3), srs), df_mul(DF(2.0 * b4), rs))));
-    const dfl deps = df_add(df_mul(DF(-2.0 * A * a1), L),
-                            df_div(df_mul(df_mul(DF(2.0 * A), df_add(DF(1.0), df_mul(DF(a1), rs))), dD),
-                                   df_add(df_mul(D, D), D)));
-    const dfl inv_n = df_rcp(nd);
-    const dfl dqn = df_mul(df_add(df_add(df_mul(kF, DF(1.0 / 3.0)), df_mul(df_mul(DF(4.0 * PI / 9.0), deps), rs)),
-                                  df_mul(DF(-7.0 / 3.0), G)),
-                           inv_n);
-    const float dq_dn = dqn.hi;
-    const float dq_ds = -(float)(Z / 36.0) * ikF.hi * in2.hi;
-    r.dqdn = dh * dq_dn;
-    r.dqds = dh * dq_ds;
+    const dfl qj = tb->qd[lo];
+    r.B = ((q0.hi - qj.hi) + (q0.lo - qj.lo)) * tb->invhd[lo].hi;
+    if (dh == 0.f) return r;
+    // dq_raw/dn = (k_F/3 + (4 pi/9) r_s deps/dr_s - (7/3) G) / n; the sum can
+    // cancel, so it is formed in double-float; dq_raw/dsigma is a plain product
+    const dfl isrs = df_mul(srs, df_mul(kF, DF(1.0 / 1.9191582926775128)));   // r_s^(-1/2)
+    dfl dD = df_add_pos(df_mul(DF(0.5 * b1), isrs), DF(b2));
+    dD = df_add_pos(dD, df_mul(DF(1.5 * b3), srs));
+    dD = df_add_pos(dD, df_mul(DF(2.0 * b4), rs));
+    dD = df_mul(dD, DF(2.0 * A));
+    const dfl qd = df_mul(dD, df_rcp_fast(df_mul(D, df_add_pos(D, DF(1.0)))));
+    const dfl deps = df_sub(df_mul(df_mul(DF(2.0 * A), ar), qd), df_mul(DF(2.0 * A * a1), L));
+    const dfl t12 = df_add(df_mul(kF, DF(1.0 / 3.0)), df_mul(df_mul(DF(4.0 * PI / 9.0), rs), deps));
+    const dfl dqn = df_mul(df_sub(t12, df_mul(DF(7.0 / 3.0), G)), df_rcp_fast(nd));
+    r.dqdn = dh * dqn.hi;
+    r.dqds = dh * (zc.hi * ikF.hi * in2.hi);
     return r;
 }
 
@@ -287,20 +368,18 @@ template <typename T>
 struct QShared {
     double q[NQ];
     double invh[NQ];
-    dfl qd[NQ];      // the mesh and 1/h in double-float (FP32-mixed q0)
-    dfl invhd[NQ];
+    Q0Tab q0t;       // double-float mesh and ln / exp tables (FP32-mixed q0)
     T h[NQ];
-    T d2[NQ * NQ];
+    alignas(16) T d2[NQ * NQ];
 };
 
 template <typename T>
 __device__ __forceinline__ void load_qshared(QShared<T> *qs) {
     for (int i = threadIdx.x; i < NQ * NQ; i += blockDim.x) qs->d2[i] = (T)c_qm.d2[i];
+    load_q0tab(&qs->q0t);
     for (int i = threadIdx.x; i < NQ; i += blockDim.x) {
         qs->q[i] = c_qm.q[i];
         qs->invh[i] = c_qm.invh[i];
-        qs->qd[i] = df_from(c_qm.q[i]);
-        qs->invhd[i] = df_from(c_qm.invh[i]);
         qs->h[i] = (T)c_qm.h[i];
     }
 }
@@ -338,7 +417,7 @@ __device__ __forceinline__ void d2_rows(int j, const T *d2s, T *r0, T *r1) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_zfwd(const SysDev *__restrict__ sys, const int *__restrict__ prefix,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zfwd(const SysDev *__restrict__ sys, const int *__restrict__ prefix,
                                               int nsys, int total) {
     extern __shared__ __align__(16) unsigned char smem[];
     QShared<T> *qs = reinterpret_cast<QShared<T> *>(smem);
@@ -364,6 +443,7 @@ __global__ void __launch_bounds__(256) k_zfwd(const SysDev *__restrict__ sys, co
         Rec<T> *rec = reinterpret_cast<Rec<T> *>(S.rec);
         const size_t p0 = (size_t)l0 * nz;
         const double *gn = S.n + p0, *gs = S.sigma + p0;
+        const dfl zc = df_from(-S.Z / 36.0);
         {
             // points i = li * nz + z, walked without division
             const int dz = nt % nz, dli = nt / nz;
@@ -376,7 +456,7 @@ __global__ void __launch_bounds__(256) k_zfwd(const SysDev *__restrict__ sys, co
                 int j = -1;
                 T B = (T)0, ndqn = (T)0, ndqs = (T)0;
                 if (sizeof(T) == 4) {
-                    const Q0M q = q0_point_df(n, sg, S.Z, qs->qd, qs->invhd);
+                    const Q0M q = q0_point_df(n, sg, zc, &qs->q0t);
                     j = q.j;
                     B = (T)q.B;
                     ndqn = (T)((float)n * q.dqdn);
@@ -792,7 +872,7 @@ __device__ __forceinline__ void zinv_issue(const SysDev *__restrict__ sys, const
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_zinv(const SysDev *__restrict__ sys, const int *__restrict__ prefix,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zinv(const SysDev *__restrict__ sys, const int *__restrict__ prefix,
                                               int nsys, int total, int nzmax, int inelems, int recelems,
                                               int abelems, int *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -983,16 +1063,13 @@ __global__ void k_efinish(const SysDev *__restrict__ sys, int nsys) {
 template <typename T>
 __global__ void k_q0(int npts, const double *__restrict__ n, const double *__restrict__ s, double Z,
                      double *__restrict__ q0, double *__restrict__ dqdn, double *__restrict__ dqds) {
-    __shared__ dfl qd[NQ], ih[NQ];
-    if (threadIdx.x < NQ) {
-        qd[threadIdx.x] = df_from(c_qm.q[threadIdx.x]);
-        ih[threadIdx.x] = df_from(c_qm.invh[threadIdx.x]);
-    }
+    __shared__ Q0Tab tb;
+    load_q0tab(&tb);
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npts) return;
     if (sizeof(T) == 4) {
-        const Q0M q = q0_point_df(n[i], s[i], Z, qd, ih);
+        const Q0M q = q0_point_df(n[i], s[i], df_from(-Z / 36.0), &tb);
         q0[i] = q.q0;
         dqdn[i] = q.dqdn;
         dqds[i] = q.dqds;
