@@ -135,6 +135,7 @@ def stage_bytes(shape, prec_bytes):
     spec = 20 * nk * c
     return {
         "zfwd": 16 * N + rec * N + spec,          # n, sigma in; records, spectrum out
+        "plane": 2 * spec,                         # cluster plane kernel (when enabled)
         "yfwd": 2 * spec,
         "xfwd": 2 * spec,
         "contract": 2 * spec + 4 * nk,
@@ -409,6 +410,7 @@ def main():
                            "GBps": (sb[n] / (m / 1000.0) / 1e9) if m > 0 else None}
                        for n, m in zip(names, per_launch_ms)}}
 
+    launches_per_step = B.vdwgb_batch_launches(bt)
     for f in f32:
         f.close()
     B.vdwgb_batch_free(bt)
@@ -437,7 +439,7 @@ def main():
             "roofline": roof,
             "e2e": {"value": e2e_val, "unit": "grid pts/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "api": "vdwgb_batch_calculate (host arrays, pinned)"},
-            "gpu_launches": int(args.steps * B.vdwgb_num_stages()),
+            "gpu_launches": int(args.steps * launches_per_step),
             "clocks": clocks,
             "table_build_s": B.vdwgb_table_build_seconds(local),
         }

@@ -134,7 +134,8 @@ size_t vdwgb_footprint_bytes(int nx, int ny, int nz, int precision);
  * device-pointer calls check it after synchronising. */
 int vdwgb_device_status(int device);
 
-/* Number of our kernel launches one evaluation enqueues (all stages). */
+/* Number of our kernel launches one evaluation enqueues (stages without
+ * work for this handle are not launched). */
 int vdwgb_launches_per_call(vdwgb_handle h);
 
 /* ---- kernel table (setup, resident per device) ------------------------ */
@@ -159,6 +160,17 @@ int vdwgb_phi(int device, int npts, const double *d1, const double *d2, double *
 int vdwgb_q0(int device, int precision, int functional, int npts, const double *n, const double *sigma,
              double *q0, double *dq0dn, double *dq0dsigma);
 
+/* Plane kernel on (1) or off (0, default) for handles initialised after the
+ * call.  On: FP32-mixed handles whose x and y lengths are multiples of 16
+ * with a compiled two-pass split (16..256) and whose kz-plane fits the shared
+ * memory of a 16-CTA cluster run the y transforms, x transforms, kernel
+ * contraction and inverses of each kz-plane in one cluster (one HBM round trip
+ * of the work buffer instead of five; experimental: slower than the separate
+ * passes on 96^3 grids).  Off: separate y, x and contraction passes for every
+ * handle.  The environment variable VDWGB_FUSED=1 sets the default to on.
+ * Results agree within FP32 rounding either way. */
+int vdwgb_set_fused(int enable);
+
 /* Autotuning of tile shapes: when enabled (here or by the environment
  * variable VDWGB_AUTOTUNE=1), vdwgb_init_cuda times every stage kernel for
  * each candidate tile shape that fits shared memory (z-forward lines, y / x
@@ -168,11 +180,11 @@ int vdwgb_q0(int device, int precision, int functional, int npts, const double *
  * reused by later handles, batches and the server.  Default off. */
 int vdwgb_set_autotune(int enable);
 
-/* Plan of an initialised handle: info[0..7] = z-forward lines per tile,
+/* Plan of an initialised handle: info[0..8] = z-forward lines per tile,
  * z-inverse lines per tile, y-pass kz-columns, x-pass kz-columns, row
  * buffers of the y and x passes as 10 * y + x (3 prefetching, 2 not),
- * contraction chunks,
- * kernel launches per evaluation, 1 if the tile shapes were autotuned. */
+ * contraction chunks, kernel launches per evaluation, 1 if the tile shapes
+ * were autotuned, cluster size of the plane kernel (0: separate passes). */
 int vdwgb_plan_info(vdwgb_handle h, int *info);
 
 /* Seconds spent building the table on `device` (0 if not built). */
@@ -201,6 +213,9 @@ int vdwgb_batch_calculate_device(vdwgb_batch b, const double *const *d_rho,
  * Blocking. */
 int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double *const *sigma,
                           double *const *dedrho, double *const *dedsigma, double *energy);
+
+/* Kernel launches one evaluation of the batch enqueues. */
+int vdwgb_batch_launches(vdwgb_batch b);
 
 /* Stage timing: with timing enabled, each batch evaluation records CUDA
  * events between its kernel launches (launched directly, not from the

@@ -54,6 +54,7 @@ _SIGS = {
     "vdwgb_batch_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "vdwgb_batch_stage_ms": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "vdwgb_num_stages": (ctypes.c_int, []),
+    "vdwgb_batch_launches": (ctypes.c_int, [ctypes.c_void_p]),
     "vdwgb_stage_name": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
@@ -82,6 +83,7 @@ _SIGS.update({
     "vdwgb_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerStats)]),
     "vdwgb_server_free": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p)]),
     "vdwgb_calculate_noalloc": (ctypes.c_int, [ctypes.c_int] * 5 + [ctypes.c_void_p] * 7),
+    "vdwgb_set_fused": (ctypes.c_int, [ctypes.c_int]),
 })
 
 
@@ -158,6 +160,11 @@ def vdwgb_calculate_device(h, rho, sigma, dedrho, dedsigma, energy, stream=0):
                                      ctypes.c_void_p(int(stream))), "vdwgb_calculate_device")
 
 
+def vdwgb_set_fused(enable):
+    """Plane kernel on or off for handles initialised afterwards."""
+    _ck(lib().vdwgb_set_fused(int(bool(enable))), "vdwgb_set_fused")
+
+
 def vdwgb_calculate_noalloc(device, functional, shape, cell, rho, sigma, dedrho, dedsigma, energy, stream=0):
     """Handle-free evaluation without device allocation (device tensors,
     float64, contiguous; FP32-mixed, cubic).  The kernel table of ``device``
@@ -200,6 +207,10 @@ def vdwgb_device_status(device=0):
     _ck(lib().vdwgb_device_status(int(device)), "vdwgb_device_status")
 
 
+def vdwgb_batch_launches(b):
+    return int(lib().vdwgb_batch_launches(b))
+
+
 def vdwgb_launches_per_call(h):
     return int(lib().vdwgb_launches_per_call(h))
 
@@ -236,9 +247,9 @@ def vdwgb_set_autotune(enable):
 
 
 def vdwgb_plan_info(h):
-    info = np.zeros(8, dtype=np.int32)
+    info = np.zeros(9, dtype=np.int32)
     _ck(lib().vdwgb_plan_info(h, info.ctypes.data), "vdwgb_plan_info")
-    keys = ["LZ", "LZi", "Wy", "Wx", "nbuf_yx", "chunks", "launches", "autotuned"]
+    keys = ["LZ", "LZi", "Wy", "Wx", "nbuf_yx", "chunks", "launches", "autotuned", "cluster"]
     return {k: int(v) for k, v in zip(keys, info)}
 
 

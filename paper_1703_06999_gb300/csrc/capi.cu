@@ -11,9 +11,11 @@
 #include <map>
 #include <tuple>
 #include <cstdlib>
+#include <algorithm>
 
 #include "internal.h"
 #include "table.h"
+#include "fftreg.cuh"
 
 using namespace vdwgb;
 
@@ -152,8 +154,10 @@ static void release(vdwgb_data *h) {
     for (int i = 0; i < 3; ++i) dfree(h, h->tw[i]);
     dfree(h, h->kidx);
     dfree(h, h->chunks);
+    dfree(h, h->kord);
     h->kidx = nullptr;
     h->chunks = nullptr;
+    h->kord = nullptr;
     dfree(h, h->dsys);
     dfree(h, h->dprefix);
     dfree(h, h->d_io);
@@ -261,6 +265,96 @@ static void build_chunks(const SysDev &S, int maxspan, std::vector<unsigned> &ki
     }
 }
 
+// ---------------------------------------------------------------------------
+// Fused plane kernel: eligibility and the per-(kz, rank) k-point order
+// ---------------------------------------------------------------------------
+static int g_fused = -1;   // -1: read VDWGB_FUSED once (default off)
+static std::mutex g_fused_mu;
+
+static bool fused_on() {
+    std::lock_guard<std::mutex> lk(g_fused_mu);
+    if (g_fused < 0) {
+        const char *e = std::getenv("VDWGB_FUSED");
+        g_fused = (e && e[0] == '1') ? 1 : 0;
+    }
+    return g_fused == 1;
+}
+
+// Cluster size for the plane kernel on this system (16), 0 if it takes the
+// separate y / x / contraction passes: FP32-mixed, both in-plane axes with a
+// two-pass split and divisible by C, one chunk small enough for the swap
+// registers (XL YL 20 <= 3072), nx YL < 65536, the CTA's share of the plane in shared memory.
+static int fused_cluster(const vdwgb_data *h, size_t lim, int &maxcl) {
+    maxcl = 0;
+    if (h->prec != VDWGB_FP32_MIXED || !fused_on()) return 0;
+    const int nx = h->nx, ny = h->ny;
+    if (!fft_split(nx) || !fft_split(ny)) return 0;
+    const int cand[1] = {16};         // one cluster size, so any fused systems share a launch
+    for (int C : cand) {
+        if (nx % C || ny % C) continue;
+        const int XL = nx / C, YL = ny / C;
+        if (XL * YL * NQ > 3072 || nx * YL > 65535) continue;     // swap registers; 16-bit k-point ids
+        const size_t sm = plane_smem(nx, ny, C);
+        if (sm > lim - 64) continue;
+        const int m = plane_max_clusters(C, sm);
+        if (m < 1) continue;
+        maxcl = m;
+        return C;
+    }
+    return 0;
+}
+
+// kord: for each kz and rank, the local indices px YL + yl of the rank's
+// k-points (x position px, y position rank YL + yl, both in the permuted
+// order of the in-place transforms), sorted by kernel-table interval
+static void build_kord(const SysDev &S, int C, std::vector<unsigned short> &kord, int &kstride) {
+    const int nx = S.nx, ny = S.ny, nz = S.nz, nzh = S.nzh;
+    const int YL = ny / C;
+    const int n1x = fft_split(nx), n2x = nx / n1x, n1y = fft_split(ny), n2y = ny / n1y;
+    const int npts = nx * YL;
+    kstride = (npts + 7) & ~7;
+    kord.assign((size_t)nzh * C * kstride, 0);
+    const double dk = 2.0 * M_PI / RMAX;
+    std::vector<int> bin(npts);
+    std::vector<int> start(NK + 1);
+    auto fold = [](int i, int n) { return i <= (n - 1) / 2 ? i : i - n; };
+    for (int kz = 0; kz < nzh; ++kz) {
+        const bool qz = (nz % 2 == 0) && (kz == nz / 2);
+        const int mz = qz ? -kz : kz;
+        const double cz = qz ? 0.0 : mz;
+        for (int c = 0; c < C; ++c) {
+            std::fill(start.begin(), start.end(), 0);
+            for (int li = 0; li < npts; ++li) {
+                const int px = li / YL, yl = li % YL;
+                const int x = fft_perm_freq(px, n1x, n2x), y = fft_perm_freq(c * YL + yl, n1y, n2y);
+                const int mx = fold(x, nx), my = fold(y, ny);
+                const bool qx = (nx % 2 == 0) && (x == nx / 2), qy = (ny % 2 == 0) && (y == ny / 2);
+                const double cx = qx ? 0.0 : mx, cy = qy ? 0.0 : my;
+                double k2 = S.g[0] * mx * mx + S.g[1] * (double)my * my + S.g[2] * (double)mz * mz +
+                            2.0 * (S.g[3] * cx * cy + S.g[4] * cx * cz + S.g[5] * cy * cz);
+                if (k2 < 0) k2 = 0;
+                long j = (long)(std::sqrt(k2) / dk);
+                if (j > NK - 1) j = NK - 1;
+                bin[li] = (int)j;
+                ++start[j + 1];
+            }
+            for (int j = 1; j <= NK; ++j) start[j] += start[j - 1];
+            unsigned short *out = kord.data() + ((size_t)kz * C + c) * kstride;
+            for (int li = 0; li < npts; ++li) out[start[bin[li]]++] = (unsigned short)li;
+        }
+    }
+}
+
+// kernel launches one evaluation of a launch set enqueues (stages without tiles are skipped)
+static int count_launches(const LaunchSet &L) {
+    int n = 0;
+    for (int k = 0; k < NSTAGE; ++k) {
+        const int kind = stage_kind(k);
+        if (kind < 0 || L.total[kind] > 0) ++n;
+    }
+    return n;
+}
+
 // Tile-dependent parts of a handle's plan: tile counts of the z, y, x passes
 // and the matching launch-set fields.
 static void set_tiles(vdwgb_data *h, int LZ, int LZi, int Wy, int Wx, int nby, int nbx) {
@@ -274,8 +368,8 @@ static void set_tiles(vdwgb_data *h, int LZ, int LZi, int Wy, int Wx, int nby, i
     S.Wy = Wy;
     S.Wx = Wx;
     S.tiles[0] = (nx * ny + LZ - 1) / LZ;
-    S.tiles[1] = nx * ((nzh + Wy - 1) / Wy);
-    S.tiles[2] = ny * ((nzh + Wx - 1) / Wx);
+    S.tiles[1] = S.fused ? 0 : nx * ((nzh + Wy - 1) / Wy);
+    S.tiles[2] = S.fused ? 0 : ny * ((nzh + Wx - 1) / Wx);
     S.tiles[3] = (nx * ny + LZi - 1) / LZi;
     for (int s = 0; s < 4; ++s) {
         L.prefix[s] = h->dprefix + 2 * s;
@@ -402,6 +496,7 @@ static int apply_tuned(vdwgb_data *h) {
     const int cand[6] = {1, 2, 3, 4, 6, 8};
     // z forward first (it writes the records and spectrum the other stages read)
     for (int pass = 0; pass < 4 && !rc; ++pass) {
+        if (S.fused && (pass == 1 || pass == 2)) continue;   // y / x run inside the plane kernel
         float best_ms = 1e30f;
         for (int ci = 0; ci < 12; ++ci) {
             const int c = cand[ci % 6];
@@ -426,7 +521,7 @@ static int apply_tuned(vdwgb_data *h) {
             set_tiles(h, v.LZ, v.LZi, v.Wy, v.Wx, v.nby, v.nbx);
             set_io_dev();
             float ms = 0.f;
-            const int stage = pass == 0 ? 0 : (pass == 1 ? 1 : (pass == 2 ? 2 : 6));
+            const int stage = pass == 0 ? 0 : (pass == 1 ? 2 : (pass == 2 ? 3 : 7));
             rc = time_stage(h, stage, ms);
             if (rc) break;
             if (ms < best_ms) {
@@ -499,22 +594,44 @@ static int plan(vdwgb_data *h) {
     S.invN = 1.0 / N;
     S.Z = h->functional == VDWGB_DF2 ? -1.887 : -0.8491;
     // half-spectrum k-points sorted by kernel-table interval, cut into chunks
+    // (or, for the plane kernel, per plane and cluster rank)
     const int maxspan = prec == VDWGB_FP32_MIXED ? 16 : 8;
     std::vector<unsigned> kidx;
     std::vector<int4> chunks;
-    build_chunks(S, maxspan, kidx, chunks);
-    S.tiles[4] = (int)chunks.size();
+    std::vector<unsigned short> kord;
+    int maxcl = 0;
+    const int C = fused_cluster(h, di.maxsmem - 1024, maxcl);
+    S.fused = C;
+    if (C) {
+        build_kord(S, C, kord, S.kstride);
+        S.sx1 = fft_split(nx);
+        S.sy1 = fft_split(ny);
+        S.tiles[4] = 0;
+        S.tiles[5] = nzh;
+        S.nepart = nzh * C;
+    } else {
+        build_chunks(S, maxspan, kidx, chunks);
+        S.tiles[4] = (int)chunks.size();
+        S.tiles[5] = 0;
+        S.nepart = S.tiles[4];
+    }
     // memory
     const size_t nspec = (size_t)nx * ny * nzh * NQ;
     CK(dalloc(h, &h->spec, nspec * elem_bytes(prec)), "work buffer");
     CK(dalloc(h, &h->rec, (size_t)nx * ny * nz * rec_bytes(prec)), "point records");
-    CK(dalloc(h, &h->epart, (size_t)S.tiles[4] * sizeof(double)), "energy partials");
-    CK(dalloc(h, &h->kidx, kidx.size() * sizeof(unsigned)), "k-point order");
-    CK(dupload(h, h->kidx, kidx.data(), kidx.size() * sizeof(unsigned)), "k-point order");
-    CK(dalloc(h, &h->chunks, chunks.size() * sizeof(int4)), "chunks");
-    CK(dupload(h, h->chunks, chunks.data(), chunks.size() * sizeof(int4)), "chunks");
+    CK(dalloc(h, &h->epart, (size_t)S.nepart * sizeof(double)), "energy partials");
+    if (C) {
+        CK(dalloc(h, &h->kord, kord.size() * sizeof(unsigned short)), "plane k-point order");
+        CK(dupload(h, h->kord, kord.data(), kord.size() * sizeof(unsigned short)), "plane k-point order");
+    } else {
+        CK(dalloc(h, &h->kidx, kidx.size() * sizeof(unsigned)), "k-point order");
+        CK(dupload(h, h->kidx, kidx.data(), kidx.size() * sizeof(unsigned)), "k-point order");
+        CK(dalloc(h, &h->chunks, chunks.size() * sizeof(int4)), "chunks");
+        CK(dupload(h, h->chunks, chunks.data(), chunks.size() * sizeof(int4)), "chunks");
+    }
     S.kidx = h->kidx;
     S.chunks = h->chunks;
+    S.kord = h->kord;
     for (int a = 0; a < 3; ++a) {
         std::vector<double> w = twiddles(dims[a]);
         if (prec == VDWGB_FP32_MIXED) {
@@ -531,8 +648,8 @@ static int plan(vdwgb_data *h) {
     S.spec = h->spec;
     S.rec = h->rec;
     S.epart = h->epart;
-    h->bytes = nspec * elem_bytes(prec) + (size_t)nx * ny * nz * rec_bytes(prec) + S.tiles[4] * sizeof(double) +
-               kidx.size() * sizeof(unsigned) + chunks.size() * sizeof(int4);
+    h->bytes = nspec * elem_bytes(prec) + (size_t)nx * ny * nz * rec_bytes(prec) + S.nepart * sizeof(double) +
+               kidx.size() * sizeof(unsigned) + chunks.size() * sizeof(int4) + kord.size() * sizeof(unsigned short);
     CK(dalloc(h, &h->dsys, sizeof(SysDev)), "descriptor");
     CK(dalloc(h, &h->dprefix, 2 * NKIND * sizeof(int)), "prefix");
     // launch set
@@ -550,6 +667,11 @@ static int plan(vdwgb_data *h) {
         per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
         L.grid[4] = L.total[4] < di.sms * per_sm ? L.total[4] : di.sms * per_sm;
     }
+    L.prefix[5] = h->dprefix + 10;
+    L.total[5] = S.tiles[5];
+    L.cluster = C;
+    L.smem[5] = C ? plane_smem(nx, ny, C) : 0;
+    L.grid[5] = C ? (nzh < maxcl ? nzh : maxcl) : 0;       // clusters
     set_tiles(h, S.LZ, S.LZi, S.Wy, S.Wx, nbuf, nbuf);
     TableRefs tr;
     CK(table_get(h->device, tr), "kernel table");
@@ -793,8 +915,8 @@ size_t vdwgb_footprint_bytes(int nx, int ny, int nz, int precision) {
 }
 
 int vdwgb_launches_per_call(vdwgb_handle h) {
-    (void)h;
-    return NSTAGE;
+    if (!h || !h->inited) return 0;
+    return count_launches(h->ls);
 }
 
 int vdwgb_kernel_table(int device, double *phik, double *phir, double *qmesh) {
@@ -831,6 +953,12 @@ int vdwgb_phi(int device, int npts, const double *d1, const double *d2, double *
 
 double vdwgb_table_build_seconds(int device) { return table_seconds(device); }
 
+int vdwgb_set_fused(int enable) {
+    std::lock_guard<std::mutex> lk(g_fused_mu);
+    g_fused = enable ? 1 : 0;
+    return 0;
+}
+
 int vdwgb_set_autotune(int enable) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_autotune = enable ? 1 : 0;
@@ -847,7 +975,8 @@ int vdwgb_plan_info(vdwgb_handle h, int *info) {
     info[3] = S.Wx;
     info[4] = h->ls.nbuf[1] * 10 + h->ls.nbuf[2];
     info[5] = S.tiles[4];
-    info[6] = NSTAGE;
+    info[6] = count_launches(h->ls);
+    info[8] = S.fused;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     info[7] = g_tune.count(TuneKey{S.nx, S.ny, S.nz, h->prec}) ? 1 : 0;
     return 0;
@@ -943,6 +1072,21 @@ int vdwgb::batch_launchset(vdwgb_data *const *hs, int count, SysDev *hdesc, int 
         per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
         const int cap = di.sms * per_sm;
         L.grid[s] = L.total[s] < cap ? L.total[s] : cap;
+    }
+    // plane kernel: one cluster size per launch; grid in clusters
+    L.cluster = 0;
+    for (int i = 0; i < count; ++i) {
+        const int C = hs[i]->hsys.fused;
+        if (!C) continue;
+        if (L.cluster && C != L.cluster) return fail(VDWGB_EINVAL, "batch: systems need different cluster sizes");
+        L.cluster = C;
+    }
+    L.grid[5] = 0;
+    if (L.total[5] > 0) {
+        const int m = plane_max_clusters(L.cluster, L.smem[5]);
+        if (m < 1) return fail(VDWGB_EINVAL, "batch: plane kernel does not fit (cluster %d, %zu bytes)", L.cluster,
+                               L.smem[5]);
+        L.grid[5] = L.total[5] < m ? L.total[5] : m;
     }
     return 0;
 }
@@ -1105,6 +1249,11 @@ int vdwgb_batch_stage_ms(vdwgb_batch b, double *ms, int *ncalls) {
     if (ncalls) *ncalls = (int)b->pending.size();
     b->pending.clear();
     return 0;
+}
+
+int vdwgb_batch_launches(vdwgb_batch b) {
+    if (!b) return 0;
+    return count_launches(b->ls);
 }
 
 const char *vdwgb_stage_name(int i) { return stage_name(i); }

@@ -78,7 +78,7 @@ struct SysDev {
     int LZ;          // z-lines per tile of the z-forward pass
     int LZi;         // z-lines per tile of the z-inverse pass
     int Wy, Wx;      // k_z columns per tile of the y and x passes
-    int tiles[5];    // tiles of: z-forward, y, x, z-inverse, contraction chunks
+    int tiles[6];    // tiles of: z-forward, y, x, z-inverse, contraction chunks, kz-planes
     AxisPlan ax[3];  // x, y, z
     const void *tw[3];   // twiddles exp(-2 pi i m / n), m < n, per axis (T complex)
     double g[6];     // reciprocal metric g00 g11 g22 g01 g02 g12 (|k|^2 = m^T g m)
@@ -93,7 +93,13 @@ struct SysDev {
     void *rec;       // [nx*ny*nz] Rec<T>
     const unsigned *kidx;   // half-spectrum k-points sorted by kernel-table interval
     const int4 *chunks;     // contraction chunks: {first, count, first interval, intervals}
-    double *epart;   // one energy partial per contraction chunk
+    double *epart;   // energy partials (per contraction chunk, or per plane and cluster rank)
+    int nepart;      // number of energy partials
+    // plane kernel (fused y / x transforms and contraction), else zero:
+    int fused;       // cluster size C; each CTA owns nx / C x-rows, then ny / C y-rows
+    int sx1, sy1;    // N1 of the two-pass splits of the x and y axes
+    int kstride;     // entries per (kz, rank) list of kord
+    const unsigned short *kord;   // per (kz, rank): local k-point indices sorted by table interval
     double *energy;  // output (device)
 };
 

@@ -210,4 +210,101 @@ __device__ __forceinline__ cx<T> *fft_auto(cx<T> *a, cx<T> *b, const AxisPlan &p
     return fft_lines<INV>(a, b, p, nlines, ld, tw);
 }
 
+// ---- in-place transforms with a permuted spectrum --------------------------
+// Forward: natural input; position p = k1 N2 + k2 of the result holds
+// frequency k1 + N1 k2.  Inverse: takes that permuted order, returns natural
+// order.  Both passes of either direction read and write the same positions
+// per work item, so no scratch buffer is needed.  Layout [i][ld] as above.
+__host__ __device__ constexpr int fft_split(int n) {   // N1 of the two-pass split, 0: none
+    return n == 16 ? 4 : n == 24 ? 8 : n == 32 ? 8 : n == 40 ? 8 : n == 48 ? 8 : n == 64 ? 8 : n == 72 ? 8
+         : n == 80 ? 10 : n == 96 ? 12 : n == 112 ? 14 : n == 128 ? 16 : n == 144 ? 12 : n == 160 ? 16
+         : n == 192 ? 16 : n == 224 ? 16 : n == 256 ? 16 : 0;
+}
+
+// frequency held at position p of a permuted spectrum of length n1 * n2
+__host__ __device__ inline int fft_perm_freq(int p, int n1, int n2) { return p / n2 + n1 * (p % n2); }
+
+template <int N1, int N2, bool INV, typename T>
+__device__ __noinline__ void fft_ip(cx<T> *a, int nlines, int ld, const cx<T> *tw) {
+    const int nt = blockDim.x;
+    const int dl = nt % nlines, dj = nt / nlines;
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+        // forward: strided pass then block pass; inverse: block pass then strided pass
+        const bool strided = (pass == 0) != INV;
+        int l = threadIdx.x % nlines, q = threadIdx.x / nlines;
+        if (strided) {
+            for (; q < N2;) {                 // item (l, j2): positions j1 N2 + j2
+                cx<T> v[N1];
+                cx<T> *p = a + (size_t)q * ld + l;
+#pragma unroll
+                for (int j1 = 0; j1 < N1; ++j1) v[j1] = p[(size_t)j1 * N2 * ld];
+                dftr<N1, INV>(v);
+                if (!INV) {
+#pragma unroll
+                    for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul(v[k1], tw[q * k1]);
+                }
+#pragma unroll
+                for (int j1 = 0; j1 < N1; ++j1) p[(size_t)j1 * N2 * ld] = v[j1];
+                l += dl;
+                q += dj;
+                if (l >= nlines) {
+                    l -= nlines;
+                    ++q;
+                }
+            }
+        } else {
+            for (; q < N1;) {                 // item (l, k1): positions k1 N2 + j2
+                cx<T> v[N2];
+                cx<T> *p = a + (size_t)q * N2 * ld + l;
+#pragma unroll
+                for (int j2 = 0; j2 < N2; ++j2) v[j2] = p[(size_t)j2 * ld];
+                dftr<N2, INV>(v);
+                if (INV) {
+#pragma unroll
+                    for (int j2 = 1; j2 < N2; ++j2) {
+                        cx<T> w = tw[q * j2];
+                        w.y = -w.y;
+                        v[j2] = cmul(v[j2], w);
+                    }
+                }
+#pragma unroll
+                for (int j2 = 0; j2 < N2; ++j2) p[(size_t)j2 * ld] = v[j2];
+                l += dl;
+                q += dj;
+                if (l >= nlines) {
+                    l -= nlines;
+                    ++q;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// In-place permuted transform of `nlines` lines of length n (an fft_split
+// length); all threads of the block call; ends with a barrier.
+template <bool INV, typename T>
+__device__ __forceinline__ void fft_ip_auto(cx<T> *a, int n, int nlines, int ld, const cx<T> *tw) {
+    switch (n) {
+        case 16: fft_ip<4, 4, INV>(a, nlines, ld, tw); break;
+        case 24: fft_ip<8, 3, INV>(a, nlines, ld, tw); break;
+        case 32: fft_ip<8, 4, INV>(a, nlines, ld, tw); break;
+        case 40: fft_ip<8, 5, INV>(a, nlines, ld, tw); break;
+        case 48: fft_ip<8, 6, INV>(a, nlines, ld, tw); break;
+        case 64: fft_ip<8, 8, INV>(a, nlines, ld, tw); break;
+        case 72: fft_ip<8, 9, INV>(a, nlines, ld, tw); break;
+        case 80: fft_ip<10, 8, INV>(a, nlines, ld, tw); break;
+        case 96: fft_ip<12, 8, INV>(a, nlines, ld, tw); break;
+        case 112: fft_ip<14, 8, INV>(a, nlines, ld, tw); break;
+        case 128: fft_ip<16, 8, INV>(a, nlines, ld, tw); break;
+        case 144: fft_ip<12, 12, INV>(a, nlines, ld, tw); break;
+        case 160: fft_ip<16, 10, INV>(a, nlines, ld, tw); break;
+        case 192: fft_ip<16, 12, INV>(a, nlines, ld, tw); break;
+        case 224: fft_ip<16, 14, INV>(a, nlines, ld, tw); break;
+        case 256: fft_ip<16, 16, INV>(a, nlines, ld, tw); break;
+        default: break;
+    }
+}
+
 }  // namespace vdwgb

@@ -23,6 +23,7 @@ struct vdwgb_data {
     void *tw[3] = {nullptr, nullptr, nullptr};
     unsigned *kidx = nullptr;
     int4 *chunks = nullptr;
+    unsigned short *kord = nullptr;    // plane kernel k-point order
     vdwgb::SysDev *dsys = nullptr;
     int *dprefix = nullptr;
     vdwgb::SysDev hsys;

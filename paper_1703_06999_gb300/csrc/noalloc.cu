@@ -221,6 +221,7 @@ extern "C" int vdwgb_calculate_noalloc(int device, int functional, int nx, int n
     const int nch = sort_chunks(S);
     if (nch < 0) return fail(VDWGB_EINVAL, "too many contraction chunks for the fixed scratch");
     S.tiles[4] = nch;
+    S.nepart = nch;
     for (int a = 0; a < 3; ++a)
         for (int m = 0; m < dims[a]; ++m) {
             const double ang = 2.0 * M_PI * (double)m / (double)dims[a];

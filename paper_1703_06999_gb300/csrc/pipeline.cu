@@ -1032,7 +1032,7 @@ __global__ void k_efinish(const SysDev *__restrict__ sys, int nsys) {
     __shared__ double ssum[256], scmp[256];
     for (int si = blockIdx.x; si < nsys; si += gridDim.x) {
         const SysDev &S = sys[si];
-        const int n = S.tiles[4];
+        const int n = S.nepart;
         double s = 0.0, c = 0.0;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             const double v = S.epart[i];
@@ -1150,39 +1150,49 @@ static cudaError_t init_kernels_t(size_t maxsmem) {
 cudaError_t init_kernels(size_t maxsmem) {
     cudaError_t e = init_kernels_t<float>(maxsmem);
     if (e != cudaSuccess) return e;
+    if ((e = init_plane_kernel(maxsmem)) != cudaSuccess) return e;
     return init_kernels_t<double>(maxsmem);
 }
 
+// stage -> tile kind (-1: efinish)
+int stage_kind(int stage) {
+    static const int kind[NSTAGE] = {0, 5, 1, 2, 4, 2, 1, 3, -1};
+    return (stage >= 0 && stage < NSTAGE) ? kind[stage] : -1;
+}
+
 template <typename T>
-static void launch_stage_t(const LaunchSet &ls, int stage, cudaStream_t st) {
+static cudaError_t launch_stage_t(const LaunchSet &ls, int stage, cudaStream_t st) {
     const typename KTab<T>::V *tab = reinterpret_cast<const typename KTab<T>::V *>(ls.table);
+    const int kind = stage_kind(stage);
+    if (kind >= 0 && ls.total[kind] == 0) return cudaSuccess;     // no tiles of this kind
     switch (stage) {
         case 0:
             k_zfwd<T><<<ls.grid[0], 256, ls.smem[0], st>>>(ls.sys, ls.prefix[0], ls.nsys, ls.total[0]);
             break;
         case 1:
-        case 5:
-            if (stage == 1)
-                k_xy<T, 0><<<ls.grid[1], 256, ls.smem[1], st>>>(ls.sys, ls.prefix[1], ls.nsys, ls.total[1],
-                                                                 ls.twmax[1], ls.bufelems[1], ls.nbuf[1], ls.err);
-            else
-                k_xy<T, 1><<<ls.grid[1], 256, ls.smem[1], st>>>(ls.sys, ls.prefix[1], ls.nsys, ls.total[1],
-                                                                 ls.twmax[1], ls.bufelems[1], ls.nbuf[1], ls.err);
+            if (sizeof(T) == 4) return launch_plane(ls, st);
             break;
         case 2:
-        case 4:
-            if (stage == 2)
-                k_xy<T, 2><<<ls.grid[2], 256, ls.smem[2], st>>>(ls.sys, ls.prefix[2], ls.nsys, ls.total[2],
-                                                                 ls.twmax[2], ls.bufelems[2], ls.nbuf[2], ls.err);
-            else
-                k_xy<T, 3><<<ls.grid[2], 256, ls.smem[2], st>>>(ls.sys, ls.prefix[2], ls.nsys, ls.total[2],
-                                                                 ls.twmax[2], ls.bufelems[2], ls.nbuf[2], ls.err);
+            k_xy<T, 0><<<ls.grid[1], 256, ls.smem[1], st>>>(ls.sys, ls.prefix[1], ls.nsys, ls.total[1],
+                                                             ls.twmax[1], ls.bufelems[1], ls.nbuf[1], ls.err);
+            break;
+        case 6:
+            k_xy<T, 1><<<ls.grid[1], 256, ls.smem[1], st>>>(ls.sys, ls.prefix[1], ls.nsys, ls.total[1],
+                                                             ls.twmax[1], ls.bufelems[1], ls.nbuf[1], ls.err);
             break;
         case 3:
+            k_xy<T, 2><<<ls.grid[2], 256, ls.smem[2], st>>>(ls.sys, ls.prefix[2], ls.nsys, ls.total[2],
+                                                             ls.twmax[2], ls.bufelems[2], ls.nbuf[2], ls.err);
+            break;
+        case 5:
+            k_xy<T, 3><<<ls.grid[2], 256, ls.smem[2], st>>>(ls.sys, ls.prefix[2], ls.nsys, ls.total[2],
+                                                             ls.twmax[2], ls.bufelems[2], ls.nbuf[2], ls.err);
+            break;
+        case 4:
             k_contract<T><<<ls.grid[4], 256, ls.smem[4], st>>>(ls.sys, ls.prefix[4], ls.nsys, ls.total[4],
                                                                 ls.maxspan, tab, ls.err);
             break;
-        case 6:
+        case 7:
             k_zinv<T><<<ls.grid[3], 256, ls.smem[3], st>>>(ls.sys, ls.prefix[3], ls.nsys, ls.total[3], ls.twmax[3],
                                                             ls.bufelems[3], ls.recelems, ls.abelems, ls.err);
             break;
@@ -1190,19 +1200,19 @@ static void launch_stage_t(const LaunchSet &ls, int stage, cudaStream_t st) {
             k_efinish<<<ls.nsys < 1024 ? ls.nsys : 1024, 256, 0, st>>>(ls.sys, ls.nsys);
             break;
     }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_stage(const LaunchSet &ls, int prec, int stage, cudaStream_t st) {
-    if (prec == 1) launch_stage_t<float>(ls, stage, st);
-    else launch_stage_t<double>(ls, stage, st);
-    return cudaGetLastError();
+    if (prec == 1) return launch_stage_t<float>(ls, stage, st);
+    return launch_stage_t<double>(ls, stage, st);
 }
 
 cudaError_t launch_all(const LaunchSet &ls, int prec, cudaStream_t st, cudaEvent_t *ev) {
     if (ev) cudaEventRecord(ev[0], st);
     for (int k = 0; k < NSTAGE; ++k) {
-        if (prec == 1) launch_stage_t<float>(ls, k, st);
-        else launch_stage_t<double>(ls, k, st);
+        const cudaError_t e = prec == 1 ? launch_stage_t<float>(ls, k, st) : launch_stage_t<double>(ls, k, st);
+        if (e != cudaSuccess) return e;
         if (ev) cudaEventRecord(ev[k + 1], st);
     }
     return cudaGetLastError();
@@ -1213,7 +1223,8 @@ size_t contract_smem(int prec, int maxspan) {
 }
 
 const char *stage_name(int i) {
-    static const char *names[NSTAGE] = {"zfwd", "yfwd", "xfwd", "contract", "xinv", "yinv", "zinv", "efinish"};
+    static const char *names[NSTAGE] = {"zfwd", "plane", "yfwd", "xfwd", "contract", "xinv", "yinv", "zinv",
+                                        "efinish"};
     return (i >= 0 && i < NSTAGE) ? names[i] : "";
 }
 

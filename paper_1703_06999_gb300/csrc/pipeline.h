@@ -8,22 +8,23 @@ namespace vdwgb {
 // Everything one launch of the five stages needs: device descriptors of all
 // systems, per-stage tile prefix sums (device), grid and shared memory.
 // Tile kinds: 0 z-forward, 1 y (both directions), 2 x (both directions),
-// 3 z-inverse, 4 contraction chunks.
+// 3 z-inverse, 4 contraction chunks, 5 kz-planes (fused plane kernel).
 struct LaunchSet {
     const SysDev *sys;       // device array [nsys]
-    const int *prefix[5];    // device arrays [nsys + 1]
+    const int *prefix[6];    // device arrays [nsys + 1]
     int nsys;
-    int total[5];            // tiles per kind over all systems
-    int grid[5];
-    size_t smem[5];
+    int total[6];            // tiles per kind over all systems
+    int grid[6];
+    size_t smem[6];
     int maxspan;             // contraction: kernel-table intervals staged per chunk
     const void *table;       // kernel polynomial table (float4 or dvec4), [210][NK-1]
-    int twmax[5];            // longest axis of the stage over all systems (twiddle slots)
-    int bufelems[5];         // complex elements of one row-tile buffer (x / y stages)
-    int nbuf[5];             // row-tile buffers of the x / y stages: 3 (prefetching) or 2
+    int twmax[6];            // longest axis of the stage over all systems (twiddle slots)
+    int bufelems[6];         // complex elements of one row-tile buffer (x / y stages)
+    int nbuf[6];             // row-tile buffers of the x / y stages: 3 (prefetching) or 2
     int recelems;            // z-inverse: point records per staged tile
     int abelems;             // z-inverse: complex elements of one transform buffer
     int *err;                // device flag set by a stage whose bounded wait ran out
+    int cluster;             // plane kernel: CTAs per cluster
 };
 
 // Row stride (complex elements) of the z-pass transform buffers for nl lines
@@ -34,12 +35,19 @@ size_t stage_smem(int stage, int prec, int n, int tile, int nbuf = 3);
 size_t zinv_smem(int prec, int nzmax, int inelems, int recelems, int abelems);
 size_t contract_smem(int prec, int maxspan);
 cudaError_t init_kernels(size_t maxsmem);
-constexpr int NSTAGE = 8;   // kernel launches per evaluation
-constexpr int NKIND = 5;    // tile kinds
+constexpr int NSTAGE = 9;   // stages per evaluation (stages without tiles are not launched)
+constexpr int NKIND = 6;    // tile kinds
 // Enqueue all stages; if ev != nullptr, record ev[0..NSTAGE] around them.
 cudaError_t launch_all(const LaunchSet &ls, int prec, cudaStream_t st, cudaEvent_t *ev = nullptr);
-// one stage: 0 zfwd, 1 yfwd, 2 xfwd, 3 contract, 4 xinv, 5 yinv, 6 zinv, 7 efinish
+// one stage: 0 zfwd, 1 plane, 2 yfwd, 3 xfwd, 4 contract, 5 xinv, 6 yinv, 7 zinv, 8 efinish
 cudaError_t launch_stage(const LaunchSet &ls, int prec, int stage, cudaStream_t st);
+// tile kind a stage walks (-1: efinish, one block per system)
+int stage_kind(int stage);
+// plane kernel: shared memory per CTA, launch, attributes, clusters per GPU
+size_t plane_smem(int nx, int ny, int C);
+cudaError_t launch_plane(const LaunchSet &ls, cudaStream_t st);
+cudaError_t init_plane_kernel(size_t maxsmem);
+int plane_max_clusters(int C, size_t smem);
 const char *stage_name(int i);
 cudaError_t upload_qmesh(const QMeshDev &q);
 cudaError_t launch_q0(int prec, int npts, const double *n, const double *s, double Z, double *q0, double *dqdn,
