@@ -208,9 +208,10 @@ static void choose_tiles(int prec, int nx, int ny, int nz, int nzh, size_t lim, 
 // Sort the half-spectrum k-points of a system by kernel-table interval
 // j = floor(|k| / dk) (|k| with the same Nyquist convention as the kernels;
 // intervals beyond the table form their own group) and cut the order into
-// chunks of at most 256 k-points spanning at most `maxspan` intervals.
+// chunks of at most `chunkmax` k-points spanning at most `maxspan` intervals.
 // chunk = {first index into kidx, count, first interval, intervals (0 beyond)}.
-static void build_chunks(const SysDev &S, int maxspan, std::vector<unsigned> &kidx, std::vector<int4> &chunks) {
+static void build_chunks(const SysDev &S, int maxspan, int chunkmax, std::vector<unsigned> &kidx,
+                         std::vector<int4> &chunks) {
     const int nx = S.nx, ny = S.ny, nz = S.nz, nzh = S.nzh;
     const size_t nk = (size_t)nx * ny * nzh;
     const double dk = 2.0 * M_PI / RMAX;
@@ -252,7 +253,7 @@ static void build_chunks(const SysDev &S, int maxspan, std::vector<unsigned> &ki
         c.z = j0;
         size_t n = 0;
         int jl = j0;
-        while (i + n < nk && n < 256) {
+        while (i + n < nk && n < (size_t)chunkmax) {
             const int jb = bin[kidx[i + n]];
             if (j0 == NK - 1 ? jb != NK - 1 : (jb == NK - 1 || jb - j0 >= maxspan)) break;
             jl = jb;
@@ -588,6 +589,7 @@ static int plan(vdwgb_data *h) {
     S.g[3] = g[0][1];
     S.g[4] = g[0][2];
     S.g[5] = g[1][2];
+    for (int i = 0; i < 6; ++i) S.gf[i] = (float)S.g[i];
     const double N = (double)nx * ny * nz;
     const double omega = std::fabs(det);
     S.escale = 0.5 * omega / (N * N);
@@ -595,7 +597,8 @@ static int plan(vdwgb_data *h) {
     S.Z = h->functional == VDWGB_DF2 ? -1.887 : -0.8491;
     // half-spectrum k-points sorted by kernel-table interval, cut into chunks
     // (or, for the plane kernel, per plane and cluster rank)
-    const int maxspan = prec == VDWGB_FP32_MIXED ? 16 : 8;
+    const int maxspan = prec == VDWGB_FP32_MIXED ? SPAN32 : SPAN64;
+    const int chunkmax = prec == VDWGB_FP32_MIXED ? CHUNK32 : CHUNK64;
     std::vector<unsigned> kidx;
     std::vector<int4> chunks;
     std::vector<unsigned short> kord;
@@ -610,7 +613,7 @@ static int plan(vdwgb_data *h) {
         S.tiles[5] = nzh;
         S.nepart = nzh * C;
     } else {
-        build_chunks(S, maxspan, kidx, chunks);
+        build_chunks(S, maxspan, chunkmax, kidx, chunks);
         S.tiles[4] = (int)chunks.size();
         S.tiles[5] = 0;
         S.nepart = S.tiles[4];

@@ -82,6 +82,7 @@ struct SysDev {
     AxisPlan ax[3];  // x, y, z
     const void *tw[3];   // twiddles exp(-2 pi i m / n), m < n, per axis (T complex)
     double g[6];     // reciprocal metric g00 g11 g22 g01 g02 g12 (|k|^2 = m^T g m)
+    float gf[6];     // the same in FP32
     double escale;   // 1/2 Omega / N^2
     double invN;     // 1 / N
     double Z;        // Z_ab of the functional
@@ -306,6 +307,21 @@ __device__ __forceinline__ int find_sys(const int *prefix, int nsys, int t) {
         else hi = mid - 1;
     }
     return lo;
+}
+
+// Tiles are walked in increasing order, so the owning system only moves
+// forward: advance from the current owner (usually zero or one step).
+__device__ __forceinline__ int advance_sys(const int *prefix, int nsys, int t, int si) {
+    if (si < 0) return find_sys(prefix, nsys, t);
+    while (si + 1 < nsys && prefix[si + 1] <= t) ++si;
+    return si;
+}
+
+// Copy a system descriptor into shared memory (all threads of the block).
+__device__ __forceinline__ void copy_sys(SysDev *dst, const SysDev *src) {
+    const int *s = reinterpret_cast<const int *>(src);
+    int *d = reinterpret_cast<int *>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(SysDev) / sizeof(int)); i += blockDim.x) d[i] = s[i];
 }
 
 }  // namespace vdwgb

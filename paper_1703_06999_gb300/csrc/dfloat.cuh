@@ -34,6 +34,36 @@ __device__ __forceinline__ dfl df_from(double x) {
 }
 __device__ __forceinline__ double df_to(dfl a) { return (double)a.hi + (double)a.lo; }
 
+// Split a double into hi + lo on the integer and FP32 pipes (GB300's FP64 pipe,
+// which also converts, runs at 1/64 of the FP32 rate): hi keeps the top 24
+// significand bits (truncated), lo the next bits rounded to FP32, then one
+// renormalising fast two-sum.  Outside the normal FP32 range of hi the
+// hardware conversion is used (rare: densities and gradients there are
+// negligible or the point is below the density cut-off).
+__device__ __forceinline__ dfl df_from_bits(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ed = (int)((b >> 52) & 0x7ff);
+    const int ef = ed - 1023 + 127;          // FP32 biased exponent of hi
+    const int el = ed - 1075 + 127;          // FP32 biased exponent of the unit of the low 29 bits
+    if (ef < 1 || ef > 254 || el < 1) return df_from(x);
+    const unsigned sign = (unsigned)(b >> 63) << 31;
+    const float hi = __uint_as_float(sign | ((unsigned)ef << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+    const float lmag = __uint2float_rn((unsigned)(b & 0x1fffffffu)) * __uint_as_float((unsigned)el << 23);
+    return df_quick(hi, sign ? -lmag : lmag);
+}
+
+// Widen an FP32 value to FP64 on the integer pipe (zero and values outside the
+// normal range via the hardware conversion).
+__device__ __forceinline__ double f2d_bits(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 255u) return (double)f;
+    const unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
+                                 ((unsigned long long)(e - 127u + 1023u) << 52) |
+                                 ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
 __device__ __forceinline__ dfl df_add(dfl a, dfl b) {
     float s, e, t, f;
     two_sum(a.hi, b.hi, s, e);

@@ -27,8 +27,9 @@ namespace {
 constexpr int NA_MAX_AXIS = 64;
 constexpr size_t NA_MAX_POINTS = 32768;     // nx * ny * nz
 constexpr size_t NA_MAX_KPOINTS = 17408;    // nx * ny * (nz / 2 + 1), e.g. 32 x 32 x 17
-constexpr int NA_MAXSPAN = 16;               // kernel-table intervals per contraction chunk
-constexpr int NA_MAX_CHUNKS = (int)(NA_MAX_KPOINTS / 256) + NK / NA_MAXSPAN + 4;
+constexpr int NA_MAXSPAN = SPAN32;           // kernel-table intervals per contraction chunk
+constexpr int NA_CHUNK = CHUNK32;            // k-points per contraction chunk
+constexpr int NA_MAX_CHUNKS = (int)(NA_MAX_KPOINTS / NA_CHUNK) + NK / NA_MAXSPAN + 4;
 
 constexpr size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 constexpr size_t OFF_SPEC = 0;
@@ -125,7 +126,7 @@ int sort_chunks(const SysDev &S) {
         const int j0 = h_bin[h_kidx[i]];
         size_t n = 0;
         int jl = j0;
-        while (i + n < nk && n < 256) {
+        while (i + n < nk && n < (size_t)NA_CHUNK) {
             const int jb = h_bin[h_kidx[i + n]];
             if (j0 == NK - 1 ? jb != NK - 1 : (jb == NK - 1 || jb - j0 >= NA_MAXSPAN)) break;
             jl = jb;
@@ -192,6 +193,7 @@ extern "C" int vdwgb_calculate_noalloc(int device, int functional, int nx, int n
     S.g[3] = gdot(0, 1);
     S.g[4] = gdot(0, 2);
     S.g[5] = gdot(1, 2);
+    for (int i = 0; i < 6; ++i) S.gf[i] = (float)S.g[i];
     const double N = (double)nx * ny * nz;
     S.escale = 0.5 * std::fabs(det) / (N * N);
     S.invN = 1.0 / N;

@@ -103,6 +103,7 @@ struct Q0M {
     int j;
     float B;
     float dqdn, dqds;
+    float nf;        // n rounded to FP32
     double q0;
 };
 
@@ -219,20 +220,24 @@ __device__ __forceinline__ dfl df_exp_neg2(dfl S, const float2 *ex2) {
 // zc = -Z_ab / 36 in double-float (positive)
 __device__ __forceinline__ Q0M q0_point_df(double n, double s, dfl zc, const Q0Tab *tb) {
     Q0M r;
-    r.live = n > c_qm.n_min;
+    // n > n_min and sigma < 0 -> 0 compared as integers (IEEE order of
+    // non-negative doubles), keeping the FP64 pipe free
+    r.live = __double_as_longlong(n) > __double_as_longlong(c_qm.n_min);
     r.dqdn = 0.f;
     r.dqds = 0.f;
+    r.nf = 0.f;
     if (!r.live) {
         r.j = -1;
         r.B = 0.f;
         r.q0 = c_qm.q_min;
         return r;
     }
-    s = s > 0.0 ? s : 0.0;
+    if (__double_as_longlong(s) <= 0) s = 0.0;
     const double A = 0.031091, a1 = 0.2137;
     const double b1 = 7.5957, b2 = 3.5876, b3 = 1.6382, b4 = 0.49294;
     const double PI = 3.14159265358979323846;
-    const dfl nd = df_from(n), sd = df_from(s);
+    const dfl nd = df_from_bits(n), sd = df_from_bits(s);
+    r.nf = nd.hi + nd.lo;
     const dfl kF = df_cbrt(df_mul(nd, DF(3.0 * PI * PI)));
     const dfl ikF = df_rcp_fast(kF);
     const dfl rs = df_mul(ikF, DF(1.9191582926775128));      // (9 pi / 4)^(1/3) / k_F
@@ -424,10 +429,20 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zfwd(const SysD
     unsigned char *base = smem + align_up(sizeof(QShared<T>), 16);
     load_qshared(qs);
     const int nt = blockDim.x;
+    __shared__ SysDev sS;                    // descriptor of the current tile's system
+    int cur_sys = -1, tbase = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
-        const int si = find_sys(prefix, nsys, t);
-        const SysDev &S = sys[si];
-        const int lt = t - prefix[si];
+        const int nsi = advance_sys(prefix, nsys, t, cur_sys);
+        const bool changed = nsi != cur_sys;
+        if (changed) {
+            __syncthreads();                 // readers of the previous descriptor are done
+            copy_sys(&sS, &sys[nsi]);
+            __syncthreads();
+            cur_sys = nsi;
+            tbase = prefix[nsi];
+        }
+        const SysDev &S = sS;
+        const int lt = t - tbase;
         const int nz = S.nz, nzh = S.nzh, LZ = S.LZ;
         const int nlines_tot = S.nx * S.ny;
         const int l0 = lt * LZ;
@@ -437,9 +452,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zfwd(const SysD
         cx<T> *tw = reinterpret_cast<cx<T> *>(base);
         cx<T> *bufA = tw + ((nz + 1) & ~1);
         cx<T> *bufB = bufA + (size_t)nz * ld;
-        const cx<T> *twg = reinterpret_cast<const cx<T> *>(S.tw[2]);
-        for (int i = threadIdx.x; i < nz; i += nt) tw[i] = twg[i];
-        __syncthreads();   // q tables and twiddles ready
+        if (changed) {
+            const cx<T> *twg = reinterpret_cast<const cx<T> *>(S.tw[2]);
+            for (int i = threadIdx.x; i < nz; i += nt) tw[i] = twg[i];
+            __syncthreads();   // q tables and twiddles ready
+        }
         Rec<T> *rec = reinterpret_cast<Rec<T> *>(S.rec);
         const size_t p0 = (size_t)l0 * nz;
         const double *gn = S.n + p0, *gs = S.sigma + p0;
@@ -454,14 +471,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zfwd(const SysD
                 const double sg = gs[i];
                 Rec<T> r;
                 int j = -1;
-                T B = (T)0, ndqn = (T)0, ndqs = (T)0;
+                T B = (T)0, ndqn = (T)0, ndqs = (T)0, nn = (T)0;
                 if (sizeof(T) == 4) {
                     const Q0M q = q0_point_df(n, sg, zc, &qs->q0t);
                     j = q.j;
                     B = (T)q.B;
-                    ndqn = (T)((float)n * q.dqdn);
-                    ndqs = (T)((float)n * q.dqds);
+                    nn = (T)q.nf;
+                    ndqn = (T)(q.nf * q.dqdn);
+                    ndqs = (T)(q.nf * q.dqds);
                 } else {
+                    nn = (T)n;
                     const Q0 q = q0_point(n, sg, S.Z);
                     if (q.live) {
                         j = q_interval(q.q0, qs->q);
@@ -477,7 +496,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zfwd(const SysD
                     T r0[NQ], r1[NQ];
                     d2_rows<T>(j, qs->d2, r0, r1);
                     const T h = qs->h[j], A = (T)1 - B;
-                    const T nn = (T)n;
                     const T cA = nn * (A * A * A - A) * h * h / (T)6;
                     const T cB = nn * (B * B * B - B) * h * h / (T)6;
 #pragma unroll
@@ -599,12 +617,10 @@ struct XYTile {
 };
 
 template <bool XPASS>
-__device__ __forceinline__ XYTile xy_tile(const SysDev *__restrict__ sys, const int *__restrict__ prefix, int nsys,
-                                          int t) {
+__device__ __forceinline__ XYTile xy_tile(const SysDev &S, int si, int lt) {
     XYTile g;
-    g.si = find_sys(prefix, nsys, t);
-    const SysDev &S = sys[g.si];
-    g.lt = t - prefix[g.si];
+    g.si = si;
+    g.lt = lt;
     const int W = XPASS ? S.Wx : S.Wy;
     const int ncol = (S.nzh + W - 1) / W;
     g.outer = g.lt / ncol;
@@ -623,12 +639,18 @@ __device__ __forceinline__ XYTile xy_tile(const SysDev *__restrict__ sys, const 
     return g;
 }
 
-// warp 0 issues the bulk copies of tile t into buf (completion on bar)
+// warp 0 issues the bulk copies of tile t into buf (completion on bar); the
+// tile's system descriptor is `cached` (shared memory) when it is system
+// `cached_si`, else read from global memory
 template <typename T, bool XPASS>
 __device__ __forceinline__ void xy_issue(const SysDev *__restrict__ sys, const int *__restrict__ prefix, int nsys,
-                                         int t, cx<T> *buf, unsigned long long *bar) {
-    const XYTile g = xy_tile<XPASS>(sys, prefix, nsys, t);
-    const cx<T> *spec = reinterpret_cast<const cx<T> *>(sys[g.si].spec);
+                                         int t, cx<T> *buf, unsigned long long *bar, const SysDev *cached = nullptr,
+                                         int cached_si = -1, int cached_base = 0) {
+    const int si = advance_sys(prefix, nsys, t, cached_si);
+    const bool hit = cached && si == cached_si;
+    const SysDev &S = hit ? *cached : sys[si];
+    const XYTile g = xy_tile<XPASS>(S, si, t - (hit ? cached_base : prefix[si]));
+    const cx<T> *spec = reinterpret_cast<const cx<T> *>(S.spec);
     const unsigned rowbytes = (unsigned)(g.L * sizeof(cx<T>));
     const int lane = threadIdx.x & 31;
     fence_proxy_async();
@@ -663,20 +685,26 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_xy(const SysDev
     unsigned ph[2] = {0u, 0u};
     int t = blockIdx.x;
     if (t < total && threadIdx.x < 32) xy_issue<T, XPASS>(sys, prefix, nsys, t, bufs[0], &bar[0]);
-    int cur_sys = -1;
+    __shared__ SysDev sS;                    // descriptor of the current tile's system
+    int cur_sys = -1, tbase = 0;
     for (int i = 0; t < total; ++i, t += gridDim.x) {
         const int cur = i & 1;
         const int tn = t + gridDim.x;
-        if (nbuf == 3 && tn < total && threadIdx.x < 32)
-            xy_issue<T, XPASS>(sys, prefix, nsys, tn, bufs[cur ^ 1], &bar[cur ^ 1]);
-        const XYTile g = xy_tile<XPASS>(sys, prefix, nsys, t);
-        const SysDev &S = sys[g.si];
-        const AxisPlan &ap = S.ax[XPASS ? 0 : 1];
-        if (g.si != cur_sys) {
-            const cx<T> *twg = reinterpret_cast<const cx<T> *>(S.tw[XPASS ? 0 : 1]);
-            for (int k = threadIdx.x; k < ap.n; k += blockDim.x) tw[k] = twg[k];
-            cur_sys = g.si;
+        const int nsi = advance_sys(prefix, nsys, t, cur_sys);
+        if (nsi != cur_sys) {
+            __syncthreads();                 // readers of the previous descriptor are done
+            copy_sys(&sS, &sys[nsi]);
+            __syncthreads();
+            const cx<T> *twg = reinterpret_cast<const cx<T> *>(sS.tw[XPASS ? 0 : 1]);
+            for (int k = threadIdx.x; k < sS.ax[XPASS ? 0 : 1].n; k += blockDim.x) tw[k] = twg[k];
+            cur_sys = nsi;
+            tbase = prefix[nsi];
         }
+        if (nbuf == 3 && tn < total && threadIdx.x < 32)
+            xy_issue<T, XPASS>(sys, prefix, nsys, tn, bufs[cur ^ 1], &bar[cur ^ 1], &sS, cur_sys, tbase);
+        const SysDev &S = sS;
+        const XYTile g = xy_tile<XPASS>(S, nsi, t - tbase);
+        const AxisPlan &ap = S.ax[XPASS ? 0 : 1];
         bool ok = mbar_wait(&bar[cur], ph[cur]);
         ph[cur] ^= 1u;
         if (!__syncthreads_and(ok)) {
@@ -706,7 +734,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_xy(const SysDev
         fence_proxy_async();   // this tile's generic accesses before the next bulk writes
         __syncthreads();
         if (nbuf == 2 && tn < total && threadIdx.x < 32)
-            xy_issue<T, XPASS>(sys, prefix, nsys, tn, bufs[cur ^ 1], &bar[cur ^ 1]);
+            xy_issue<T, XPASS>(sys, prefix, nsys, tn, bufs[cur ^ 1], &bar[cur ^ 1], &sS, cur_sys, tbase);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -850,6 +878,223 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_contract(const 
 }
 
 // ---------------------------------------------------------------------------
+// FP32-mixed contraction (procedure step 3, as k_contract) with a producer
+// warp: warp 0 walks the chunk list (system, chunk record, k-point order) and
+// issues the loads of the next chunk — ten 16-byte cp.async copies per k-point
+// record and one bulk copy of the chunk's table rows — into the free half of
+// a double buffer, while warps 1..15 compute the current chunk entirely from
+// shared memory (one k-point per thread, up to CHUNK32 = 480 per chunk).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+// arrive on bar when all earlier cp.async copies of this thread have landed
+__device__ __forceinline__ void cp_async_arrive(unsigned long long *bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_local(unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+constexpr int C32_THREADS = 512;            // warp 0 producer, warps 1..15 consumers
+constexpr int C32_ARRIVALS = 33;            // 32 cp.async arrivals + the row copy's expect-tx arrive
+
+struct C32Smem {
+    unsigned long long *full;   // [2]
+    SysDev *sys;                // [2] descriptor of the buffered chunk's system
+    int4 *meta;                 // [2] {count, first interval, intervals, chunk index in its system}
+    unsigned *idx;              // [2][CHUNK32] k-point indices
+    float4 *th;                 // [2][CHUNK32][10] theta records
+    float4 *rows;               // [2][SPAN32][NPAIR] table rows
+};
+
+__host__ __device__ inline size_t c32_off_sys() { return 64; }
+__host__ __device__ inline size_t c32_off_meta() { return c32_off_sys() + 2 * ((sizeof(SysDev) + 15) / 16) * 16; }
+__host__ __device__ inline size_t c32_off_idx() { return c32_off_meta() + 2 * sizeof(int4); }
+__host__ __device__ inline size_t c32_off_th() { return c32_off_idx() + 2 * CHUNK32 * sizeof(unsigned); }
+__host__ __device__ inline size_t c32_off_rows() { return c32_off_th() + 2 * (size_t)CHUNK32 * 10 * sizeof(float4); }
+__host__ __device__ inline size_t c32_smem_bytes() { return c32_off_rows() + 2 * (size_t)SPAN32 * NPAIR * sizeof(float4); }
+
+__device__ __forceinline__ C32Smem c32_smem(unsigned char *smem) {
+    C32Smem m;
+    m.full = reinterpret_cast<unsigned long long *>(smem);
+    m.sys = reinterpret_cast<SysDev *>(smem + c32_off_sys());
+    m.meta = reinterpret_cast<int4 *>(smem + c32_off_meta());
+    m.idx = reinterpret_cast<unsigned *>(smem + c32_off_idx());
+    m.th = reinterpret_cast<float4 *>(smem + c32_off_th());
+    m.rows = reinterpret_cast<float4 *>(smem + c32_off_rows());
+    return m;
+}
+
+// producer warp: loads of global chunk t into buffer half b
+__device__ __forceinline__ void c32_produce(const SysDev *__restrict__ sys, const int *__restrict__ prefix, int nsys,
+                                            int t, int b, int &psi, const C32Smem &m, const float4 *__restrict__ tab) {
+    const int lane = threadIdx.x & 31;
+    psi = advance_sys(prefix, nsys, t, psi);
+    const SysDev &S = sys[psi];
+    const int lt = t - prefix[psi];
+    const int4 c = S.chunks[lt];
+    // descriptor copy for the consumers
+    {
+        const int *src = reinterpret_cast<const int *>(&S);
+        int *dst = reinterpret_cast<int *>(&m.sys[b]);
+        for (int i = lane; i < (int)(sizeof(SysDev) / sizeof(int)); i += 32) dst[i] = src[i];
+    }
+    if (lane == 0) m.meta[b] = make_int4(c.y, c.z, c.w, lt);
+    const float4 *spec = reinterpret_cast<const float4 *>(S.spec);
+    unsigned kidx[CHUNK32 / 32];
+#pragma unroll
+    for (int r = 0; r < CHUNK32 / 32; ++r) {
+        const int k = lane + 32 * r;
+        kidx[r] = k < c.y ? S.kidx[c.x + k] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < CHUNK32 / 32; ++r) {
+        const int k = lane + 32 * r;
+        if (k < c.y) {
+            m.idx[b * CHUNK32 + k] = kidx[r];
+            const float4 *src = spec + (size_t)kidx[r] * 10;
+            float4 *dst = m.th + ((size_t)b * CHUNK32 + k) * 10;
+#pragma unroll
+            for (int a = 0; a < 10; ++a) cp_async16(dst + a, src + a);
+        }
+    }
+    cp_async_arrive(&m.full[b]);
+    __syncwarp();                                  // descriptor, meta and indices written
+    if (lane == 0) {
+        const int span = min(c.w, SPAN32);
+        if (span > 0) {
+            const unsigned bytes = (unsigned)(span * NPAIR * sizeof(float4));
+            fence_proxy_async();
+            mbar_expect_tx(&m.full[b], bytes);
+            bulk_g2s(m.rows + (size_t)b * SPAN32 * NPAIR, tab + (size_t)c.z * NPAIR, bytes, &m.full[b]);
+        } else {
+            mbar_arrive_local(&m.full[b]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__restrict__ sys, const int *__restrict__ prefix,
+                                                             int nsys, int total, const float4 *__restrict__ tab,
+                                                             int *__restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double red[C32_THREADS / 32];
+    const C32Smem m = c32_smem(smem);
+    const bool producer = threadIdx.x < 32;
+    __shared__ int s_failed;
+    if (threadIdx.x == 0) {
+        s_failed = 0;
+        mbar_init(&m.full[0], C32_ARRIVALS);
+        mbar_init(&m.full[1], C32_ARRIVALS);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    unsigned ph[2] = {0u, 0u};
+    int psi = -1;
+    bool failed = false;
+    const float inv_dk = (float)(RMAX / (2.0 * 3.14159265358979323846));
+    int t = blockIdx.x;
+    if (t < total && producer) c32_produce(sys, prefix, nsys, t, 0, psi, m, tab);
+    for (int i = 0; t < total; ++i, t += gridDim.x) {
+        const int b = i & 1;
+        const int tn = t + gridDim.x;
+        double eacc = 0.0;
+        if (producer) {
+            if (tn < total) c32_produce(sys, prefix, nsys, tn, b ^ 1, psi, m, tab);
+        } else {
+            const bool ok = !failed && mbar_wait(&m.full[b], ph[b]);
+            if (!ok && !failed) {
+                atomicExch(err, 1);
+                failed = true;
+                s_failed = 1;
+            }
+            const int4 mt = m.meta[b];
+            const int k = threadIdx.x - 32;
+            if (ok && k < mt.x) {
+                const SysDev &S = m.sys[b];
+                const unsigned idx = m.idx[b * CHUNK32 + k];
+                const int nx = S.nx, ny = S.ny, nz = S.nz, nzh = S.nzh;
+                const int kz = (int)(idx % (unsigned)nzh);
+                const int rest = (int)(idx / (unsigned)nzh);
+                const int y = rest % ny, x = rest / ny;
+                const int mx = fold(x, nx), my = fold(y, ny);
+                const bool nyq_x = (nx % 2 == 0) && (x == nx / 2);
+                const bool nyq_y = (ny % 2 == 0) && (y == ny / 2);
+                const bool nyq_z = (nz % 2 == 0) && (kz == nz / 2);
+                const int mz = nyq_z ? -kz : kz;
+                const float fx = (float)mx, fy = (float)my, fz = (float)mz;
+                const float cxv = nyq_x ? 0.f : fx, cyv = nyq_y ? 0.f : fy, czv = nyq_z ? 0.f : fz;
+                float k2 = S.gf[0] * fx * fx + S.gf[1] * fy * fy + S.gf[2] * fz * fz +
+                           2.f * (S.gf[3] * cxv * cyv + S.gf[4] * cxv * czv + S.gf[5] * cyv * czv);
+                k2 = k2 > 0.f ? k2 : 0.f;
+                const float xk = sqrtf(k2) * inv_dk;
+                const int j = (int)xk;
+                const float tt = xk - (float)j;
+                const float4 *v4 = m.th + ((size_t)b * CHUNK32 + k) * 10;
+                cx<float> th[NQ], F[NQ];
+#pragma unroll
+                for (int a = 0; a < NQ / 2; ++a) {
+                    const float4 q = v4[a];
+                    th[2 * a] = cx<float>{q.x, q.y};
+                    th[2 * a + 1] = cx<float>{q.z, q.w};
+                }
+#pragma unroll
+                for (int a = 0; a < NQ; ++a) F[a] = cx<float>{0.f, 0.f};
+                const int span = min(mt.z, SPAN32);
+                if (j < NK - 1) {
+                    // the interval's row: staged, else (rounding at a chunk edge) global
+                    const bool staged = span > 0 && j >= mt.y && j < mt.y + span;
+                    const float4 *row = staged ? m.rows + ((size_t)b * SPAN32 + (j - mt.y)) * NPAIR
+                                               : tab + (size_t)j * NPAIR;
+                    int pidx = 0;
+#pragma unroll
+                    for (int a = 0; a < NQ; ++a) {
+#pragma unroll
+                        for (int bb = a; bb < NQ; ++bb) {
+                            const float4 cf = staged ? row[pidx] : __ldg(row + pidx);
+                            const float phi = cf.x + tt * (cf.y + tt * (cf.z + tt * cf.w));
+                            F[a].x += phi * th[bb].x;
+                            F[a].y += phi * th[bb].y;
+                            if (bb != a) {
+                                F[bb].x += phi * th[a].x;
+                                F[bb].y += phi * th[a].y;
+                            }
+                            ++pidx;
+                        }
+                    }
+                }
+                float e = 0.f;
+#pragma unroll
+                for (int a = 0; a < NQ; ++a) e += th[a].x * F[a].x + th[a].y * F[a].y;
+                const float weight = (kz == 0 || nyq_z) ? 1.f : 2.f;
+                eacc = (double)(weight * e);
+                float4 *out = reinterpret_cast<float4 *>(S.spec) + (size_t)idx * 10;
+#pragma unroll
+                for (int a = 0; a < NQ / 2; ++a)
+                    out[a] = make_float4(F[2 * a].x, F[2 * a].y, F[2 * a + 1].x, F[2 * a + 1].y);
+            }
+        }
+        ph[b] ^= 1u;
+        const double es = block_sum<float>(eacc, red);
+        if (threadIdx.x == 0) m.sys[b].epart[m.meta[b].w] = es;
+        __syncthreads();                             // buffer half b free for chunk t + 2 gridDim
+        if (s_failed) {
+            // a bounded wait ran out: let the copies of the chunk in flight land, then stop
+            if (producer) cp_async_wait_all();
+            if (threadIdx.x == 0 && tn < total) mbar_wait(&m.full[b ^ 1], ph[b ^ 1]);
+            break;
+        }
+    }
+    if (producer) cp_async_wait_all();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_inval(&m.full[0]);
+        mbar_inval(&m.full[1]);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // z-inverse: complex-to-real along z, then the potential.  A tile is LZi
 // consecutive (x, y) lines; their half spectra and point records are one
 // contiguous range each, fetched by two bulk copies into a double-buffered
@@ -857,10 +1102,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_contract(const 
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void zinv_issue(const SysDev *__restrict__ sys, const int *__restrict__ prefix, int nsys,
-                                           int t, cx<T> *ibuf, Rec<T> *rbuf, unsigned long long *bar) {
-    const int si = find_sys(prefix, nsys, t);
-    const SysDev &S = sys[si];
-    const int lt = t - prefix[si];
+                                           int t, cx<T> *ibuf, Rec<T> *rbuf, unsigned long long *bar,
+                                           const SysDev *cached = nullptr, int cached_si = -1, int cached_base = 0) {
+    const int si = advance_sys(prefix, nsys, t, cached_si);
+    const bool hit = cached && si == cached_si;
+    const SysDev &S = hit ? *cached : sys[si];
+    const int lt = t - (hit ? cached_base : prefix[si]);
     const int l0 = lt * S.LZi;
     const int nl = min(S.LZi, S.nx * S.ny - l0);
     const unsigned sb = (unsigned)((size_t)nl * S.nzh * NQ * sizeof(cx<T>));
@@ -895,23 +1142,29 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zinv(const SysD
     unsigned ph[2] = {0u, 0u};
     int t = blockIdx.x;
     if (t < total && threadIdx.x == 0) zinv_issue<T>(sys, prefix, nsys, t, ins[0], recs[0], &bar[0]);
-    int cur_sys = -1;
+    __shared__ SysDev sS;                    // descriptor of the current tile's system
+    int cur_sys = -1, tbase = 0;
     for (int it = 0; t < total; ++it, t += gridDim.x) {
         const int cur = it & 1;
         const int tn = t + gridDim.x;
-        if (tn < total && threadIdx.x == 0) zinv_issue<T>(sys, prefix, nsys, tn, ins[cur ^ 1], recs[cur ^ 1], &bar[cur ^ 1]);
-        const int si = find_sys(prefix, nsys, t);
-        const SysDev &S = sys[si];
-        const int lt = t - prefix[si];
+        const int nsi = advance_sys(prefix, nsys, t, cur_sys);
+        if (nsi != cur_sys) {
+            __syncthreads();                 // readers of the previous descriptor are done
+            copy_sys(&sS, &sys[nsi]);
+            __syncthreads();
+            const cx<T> *twg = reinterpret_cast<const cx<T> *>(sS.tw[2]);
+            for (int i = threadIdx.x; i < sS.nz; i += blockDim.x) tw[i] = twg[i];
+            cur_sys = nsi;
+            tbase = prefix[nsi];
+        }
+        if (tn < total && threadIdx.x == 0)
+            zinv_issue<T>(sys, prefix, nsys, tn, ins[cur ^ 1], recs[cur ^ 1], &bar[cur ^ 1], &sS, cur_sys, tbase);
+        const SysDev &S = sS;
+        const int lt = t - tbase;
         const int nz = S.nz, nzh = S.nzh;
         const int l0 = lt * S.LZi;
         const int nl = min(S.LZi, S.nx * S.ny - l0);
         const int L = 10 * nl;
-        if (si != cur_sys) {
-            const cx<T> *twg = reinterpret_cast<const cx<T> *>(S.tw[2]);
-            for (int i = threadIdx.x; i < nz; i += blockDim.x) tw[i] = twg[i];
-            cur_sys = si;
-        }
         const bool ok = mbar_wait(&bar[cur], ph[cur]);
         ph[cur] ^= 1u;
         if (!__syncthreads_and(ok)) {
@@ -1001,8 +1254,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zinv(const SysD
                     const T dB = ((T)3 * B * B - (T)1) * h / (T)6;
                     const T s0 = (A * Fj + B * Fj1 + cA * D0 + cB * D1) * invN;
                     const T s1 = ((Fj1 - Fj) / h + dA * D0 + dB * D1) * invN;
-                    dn = (double)(s0 + r.ndqn * s1);
-                    ds = (double)(r.ndqs * s1);
+                    if (sizeof(T) == 4) {
+                        dn = f2d_bits((float)(s0 + r.ndqn * s1));
+                        ds = f2d_bits((float)(r.ndqs * s1));
+                    } else {
+                        dn = (double)(s0 + r.ndqn * s1);
+                        ds = (double)(r.ndqs * s1);
+                    }
                 }
                 gdn[i] = dn;
                 gds[i] = ds;
@@ -1028,33 +1286,28 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zinv(const SysD
 // Energy: E = 1/2 (Omega / N^2) sum_k w_k sum_a Re(theta_a^* F_a), partials
 // summed in a fixed order with Neumaier compensation (one block per system).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void neumaier_add(double &s, double &c, double v) {
+    const double t = s + v;
+    c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
+    s = t;
+}
+
 __global__ void k_efinish(const SysDev *__restrict__ sys, int nsys) {
-    __shared__ double ssum[256], scmp[256];
-    for (int si = blockIdx.x; si < nsys; si += gridDim.x) {
+    // one warp per system: each lane sums a strided share of the partials,
+    // then the (sum, compensation) pairs meet in a fixed shuffle tree
+    const int lane = threadIdx.x & 31;
+    for (int si = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); si < nsys; si += gridDim.x * (blockDim.x >> 5)) {
         const SysDev &S = sys[si];
         const int n = S.nepart;
         double s = 0.0, c = 0.0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const double v = S.epart[i];
-            const double tt = s + v;
-            c += fabs(s) >= fabs(v) ? (s - tt) + v : (v - tt) + s;
-            s = tt;
+        for (int i = lane; i < n; i += 32) neumaier_add(s, c, S.epart[i]);
+        for (int o = 16; o > 0; o >>= 1) {
+            const double s2 = __shfl_down_sync(0xffffffffu, s, o);
+            const double c2 = __shfl_down_sync(0xffffffffu, c, o);
+            neumaier_add(s, c, s2);
+            c += c2;
         }
-        ssum[threadIdx.x] = s;
-        scmp[threadIdx.x] = c;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double S2 = 0.0, C2 = 0.0;
-            for (int i = 0; i < (int)blockDim.x; ++i) {
-                const double v = ssum[i];
-                const double tt = S2 + v;
-                C2 += fabs(S2) >= fabs(v) ? (S2 - tt) + v : (v - tt) + S2;
-                S2 = tt;
-                C2 += scmp[i];
-            }
-            *S.energy = S.escale * (S2 + C2);
-        }
-        __syncthreads();
+        if (lane == 0) *S.energy = S.escale * (s + c);
     }
 }
 
@@ -1143,6 +1396,9 @@ static cudaError_t init_kernels_t(size_t maxsmem) {
     if ((e = set_smem((const void *)k_xy<T, 2>, maxsmem)) != cudaSuccess) return e;
     if ((e = set_smem((const void *)k_xy<T, 3>, maxsmem)) != cudaSuccess) return e;
     if ((e = set_smem((const void *)k_contract<T>, maxsmem - 32 * sizeof(double))) != cudaSuccess) return e;
+    if (sizeof(T) == 4 && (e = set_smem((const void *)k_contract32, maxsmem - (C32_THREADS / 32) * sizeof(double))) !=
+                              cudaSuccess)
+        return e;
     if ((e = set_smem((const void *)k_zinv<T>, maxsmem)) != cudaSuccess) return e;
     return cudaSuccess;
 }
@@ -1189,15 +1445,19 @@ static cudaError_t launch_stage_t(const LaunchSet &ls, int stage, cudaStream_t s
                                                              ls.twmax[2], ls.bufelems[2], ls.nbuf[2], ls.err);
             break;
         case 4:
-            k_contract<T><<<ls.grid[4], 256, ls.smem[4], st>>>(ls.sys, ls.prefix[4], ls.nsys, ls.total[4],
-                                                                ls.maxspan, tab, ls.err);
+            if (sizeof(T) == 4)
+                k_contract32<<<ls.grid[4], C32_THREADS, ls.smem[4], st>>>(ls.sys, ls.prefix[4], ls.nsys, ls.total[4],
+                                                                           reinterpret_cast<const float4 *>(tab), ls.err);
+            else
+                k_contract<T><<<ls.grid[4], 256, ls.smem[4], st>>>(ls.sys, ls.prefix[4], ls.nsys, ls.total[4],
+                                                                    ls.maxspan, tab, ls.err);
             break;
         case 7:
             k_zinv<T><<<ls.grid[3], 256, ls.smem[3], st>>>(ls.sys, ls.prefix[3], ls.nsys, ls.total[3], ls.twmax[3],
                                                             ls.bufelems[3], ls.recelems, ls.abelems, ls.err);
             break;
         default:
-            k_efinish<<<ls.nsys < 1024 ? ls.nsys : 1024, 256, 0, st>>>(ls.sys, ls.nsys);
+            k_efinish<<<(ls.nsys + 3) / 4 < 1024 ? (ls.nsys + 3) / 4 : 1024, 128, 0, st>>>(ls.sys, ls.nsys);
             break;
     }
     return cudaGetLastError();
@@ -1219,7 +1479,8 @@ cudaError_t launch_all(const LaunchSet &ls, int prec, cudaStream_t st, cudaEvent
 }
 
 size_t contract_smem(int prec, int maxspan) {
-    return 32 + (size_t)maxspan * NPAIR * (prec == 1 ? sizeof(float4) : sizeof(dvec4));
+    if (prec == 1) return c32_smem_bytes();
+    return 32 + (size_t)maxspan * NPAIR * sizeof(dvec4);
 }
 
 const char *stage_name(int i) {

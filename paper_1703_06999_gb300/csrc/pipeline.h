@@ -31,6 +31,10 @@ struct LaunchSet {
 // (10 complex lines each); odd, so that consecutive rows start in different banks.
 __host__ __device__ inline int z_ld(int nl) { return 10 * nl + 1; }
 
+// contraction chunks: at most CHUNK k-points spanning at most SPAN table
+// intervals (FP32-mixed: one k-point per consumer thread, 15 consumer warps)
+constexpr int CHUNK32 = 480, SPAN32 = 8, CHUNK64 = 256, SPAN64 = 8;
+
 size_t stage_smem(int stage, int prec, int n, int tile, int nbuf = 3);
 size_t zinv_smem(int prec, int nzmax, int inelems, int recelems, int abelems);
 size_t contract_smem(int prec, int maxspan);
