@@ -13,6 +13,8 @@
 #include <cstdlib>
 #include <algorithm>
 
+#include <cuda.h>
+
 #include "internal.h"
 #include "table.h"
 #include "fftreg.cuh"
@@ -155,6 +157,8 @@ static void release(vdwgb_data *h) {
     dfree(h, h->kidx);
     dfree(h, h->chunks);
     dfree(h, h->kord);
+    dfree(h, h->tmap);
+    h->tmap = nullptr;
     h->kidx = nullptr;
     h->chunks = nullptr;
     h->kord = nullptr;
@@ -400,7 +404,73 @@ static void set_tiles(vdwgb_data *h, int LZ, int LZi, int Wy, int Wx, int nby, i
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor maps of the spectrum for the x / y passes (FP32): a 3-D view
+// [x][y][kz 20 + a] of 8-byte complex values; the y-pass box is W_y 20 x ny x 1
+// at (kz0 20, 0, x), the x-pass box W_x 20 x 1 x nx at (kz0 20, y, 0).  The
+// encoder comes from the driver through the runtime (no link to libcuda).
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// both maps of a handle's current plan; false if a box does not fit the
+// tensor-copy limits (each box side <= 256) or no encoder is available
+static bool encode_xy_maps(const SysDev &S, CUtensorMap maps[2]) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc || !S.spec) return false;
+    const int nzh = S.nzh;
+    if (S.nx > 256 || S.ny > 256 || S.Wy * NQ > 256 || S.Wx * NQ > 256) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)nzh * NQ, (cuuint64_t)S.ny, (cuuint64_t)S.nx};
+    const cuuint64_t strides[2] = {(cuuint64_t)nzh * NQ * 8, (cuuint64_t)S.ny * nzh * NQ * 8};
+    const cuuint32_t one[3] = {1, 1, 1};
+    const cuuint32_t box_y[3] = {(cuuint32_t)(S.Wy * NQ), (cuuint32_t)S.ny, 1};
+    const cuuint32_t box_x[3] = {(cuuint32_t)(S.Wx * NQ), 1, (cuuint32_t)S.nx};
+    for (int m = 0; m < 2; ++m) {
+        const CUresult r = enc(&maps[m], CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, S.spec, dims, strides,
+                               m == 0 ? box_y : box_x, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return false;
+    }
+    return true;
+}
+
+// encode the maps for the current tiles and point the descriptor at them (or
+// clear the pointer: row-by-row copies)
+static int upload_maps(vdwgb_data *h, bool sync) {
+    SysDev &S = h->hsys;
+    S.tmap = nullptr;
+    if (!h->tmap) return 0;
+    alignas(64) CUtensorMap maps[2];
+    if (!encode_xy_maps(S, maps)) return 0;
+    if (sync) CK(cudaMemcpy(h->tmap, maps, sizeof maps, cudaMemcpyHostToDevice), "tensor maps");
+    else CK(dupload(h, h->tmap, maps, sizeof maps), "tensor maps");
+    S.tmap = h->tmap;
+    return 0;
+}
+
 static int upload_plan(vdwgb_data *h) {
+    {
+        const int rc = upload_maps(h, false);
+        if (rc) return rc;
+    }
     int pre[2 * NKIND];
     for (int s = 0; s < NKIND; ++s) {
         pre[2 * s] = 0;
@@ -447,6 +517,10 @@ static int time_stage(vdwgb_data *h, int stage, float &ms) {
         pre[2 * s + 1] = h->hsys.tiles[s];
     }
     CK(cudaMemcpy(h->dprefix, pre, sizeof pre, cudaMemcpyHostToDevice), "prefix");
+    {
+        const int rc = upload_maps(h, true);
+        if (rc) return rc;
+    }
     CK(cudaMemcpy(h->dsys, &h->hsys, sizeof(SysDev), cudaMemcpyHostToDevice), "descriptor");
     cudaEvent_t a, b;
     CK(cudaEventCreate(&a), "event");
@@ -655,6 +729,7 @@ static int plan(vdwgb_data *h) {
                kidx.size() * sizeof(unsigned) + chunks.size() * sizeof(int4) + kord.size() * sizeof(unsigned short);
     CK(dalloc(h, &h->dsys, sizeof(SysDev)), "descriptor");
     CK(dalloc(h, &h->dprefix, 2 * NKIND * sizeof(int)), "prefix");
+    if (prec == VDWGB_FP32_MIXED) CK(dalloc(h, &h->tmap, 2 * sizeof(CUtensorMap)), "tensor maps");
     // launch set
     LaunchSet &L = h->ls;
     L.sys = h->dsys;
@@ -1063,7 +1138,7 @@ int vdwgb::batch_launchset(vdwgb_data *const *hs, int count, SysDev *hdesc, int 
     // x / y stages: shared memory from the largest row tile and twiddle table of the batch
     const size_t c = prec == VDWGB_FP32_MIXED ? 8 : 16;
     for (int s = 1; s <= 2; ++s)
-        L.smem[s] = 16 + c * ((size_t)((L.twmax[s] + 7) & ~7) + (size_t)L.nbuf[s] * L.bufelems[s]);
+        L.smem[s] = xy_smem_bytes(L.twmax[s], L.bufelems[s], L.nbuf[s], c);
     L.smem[3] = zinv_smem(prec, L.twmax[3], L.bufelems[3], L.recelems, L.abelems);
     const size_t lim = di.maxsmem - 1024;
     if (L.smem[1] > lim || L.smem[2] > lim || L.smem[3] > lim)

@@ -101,6 +101,7 @@ struct SysDev {
     int sx1, sy1;    // N1 of the two-pass splits of the x and y axes
     int kstride;     // entries per (kz, rank) list of kord
     const unsigned short *kord;   // per (kz, rank): local k-point indices sorted by table interval
+    const void *tmap;    // FP32: two tensor maps of spec (y-pass tile box, x-pass tile box), else null
     double *energy;  // output (device)
 };
 

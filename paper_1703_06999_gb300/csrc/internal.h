@@ -24,6 +24,7 @@ struct vdwgb_data {
     unsigned *kidx = nullptr;
     int4 *chunks = nullptr;
     unsigned short *kord = nullptr;    // plane kernel k-point order
+    void *tmap = nullptr;              // FP32: tensor maps of the x / y pass tiles
     vdwgb::SysDev *dsys = nullptr;
     int *dprefix = nullptr;
     vdwgb::SysDev hsys;

@@ -612,7 +612,7 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 }
 
 struct XYTile {
-    int si, lt, nrows, wt, L, outer, kz0;
+    int si, lt, nrows, wt, L, ldr, outer, kz0;   // L = wt 20 lines; rows W 20 apart in shared memory
     size_t g0, rowstride;
 };
 
@@ -627,6 +627,7 @@ __device__ __forceinline__ XYTile xy_tile(const SysDev &S, int si, int lt) {
     g.kz0 = (g.lt - g.outer * ncol) * W;
     g.wt = min(W, S.nzh - g.kz0);
     g.L = g.wt * NQ;
+    g.ldr = W * NQ;
     if (XPASS) {
         g.nrows = S.nx;
         g.g0 = ((size_t)g.outer * S.nzh + g.kz0) * NQ;
@@ -651,13 +652,24 @@ __device__ __forceinline__ void xy_issue(const SysDev *__restrict__ sys, const i
     const SysDev &S = hit ? *cached : sys[si];
     const XYTile g = xy_tile<XPASS>(S, si, t - (hit ? cached_base : prefix[si]));
     const cx<T> *spec = reinterpret_cast<const cx<T> *>(S.spec);
-    const unsigned rowbytes = (unsigned)(g.L * sizeof(cx<T>));
     const int lane = threadIdx.x & 31;
     fence_proxy_async();
+    if (S.tmap) {
+        // the whole tile in one tensor copy (box W 20 x rows; columns past
+        // the last kz are filled with zeros and never stored back)
+        if (lane == 0) {
+            const void *map = static_cast<const unsigned char *>(S.tmap) + (XPASS ? 128 : 0);
+            fence_tensormap(map);
+            mbar_expect_tx(bar, (unsigned)((size_t)g.ldr * g.nrows * sizeof(cx<T>)));
+            tma_load_3d(buf, map, g.kz0 * NQ, XPASS ? g.outer : 0, XPASS ? 0 : g.outer, bar);
+        }
+        return;
+    }
+    const unsigned rowbytes = (unsigned)(g.L * sizeof(cx<T>));
     if (lane == 0) mbar_expect_tx(bar, rowbytes * (unsigned)g.nrows);
     __syncwarp();
     for (int r = lane; r < g.nrows; r += 32)
-        bulk_g2s(buf + (size_t)r * g.L, spec + g.g0 + r * g.rowstride, rowbytes, bar);
+        bulk_g2s(buf + (size_t)r * g.ldr, spec + g.g0 + r * g.rowstride, rowbytes, bar);
 }
 
 // MODE 0: forward y, 1: inverse y, 2: forward x, 3: inverse x
@@ -668,14 +680,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_xy(const SysDev
                                                                    int *__restrict__ err) {
     constexpr bool XPASS = MODE >= 2;
     constexpr bool INV = (MODE & 1) != 0;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);   // 128-byte aligned
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem);
     cx<T> *tw = reinterpret_cast<cx<T> *>(smem + 16);
-    cx<T> *in0 = tw + ((twmax + 7) & ~7);
+    const size_t bstride = xy_buf_stride(bufelems, sizeof(cx<T>));
+    unsigned char *in0 = smem + xy_off_in(twmax, sizeof(cx<T>));
     // nbuf 3: two input stages (prefetch of the next tile) + transform scratch;
     // nbuf 2: one input stage, loaded after the previous tile is stored.
-    cx<T> *bufs[2] = {in0, nbuf == 3 ? in0 + bufelems : in0};
-    cx<T> *work = in0 + (size_t)(nbuf - 1) * bufelems;
+    cx<T> *bufs[2] = {reinterpret_cast<cx<T> *>(in0), reinterpret_cast<cx<T> *>(nbuf == 3 ? in0 + bstride : in0)};
+    cx<T> *work = reinterpret_cast<cx<T> *>(in0 + (size_t)(nbuf - 1) * bstride);
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -712,7 +726,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_xy(const SysDev
             if (nbuf == 3 && tn < total) mbar_wait(&bar[cur ^ 1], ph[cur ^ 1]);
             return;
         }
-        cx<T> *R = fft_auto<INV>(bufs[cur], work, ap, g.L, g.L, tw);
+        cx<T> *R = fft_auto<INV>(bufs[cur], work, ap, g.L, g.ldr, tw);
         // store the rows back (16-byte vectors), walking (row, e) without division
         cx<T> *spec = reinterpret_cast<cx<T> *>(S.spec) + g.g0;
         {
@@ -721,7 +735,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_xy(const SysDev
             const int de = blockDim.x % h, dr = blockDim.x / h;
             int e = threadIdx.x % h, r = threadIdx.x / h;
             for (; r < g.nrows;) {
-                const float4 v = *reinterpret_cast<const float4 *>(R + (size_t)r * g.L + PER * e);
+                const float4 v = *reinterpret_cast<const float4 *>(R + (size_t)r * g.ldr + PER * e);
                 *reinterpret_cast<float4 *>(spec + r * g.rowstride + PER * e) = v;
                 e += de;
                 r += dr;
@@ -1352,7 +1366,7 @@ size_t smem_z(int nz, int LZ) {
 }
 template <typename T>
 size_t smem_xy(int n, int W, int nbuf) {
-    return 16 + sizeof(cx<T>) * ((size_t)((n + 7) & ~7) + (size_t)nbuf * n * NQ * W);
+    return xy_smem_bytes(n, n * NQ * W, nbuf, sizeof(cx<T>));
 }
 
 template <typename T>

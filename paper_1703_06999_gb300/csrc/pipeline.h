@@ -35,6 +35,19 @@ __host__ __device__ inline int z_ld(int nl) { return 10 * nl + 1; }
 // intervals (FP32-mixed: one k-point per consumer thread, 15 consumer warps)
 constexpr int CHUNK32 = 480, SPAN32 = 8, CHUNK64 = 256, SPAN64 = 8;
 
+// Shared memory of an x / y pass block: barriers and twiddles, then nbuf
+// row-tile buffers at 128-byte aligned offsets (tensor copies land there);
+// 128 bytes of slack align the dynamic base at run time.
+__host__ __device__ inline size_t xy_off_in(int twmax, size_t csize) {
+    return (16 + (size_t)twmax * csize + 127) / 128 * 128;
+}
+__host__ __device__ inline size_t xy_buf_stride(int bufelems, size_t csize) {
+    return ((size_t)bufelems * csize + 127) / 128 * 128;
+}
+inline size_t xy_smem_bytes(int twmax, int bufelems, int nbuf, size_t csize) {
+    return 128 + xy_off_in(twmax, csize) + (size_t)nbuf * xy_buf_stride(bufelems, csize);
+}
+
 size_t stage_smem(int stage, int prec, int n, int tile, int nbuf = 3);
 size_t zinv_smem(int prec, int nzmax, int inelems, int recelems, int abelems);
 size_t contract_smem(int prec, int maxspan);

@@ -203,7 +203,6 @@ __global__ void __launch_bounds__(PLANE_THREADS, 2)
     unsigned lph = 0u, xph = 0u;
     bool failed = false;
     int cur_sys = -1;
-    const float inv_dk = (float)(RMAX / (2.0 * 3.14159265358979323846));
     for (int t = (int)cluster_index(); t < total; t += (int)cluster_count()) {
         const int si = find_sys(prefix, nsys, t);
         const SysDev &S = sys[si];
