@@ -37,18 +37,21 @@ __device__ __forceinline__ double df_to(dfl a) { return (double)a.hi + (double)a
 // Split a double into hi + lo on the integer and FP32 pipes (GB300's FP64 pipe,
 // which also converts, runs at 1/64 of the FP32 rate): hi keeps the top 24
 // significand bits (truncated), lo the next bits rounded to FP32, then one
-// renormalising fast two-sum.  Outside the normal FP32 range of hi the
-// hardware conversion is used (rare: densities and gradients there are
-// negligible or the point is below the density cut-off).
+// renormalising fast two-sum.  Below the normal FP32 range of hi (|x| under
+// about 1.2e-38) and above it the hardware conversion is used.
 __device__ __forceinline__ dfl df_from_bits(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const int ed = (int)((b >> 52) & 0x7ff);
     const int ef = ed - 1023 + 127;          // FP32 biased exponent of hi
     const int el = ed - 1075 + 127;          // FP32 biased exponent of the unit of the low 29 bits
-    if (ef < 1 || ef > 254 || el < 1) return df_from(x);
+    if (ef < 1 || ef > 254) return df_from(x);
     const unsigned sign = (unsigned)(b >> 63) << 31;
     const float hi = __uint_as_float(sign | ((unsigned)ef << 23) | (unsigned)((b >> 29) & 0x7fffffu));
-    const float lmag = __uint2float_rn((unsigned)(b & 0x1fffffffu)) * __uint_as_float((unsigned)el << 23);
+    // lo = rem 2^(el - 127), scaled in two exact steps: 2^-30, then
+    // 2^(el - 97) >= 2^-148 (a normal or subnormal power of two, as ef >= 1)
+    const int k = el - 97;
+    const float unit = k >= -126 ? __uint_as_float((unsigned)(k + 127) << 23) : __uint_as_float(1u << (k + 149));
+    const float lmag = (__uint2float_rn((unsigned)(b & 0x1fffffffu)) * 9.31322574615478515625e-10f) * unit;
     return df_quick(hi, sign ? -lmag : lmag);
 }
 

@@ -989,6 +989,30 @@ __device__ __forceinline__ void c32_produce(const SysDev *__restrict__ sys, cons
     }
 }
 
+// F_a += sum_b phi_ab(t) theta_b over the 210 symmetric pairs of one table
+// row (cubic in t); GLOBAL: the row is read from global memory, else from
+// shared memory
+template <bool GLOBAL>
+__device__ __forceinline__ void contract_row(const float4 *__restrict__ row, float tt, const cx<float> *th,
+                                             cx<float> *F) {
+    int pidx = 0;
+#pragma unroll
+    for (int a = 0; a < NQ; ++a) {
+#pragma unroll
+        for (int bb = a; bb < NQ; ++bb) {
+            const float4 cf = GLOBAL ? __ldg(row + pidx) : row[pidx];
+            const float phi = cf.x + tt * (cf.y + tt * (cf.z + tt * cf.w));
+            F[a].x += phi * th[bb].x;
+            F[a].y += phi * th[bb].y;
+            if (bb != a) {
+                F[bb].x += phi * th[a].x;
+                F[bb].y += phi * th[a].y;
+            }
+            ++pidx;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__restrict__ sys, const int *__restrict__ prefix,
                                                              int nsys, int total, const float4 *__restrict__ tab,
                                                              int *__restrict__ err) {
@@ -1058,24 +1082,14 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
                 const int span = min(mt.z, SPAN32);
                 if (j < NK - 1) {
                     // the interval's row: staged, else (rounding at a chunk edge) global
+                    // (two copies of the loop, so that the staged one compiles to
+                    // shared-memory loads rather than generic ones)
                     const bool staged = span > 0 && j >= mt.y && j < mt.y + span;
-                    const float4 *row = staged ? m.rows + ((size_t)b * SPAN32 + (j - mt.y)) * NPAIR
-                                               : tab + (size_t)j * NPAIR;
-                    int pidx = 0;
-#pragma unroll
-                    for (int a = 0; a < NQ; ++a) {
-#pragma unroll
-                        for (int bb = a; bb < NQ; ++bb) {
-                            const float4 cf = staged ? row[pidx] : __ldg(row + pidx);
-                            const float phi = cf.x + tt * (cf.y + tt * (cf.z + tt * cf.w));
-                            F[a].x += phi * th[bb].x;
-                            F[a].y += phi * th[bb].y;
-                            if (bb != a) {
-                                F[bb].x += phi * th[a].x;
-                                F[bb].y += phi * th[a].y;
-                            }
-                            ++pidx;
-                        }
+                    if (staged) {
+                        const float4 *row = m.rows + ((size_t)b * SPAN32 + (j - mt.y)) * NPAIR;
+                        contract_row<false>(row, tt, th, F);
+                    } else {
+                        contract_row<true>(tab + (size_t)j * NPAIR, tt, th, F);
                     }
                 }
                 float e = 0.f;
