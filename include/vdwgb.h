@@ -181,8 +181,9 @@ int vdwgb_set_fused(int enable);
 int vdwgb_set_autotune(int enable);
 
 /* Plan of an initialised handle: info[0..8] = z-forward lines per tile,
- * z-inverse lines per tile, y-pass kz-columns, x-pass kz-columns, row
- * buffers of the y and x passes as 10 * y + x (3 prefetching, 2 not),
+ * z-inverse lines per tile, y-pass kz-columns, x-pass kz-columns,
+ * input buffers in the ring of the y and x passes as 10 * y + x (1: no
+ * prefetch, n: n - 1 tiles requested ahead),
  * contraction chunks, kernel launches per evaluation, 1 if the tile shapes
  * were autotuned, cluster size of the plane kernel (0: separate passes). */
 int vdwgb_plan_info(vdwgb_handle h, int *info);

@@ -185,15 +185,17 @@ static size_t rec_bytes(int prec) { return prec == VDWGB_FP32_MIXED ? 16 : 32; }
 // prefetch).  The autotuner below replaces them by measured choices.
 static const size_t TILE_BUDGET = 110 * 1024;
 
-static int best_w(int prec, int n, int nzh) {
+static int best_w(int prec, int n, int nzh, int slots) {
     int W = 1;
     for (int w = 8; w >= 1; --w)
-        if (stage_smem(1, prec, n, w, 3) <= TILE_BUDGET) { W = w; break; }
+        if (stage_smem(1, prec, n, w, slots) <= TILE_BUDGET) { W = w; break; }
     return W > nzh ? nzh : W;
 }
 
-static void choose_tiles(int prec, int nx, int ny, int nz, int nzh, size_t lim, int &LZ, int &LZi, int &Wy, int &Wx,
-                         int &nbuf) {
+// x / y passes: two ring buffers (one tile prefetched) plus the scratch
+// buffer on axes without an in-place transform (workx / worky)
+static void choose_tiles(int prec, int nx, int ny, int nz, int nzh, size_t lim, int workx, int worky, int &LZ,
+                         int &LZi, int &Wy, int &Wx, int &nbuf) {
     LZ = 1;
     for (int l = 8; l >= 1; --l)
         if (stage_smem(0, prec, nz, l) <= TILE_BUDGET) { LZ = l; break; }
@@ -202,11 +204,10 @@ static void choose_tiles(int prec, int nx, int ny, int nz, int nzh, size_t lim, 
         if (stage_smem(3, prec, nz, l) <= TILE_BUDGET) { LZi = l; break; }
     if (LZi > nx * ny) LZi = nx * ny;
     if (LZ > nx * ny) LZ = nx * ny;
-    Wy = best_w(prec, ny, nzh);
-    Wx = best_w(prec, nx, nzh);
-    nbuf = 3;
-    const int nxy = nx > ny ? nx : ny;
-    if (stage_smem(1, prec, nxy, 1, 3) > lim) nbuf = 2;
+    nbuf = 2;
+    if (stage_smem(1, prec, ny, 1, 2 + worky) > lim || stage_smem(1, prec, nx, 1, 2 + workx) > lim) nbuf = 1;
+    Wy = best_w(prec, ny, nzh, nbuf + worky);
+    Wx = best_w(prec, nx, nzh, nbuf + workx);
 }
 
 // Sort the half-spectrum k-points of a system by kernel-table interval
@@ -222,10 +223,12 @@ static void build_chunks(const SysDev &S, int maxspan, int chunkmax, std::vector
     std::vector<int> bin(nk);
     std::vector<size_t> count(NK + 1, 0);
     auto fold = [](int i, int n) { return i <= (n - 1) / 2 ? i : i - n; };
-    for (int x = 0; x < nx; ++x) {
+    for (int px = 0; px < nx; ++px) {
+        const int x = axis_freq(px, nx, S.sx1);          // frequency at this position
         const int mx = fold(x, nx);
         const bool qx = (nx % 2 == 0) && (x == nx / 2);
-        for (int y = 0; y < ny; ++y) {
+        for (int py = 0; py < ny; ++py) {
+            const int y = axis_freq(py, ny, S.sy1);
             const int my = fold(y, ny);
             const bool qy = (ny % 2 == 0) && (y == ny / 2);
             for (int kz = 0; kz < nzh; ++kz) {
@@ -237,7 +240,7 @@ static void build_chunks(const SysDev &S, int maxspan, int chunkmax, std::vector
                 if (k2 < 0) k2 = 0;
                 long j = (long)(std::sqrt(k2) / dk);
                 if (j > NK - 1) j = NK - 1;
-                const size_t idx = ((size_t)x * ny + y) * nzh + kz;
+                const size_t idx = ((size_t)px * ny + py) * nzh + kz;
                 bin[idx] = (int)j;
                 ++count[j];
             }
@@ -392,10 +395,12 @@ static void set_tiles(vdwgb_data *h, int LZ, int LZi, int Wy, int Wx, int nby, i
     L.nbuf[0] = L.nbuf[3] = 0;
     L.nbuf[1] = nby;
     L.nbuf[2] = nbx;
+    L.work[1] = S.sy1 ? 0 : 1;
+    L.work[2] = S.sx1 ? 0 : 1;
     L.smem[0] = stage_smem(0, prec, nz, LZ);
     L.smem[3] = stage_smem(3, prec, nz, LZi);
-    L.smem[1] = stage_smem(1, prec, ny, Wy, nby);
-    L.smem[2] = stage_smem(1, prec, nx, Wx, nbx);
+    L.smem[1] = stage_smem(1, prec, ny, Wy, nby + L.work[1]);
+    L.smem[2] = stage_smem(1, prec, nx, Wx, nbx + L.work[2]);
     for (int s = 0; s < 4; ++s) {
         int per_sm = (int)((228 * 1024) / (L.smem[s] + 1024));
         per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
@@ -573,20 +578,20 @@ static int apply_tuned(vdwgb_data *h) {
     for (int pass = 0; pass < 4 && !rc; ++pass) {
         if (S.fused && (pass == 1 || pass == 2)) continue;   // y / x run inside the plane kernel
         float best_ms = 1e30f;
-        for (int ci = 0; ci < 12; ++ci) {
+        for (int ci = 0; ci < 6 * XY_MAXIN; ++ci) {
             const int c = cand[ci % 6];
-            const int nb = ci < 6 ? 3 : 2;          // x / y passes: prefetching or not
+            const int nb = 1 + ci / 6;              // x / y passes: input buffers in the ring
             if ((pass == 0 || pass == 3) && ci >= 6) break;
             TuneVal v = best;
             if (pass == 0) {
                 if (c > S.nx * S.ny || stage_smem(0, prec, S.nz, c) > lim) continue;
                 v.LZ = c;
             } else if (pass == 1) {
-                if (c > S.nzh || stage_smem(1, prec, S.ny, c, nb) > lim) continue;
+                if (c > S.nzh || stage_smem(1, prec, S.ny, c, nb + (S.sy1 ? 0 : 1)) > lim) continue;
                 v.Wy = c;
                 v.nby = nb;
             } else if (pass == 2) {
-                if (c > S.nzh || stage_smem(1, prec, S.nx, c, nb) > lim) continue;
+                if (c > S.nzh || stage_smem(1, prec, S.nx, c, nb + (S.sx1 ? 0 : 1)) > lim) continue;
                 v.Wx = c;
                 v.nbx = nb;
             } else {
@@ -630,10 +635,15 @@ static int plan(vdwgb_data *h) {
         if (!factor_axis(dims[a], S.ax[a]))
             return fail(VDWGB_EINVAL, "axis %d length %d: prime factors must be 2, 3, 5, 7", a, dims[a]);
     const size_t lim = di.maxsmem - 1024;
-    int nbuf = 3;
-    choose_tiles(prec, nx, ny, nz, nzh, lim, S.LZ, S.LZi, S.Wy, S.Wx, nbuf);
-    if (stage_smem(0, prec, nz, S.LZ) > lim || stage_smem(1, prec, nx, S.Wx, nbuf) > lim ||
-        stage_smem(1, prec, ny, S.Wy, nbuf) > lim || stage_smem(3, prec, nz, S.LZi) > lim)
+    // in-place x / y transforms (permuted spectrum between the passes) where a
+    // two-pass split is compiled (FP32); 0: out of place through the scratch buffer
+    S.sx1 = prec == VDWGB_FP32_MIXED ? fft_split(nx) : 0;
+    S.sy1 = prec == VDWGB_FP32_MIXED ? fft_split(ny) : 0;
+    const int workx = S.sx1 ? 0 : 1, worky = S.sy1 ? 0 : 1;
+    int nbuf = 2;
+    choose_tiles(prec, nx, ny, nz, nzh, lim, workx, worky, S.LZ, S.LZi, S.Wy, S.Wx, nbuf);
+    if (stage_smem(0, prec, nz, S.LZ) > lim || stage_smem(1, prec, nx, S.Wx, nbuf + workx) > lim ||
+        stage_smem(1, prec, ny, S.Wy, nbuf + worky) > lim || stage_smem(3, prec, nz, S.LZi) > lim)
         return fail(VDWGB_EINVAL, "grid %dx%dx%d too large for one block per pencil in this precision",
                     nx, ny, nz);
     // reciprocal metric g = B B^T, B = 2 pi C^{-T} (rows b_j)
@@ -681,8 +691,6 @@ static int plan(vdwgb_data *h) {
     S.fused = C;
     if (C) {
         build_kord(S, C, kord, S.kstride);
-        S.sx1 = fft_split(nx);
-        S.sy1 = fft_split(ny);
         S.tiles[4] = 0;
         S.tiles[5] = nzh;
         S.nepart = nzh * C;
@@ -1123,6 +1131,7 @@ int vdwgb::batch_launchset(vdwgb_data *const *hs, int count, SysDev *hdesc, int 
             if (hs[i]->ls.twmax[s] > L.twmax[s]) L.twmax[s] = hs[i]->ls.twmax[s];
             if (hs[i]->ls.bufelems[s] > L.bufelems[s]) L.bufelems[s] = hs[i]->ls.bufelems[s];
             if (i == 0 || hs[i]->ls.nbuf[s] < L.nbuf[s]) L.nbuf[s] = hs[i]->ls.nbuf[s];
+            if (hs[i]->ls.work[s] > L.work[s]) L.work[s] = hs[i]->ls.work[s];
         }
         if (hs[i]->ls.recelems > L.recelems) L.recelems = hs[i]->ls.recelems;
         if (hs[i]->ls.abelems > L.abelems) L.abelems = hs[i]->ls.abelems;
@@ -1138,7 +1147,7 @@ int vdwgb::batch_launchset(vdwgb_data *const *hs, int count, SysDev *hdesc, int 
     // x / y stages: shared memory from the largest row tile and twiddle table of the batch
     const size_t c = prec == VDWGB_FP32_MIXED ? 8 : 16;
     for (int s = 1; s <= 2; ++s)
-        L.smem[s] = xy_smem_bytes(L.twmax[s], L.bufelems[s], L.nbuf[s], c);
+        L.smem[s] = xy_smem_bytes(L.twmax[s], L.bufelems[s], L.nbuf[s] + L.work[s], c);
     L.smem[3] = zinv_smem(prec, L.twmax[3], L.bufelems[3], L.recelems, L.abelems);
     const size_t lim = di.maxsmem - 1024;
     if (L.smem[1] > lim || L.smem[2] > lim || L.smem[3] > lim)

@@ -19,6 +19,7 @@
 
 #include "internal.h"
 #include "table.h"
+#include "fftreg.cuh"
 
 using namespace vdwgb;
 
@@ -86,10 +87,10 @@ int tile_lines(int stage, int n, int nlines) {
     return best > nlines ? nlines : best;
 }
 
-int tile_cols(int n, int nzh) {
+int tile_cols(int n, int nzh, int slots) {
     int best = 1;
     for (int w = 8; w >= 1; --w)
-        if (stage_smem(1, 1, n, w, 3) <= 110 * 1024) { best = w; break; }
+        if (stage_smem(1, 1, n, w, slots) <= 110 * 1024) { best = w; break; }
     return best > nzh ? nzh : best;
 }
 
@@ -101,9 +102,11 @@ int sort_chunks(const SysDev &S) {
     const double dk = 2.0 * M_PI / RMAX;
     for (int j = 0; j <= NK; ++j) h_start[j] = 0;
     auto fold = [](int i, int n) { return i <= (n - 1) / 2 ? i : i - n; };
-    for (int x = 0; x < nx; ++x)
-        for (int y = 0; y < ny; ++y)
+    for (int px = 0; px < nx; ++px)
+        for (int py = 0; py < ny; ++py)
             for (int kz = 0; kz < nzh; ++kz) {
+                // frequencies at these positions (the x / y passes may leave them permuted)
+                const int x = axis_freq(px, nx, S.sx1), y = axis_freq(py, ny, S.sy1);
                 const int mx = fold(x, nx), my = fold(y, ny);
                 const bool qx = (nx % 2 == 0) && (x == nx / 2), qy = (ny % 2 == 0) && (y == ny / 2);
                 const bool qz = (nz % 2 == 0) && (kz == nz / 2);
@@ -114,7 +117,7 @@ int sort_chunks(const SysDev &S) {
                 if (k2 < 0) k2 = 0;
                 long j = (long)(std::sqrt(k2) / dk);
                 if (j > NK - 1) j = NK - 1;
-                const size_t idx = ((size_t)x * ny + y) * nzh + kz;
+                const size_t idx = ((size_t)px * ny + py) * nzh + kz;
                 h_bin[idx] = (int)j;
                 ++h_start[j + 1];
             }
@@ -202,8 +205,11 @@ extern "C" int vdwgb_calculate_noalloc(int device, int functional, int nx, int n
     const int nzh = S.nzh;
     S.LZ = tile_lines(0, nz, nx * ny);
     S.LZi = tile_lines(3, nz, nx * ny);
-    S.Wy = tile_cols(ny, nzh);
-    S.Wx = tile_cols(nx, nzh);
+    S.sx1 = fft_split(nx);                   // in-place x / y transforms where compiled
+    S.sy1 = fft_split(ny);
+    const int workx = S.sx1 ? 0 : 1, worky = S.sy1 ? 0 : 1;
+    S.Wy = tile_cols(ny, nzh, 2 + worky);
+    S.Wx = tile_cols(nx, nzh, 2 + workx);
     S.tiles[0] = (nx * ny + S.LZ - 1) / S.LZ;
     S.tiles[1] = nx * ((nzh + S.Wy - 1) / S.Wy);
     S.tiles[2] = ny * ((nzh + S.Wx - 1) / S.Wx);
@@ -267,10 +273,12 @@ extern "C" int vdwgb_calculate_noalloc(int device, int functional, int nx, int n
     L.abelems = nz * z_ld(S.LZi);
     L.bufelems[1] = ny * S.Wy * NQ;
     L.bufelems[2] = nx * S.Wx * NQ;
-    L.nbuf[1] = L.nbuf[2] = 3;
+    L.nbuf[1] = L.nbuf[2] = 2;
+    L.work[1] = worky;
+    L.work[2] = workx;
     L.smem[0] = stage_smem(0, 1, nz, S.LZ);
-    L.smem[1] = stage_smem(1, 1, ny, S.Wy, 3);
-    L.smem[2] = stage_smem(1, 1, nx, S.Wx, 3);
+    L.smem[1] = stage_smem(1, 1, ny, S.Wy, 2 + worky);
+    L.smem[2] = stage_smem(1, 1, nx, S.Wx, 2 + workx);
     L.smem[3] = stage_smem(3, 1, nz, S.LZi);
     L.smem[4] = contract_smem(1, NA_MAXSPAN);
     for (int k = 0; k < NKIND; ++k) {

@@ -672,38 +672,48 @@ __device__ __forceinline__ void xy_issue(const SysDev *__restrict__ sys, const i
         bulk_g2s(buf + (size_t)r * g.ldr, spec + g.g0 + r * g.rowstride, rowbytes, bar);
 }
 
-// MODE 0: forward y, 1: inverse y, 2: forward x, 3: inverse x
+// MODE 0: forward y, 1: inverse y, 2: forward x, 3: inverse x.
+// Row tiles cycle through a ring of `nin` input buffers (tile i + nin - 1 is
+// requested while tile i is transformed; nin = 1: the next tile is requested
+// after this one is stored).  Axes with a compiled two-pass split (FP32)
+// transform in place, the forward pass leaving frequencies in the permuted
+// order p = k1 N2 + k2 <-> k1 + N1 k2 that the contraction and the inverse
+// pass read back; other axes use the scratch buffer (haswork).
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_xy(const SysDev *__restrict__ sys,
                                                                    const int *__restrict__ prefix, int nsys,
-                                                                   int total, int twmax, int bufelems, int nbuf,
-                                                                   int *__restrict__ err) {
+                                                                   int total, int twmax, int bufelems, int nin,
+                                                                   int haswork, int *__restrict__ err) {
     constexpr bool XPASS = MODE >= 2;
     constexpr bool INV = (MODE & 1) != 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);   // 128-byte aligned
-    unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem);
-    cx<T> *tw = reinterpret_cast<cx<T> *>(smem + 16);
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem);           // [XY_MAXIN]
+    cx<T> *tw = reinterpret_cast<cx<T> *>(smem + XY_HEAD);
     const size_t bstride = xy_buf_stride(bufelems, sizeof(cx<T>));
     unsigned char *in0 = smem + xy_off_in(twmax, sizeof(cx<T>));
-    // nbuf 3: two input stages (prefetch of the next tile) + transform scratch;
-    // nbuf 2: one input stage, loaded after the previous tile is stored.
-    cx<T> *bufs[2] = {reinterpret_cast<cx<T> *>(in0), reinterpret_cast<cx<T> *>(nbuf == 3 ? in0 + bstride : in0)};
-    cx<T> *work = reinterpret_cast<cx<T> *>(in0 + (size_t)(nbuf - 1) * bstride);
+    cx<T> *work = reinterpret_cast<cx<T> *>(in0 + (size_t)nin * bstride);
+    (void)haswork;
     if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int k = 0; k < nin; ++k) mbar_init(&bar[k], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    unsigned ph[2] = {0u, 0u};
-    int t = blockIdx.x;
-    if (t < total && threadIdx.x < 32) xy_issue<T, XPASS>(sys, prefix, nsys, t, bufs[0], &bar[0]);
+    unsigned ph = 0u;              // parity bit per ring slot
+    unsigned pending = 0u;         // slots with a requested, not yet consumed tile
+    // prologue: tiles 0 .. nin - 2 of this block (nin = 1: tile 0)
+    const int pre = nin > 1 ? nin - 1 : 1;
+    for (int k = 0; k < pre; ++k) {
+        const int tk = blockIdx.x + k * gridDim.x;
+        if (tk < total) {
+            if (threadIdx.x < 32)
+                xy_issue<T, XPASS>(sys, prefix, nsys, tk, reinterpret_cast<cx<T> *>(in0 + (size_t)k * bstride), &bar[k]);
+            pending |= 1u << k;
+        }
+    }
     __shared__ SysDev sS;                    // descriptor of the current tile's system
-    int cur_sys = -1, tbase = 0;
-    for (int i = 0; t < total; ++i, t += gridDim.x) {
-        const int cur = i & 1;
-        const int tn = t + gridDim.x;
+    int cur_sys = -1, tbase = 0, cur = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
         const int nsi = advance_sys(prefix, nsys, t, cur_sys);
         if (nsi != cur_sys) {
             __syncthreads();                 // readers of the previous descriptor are done
@@ -714,19 +724,41 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_xy(const SysDev
             cur_sys = nsi;
             tbase = prefix[nsi];
         }
-        if (nbuf == 3 && tn < total && threadIdx.x < 32)
-            xy_issue<T, XPASS>(sys, prefix, nsys, tn, bufs[cur ^ 1], &bar[cur ^ 1], &sS, cur_sys, tbase);
+        if (nin > 1) {
+            // the slot of the previous tile (stored and released at its end)
+            const int tn = t + (nin - 1) * gridDim.x;
+            const int sn = cur == 0 ? nin - 1 : cur - 1;
+            if (tn < total) {
+                if (threadIdx.x < 32)
+                    xy_issue<T, XPASS>(sys, prefix, nsys, tn, reinterpret_cast<cx<T> *>(in0 + (size_t)sn * bstride),
+                                       &bar[sn], &sS, cur_sys, tbase);
+                pending |= 1u << sn;
+            }
+        }
         const SysDev &S = sS;
         const XYTile g = xy_tile<XPASS>(S, nsi, t - tbase);
         const AxisPlan &ap = S.ax[XPASS ? 0 : 1];
-        bool ok = mbar_wait(&bar[cur], ph[cur]);
-        ph[cur] ^= 1u;
+        cx<T> *in = reinterpret_cast<cx<T> *>(in0 + (size_t)cur * bstride);
+        const bool ok = mbar_wait(&bar[cur], (ph >> cur) & 1u);
+        ph ^= 1u << cur;
+        pending &= ~(1u << cur);
         if (!__syncthreads_and(ok)) {
-            if (threadIdx.x == 0) atomicExch(err, 1);
-            if (nbuf == 3 && tn < total) mbar_wait(&bar[cur ^ 1], ph[cur ^ 1]);
+            if (threadIdx.x == 0) {
+                atomicExch(err, 1);
+                for (int k = 0; k < nin; ++k)     // let the copies in flight land
+                    if ((pending >> k) & 1u) mbar_wait(&bar[k], (ph >> k) & 1u);
+            }
+            __syncthreads();
             return;
         }
-        cx<T> *R = fft_auto<INV>(bufs[cur], work, ap, g.L, g.ldr, tw);
+        const int split = sizeof(T) == 4 ? (XPASS ? S.sx1 : S.sy1) : 0;
+        cx<T> *R;
+        if (split) {
+            fft_ip_auto<INV>(in, ap.n, g.L, g.ldr, tw);
+            R = in;
+        } else {
+            R = fft_auto<INV>(in, work, ap, g.L, g.ldr, tw);
+        }
         // store the rows back (16-byte vectors), walking (row, e) without division
         cx<T> *spec = reinterpret_cast<cx<T> *>(S.spec) + g.g0;
         {
@@ -747,14 +779,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_xy(const SysDev
         }
         fence_proxy_async();   // this tile's generic accesses before the next bulk writes
         __syncthreads();
-        if (nbuf == 2 && tn < total && threadIdx.x < 32)
-            xy_issue<T, XPASS>(sys, prefix, nsys, tn, bufs[cur ^ 1], &bar[cur ^ 1], &sS, cur_sys, tbase);
+        if (nin == 1) {
+            const int tn = t + gridDim.x;
+            if (tn < total) {
+                if (threadIdx.x < 32) xy_issue<T, XPASS>(sys, prefix, nsys, tn, in, &bar[0], &sS, cur_sys, tbase);
+                pending |= 1u;
+            }
+        }
+        cur = cur + 1 == nin ? 0 : cur + 1;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        mbar_inval(&bar[0]);
-        mbar_inval(&bar[1]);
-    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < nin; ++k) mbar_inval(&bar[k]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1055,7 +1091,8 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
                 const int nx = S.nx, ny = S.ny, nz = S.nz, nzh = S.nzh;
                 const int kz = (int)(idx % (unsigned)nzh);
                 const int rest = (int)(idx / (unsigned)nzh);
-                const int y = rest % ny, x = rest / ny;
+                // positions -> frequencies (the x / y passes may leave them permuted)
+                const int y = axis_freq(rest % ny, ny, S.sy1), x = axis_freq(rest / ny, nx, S.sx1);
                 const int mx = fold(x, nx), my = fold(y, ny);
                 const bool nyq_x = (nx % 2 == 0) && (x == nx / 2);
                 const bool nyq_y = (ny % 2 == 0) && (y == ny / 2);
@@ -1379,8 +1416,8 @@ size_t smem_z(int nz, int LZ) {
            sizeof(cx<T>) * ((size_t)((nz + 1) & ~1) + 2ull * nz * z_ld(LZ));
 }
 template <typename T>
-size_t smem_xy(int n, int W, int nbuf) {
-    return xy_smem_bytes(n, n * NQ * W, nbuf, sizeof(cx<T>));
+size_t smem_xy(int n, int W, int nslots) {
+    return xy_smem_bytes(n, n * NQ * W, nslots, sizeof(cx<T>));
 }
 
 template <typename T>
@@ -1458,19 +1495,23 @@ static cudaError_t launch_stage_t(const LaunchSet &ls, int stage, cudaStream_t s
             break;
         case 2:
             k_xy<T, 0><<<ls.grid[1], 256, ls.smem[1], st>>>(ls.sys, ls.prefix[1], ls.nsys, ls.total[1],
-                                                             ls.twmax[1], ls.bufelems[1], ls.nbuf[1], ls.err);
+                                                             ls.twmax[1], ls.bufelems[1], ls.nbuf[1],
+                                                             ls.work[1], ls.err);
             break;
         case 6:
             k_xy<T, 1><<<ls.grid[1], 256, ls.smem[1], st>>>(ls.sys, ls.prefix[1], ls.nsys, ls.total[1],
-                                                             ls.twmax[1], ls.bufelems[1], ls.nbuf[1], ls.err);
+                                                             ls.twmax[1], ls.bufelems[1], ls.nbuf[1],
+                                                             ls.work[1], ls.err);
             break;
         case 3:
             k_xy<T, 2><<<ls.grid[2], 256, ls.smem[2], st>>>(ls.sys, ls.prefix[2], ls.nsys, ls.total[2],
-                                                             ls.twmax[2], ls.bufelems[2], ls.nbuf[2], ls.err);
+                                                             ls.twmax[2], ls.bufelems[2], ls.nbuf[2],
+                                                             ls.work[2], ls.err);
             break;
         case 5:
             k_xy<T, 3><<<ls.grid[2], 256, ls.smem[2], st>>>(ls.sys, ls.prefix[2], ls.nsys, ls.total[2],
-                                                             ls.twmax[2], ls.bufelems[2], ls.nbuf[2], ls.err);
+                                                             ls.twmax[2], ls.bufelems[2], ls.nbuf[2],
+                                                             ls.work[2], ls.err);
             break;
         case 4:
             if (sizeof(T) == 4)

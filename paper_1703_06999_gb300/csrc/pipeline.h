@@ -20,7 +20,8 @@ struct LaunchSet {
     const void *table;       // kernel polynomial table (float4 or dvec4), [210][NK-1]
     int twmax[6];            // longest axis of the stage over all systems (twiddle slots)
     int bufelems[6];         // complex elements of one row-tile buffer (x / y stages)
-    int nbuf[6];             // row-tile buffers of the x / y stages: 3 (prefetching) or 2
+    int nbuf[6];             // x / y stages: input buffers in the ring (1..XY_MAXIN)
+    int work[6];             // x / y stages: 1 if some system needs the scratch buffer
     int recelems;            // z-inverse: point records per staged tile
     int abelems;             // z-inverse: complex elements of one transform buffer
     int *err;                // device flag set by a stage whose bounded wait ran out
@@ -38,8 +39,10 @@ constexpr int CHUNK32 = 480, SPAN32 = 8, CHUNK64 = 256, SPAN64 = 8;
 // Shared memory of an x / y pass block: barriers and twiddles, then nbuf
 // row-tile buffers at 128-byte aligned offsets (tensor copies land there);
 // 128 bytes of slack align the dynamic base at run time.
+constexpr int XY_MAXIN = 4;     // x / y passes: input buffers in the ring at most
+constexpr int XY_HEAD = 32;     // ring barriers before the twiddles
 __host__ __device__ inline size_t xy_off_in(int twmax, size_t csize) {
-    return (16 + (size_t)twmax * csize + 127) / 128 * 128;
+    return (XY_HEAD + (size_t)twmax * csize + 127) / 128 * 128;
 }
 __host__ __device__ inline size_t xy_buf_stride(int bufelems, size_t csize) {
     return ((size_t)bufelems * csize + 127) / 128 * 128;
@@ -48,6 +51,7 @@ inline size_t xy_smem_bytes(int twmax, int bufelems, int nbuf, size_t csize) {
     return 128 + xy_off_in(twmax, csize) + (size_t)nbuf * xy_buf_stride(bufelems, csize);
 }
 
+// stage 1 (x / y): nbuf = buffers in total (ring inputs plus the scratch buffer if any)
 size_t stage_smem(int stage, int prec, int n, int tile, int nbuf = 3);
 size_t zinv_smem(int prec, int nzmax, int inelems, int recelems, int abelems);
 size_t contract_smem(int prec, int maxspan);
