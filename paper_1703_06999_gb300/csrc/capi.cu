@@ -679,6 +679,12 @@ static int plan(vdwgb_data *h) {
     S.escale = 0.5 * omega / (N * N);
     S.invN = 1.0 / N;
     S.Z = h->functional == VDWGB_DF2 ? -1.887 : -0.8491;
+    {
+        const double zc = -S.Z / 36.0;
+        S.zc[0] = (float)zc;
+        S.zc[1] = (float)(zc - (double)S.zc[0]);
+    }
+    S.invNf = (float)S.invN;
     // half-spectrum k-points sorted by kernel-table interval, cut into chunks
     // (or, for the plane kernel, per plane and cluster rank)
     const int maxspan = prec == VDWGB_FP32_MIXED ? SPAN32 : SPAN64;

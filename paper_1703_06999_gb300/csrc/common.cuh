@@ -86,6 +86,9 @@ struct SysDev {
     double escale;   // 1/2 Omega / N^2
     double invN;     // 1 / N
     double Z;        // Z_ab of the functional
+    float zc[2];     // -Z_ab / 36 as an FP32 pair (hi, lo), for the FP32-mixed q0
+    float invNf;     // 1 / N in FP32
+    int pad0;
     const double *n;
     const double *sigma;
     double *dedn;

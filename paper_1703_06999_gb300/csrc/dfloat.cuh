@@ -34,18 +34,23 @@ __device__ __forceinline__ dfl df_from(double x) {
 }
 __device__ __forceinline__ double df_to(dfl a) { return (double)a.hi + (double)a.lo; }
 
-// Split a double into hi + lo on the integer and FP32 pipes (GB300's FP64 pipe,
-// which also converts, runs at 1/64 of the FP32 rate): hi keeps the top 24
-// significand bits (truncated), lo the next bits rounded to FP32, then one
-// renormalising fast two-sum.  Below the normal FP32 range of hi (|x| under
-// about 1.2e-38) and above it the hardware conversion is used.
+// Split a double into hi + lo on the integer and FP32 pipes only (GB300's FP64
+// pipe, which also converts, runs at 1/64 of the FP32 rate): hi keeps the top
+// 24 significand bits (truncated), lo the next bits rounded to FP32, then one
+// renormalising fast two-sum.  Outside the normal FP32 range of hi the result
+// is a signed zero (|x| below 2^-126, about 1.2e-38), a signed infinity (|x|
+// of 2^128 or more) or a NaN (x a NaN), all without the FP64 pipe.
 __device__ __forceinline__ dfl df_from_bits(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const int ed = (int)((b >> 52) & 0x7ff);
     const int ef = ed - 1023 + 127;          // FP32 biased exponent of hi
     const int el = ed - 1075 + 127;          // FP32 biased exponent of the unit of the low 29 bits
-    if (ef < 1 || ef > 254) return df_from(x);
     const unsigned sign = (unsigned)(b >> 63) << 31;
+    if (ef < 1) return dfl{__uint_as_float(sign), 0.f};
+    if (ef > 254) {
+        const bool nan = ed == 0x7ff && (b & 0xfffffffffffffull) != 0ull;
+        return dfl{__uint_as_float(sign | 0x7f800000u | (nan ? 0x400000u : 0u)), 0.f};
+    }
     const float hi = __uint_as_float(sign | ((unsigned)ef << 23) | (unsigned)((b >> 29) & 0x7fffffu));
     // lo = rem 2^(el - 127), scaled in two exact steps: 2^-30, then
     // 2^(el - 97) >= 2^-148 (a normal or subnormal power of two, as ef >= 1)
@@ -55,15 +60,27 @@ __device__ __forceinline__ dfl df_from_bits(double x) {
     return df_quick(hi, sign ? -lmag : lmag);
 }
 
-// Widen an FP32 value to FP64 on the integer pipe (zero and values outside the
-// normal range via the hardware conversion).
+// Widen an FP32 value to FP64 exactly on the integer pipe: normal values by
+// re-biasing the exponent, subnormal ones by normalising the significand
+// (leading-zero count), zero, infinities and NaNs by their bit patterns.
 __device__ __forceinline__ double f2d_bits(float f) {
     const unsigned u = __float_as_uint(f);
     const unsigned e = (u >> 23) & 0xffu;
-    if (e == 0u || e == 255u) return (double)f;
-    const unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
-                                 ((unsigned long long)(e - 127u + 1023u) << 52) |
-                                 ((unsigned long long)(u & 0x7fffffu) << 29);
+    const unsigned m = u & 0x7fffffu;
+    const unsigned long long sg = (unsigned long long)(u >> 31) << 63;
+    unsigned long long b;
+    if (e == 255u) {
+        b = sg | (0x7ffull << 52) | ((unsigned long long)m << 29);
+    } else if (e != 0u) {
+        b = sg | ((unsigned long long)(e - 127u + 1023u) << 52) | ((unsigned long long)m << 29);
+    } else if (m == 0u) {
+        b = sg;
+    } else {
+        // value m 2^-149 with the top set bit of m at position p (0..22)
+        const int p = 31 - __clz((int)m);
+        const unsigned long long frac = ((unsigned long long)m << (52 - p)) & 0xfffffffffffffull;
+        b = sg | ((unsigned long long)(p - 149 + 1023) << 52) | frac;
+    }
     return __longlong_as_double((long long)b);
 }
 

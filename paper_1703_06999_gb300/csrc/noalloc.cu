@@ -201,6 +201,12 @@ extern "C" int vdwgb_calculate_noalloc(int device, int functional, int nx, int n
     S.escale = 0.5 * std::fabs(det) / (N * N);
     S.invN = 1.0 / N;
     S.Z = functional == VDWGB_DF2 ? -1.887 : -0.8491;
+    {
+        const double zc = -S.Z / 36.0;
+        S.zc[0] = (float)zc;
+        S.zc[1] = (float)(zc - (double)S.zc[0]);
+    }
+    S.invNf = (float)S.invN;
     // tiles: the same rules as the allocating path without autotuning
     const int nzh = S.nzh;
     S.LZ = tile_lines(0, nz, nx * ny);

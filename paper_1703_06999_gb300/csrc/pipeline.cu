@@ -332,42 +332,6 @@ __device__ __forceinline__ int q_interval(double q, const double *qs) {
     return lo;
 }
 
-// p_a(q) for all a, from interval j and spline coordinate B (A = 1 - B):
-// p_a = A [a==j] + B [a==j+1] + ((A^3-A) d2_a[j] + (B^3-B) d2_a[j+1]) h^2/6.
-template <typename T>
-__device__ __forceinline__ void spline_p(int j, T B, T h, const T *d2s, T *p) {
-    const T A = (T)1 - B;
-    const T cA = (A * A * A - A) * h * h / (T)6;
-    const T cB = (B * B * B - B) * h * h / (T)6;
-    const T *dj = d2s + j * NQ;
-    const T *dj1 = dj + NQ;
-#pragma unroll
-    for (int a = 0; a < NQ; ++a) p[a] = cA * dj[a] + cB * dj1[a];
-#pragma unroll
-    for (int a = 0; a < NQ; ++a) {
-        if (a == j) p[a] += A;
-        if (a == j + 1) p[a] += B;
-    }
-}
-
-// dp_a/dq: ([a==j+1] - [a==j]) / h + (-(3A^2-1) d2_a[j] + (3B^2-1) d2_a[j+1]) h / 6.
-template <typename T>
-__device__ __forceinline__ void spline_dp(int j, T B, T h, const T *d2s, T *dp) {
-    const T A = (T)1 - B;
-    const T dA = -((T)3 * A * A - (T)1) * h / (T)6;
-    const T dB = ((T)3 * B * B - (T)1) * h / (T)6;
-    const T ih = (T)1 / h;
-    const T *dj = d2s + j * NQ;
-    const T *dj1 = dj + NQ;
-#pragma unroll
-    for (int a = 0; a < NQ; ++a) dp[a] = dA * dj[a] + dB * dj1[a];
-#pragma unroll
-    for (int a = 0; a < NQ; ++a) {
-        if (a == j) dp[a] -= ih;
-        if (a == j + 1) dp[a] += ih;
-    }
-}
-
 // Shared q-mesh tables in precision T.
 template <typename T>
 struct QShared {
@@ -375,6 +339,9 @@ struct QShared {
     double invh[NQ];
     Q0Tab q0t;       // double-float mesh and ln / exp tables (FP32-mixed q0)
     T h[NQ];
+    T hh6[NQ];       // h_j^2 / 6
+    T h6[NQ];        // h_j / 6
+    T ih[NQ];        // 1 / h_j
     alignas(16) T d2[NQ * NQ];
 };
 
@@ -386,6 +353,9 @@ __device__ __forceinline__ void load_qshared(QShared<T> *qs) {
         qs->q[i] = c_qm.q[i];
         qs->invh[i] = c_qm.invh[i];
         qs->h[i] = (T)c_qm.h[i];
+        qs->hh6[i] = (T)(c_qm.h[i] * c_qm.h[i] / 6.0);
+        qs->h6[i] = (T)(c_qm.h[i] / 6.0);
+        qs->ih[i] = (T)c_qm.invh[i];
     }
 }
 
@@ -460,7 +430,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zfwd(const SysD
         Rec<T> *rec = reinterpret_cast<Rec<T> *>(S.rec);
         const size_t p0 = (size_t)l0 * nz;
         const double *gn = S.n + p0, *gs = S.sigma + p0;
-        const dfl zc = df_from(-S.Z / 36.0);
+        const dfl zc = dfl{S.zc[0], S.zc[1]};
         {
             // points i = li * nz + z, walked without division
             const int dz = nt % nz, dli = nt / nz;
@@ -495,9 +465,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zfwd(const SysD
                     // terms A [a == j] + B [a == j + 1] at the two dynamic slots
                     T r0[NQ], r1[NQ];
                     d2_rows<T>(j, qs->d2, r0, r1);
-                    const T h = qs->h[j], A = (T)1 - B;
-                    const T cA = nn * (A * A * A - A) * h * h / (T)6;
-                    const T cB = nn * (B * B * B - B) * h * h / (T)6;
+                    const T hh6 = qs->hh6[j], A = (T)1 - B;
+                    const T cA = nn * (A * A * A - A) * hh6;
+                    const T cB = nn * (B * B * B - B) * hh6;
 #pragma unroll
                     for (int c = 0; c < 10; ++c)
                         dst[c] = cx<T>{cA * r0[2 * c] + cB * r1[2 * c], cA * r0[2 * c + 1] + cB * r1[2 * c + 1]};
@@ -595,6 +565,29 @@ __device__ __forceinline__ dvec4 ld_row(const dvec4 *p) {
 }
 
 __device__ __forceinline__ int fold(int i, int n) { return i <= (n - 1) / 2 ? i : i - n; }
+
+// Block sum of per-thread FP32 terms without the FP64 pipe: FP32 sums within
+// each warp, then the warp sums added as a double-float pair by thread 0,
+// whose result (valid in thread 0 only) is widened on the integer pipe.
+__device__ __forceinline__ double block_sum_f(float v, float *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        float hi = 0.f, lo = 0.f;
+        for (int i = 0; i < nw; ++i) {
+            float e;
+            two_sum(hi, red[i], hi, e);
+            lo += e;
+        }
+        s = f2d_bits(hi) + f2d_bits(lo);
+    }
+    __syncthreads();
+    return s;
+}
 
 template <typename T>
 __device__ __forceinline__ double block_sum(double v, double *red) {
@@ -1053,7 +1046,7 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
                                                              int nsys, int total, const float4 *__restrict__ tab,
                                                              int *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double red[C32_THREADS / 32];
+    __shared__ float red[C32_THREADS / 32];
     const C32Smem m = c32_smem(smem);
     const bool producer = threadIdx.x < 32;
     __shared__ int s_failed;
@@ -1073,7 +1066,7 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
     for (int i = 0; t < total; ++i, t += gridDim.x) {
         const int b = i & 1;
         const int tn = t + gridDim.x;
-        double eacc = 0.0;
+        float eacc = 0.f;
         if (producer) {
             if (tn < total) c32_produce(sys, prefix, nsys, tn, b ^ 1, psi, m, tab);
         } else {
@@ -1133,7 +1126,7 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
 #pragma unroll
                 for (int a = 0; a < NQ; ++a) e += th[a].x * F[a].x + th[a].y * F[a].y;
                 const float weight = (kz == 0 || nyq_z) ? 1.f : 2.f;
-                eacc = (double)(weight * e);
+                eacc = weight * e;
                 float4 *out = reinterpret_cast<float4 *>(S.spec) + (size_t)idx * 10;
 #pragma unroll
                 for (int a = 0; a < NQ / 2; ++a)
@@ -1141,7 +1134,7 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
             }
         }
         ph[b] ^= 1u;
-        const double es = block_sum<float>(eacc, red);
+        const double es = block_sum_f(eacc, red);
         if (threadIdx.x == 0) m.sys[b].epart[m.meta[b].w] = es;
         __syncthreads();                             // buffer half b free for chunk t + 2 gridDim
         if (s_failed) {
@@ -1284,7 +1277,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zinv(const SysD
         cx<T> *R = fft_auto<true>(bufA, bufB, S.ax[2], L, ld, tw);
         const Rec<T> *rec = recs[cur];
         const size_t p0 = (size_t)l0 * nz;
-        const T invN = (T)S.invN;
+        const T invN = sizeof(T) == 4 ? (T)S.invNf : (T)S.invN;
         {
             // dE/dtheta_a = dV F_a; dedn = sum_a F_a (p_a + n p_a' dq0/dn),
             // dedsigma = sum_a F_a n p_a' dq0/dsigma (the 1/N of the inverse
@@ -1312,13 +1305,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zinv(const SysD
                     }
                     const T *ft = reinterpret_cast<const T *>(src);
                     const T Fj = ft[j], Fj1 = ft[j + 1];
-                    const T h = qs->h[j], B = r.B, A = (T)1 - B;
-                    const T cA = (A * A * A - A) * h * h / (T)6;
-                    const T cB = (B * B * B - B) * h * h / (T)6;
-                    const T dA = -((T)3 * A * A - (T)1) * h / (T)6;
-                    const T dB = ((T)3 * B * B - (T)1) * h / (T)6;
+                    const T hh6 = qs->hh6[j], h6 = qs->h6[j], B = r.B, A = (T)1 - B;
+                    const T cA = (A * A * A - A) * hh6;
+                    const T cB = (B * B * B - B) * hh6;
+                    const T dA = -((T)3 * A * A - (T)1) * h6;
+                    const T dB = ((T)3 * B * B - (T)1) * h6;
                     const T s0 = (A * Fj + B * Fj1 + cA * D0 + cB * D1) * invN;
-                    const T s1 = ((Fj1 - Fj) / h + dA * D0 + dB * D1) * invN;
+                    const T s1 = ((Fj1 - Fj) * qs->ih[j] + dA * D0 + dB * D1) * invN;
                     if (sizeof(T) == 4) {
                         dn = f2d_bits((float)(s0 + r.ndqn * s1));
                         ds = f2d_bits((float)(r.ndqs * s1));
