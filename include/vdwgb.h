@@ -174,11 +174,21 @@ int vdwgb_set_fused(int enable);
 /* Autotuning of tile shapes: when enabled (here or by the environment
  * variable VDWGB_AUTOTUNE=1), vdwgb_init_cuda times every stage kernel for
  * each candidate tile shape that fits shared memory (z-forward lines, y / x
- * kz-columns with 2 or 3 row buffers, z-inverse lines) on the handle's
+ * kz-columns with 1 to 4 ring buffers, z-inverse lines) on the handle's
  * own buffers and keeps the
  * fastest; the choice is cached per (grid, precision) for the process and
  * reused by later handles, batches and the server.  Default off. */
 int vdwgb_set_autotune(int enable);
+
+/* Replace the tile shapes of an initialised handle's plan (as the autotuner
+ * does): z-forward lines per tile lz, z-inverse lines lzi, y / x pass
+ * kz-columns wy / wx, and input buffers in the ring of the y / x passes
+ * nby / nbx (1..4; 1: no prefetch).  Waits for all work on the device first;
+ * call it with no evaluation of this handle in flight.  Returns VDWGB_EINVAL
+ * for a shape out of range (lines 1..nx*ny, columns 1..nz/2+1) or beyond
+ * shared memory, VDWGB_ESTATE for an uninitialised handle, a handle that a
+ * live batch holds (free the batch first) or a plane-kernel plan. */
+int vdwgb_set_tiles(vdwgb_handle h, int lz, int lzi, int wy, int wx, int nby, int nbx);
 
 /* Plan of an initialised handle: info[0..8] = z-forward lines per tile,
  * z-inverse lines per tile, y-pass kz-columns, x-pass kz-columns,

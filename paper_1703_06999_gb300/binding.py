@@ -47,6 +47,7 @@ _SIGS = {
     "vdwgb_q0": (ctypes.c_int, [ctypes.c_int] * 4 + [ctypes.c_void_p] * 5),
     "vdwgb_set_autotune": (ctypes.c_int, [ctypes.c_int]),
     "vdwgb_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "vdwgb_set_tiles": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 6),
     "vdwgb_batch_new": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "vdwgb_batch_calculate_device": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 6),
     "vdwgb_batch_free": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p)]),
@@ -244,6 +245,10 @@ def vdwgb_q0(n, sigma, functional=DF1, precision=FP64, device=0):
 
 def vdwgb_set_autotune(enable):
     _ck(lib().vdwgb_set_autotune(int(bool(enable))), "vdwgb_set_autotune")
+
+
+def vdwgb_set_tiles(h, lz, lzi, wy, wx, nby, nbx):
+    _ck(lib().vdwgb_set_tiles(h, int(lz), int(lzi), int(wy), int(wx), int(nby), int(nbx)), "vdwgb_set_tiles")
 
 
 def vdwgb_plan_info(h):

@@ -197,10 +197,10 @@ static int best_w(int prec, int n, int nzh, int slots) {
 static void choose_tiles(int prec, int nx, int ny, int nz, int nzh, size_t lim, int workx, int worky, int &LZ,
                          int &LZi, int &Wy, int &Wx, int &nbuf) {
     LZ = 1;
-    for (int l = 8; l >= 1; --l)
+    for (int l = 16; l >= 1; --l)
         if (stage_smem(0, prec, nz, l) <= TILE_BUDGET) { LZ = l; break; }
     LZi = 1;
-    for (int l = 8; l >= 1; --l)
+    for (int l = 16; l >= 1; --l)
         if (stage_smem(3, prec, nz, l) <= TILE_BUDGET) { LZi = l; break; }
     if (LZi > nx * ny) LZi = nx * ny;
     if (LZ > nx * ny) LZ = nx * ny;
@@ -395,8 +395,10 @@ static void set_tiles(vdwgb_data *h, int LZ, int LZi, int Wy, int Wx, int nby, i
     L.nbuf[0] = L.nbuf[3] = 0;
     L.nbuf[1] = nby;
     L.nbuf[2] = nbx;
+    L.work[0] = S.sz1 ? 0 : 1;
     L.work[1] = S.sy1 ? 0 : 1;
     L.work[2] = S.sx1 ? 0 : 1;
+    L.work[3] = L.work[0];
     L.smem[0] = stage_smem(0, prec, nz, LZ);
     L.smem[3] = stage_smem(3, prec, nz, LZi);
     L.smem[1] = stage_smem(1, prec, ny, Wy, nby + L.work[1]);
@@ -573,15 +575,15 @@ static int apply_tuned(vdwgb_data *h) {
     if (cudaMemcpy(tmp, host.data(), 2 * N * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
         rc = fail(VDWGB_ECUDA, "tune upload");
     set_io_dev();
-    const int cand[6] = {1, 2, 3, 4, 6, 8};
+    const int cand[8] = {1, 2, 3, 4, 6, 8, 12, 16};
     // z forward first (it writes the records and spectrum the other stages read)
     for (int pass = 0; pass < 4 && !rc; ++pass) {
         if (S.fused && (pass == 1 || pass == 2)) continue;   // y / x run inside the plane kernel
         float best_ms = 1e30f;
-        for (int ci = 0; ci < 6 * XY_MAXIN; ++ci) {
-            const int c = cand[ci % 6];
-            const int nb = 1 + ci / 6;              // x / y passes: input buffers in the ring
-            if ((pass == 0 || pass == 3) && ci >= 6) break;
+        for (int ci = 0; ci < 8 * XY_MAXIN; ++ci) {
+            const int c = cand[ci % 8];
+            const int nb = 1 + ci / 8;              // x / y passes: input buffers in the ring
+            if ((pass == 0 || pass == 3) && ci >= 8) break;
             TuneVal v = best;
             if (pass == 0) {
                 if (c > S.nx * S.ny || stage_smem(0, prec, S.nz, c) > lim) continue;
@@ -639,6 +641,7 @@ static int plan(vdwgb_data *h) {
     // two-pass split is compiled (FP32); 0: out of place through the scratch buffer
     S.sx1 = prec == VDWGB_FP32_MIXED ? fft_split(nx) : 0;
     S.sy1 = prec == VDWGB_FP32_MIXED ? fft_split(ny) : 0;
+    S.sz1 = prec == VDWGB_FP32_MIXED ? fft_split(nz) : 0;
     const int workx = S.sx1 ? 0 : 1, worky = S.sy1 ? 0 : 1;
     int nbuf = 2;
     choose_tiles(prec, nx, ny, nz, nzh, lim, workx, worky, S.LZ, S.LZi, S.Wy, S.Wx, nbuf);
@@ -1057,6 +1060,27 @@ int vdwgb_set_autotune(int enable) {
     return 0;
 }
 
+int vdwgb_set_tiles(vdwgb_handle h, int lz, int lzi, int wy, int wx, int nby, int nbx) {
+    if (!h) return fail(VDWGB_EINVAL, "null handle");
+    if (!h->inited) return fail(VDWGB_ESTATE, "handle not initialised");
+    if (h->nbatch > 0) return fail(VDWGB_ESTATE, "handle is part of a live batch");
+    SysDev &S = h->hsys;
+    if (S.fused) return fail(VDWGB_ESTATE, "plan uses the plane kernel (no y / x tiles)");
+    const int nl = S.nx * S.ny;
+    if (lz < 1 || lz > nl || lzi < 1 || lzi > nl || wy < 1 || wy > S.nzh || wx < 1 || wx > S.nzh || nby < 1 ||
+        nby > XY_MAXIN || nbx < 1 || nbx > XY_MAXIN)
+        return fail(VDWGB_EINVAL, "tile shape out of range");
+    const size_t lim = g_dev[h->device].maxsmem - 1024;
+    const int workx = S.sx1 ? 0 : 1, worky = S.sy1 ? 0 : 1;
+    if (stage_smem(0, h->prec, S.nz, lz) > lim || stage_smem(3, h->prec, S.nz, lzi) > lim ||
+        stage_smem(1, h->prec, S.ny, wy, nby + worky) > lim || stage_smem(1, h->prec, S.nx, wx, nbx + workx) > lim)
+        return fail(VDWGB_EINVAL, "tile shape exceeds shared memory");
+    cudaSetDevice(h->device);
+    CK(cudaDeviceSynchronize(), "set tiles: wait for evaluations in flight");
+    set_tiles(h, lz, lzi, wy, wx, nby, nbx);
+    return upload_plan(h);
+}
+
 int vdwgb_plan_info(vdwgb_handle h, int *info) {
     if (!h || !info) return fail(VDWGB_EINVAL, "null argument");
     if (!h->inited) return fail(VDWGB_ESTATE, "handle not initialised");
@@ -1154,7 +1178,7 @@ int vdwgb::batch_launchset(vdwgb_data *const *hs, int count, SysDev *hdesc, int 
     const size_t c = prec == VDWGB_FP32_MIXED ? 8 : 16;
     for (int s = 1; s <= 2; ++s)
         L.smem[s] = xy_smem_bytes(L.twmax[s], L.bufelems[s], L.nbuf[s] + L.work[s], c);
-    L.smem[3] = zinv_smem(prec, L.twmax[3], L.bufelems[3], L.recelems, L.abelems);
+    L.smem[3] = zinv_smem(prec, L.twmax[3], L.bufelems[3], L.recelems, L.abelems, 1 + L.work[3]);
     const size_t lim = di.maxsmem - 1024;
     if (L.smem[1] > lim || L.smem[2] > lim || L.smem[3] > lim)
         return fail(VDWGB_EINVAL, "batch: combined row tiles exceed shared memory");
@@ -1220,6 +1244,7 @@ int vdwgb_batch_new(vdwgb_handle *handles, int count, vdwgb_batch *out) {
         return rc;
     }
     b->last.assign(5 * count, nullptr);
+    for (int i = 0; i < count; ++i) ++handles[i]->nbatch;
     *out = b;
     return 0;
 }
@@ -1358,6 +1383,7 @@ int vdwgb_batch_free(vdwgb_batch *bp) {
     vdwgb_batch_s *b = *bp;
     if (b) {
         cudaSetDevice(b->device);
+        for (vdwgb_data *h : b->hs) --h->nbatch;
         if (b->exec) cudaGraphExecDestroy(b->exec);
         for (auto &v : b->pending)
             for (auto e : v) cudaEventDestroy(e);

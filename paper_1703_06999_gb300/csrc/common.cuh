@@ -40,6 +40,23 @@ template <typename T>
 __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
     return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
+// Two FP32 values in one 64-bit register pair, and the two-lane FP32 FMA of
+// sm_100-family GPUs (d = a * b + c per lane, round to nearest).
+__device__ __forceinline__ unsigned long long pack_f2(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack_f2(unsigned long long v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long fma_f2(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 // multiply by -i (forward) or +i (inverse)
 template <bool INV, typename T>
 __device__ __forceinline__ cx<T> mul_mi(cx<T> a) {
@@ -102,6 +119,7 @@ struct SysDev {
     // plane kernel (fused y / x transforms and contraction), else zero:
     int fused;       // cluster size C; each CTA owns nx / C x-rows, then ny / C y-rows
     int sx1, sy1;    // N1 of the two-pass splits of the x and y axes
+    int sz1;         // FP32: N1 of the in-place split of the z axis (0: none, out-of-place z passes)
     int kstride;     // entries per (kz, rank) list of kord
     const unsigned short *kord;   // per (kz, rank): local k-point indices sorted by table interval
     const void *tmap;    // FP32: two tensor maps of spec (y-pass tile box, x-pass tile box), else null
@@ -273,24 +291,27 @@ __device__ __forceinline__ void fft_stage(const cx<T> *in, cx<T> *out, int n, in
 
 // Full 1-D transforms of `nlines` lines (unnormalised), layout [i][ld].
 // Ping-pongs between a and b; returns the buffer that holds the result.
-// Ends with a barrier.  Requires nlines <= blockDim.x.
+// Ends with a barrier.  Lines are taken in groups of at most blockDim.x.
 template <bool INV, typename T>
 __device__ cx<T> *fft_lines(cx<T> *a, cx<T> *b, const AxisPlan &p, int nlines, int ld, const cx<T> *tw) {
-    const int jstep = blockDim.x / nlines;
-    const int j0 = threadIdx.x / nlines;
-    const int line = threadIdx.x - j0 * nlines;
-    const bool active = j0 < jstep;
+    const int nt = blockDim.x;
     int Ns = 1;
     for (int s = 0; s < p.nst; ++s) {
         const int R = p.rad[s];
-        if (active) {
-            switch (R) {
-                case 2: fft_stage<2, INV>(a, b, p.n, Ns, ld, line, j0, jstep, tw); break;
-                case 3: fft_stage<3, INV>(a, b, p.n, Ns, ld, line, j0, jstep, tw); break;
-                case 4: fft_stage<4, INV>(a, b, p.n, Ns, ld, line, j0, jstep, tw); break;
-                case 5: fft_stage<5, INV>(a, b, p.n, Ns, ld, line, j0, jstep, tw); break;
-                case 7: fft_stage<7, INV>(a, b, p.n, Ns, ld, line, j0, jstep, tw); break;
-                default: fft_stage<8, INV>(a, b, p.n, Ns, ld, line, j0, jstep, tw); break;
+        for (int lb = 0; lb < nlines; lb += nt) {
+            const int ng = min(nlines - lb, nt);      // lines in this group
+            const int jstep = nt / ng;
+            const int j0 = threadIdx.x / ng;
+            const int line = lb + threadIdx.x - j0 * ng;
+            if (j0 < jstep) {
+                switch (R) {
+                    case 2: fft_stage<2, INV>(a, b, p.n, Ns, ld, line, j0, jstep, tw); break;
+                    case 3: fft_stage<3, INV>(a, b, p.n, Ns, ld, line, j0, jstep, tw); break;
+                    case 4: fft_stage<4, INV>(a, b, p.n, Ns, ld, line, j0, jstep, tw); break;
+                    case 5: fft_stage<5, INV>(a, b, p.n, Ns, ld, line, j0, jstep, tw); break;
+                    case 7: fft_stage<7, INV>(a, b, p.n, Ns, ld, line, j0, jstep, tw); break;
+                    default: fft_stage<8, INV>(a, b, p.n, Ns, ld, line, j0, jstep, tw); break;
+                }
             }
         }
         __syncthreads();

@@ -224,6 +224,9 @@ __host__ __device__ constexpr int fft_split(int n) {   // N1 of the two-pass spl
 // frequency held at position p of a permuted spectrum of length n1 * n2
 __host__ __device__ inline int fft_perm_freq(int p, int n1, int n2) { return p / n2 + n1 * (p % n2); }
 
+// position of frequency f in a permuted spectrum of length n1 * n2
+__host__ __device__ inline int fft_perm_pos(int f, int n1, int n2) { return (f % n1) * n2 + f / n1; }
+
 // frequency index at position p of an axis of length n whose forward pass
 // left the permuted order (n1 = its split), or p itself (n1 = 0)
 __host__ __device__ inline int axis_freq(int p, int n, int n1) { return n1 ? fft_perm_freq(p, n1, n / n1) : p; }

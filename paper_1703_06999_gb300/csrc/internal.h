@@ -25,6 +25,7 @@ struct vdwgb_data {
     int4 *chunks = nullptr;
     unsigned short *kord = nullptr;    // plane kernel k-point order
     void *tmap = nullptr;              // FP32: tensor maps of the x / y pass tiles
+    int nbatch = 0;                    // live batches built on this handle (they share tmap)
     vdwgb::SysDev *dsys = nullptr;
     int *dprefix = nullptr;
     vdwgb::SysDev hsys;

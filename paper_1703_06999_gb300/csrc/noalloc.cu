@@ -213,6 +213,7 @@ extern "C" int vdwgb_calculate_noalloc(int device, int functional, int nx, int n
     S.LZi = tile_lines(3, nz, nx * ny);
     S.sx1 = fft_split(nx);                   // in-place x / y transforms where compiled
     S.sy1 = fft_split(ny);
+    S.sz1 = fft_split(nz);
     const int workx = S.sx1 ? 0 : 1, worky = S.sy1 ? 0 : 1;
     S.Wy = tile_cols(ny, nzh, 2 + worky);
     S.Wx = tile_cols(nx, nzh, 2 + workx);
@@ -280,8 +281,10 @@ extern "C" int vdwgb_calculate_noalloc(int device, int functional, int nx, int n
     L.bufelems[1] = ny * S.Wy * NQ;
     L.bufelems[2] = nx * S.Wx * NQ;
     L.nbuf[1] = L.nbuf[2] = 2;
+    L.work[0] = S.sz1 ? 0 : 1;
     L.work[1] = worky;
     L.work[2] = workx;
+    L.work[3] = L.work[0];
     L.smem[0] = stage_smem(0, 1, nz, S.LZ);
     L.smem[1] = stage_smem(1, 1, ny, S.Wy, 2 + worky);
     L.smem[2] = stage_smem(1, 1, nx, S.Wx, 2 + workx);

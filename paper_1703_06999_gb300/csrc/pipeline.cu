@@ -493,7 +493,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zfwd(const SysD
             }
         }
         __syncthreads();
-        cx<T> *R = fft_auto<false>(bufA, bufB, S.ax[2], L, ld, tw);
+        // FP32 with a split: in place, frequency f at position fft_perm_pos(f)
+        const int zs = sizeof(T) == 4 ? S.sz1 : 0;
+        cx<T> *R;
+        if (zs) {
+            fft_ip_auto<false>(bufA, nz, L, ld, tw);
+            R = bufA;
+        } else {
+            R = fft_auto<false>(bufA, bufB, S.ax[2], L, ld, tw);
+        }
+        const int zs2 = zs ? nz / zs : 0;
         // unpack the two real transforms: X_{2c}(kz) = (Z(kz) + conj Z(-kz)) / 2,
         // X_{2c+1}(kz) = (Z(kz) - conj Z(-kz)) / 2i; one thread writes the 10
         // outputs of half h (c = 5h .. 5h+4) of one (line, kz)
@@ -505,8 +514,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zfwd(const SysD
             int kz = (threadIdx.x >> 1) % nzh, li = (threadIdx.x >> 1) / nzh;
             for (; li < nl;) {
                 const int km = kz == 0 ? 0 : nz - kz;
-                const cx<T> *zk = R + (size_t)kz * ld + li * 10 + 5 * half;
-                const cx<T> *zm = R + (size_t)km * ld + li * 10 + 5 * half;
+                const int pk = zs ? fft_perm_pos(kz, zs, zs2) : kz, pm = zs ? fft_perm_pos(km, zs, zs2) : km;
+                const cx<T> *zk = R + (size_t)pk * ld + li * 10 + 5 * half;
+                const cx<T> *zm = R + (size_t)pm * ld + li * 10 + 5 * half;
                 cx<T> *out = spec + ((size_t)li * nzh + kz) * NQ + 10 * half;
 #pragma unroll
                 for (int c = 0; c < 5; ++c) {
@@ -1024,6 +1034,14 @@ __device__ __forceinline__ void c32_produce(const SysDev *__restrict__ sys, cons
 template <bool GLOBAL>
 __device__ __forceinline__ void contract_row(const float4 *__restrict__ row, float tt, const cx<float> *th,
                                              cx<float> *F) {
+    // theta and F as packed (re, im) pairs: each complex multiply-accumulate
+    // by the real phi is one two-lane FP32 FMA (same rounding as two FMAs)
+    unsigned long long th2[NQ], F2[NQ];
+#pragma unroll
+    for (int a = 0; a < NQ; ++a) {
+        th2[a] = pack_f2(th[a].x, th[a].y);
+        F2[a] = pack_f2(F[a].x, F[a].y);
+    }
     int pidx = 0;
 #pragma unroll
     for (int a = 0; a < NQ; ++a) {
@@ -1031,15 +1049,14 @@ __device__ __forceinline__ void contract_row(const float4 *__restrict__ row, flo
         for (int bb = a; bb < NQ; ++bb) {
             const float4 cf = GLOBAL ? __ldg(row + pidx) : row[pidx];
             const float phi = cf.x + tt * (cf.y + tt * (cf.z + tt * cf.w));
-            F[a].x += phi * th[bb].x;
-            F[a].y += phi * th[bb].y;
-            if (bb != a) {
-                F[bb].x += phi * th[a].x;
-                F[bb].y += phi * th[a].y;
-            }
+            const unsigned long long p2 = pack_f2(phi, phi);
+            F2[a] = fma_f2(p2, th2[bb], F2[a]);
+            if (bb != a) F2[bb] = fma_f2(p2, th2[a], F2[bb]);
             ++pidx;
         }
     }
+#pragma unroll
+    for (int a = 0; a < NQ; ++a) unpack_f2(F2[a], F[a].x, F[a].y);
 }
 
 __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__restrict__ sys, const int *__restrict__ prefix,
@@ -1233,6 +1250,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zinv(const SysD
         const cx<T> *spec = ins[cur];
         const bool even = (nz % 2) == 0;
         const int ld = z_ld(nl);
+        // FP32 with a split: packed at permuted positions, transformed in place
+        const int zs = sizeof(T) == 4 ? S.sz1 : 0, zs2 = zs ? nz / zs : 0;
         // Z_c[kz] = X_{2c}[kz] + i X_{2c+1}[kz]; Z_c[nz-kz] = conj(X_{2c}) + i conj(X_{2c+1});
         // one thread handles half h (c = 5h .. 5h+4) of one (line, kz)
         {
@@ -1242,11 +1261,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zinv(const SysD
             int kz = (threadIdx.x >> 1) % nzh, li = (threadIdx.x >> 1) / nzh;
             for (; li < nl;) {
                 const cx<T> *in = spec + ((size_t)li * nzh + kz) * NQ + 10 * half;
-                cx<T> *o1 = bufA + (size_t)kz * ld + li * 10 + 5 * half;
                 const int km = nz - kz;
                 const bool mirror = kz > 0 && km >= nzh;
                 const bool realbin = kz == 0 || (even && kz == nz / 2);
-                cx<T> *o2 = bufA + (size_t)(mirror ? km : 0) * ld + li * 10 + 5 * half;
+                const int pk = zs ? fft_perm_pos(kz, zs, zs2) : kz;
+                const int pm = mirror ? (zs ? fft_perm_pos(km, zs, zs2) : km) : 0;
+                cx<T> *o1 = bufA + (size_t)pk * ld + li * 10 + 5 * half;
+                cx<T> *o2 = bufA + (size_t)pm * ld + li * 10 + 5 * half;
 #pragma unroll
                 for (int c = 0; c < 5; ++c) {
                     cx<T> a, b;
@@ -1274,7 +1295,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zinv(const SysD
             }
         }
         __syncthreads();
-        cx<T> *R = fft_auto<true>(bufA, bufB, S.ax[2], L, ld, tw);
+        cx<T> *R;
+        if (zs) {
+            fft_ip_auto<true>(bufA, nz, L, ld, tw);
+            R = bufA;
+        } else {
+            R = fft_auto<true>(bufA, bufB, S.ax[2], L, ld, tw);
+        }
         const Rec<T> *rec = recs[cur];
         const size_t p0 = (size_t)l0 * nz;
         const T invN = sizeof(T) == 4 ? (T)S.invNf : (T)S.invN;
@@ -1403,10 +1430,15 @@ cudaError_t launch_q0(int prec, int npts, const double *n, const double *s, doub
 // ---------------------------------------------------------------------------
 // Host-side launchers
 // ---------------------------------------------------------------------------
+// z passes: one tile buffer when the FP32 transform runs in place, else two
+template <typename T>
+size_t z_nbuf(int nz) {
+    return sizeof(T) == 4 && fft_split(nz) ? 1 : 2;
+}
 template <typename T>
 size_t smem_z(int nz, int LZ) {
     return ((sizeof(QShared<T>) + 15) / 16) * 16 +
-           sizeof(cx<T>) * ((size_t)((nz + 1) & ~1) + 2ull * nz * z_ld(LZ));
+           sizeof(cx<T>) * ((size_t)((nz + 1) & ~1) + z_nbuf<T>(nz) * nz * z_ld(LZ));
 }
 template <typename T>
 size_t smem_xy(int n, int W, int nslots) {
@@ -1417,16 +1449,16 @@ template <typename T>
 size_t smem_zinv(int nz, int LZ) {
     const size_t nzh = nz / 2 + 1;
     return 16 + ((sizeof(QShared<T>) + 15) / 16) * 16 +
-           sizeof(cx<T>) * ((size_t)((nz + 7) & ~7) + 2 * (size_t)LZ * nzh * NQ + 2ull * nz * z_ld(LZ)) +
+           sizeof(cx<T>) * ((size_t)((nz + 7) & ~7) + 2 * (size_t)LZ * nzh * NQ + z_nbuf<T>(nz) * nz * z_ld(LZ)) +
            2 * (size_t)LZ * nz * sizeof(Rec<T>);
 }
 
-size_t zinv_smem(int prec, int nzmax, int inelems, int recelems, int abelems) {
+size_t zinv_smem(int prec, int nzmax, int inelems, int recelems, int abelems, int nab) {
     const bool f = prec == 1;
     const size_t c = f ? sizeof(cx<float>) : sizeof(cx<double>);
     const size_t rs = f ? sizeof(Rec<float>) : sizeof(Rec<double>);
     const size_t qsz = f ? ((sizeof(QShared<float>) + 15) / 16) * 16 : ((sizeof(QShared<double>) + 15) / 16) * 16;
-    return 16 + qsz + c * ((size_t)((nzmax + 7) & ~7) + 2 * (size_t)inelems + 2 * (size_t)abelems) +
+    return 16 + qsz + c * ((size_t)((nzmax + 7) & ~7) + 2 * (size_t)inelems + (size_t)nab * abelems) +
            2 * (size_t)recelems * rs;
 }
 

@@ -21,7 +21,7 @@ struct LaunchSet {
     int twmax[6];            // longest axis of the stage over all systems (twiddle slots)
     int bufelems[6];         // complex elements of one row-tile buffer (x / y stages)
     int nbuf[6];             // x / y stages: input buffers in the ring (1..XY_MAXIN)
-    int work[6];             // x / y stages: 1 if some system needs the scratch buffer
+    int work[6];             // per kind: 1 if some system needs the scratch buffer (z, y, x, z inverse)
     int recelems;            // z-inverse: point records per staged tile
     int abelems;             // z-inverse: complex elements of one transform buffer
     int *err;                // device flag set by a stage whose bounded wait ran out
@@ -53,7 +53,8 @@ inline size_t xy_smem_bytes(int twmax, int bufelems, int nbuf, size_t csize) {
 
 // stage 1 (x / y): nbuf = buffers in total (ring inputs plus the scratch buffer if any)
 size_t stage_smem(int stage, int prec, int n, int tile, int nbuf = 3);
-size_t zinv_smem(int prec, int nzmax, int inelems, int recelems, int abelems);
+// nab: z-inverse tile buffers (1 when every system of the launch transforms in place)
+size_t zinv_smem(int prec, int nzmax, int inelems, int recelems, int abelems, int nab);
 size_t contract_smem(int prec, int maxspan);
 cudaError_t init_kernels(size_t maxsmem);
 constexpr int NSTAGE = 9;   // stages per evaluation (stages without tiles are not launched)
