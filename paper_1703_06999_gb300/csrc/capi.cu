@@ -707,7 +707,7 @@ static int plan(vdwgb_data *h) {
         build_chunks(S, maxspan, chunkmax, kidx, chunks);
         S.tiles[4] = (int)chunks.size();
         S.tiles[5] = 0;
-        S.nepart = S.tiles[4];
+        S.nepart = S.tiles[4] * (prec == VDWGB_FP32_MIXED ? C32_CWARPS : 1);   // FP32: one per consumer warp
     }
     // memory
     const size_t nspec = (size_t)nx * ny * nzh * NQ;

@@ -38,7 +38,7 @@ constexpr size_t OFF_REC = al256(OFF_SPEC + NA_MAX_KPOINTS * NQ * sizeof(cx<floa
 constexpr size_t OFF_KIDX = al256(OFF_REC + NA_MAX_POINTS * sizeof(Rec<float>));
 constexpr size_t OFF_CHUNK = al256(OFF_KIDX + NA_MAX_KPOINTS * sizeof(unsigned));
 constexpr size_t OFF_EPART = al256(OFF_CHUNK + NA_MAX_CHUNKS * sizeof(int4));
-constexpr size_t OFF_TW = al256(OFF_EPART + NA_MAX_CHUNKS * sizeof(double));
+constexpr size_t OFF_TW = al256(OFF_EPART + NA_MAX_CHUNKS * C32_CWARPS * sizeof(double));
 constexpr size_t OFF_DESC = al256(OFF_TW + 3 * NA_MAX_AXIS * sizeof(cx<float>));
 constexpr size_t OFF_PRE = al256(OFF_DESC + sizeof(SysDev));
 constexpr size_t SCRATCH_BYTES = al256(OFF_PRE + 2 * NKIND * sizeof(int));   // about 3.4 MiB
@@ -236,7 +236,7 @@ extern "C" int vdwgb_calculate_noalloc(int device, int functional, int nx, int n
     const int nch = sort_chunks(S);
     if (nch < 0) return fail(VDWGB_EINVAL, "too many contraction chunks for the fixed scratch");
     S.tiles[4] = nch;
-    S.nepart = nch;
+    S.nepart = nch * C32_CWARPS;             // one energy partial per chunk and consumer warp
     for (int a = 0; a < 3; ++a)
         for (int m = 0; m < dims[a]; ++m) {
             const double ang = 2.0 * M_PI * (double)m / (double)dims[a];

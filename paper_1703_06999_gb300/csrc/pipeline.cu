@@ -16,6 +16,7 @@
 #include "tma.cuh"
 #include "dfloat.cuh"
 #include "fftreg.cuh"
+#include "contract.cuh"
 
 namespace vdwgb {
 
@@ -935,8 +936,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_contract(const 
 // warp: warp 0 walks the chunk list (system, chunk record, k-point order) and
 // issues the loads of the next chunk — ten 16-byte cp.async copies per k-point
 // record and one bulk copy of the chunk's table rows — into the free half of
-// a double buffer, while warps 1..15 compute the current chunk entirely from
-// shared memory (one k-point per thread, up to CHUNK32 = 480 per chunk).
+// a double buffer, while warps 1..11 compute the current chunk entirely from
+// shared memory (one k-point per thread, up to CHUNK32 = 352 per chunk).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
@@ -950,11 +951,13 @@ __device__ __forceinline__ void mbar_arrive_local(unsigned long long *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-constexpr int C32_THREADS = 512;            // warp 0 producer, warps 1..15 consumers
+constexpr int C32_THREADS = 32 * (1 + C32_CWARPS);   // warp 0 producer, warps 1.. consumers
+static_assert(CHUNK32 == C32_THREADS - 32, "one k-point per consumer thread");
 constexpr int C32_ARRIVALS = 33;            // 32 cp.async arrivals + the row copy's expect-tx arrive
 
 struct C32Smem {
-    unsigned long long *full;   // [2]
+    unsigned long long *full;   // [2] chunk landed
+    unsigned long long *empty;  // [2] chunk released by every consumer warp
     SysDev *sys;                // [2] descriptor of the buffered chunk's system
     int4 *meta;                 // [2] {count, first interval, intervals, chunk index in its system}
     unsigned *idx;              // [2][CHUNK32] k-point indices
@@ -972,6 +975,7 @@ __host__ __device__ inline size_t c32_smem_bytes() { return c32_off_rows() + 2 *
 __device__ __forceinline__ C32Smem c32_smem(unsigned char *smem) {
     C32Smem m;
     m.full = reinterpret_cast<unsigned long long *>(smem);
+    m.empty = m.full + 2;
     m.sys = reinterpret_cast<SysDev *>(smem + c32_off_sys());
     m.meta = reinterpret_cast<int4 *>(smem + c32_off_meta());
     m.idx = reinterpret_cast<unsigned *>(smem + c32_off_idx());
@@ -1028,145 +1032,132 @@ __device__ __forceinline__ void c32_produce(const SysDev *__restrict__ sys, cons
     }
 }
 
-// F_a += sum_b phi_ab(t) theta_b over the 210 symmetric pairs of one table
-// row (cubic in t); GLOBAL: the row is read from global memory, else from
-// shared memory
-template <bool GLOBAL>
-__device__ __forceinline__ void contract_row(const float4 *__restrict__ row, float tt, const cx<float> *th,
-                                             cx<float> *F) {
-    // theta and F as packed (re, im) pairs: each complex multiply-accumulate
-    // by the real phi is one two-lane FP32 FMA (same rounding as two FMAs)
-    unsigned long long th2[NQ], F2[NQ];
-#pragma unroll
-    for (int a = 0; a < NQ; ++a) {
-        th2[a] = pack_f2(th[a].x, th[a].y);
-        F2[a] = pack_f2(F[a].x, F[a].y);
-    }
-    int pidx = 0;
-#pragma unroll
-    for (int a = 0; a < NQ; ++a) {
-#pragma unroll
-        for (int bb = a; bb < NQ; ++bb) {
-            const float4 cf = GLOBAL ? __ldg(row + pidx) : row[pidx];
-            const float phi = cf.x + tt * (cf.y + tt * (cf.z + tt * cf.w));
-            const unsigned long long p2 = pack_f2(phi, phi);
-            F2[a] = fma_f2(p2, th2[bb], F2[a]);
-            if (bb != a) F2[bb] = fma_f2(p2, th2[a], F2[bb]);
-            ++pidx;
-        }
-    }
-#pragma unroll
-    for (int a = 0; a < NQ; ++a) unpack_f2(F2[a], F[a].x, F[a].y);
+// |k| of half-spectrum index idx (positions of the x / y passes mapped to
+// frequencies, Nyquist planes with the convention of the FP64 path) as table
+// interval j and offset tt in [0, 1); weight 1 on the kz = 0 and Nyquist
+// planes, 2 elsewhere (the other half of the spectrum)
+__device__ __forceinline__ void c32_kpoint(const SysDev &S, unsigned idx, float inv_dk, int &j, float &tt,
+                                           float &weight) {
+    const int nx = S.nx, ny = S.ny, nz = S.nz, nzh = S.nzh;
+    const int kz = (int)(idx % (unsigned)nzh);
+    const int rest = (int)(idx / (unsigned)nzh);
+    const int y = axis_freq(rest % ny, ny, S.sy1), x = axis_freq(rest / ny, nx, S.sx1);
+    const int mx = fold(x, nx), my = fold(y, ny);
+    const bool nyq_x = (nx % 2 == 0) && (x == nx / 2);
+    const bool nyq_y = (ny % 2 == 0) && (y == ny / 2);
+    const bool nyq_z = (nz % 2 == 0) && (kz == nz / 2);
+    const int mz = nyq_z ? -kz : kz;
+    const float fx = (float)mx, fy = (float)my, fz = (float)mz;
+    const float cxv = nyq_x ? 0.f : fx, cyv = nyq_y ? 0.f : fy, czv = nyq_z ? 0.f : fz;
+    float k2 = S.gf[0] * fx * fx + S.gf[1] * fy * fy + S.gf[2] * fz * fz +
+               2.f * (S.gf[3] * cxv * cyv + S.gf[4] * cxv * czv + S.gf[5] * cyv * czv);
+    k2 = k2 > 0.f ? k2 : 0.f;
+    const float xk = sqrtf(k2) * inv_dk;
+    j = (int)xk;
+    tt = xk - (float)j;
+    weight = (kz == 0 || nyq_z) ? 1.f : 2.f;
 }
 
+// Warp 0 fills the two buffer halves in turn (chunk i into half i & 1, after
+// every consumer warp has released that half's previous chunk); the consumer
+// warps run through the chunks without block-wide barriers, each writing one
+// energy partial per chunk (epart[chunk * C32_CWARPS + warp]).
 __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__restrict__ sys, const int *__restrict__ prefix,
                                                              int nsys, int total, const float4 *__restrict__ tab,
                                                              int *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ float red[C32_THREADS / 32];
     const C32Smem m = c32_smem(smem);
-    const bool producer = threadIdx.x < 32;
     __shared__ int s_failed;
     if (threadIdx.x == 0) {
         s_failed = 0;
-        mbar_init(&m.full[0], C32_ARRIVALS);
-        mbar_init(&m.full[1], C32_ARRIVALS);
+        for (int h = 0; h < 2; ++h) {
+            mbar_init(&m.full[h], C32_ARRIVALS);
+            mbar_init(&m.empty[h], C32_CWARPS);
+        }
         fence_mbar_init();
     }
     __syncthreads();
-    unsigned ph[2] = {0u, 0u};
-    int psi = -1;
-    bool failed = false;
-    const float inv_dk = (float)(RMAX / (2.0 * 3.14159265358979323846));
-    int t = blockIdx.x;
-    if (t < total && producer) c32_produce(sys, prefix, nsys, t, 0, psi, m, tab);
-    for (int i = 0; t < total; ++i, t += gridDim.x) {
-        const int b = i & 1;
-        const int tn = t + gridDim.x;
-        float eacc = 0.f;
-        if (producer) {
-            if (tn < total) c32_produce(sys, prefix, nsys, tn, b ^ 1, psi, m, tab);
-        } else {
-            const bool ok = !failed && mbar_wait(&m.full[b], ph[b]);
-            if (!ok && !failed) {
-                atomicExch(err, 1);
-                failed = true;
-                s_failed = 1;
+    if (threadIdx.x < 32) {
+        // producer
+        int psi = -1;
+        int last0 = -1, last1 = -1;   // last chunk (local count) issued into each half
+        int i = 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+            const int b = i & 1;
+            if (i >= 2) {
+                // chunk i - 2 released: completion (i - 2) / 2 of empty[b]
+                const bool ok = mbar_wait(&m.empty[b], ((i >> 1) + 1) & 1u);
+                if (!__all_sync(0xffffffffu, ok) || *(volatile int *)&s_failed) {
+                    if (threadIdx.x == 0) {
+                        atomicExch(err, 1);
+                        s_failed = 1;
+                    }
+                    break;
+                }
             }
+            c32_produce(sys, prefix, nsys, t, b, psi, m, tab);
+            if (b) last1 = i;
+            else last0 = i;
+        }
+        // every copy issued has landed before the block exits
+        cp_async_wait_all();
+        if (threadIdx.x == 0) {
+            if (last0 >= 0) mbar_wait(&m.full[0], (last0 >> 1) & 1u);
+            if (last1 >= 0) mbar_wait(&m.full[1], (last1 >> 1) & 1u);
+        }
+    } else {
+        const int cw = (threadIdx.x >> 5) - 1;   // consumer warp
+        const int lane = threadIdx.x & 31;
+        const float inv_dk = (float)(RMAX / (2.0 * 3.14159265358979323846));
+        int i = 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+            const int b = i & 1;
+            const bool ok = !*(volatile int *)&s_failed && mbar_wait(&m.full[b], (i >> 1) & 1u);
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) {
+                    atomicExch(err, 1);
+                    s_failed = 1;
+                }
+                break;
+            }
+            float eacc = 0.f;
             const int4 mt = m.meta[b];
             const int k = threadIdx.x - 32;
-            if (ok && k < mt.x) {
+            if (k < mt.x) {
                 const SysDev &S = m.sys[b];
                 const unsigned idx = m.idx[b * CHUNK32 + k];
-                const int nx = S.nx, ny = S.ny, nz = S.nz, nzh = S.nzh;
-                const int kz = (int)(idx % (unsigned)nzh);
-                const int rest = (int)(idx / (unsigned)nzh);
-                // positions -> frequencies (the x / y passes may leave them permuted)
-                const int y = axis_freq(rest % ny, ny, S.sy1), x = axis_freq(rest / ny, nx, S.sx1);
-                const int mx = fold(x, nx), my = fold(y, ny);
-                const bool nyq_x = (nx % 2 == 0) && (x == nx / 2);
-                const bool nyq_y = (ny % 2 == 0) && (y == ny / 2);
-                const bool nyq_z = (nz % 2 == 0) && (kz == nz / 2);
-                const int mz = nyq_z ? -kz : kz;
-                const float fx = (float)mx, fy = (float)my, fz = (float)mz;
-                const float cxv = nyq_x ? 0.f : fx, cyv = nyq_y ? 0.f : fy, czv = nyq_z ? 0.f : fz;
-                float k2 = S.gf[0] * fx * fx + S.gf[1] * fy * fy + S.gf[2] * fz * fz +
-                           2.f * (S.gf[3] * cxv * cyv + S.gf[4] * cxv * czv + S.gf[5] * cyv * czv);
-                k2 = k2 > 0.f ? k2 : 0.f;
-                const float xk = sqrtf(k2) * inv_dk;
-                const int j = (int)xk;
-                const float tt = xk - (float)j;
-                const float4 *v4 = m.th + ((size_t)b * CHUNK32 + k) * 10;
-                cx<float> th[NQ], F[NQ];
+                int j;
+                float tt, w;
+                c32_kpoint(S, idx, inv_dk, j, tt, w);
+                f2_t th[NQ], F[NQ];
+                load_rec_f2(m.th + ((size_t)b * CHUNK32 + k) * 10, th);
 #pragma unroll
-                for (int a = 0; a < NQ / 2; ++a) {
-                    const float4 q = v4[a];
-                    th[2 * a] = cx<float>{q.x, q.y};
-                    th[2 * a + 1] = cx<float>{q.z, q.w};
-                }
-#pragma unroll
-                for (int a = 0; a < NQ; ++a) F[a] = cx<float>{0.f, 0.f};
-                const int span = min(mt.z, SPAN32);
+                for (int a = 0; a < NQ; ++a) F[a] = 0ull;
                 if (j < NK - 1) {
                     // the interval's row: staged, else (rounding at a chunk edge) global
                     // (two copies of the loop, so that the staged one compiles to
                     // shared-memory loads rather than generic ones)
-                    const bool staged = span > 0 && j >= mt.y && j < mt.y + span;
-                    if (staged) {
-                        const float4 *row = m.rows + ((size_t)b * SPAN32 + (j - mt.y)) * NPAIR;
-                        contract_row<false>(row, tt, th, F);
-                    } else {
+                    const int span = min(mt.z, SPAN32);
+                    if (span > 0 && j >= mt.y && j < mt.y + span)
+                        contract_row<false>(m.rows + ((size_t)b * SPAN32 + (j - mt.y)) * NPAIR, tt, th, F);
+                    else
                         contract_row<true>(tab + (size_t)j * NPAIR, tt, th, F);
-                    }
                 }
-                float e = 0.f;
-#pragma unroll
-                for (int a = 0; a < NQ; ++a) e += th[a].x * F[a].x + th[a].y * F[a].y;
-                const float weight = (kz == 0 || nyq_z) ? 1.f : 2.f;
-                eacc = weight * e;
-                float4 *out = reinterpret_cast<float4 *>(S.spec) + (size_t)idx * 10;
-#pragma unroll
-                for (int a = 0; a < NQ / 2; ++a)
-                    out[a] = make_float4(F[2 * a].x, F[2 * a].y, F[2 * a + 1].x, F[2 * a + 1].y);
+                eacc = w * energy_f2(th, F);
+                store_rec_f2(reinterpret_cast<float4 *>(S.spec) + (size_t)idx * 10, F);
             }
-        }
-        ph[b] ^= 1u;
-        const double es = block_sum_f(eacc, red);
-        if (threadIdx.x == 0) m.sys[b].epart[m.meta[b].w] = es;
-        __syncthreads();                             // buffer half b free for chunk t + 2 gridDim
-        if (s_failed) {
-            // a bounded wait ran out: let the copies of the chunk in flight land, then stop
-            if (producer) cp_async_wait_all();
-            if (threadIdx.x == 0 && tn < total) mbar_wait(&m.full[b ^ 1], ph[b ^ 1]);
-            break;
+            for (int o = 16; o > 0; o >>= 1) eacc += __shfl_down_sync(0xffffffffu, eacc, o);
+            if (lane == 0) m.sys[b].epart[(size_t)mt.w * C32_CWARPS + cw] = f2d_bits(eacc);
+            __syncwarp();                        // the warp's reads of half b are done
+            if (lane == 0) mbar_arrive_local(&m.empty[b]);
         }
     }
-    if (producer) cp_async_wait_all();
     __syncthreads();
-    if (threadIdx.x == 0) {
-        mbar_inval(&m.full[0]);
-        mbar_inval(&m.full[1]);
-    }
+    if (threadIdx.x == 0)
+        for (int h = 0; h < 2; ++h) {
+            mbar_inval(&m.full[h]);
+            mbar_inval(&m.empty[h]);
+        }
 }
 
 // ---------------------------------------------------------------------------
@@ -1377,22 +1368,75 @@ __device__ __forceinline__ void neumaier_add(double &s, double &c, double v) {
     s = t;
 }
 
-__global__ void k_efinish(const SysDev *__restrict__ sys, int nsys) {
-    // one warp per system: each lane sums a strided share of the partials,
-    // then the (sum, compensation) pairs meet in a fixed shuffle tree
-    const int lane = threadIdx.x & 31;
-    for (int si = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); si < nsys; si += gridDim.x * (blockDim.x >> 5)) {
+constexpr int EF_THREADS = 256, EF_BATCH = 16;
+
+// (s, c) += v: Neumaier compensated sum in FP32 (the pair s + c carries the
+// sum to about twice FP32 precision)
+__device__ __forceinline__ void neumaier_add_f(float &s, float &c, float v) {
+    const float t = s + v;
+    c += fabsf(s) >= fabsf(v) ? (s - t) + v : (v - t) + s;
+    s = t;
+}
+
+// T = double: FP64 partials, FP64 compensated sums.  T = float: the partials
+// (FP32 values widened exactly, one per chunk and consumer warp; or doubles
+// from the plane kernel, split into FP32 pairs) are summed as compensated
+// FP32 pairs on the FP32 pipe (GB300's FP64 pipe runs at 1/64 of the FP32
+// rate) and widened on the integer pipe at the end.
+template <typename T>
+__global__ void __launch_bounds__(EF_THREADS) k_efinish(const SysDev *__restrict__ sys, int nsys) {
+    // one block per system: each thread sums a strided share of the partials,
+    // then the (sum, compensation) pairs meet in a fixed tree (shuffles within
+    // warps, then across warps): the same order on every run
+    __shared__ T rs[EF_THREADS / 32], rc[EF_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int si = blockIdx.x; si < nsys; si += gridDim.x) {
         const SysDev &S = sys[si];
         const int n = S.nepart;
-        double s = 0.0, c = 0.0;
-        for (int i = lane; i < n; i += 32) neumaier_add(s, c, S.epart[i]);
+        const double *ep = S.epart;
+        T s = 0, c = 0;
+        // batches of EF_BATCH strided loads in flight, then their sums in order
+        for (int i0 = threadIdx.x; i0 < n; i0 += EF_THREADS * EF_BATCH) {
+            double v[EF_BATCH];
+#pragma unroll
+            for (int u = 0; u < EF_BATCH; ++u) {
+                const int i = i0 + u * EF_THREADS;
+                v[u] = i < n ? ep[i] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < EF_BATCH; ++u) {
+                if constexpr (sizeof(T) == 8) {
+                    neumaier_add(s, c, v[u]);
+                } else {
+                    const dfl d = df_from_bits(v[u]);   // lo = 0 for widened FP32 partials
+                    neumaier_add_f(s, c, d.hi);
+                    c += d.lo;
+                }
+            }
+        }
         for (int o = 16; o > 0; o >>= 1) {
-            const double s2 = __shfl_down_sync(0xffffffffu, s, o);
-            const double c2 = __shfl_down_sync(0xffffffffu, c, o);
-            neumaier_add(s, c, s2);
+            const T s2 = __shfl_down_sync(0xffffffffu, s, o);
+            const T c2 = __shfl_down_sync(0xffffffffu, c, o);
+            if constexpr (sizeof(T) == 8) neumaier_add(s, c, s2);
+            else neumaier_add_f(s, c, s2);
             c += c2;
         }
-        if (lane == 0) *S.energy = S.escale * (s + c);
+        if (lane == 0) {
+            rs[w] = s;
+            rc[w] = c;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            T ts = rs[0], tc = rc[0];
+            for (int k = 1; k < EF_THREADS / 32; ++k) {
+                if constexpr (sizeof(T) == 8) neumaier_add(ts, tc, rs[k]);
+                else neumaier_add_f(ts, tc, rs[k]);
+                tc += rc[k];
+            }
+            if constexpr (sizeof(T) == 8) *S.energy = S.escale * (ts + tc);
+            else *S.energy = S.escale * (f2d_bits(ts) + f2d_bits(tc));
+        }
+        __syncthreads();
     }
 }
 
@@ -1551,7 +1595,7 @@ static cudaError_t launch_stage_t(const LaunchSet &ls, int stage, cudaStream_t s
                                                             ls.bufelems[3], ls.recelems, ls.abelems, ls.err);
             break;
         default:
-            k_efinish<<<(ls.nsys + 3) / 4 < 1024 ? (ls.nsys + 3) / 4 : 1024, 128, 0, st>>>(ls.sys, ls.nsys);
+            k_efinish<T><<<ls.nsys < 1024 ? ls.nsys : 1024, EF_THREADS, 0, st>>>(ls.sys, ls.nsys);
             break;
     }
     return cudaGetLastError();

@@ -19,6 +19,7 @@
 // five (y, x, contraction, x, y passes).
 #include "common.cuh"
 #include "fftreg.cuh"
+#include "contract.cuh"
 #include "pipeline.h"
 #include "tma.cuh"
 
@@ -143,41 +144,13 @@ __device__ __noinline__ double contract_plane(cx<float> *buf, const unsigned sho
         const int j = (int)xk;
         const float tt = xk - (float)j;
         float4 *v4 = reinterpret_cast<float4 *>(buf + (size_t)li * NQ);
-        cx<float> th[NQ], F[NQ];
+        f2_t th[NQ], F[NQ];
+        load_rec_f2(v4, th);
 #pragma unroll
-        for (int a = 0; a < NQ / 2; ++a) {
-            const float4 q = v4[a];
-            th[2 * a] = cx<float>{q.x, q.y};
-            th[2 * a + 1] = cx<float>{q.z, q.w};
-        }
-#pragma unroll
-        for (int a = 0; a < NQ; ++a) F[a] = cx<float>{0.f, 0.f};
-        if (j < NK - 1) {
-            const float4 *row = tab + (size_t)j * NPAIR;
-            int pidx = 0;
-#pragma unroll
-            for (int a = 0; a < NQ; ++a) {
-#pragma unroll
-                for (int b = a; b < NQ; ++b) {
-                    const float4 cf = __ldg(row + pidx);
-                    const float phi = cf.x + tt * (cf.y + tt * (cf.z + tt * cf.w));
-                    F[a].x += phi * th[b].x;
-                    F[a].y += phi * th[b].y;
-                    if (b != a) {
-                        F[b].x += phi * th[a].x;
-                        F[b].y += phi * th[a].y;
-                    }
-                    ++pidx;
-                }
-            }
-        }
-        float e = 0.f;
-#pragma unroll
-        for (int a = 0; a < NQ; ++a) e += th[a].x * F[a].x + th[a].y * F[a].y;
-        eacc += (double)e;
-#pragma unroll
-        for (int a = 0; a < NQ / 2; ++a)
-            v4[a] = make_float4(F[2 * a].x, F[2 * a].y, F[2 * a + 1].x, F[2 * a + 1].y);
+        for (int a = 0; a < NQ; ++a) F[a] = 0ull;
+        if (j < NK - 1) contract_row<true>(tab + (size_t)j * NPAIR, tt, th, F);
+        eacc += (double)energy_f2(th, F);
+        store_rec_f2(v4, F);
     }
     return eacc;
 }

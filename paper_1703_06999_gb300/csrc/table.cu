@@ -254,9 +254,18 @@ __global__ void k_kspline(const double *__restrict__ phik, double *__restrict__ 
         const double c3 = h26 * (s1 - s0);
         const size_t o = (size_t)j * NPAIR + pair;     // [interval][pair]
         cub64[o] = make_dvec4(c0, c1, c2, c3);
-        cub32[o] = make_float4((float)c0, (float)c1, (float)c2, (float)c3);
         lin64[o] = make_dvec4(y[j], y[j + 1] - y[j], 0.0, 0.0);
-        lin32[o] = make_float4((float)y[j], (float)(y[j + 1] - y[j]), 0.f, 0.f);
+        // FP32: pairs 2m, 2m + 1 interleaved as {c0, c0', c1, c1'} {c2, c2', c3, c3'}
+        const size_t f = (size_t)j * NPAIR * 4 + (size_t)(pair >> 1) * 8 + (pair & 1);
+        float *c32 = reinterpret_cast<float *>(cub32), *l32 = reinterpret_cast<float *>(lin32);
+        c32[f] = (float)c0;
+        c32[f + 2] = (float)c1;
+        c32[f + 4] = (float)c2;
+        c32[f + 6] = (float)c3;
+        l32[f] = (float)y[j];
+        l32[f + 2] = (float)(y[j + 1] - y[j]);
+        l32[f + 4] = 0.f;
+        l32[f + 6] = 0.f;
     }
 }
 
