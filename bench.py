@@ -146,6 +146,21 @@ def stage_bytes(shape, prec_bytes):
     }
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch and per
+# 96^3 dimer system, from one full ncu capture of the current kernels on two
+# such systems (profiles/fp32_kernels_dimer96_batch2.md); a launch over nb
+# systems moves nb times this.  Clear an entry when its kernel changes.
+MEASURED_TRAFFIC_PER_SYSTEM = {
+    "zfwd": (28.770048e6 + 113.816832e6) / 2,
+    "yfwd": (144.588544e6 + 84.737792e6) / 2,
+    "xfwd": (144.602880e6 + 84.997632e6) / 2,
+    "contract": (149.682176e6 + 94.388224e6) / 2,
+    "xinv": (144.595200e6 + 84.561920e6) / 2,
+    "yinv": (144.596480e6 + 84.507648e6) / 2,
+    "zinv": (173.128960e6 + 18.168832e6) / 2,
+}
+
+
 def run_reference(args, rank):
     """The oracle (FP64 CPU, test infrastructure) timed on the host cores on a
     bounded sample of the workload: one 48^3 grid of the same dimer density
@@ -402,10 +417,12 @@ def main():
             sb[k] += v
     pk, pk_kind = peaks()
     achieved = sb[names[dom]] / (per_launch_ms[dom] / 1000.0) / 1e9
-    traffic = None
+    tps = MEASURED_TRAFFIC_PER_SYSTEM.get(names[dom]) if tuple(SHAPE) == (96, 96, 96) else None
+    traffic = tps * nb if tps is not None else None
     roof = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": pk["hbm_gbs"],
             "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
             "peak_source": pk_kind,
+            "traffic_source": "ncu capture on 2 systems, scaled per system" if traffic is not None else None,
             "stages": {n: {"ms_per_launch": float(m), "alg_bytes": int(sb[n]),
                            "GBps": (sb[n] / (m / 1000.0) / 1e9) if m > 0 else None}
                        for n, m in zip(names, per_launch_ms)}}
