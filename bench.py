@@ -8,6 +8,12 @@ One step = the whole hot path (q0/theta, forward FFTs, kernel contraction and
 energy, inverse FFTs, potential) over the batch, one launch per stage.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload dimer96_batch8|cubic24|shell192|uneven64]
+
+The other workloads (the small 24^3 case, one 192^3 ligand-shell-like system,
+a batch of 64 uneven grids) measure the same quantities for the record; they
+skip the serving stream, and the CPU baseline runs only on the default and
+the 24^3 workload.
 
 N > 1: run under torch.distributed.run; each rank evaluates its own batch
 (independent systems, no data-path collective), weak scaling.
@@ -39,6 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "cubic24", "shell192", "uneven64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-stream measurement")
     ap.add_argument("--only-timed", action="store_true",
@@ -274,6 +281,18 @@ def cpu_baseline():
             "sample": "one 96^3 dimer system (seed 0, vdW-DF1), %.1f s" % dt}
 
 
+def cpu_baseline_small(s):
+    """Oracle (as it stands) on the whole (small) workload system, on the host."""
+    from oracle import vdw
+    o = vdw.Oracle()
+    n, sg = s.n.cpu().numpy(), s.sigma.cpu().numpy()
+    t0 = time.perf_counter()
+    o.energy_potential(n, sg, s.cell, s.functional)
+    dt = time.perf_counter() - t0
+    return {"value": s.npts / dt, "unit": "grid pts/s", "cores": 1, "kind": "oracle",
+            "sample": "the whole %s system, %.2f s" % ("x".join(map(str, s.shape)), dt)}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -292,10 +311,23 @@ def main():
     B.lib()   # fails loudly if the CUDA library is missing
     B.vdwgb_set_autotune(True)   # tile shapes measured once per grid at init (outside the timed region)
 
-    nb = args.batch
-    seeds = rank_seeds(rank, nb)
-    systems = [inputs.dimer(seeds[i], shape=SHAPE, cell_lengths=CELL, functional=1 + i % 2,
-                            device=dev) for i in range(nb)]
+    default = args.workload == WORKLOAD
+    if default:
+        nb = args.batch
+        seeds = rank_seeds(rank, nb)
+        systems = [inputs.dimer(seeds[i], shape=SHAPE, cell_lengths=CELL, functional=1 + i % 2,
+                                device=dev) for i in range(nb)]
+    elif args.workload == "cubic24":
+        systems = [inputs.small_cubic(rank, ngrid=24, device=dev)]
+    elif args.workload == "shell192":
+        systems = [inputs.ligand_shell(rank, device=dev)]
+    else:
+        systems = inputs.uneven_batch(rank, count=64, device=dev)
+    if not default:
+        nb = len(systems)
+        args.no_serve = True
+        if args.workload != "cubic24":
+            args.no_cpu_baseline = True
     pts = sum(s.npts for s in systems)
 
     def make(prec):
@@ -417,7 +449,7 @@ def main():
             sb[k] += v
     pk, pk_kind = peaks()
     achieved = sb[names[dom]] / (per_launch_ms[dom] / 1000.0) / 1e9
-    tps = MEASURED_TRAFFIC_PER_SYSTEM.get(names[dom]) if tuple(SHAPE) == (96, 96, 96) else None
+    tps = MEASURED_TRAFFIC_PER_SYSTEM.get(names[dom]) if default else None
     traffic = tps * nb if tps is not None else None
     roof = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": pk["hbm_gbs"],
             "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
@@ -439,11 +471,14 @@ def main():
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32-mixed (f64 q0 and energy sum)",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": list(SHAPE), "cell_bohr": list(CELL), "systems": nb,
-                       "functionals": "DF1+DF2", "precision": "fp32_mixed", "parallelism": "replicas",
-                       "plan": plan_info,
+            "config": {"workload": args.workload,
+                       "grid": list(SHAPE) if default else sorted({tuple(s.shape) for s in systems}),
+                       "cell_bohr": list(CELL) if default else None, "systems": nb,
+                       "functionals": sorted({int(s.functional) for s in systems}), "precision": "fp32_mixed",
+                       "parallelism": "replicas", "plan": plan_info,
                        "l2": "flushed between timed steps (256 MB write); working set %.0f MB"
-                             % (nb * (SHAPE[0] * SHAPE[1] * (SHAPE[2] // 2 + 1) * 160 + 48 * np.prod(SHAPE)) / 1e6)},
+                             % (sum(s.shape[0] * s.shape[1] * (s.shape[2] // 2 + 1) * 160 + 48 * s.npts
+                                    for s in systems) / 1e6)},
             "fp64_plain": {"value": fp64_value, "unit": "grid pts/s", "steps": k64,
                            "ms_per_step": t64 / k64, "form": "one system at a time"},
             "speedup_fp32_batched_vs_fp64_plain": value / (fp64_value * world),
@@ -463,7 +498,7 @@ def main():
         if serving is not None:
             out["serving"] = serving
         if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline()
+            out["cpu_baseline"] = cpu_baseline() if default else cpu_baseline_small(systems[0])
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
