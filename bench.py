@@ -161,7 +161,6 @@ MEASURED_TRAFFIC_PER_SYSTEM = {
     "zfwd": (28.770048e6 + 113.816832e6) / 2,
     "yfwd": (144.588544e6 + 84.737792e6) / 2,
     "xfwd": (144.602880e6 + 84.997632e6) / 2,
-    "contract": (149.682176e6 + 94.388224e6) / 2,
     "xinv": (144.595200e6 + 84.561920e6) / 2,
     "yinv": (144.596480e6 + 84.507648e6) / 2,
     "zinv": (173.128960e6 + 18.168832e6) / 2,

@@ -129,9 +129,12 @@ int vdwgb_has_cuda(void);
 size_t vdwgb_footprint_bytes(int nx, int ny, int nz, int precision);
 
 /* 0, or VDWGB_ETIMEDOUT if a kernel on `device` gave up a bounded wait for
- * its staged data since the last call (its results are then invalid); the
- * flag is cleared.  The host-array calls check it themselves; callers of the
- * device-pointer calls check it after synchronising. */
+ * its staged data since the last call, or VDWGB_ECUDA if the FP32
+ * contraction met a k-point outside the table rows staged for its chunk (an
+ * internal invariant: host and device sort k-points with the same FP32
+ * arithmetic); the results are then invalid.  The flag is cleared.  The
+ * host-array calls check it themselves; callers of the device-pointer calls
+ * check it after synchronising. */
 int vdwgb_device_status(int device);
 
 /* Number of our kernel launches one evaluation enqueues (stages without

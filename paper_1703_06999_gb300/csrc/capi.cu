@@ -18,6 +18,7 @@
 #include "internal.h"
 #include "table.h"
 #include "fftreg.cuh"
+#include "contract.cuh"
 
 using namespace vdwgb;
 
@@ -215,7 +216,9 @@ static void choose_tiles(int prec, int nx, int ny, int nz, int nzh, size_t lim, 
 // intervals beyond the table form their own group) and cut the order into
 // chunks of at most `chunkmax` k-points spanning at most `maxspan` intervals.
 // chunk = {first index into kidx, count, first interval, intervals (0 beyond)}.
-static void build_chunks(const SysDev &S, int maxspan, int chunkmax, std::vector<unsigned> &kidx,
+// FP32-mixed (f32): intervals from kpoint_interval32, the decision the
+// contraction kernel repeats; FP64: |k| in FP64.
+static void build_chunks(const SysDev &S, bool f32, int maxspan, int chunkmax, std::vector<unsigned> &kidx,
                          std::vector<int4> &chunks) {
     const int nx = S.nx, ny = S.ny, nz = S.nz, nzh = S.nzh;
     const size_t nk = (size_t)nx * ny * nzh;
@@ -234,12 +237,20 @@ static void build_chunks(const SysDev &S, int maxspan, int chunkmax, std::vector
             for (int kz = 0; kz < nzh; ++kz) {
                 const bool qz = (nz % 2 == 0) && (kz == nz / 2);
                 const int mz = qz ? -kz : kz;
-                const double cx = qx ? 0.0 : mx, cy = qy ? 0.0 : my, cz = qz ? 0.0 : mz;
-                double k2 = S.g[0] * mx * mx + S.g[1] * (double)my * my + S.g[2] * (double)mz * mz +
-                            2.0 * (S.g[3] * cx * cy + S.g[4] * cx * cz + S.g[5] * cy * cz);
-                if (k2 < 0) k2 = 0;
-                long j = (long)(std::sqrt(k2) / dk);
-                if (j > NK - 1) j = NK - 1;
+                long j;
+                if (f32) {
+                    int j32;
+                    float tt;
+                    kpoint_interval32(S.gf, mx, my, mz, qx, qy, qz, j32, tt);
+                    j = j32;
+                } else {
+                    const double cx = qx ? 0.0 : mx, cy = qy ? 0.0 : my, cz = qz ? 0.0 : mz;
+                    double k2 = S.g[0] * mx * mx + S.g[1] * (double)my * my + S.g[2] * (double)mz * mz +
+                                2.0 * (S.g[3] * cx * cy + S.g[4] * cx * cz + S.g[5] * cy * cz);
+                    if (k2 < 0) k2 = 0;
+                    j = (long)(std::sqrt(k2) / dk);
+                    if (j > NK - 1) j = NK - 1;
+                }
                 const size_t idx = ((size_t)px * ny + py) * nzh + kz;
                 bin[idx] = (int)j;
                 ++count[j];
@@ -704,7 +715,7 @@ static int plan(vdwgb_data *h) {
         S.tiles[5] = nzh;
         S.nepart = nzh * C;
     } else {
-        build_chunks(S, maxspan, chunkmax, kidx, chunks);
+        build_chunks(S, prec == VDWGB_FP32_MIXED, maxspan, chunkmax, kidx, chunks);
         S.tiles[4] = (int)chunks.size();
         S.tiles[5] = 0;
         S.nepart = S.tiles[4] * (prec == VDWGB_FP32_MIXED ? C32_CWARPS : 1);   // FP32: one per consumer warp
@@ -934,6 +945,7 @@ int vdwgb_device_status(int device) {
     CK(cudaMemcpy(&v, g_dev[device].err, sizeof(int), cudaMemcpyDeviceToHost), "status");
     if (v) {
         CK(cudaMemset(g_dev[device].err, 0, sizeof(int)), "status");
+        if (v == 2) return fail(VDWGB_ECUDA, "contraction: a k-point's table interval was outside its chunk's rows");
         return fail(VDWGB_ETIMEDOUT, "a kernel's bounded wait for its staged tile ran out");
     }
     return 0;

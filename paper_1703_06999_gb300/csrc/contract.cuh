@@ -19,6 +19,26 @@ namespace vdwgb {
 
 typedef unsigned long long f2_t;   // two FP32 lanes (lo = re, hi = im)
 
+constexpr float INV_DK32 = (float)(RMAX / (2.0 * 3.14159265358979323846));   // 1 / table spacing in |k|
+
+// |k| of the signed frequency (mx, my, mz) with the reciprocal metric gf
+// (|k|^2 = m^T g m; a Nyquist component enters the diagonal but not the cross
+// terms), in FP32, as table interval j (clamped to NK - 1) and offset tt.
+// Every rounding is explicit (standalone products, fused multiply-adds and a
+// correctly rounded square root), so the host's sort of the k-points into
+// intervals and the device's evaluation reach the same j bit for bit.
+__host__ __device__ inline void kpoint_interval32(const float *gf, int mx, int my, int mz, bool nyq_x, bool nyq_y,
+                                                  bool nyq_z, int &j, float &tt) {
+    const float fx = (float)mx, fy = (float)my, fz = (float)mz;
+    const float cx = nyq_x ? 0.f : fx, cy = nyq_y ? 0.f : fy, cz = nyq_z ? 0.f : fz;
+    const float cross = fmaf(gf[3] * cx, cy, fmaf(gf[4] * cx, cz, (gf[5] * cy) * cz));
+    float k2 = fmaf(gf[0] * fx, fx, fmaf(gf[1] * fy, fy, fmaf(gf[2] * fz, fz, 2.f * cross)));
+    k2 = k2 > 0.f ? k2 : 0.f;
+    const float xk = sqrtf(k2) * INV_DK32;
+    j = xk < (float)(NK - 1) ? (int)xk : NK - 1;
+    tt = xk - (float)j;
+}
+
 // the 20 packed theta_a of a record (generic pointer: shared or global)
 __device__ __forceinline__ void load_rec_f2(const float4 *rec, f2_t *v) {
     const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(rec);

@@ -20,6 +20,7 @@
 #include "internal.h"
 #include "table.h"
 #include "fftreg.cuh"
+#include "contract.cuh"
 
 using namespace vdwgb;
 
@@ -99,7 +100,6 @@ int tile_cols(int n, int nzh, int slots) {
 int sort_chunks(const SysDev &S) {
     const int nx = S.nx, ny = S.ny, nz = S.nz, nzh = S.nzh;
     const size_t nk = (size_t)nx * ny * nzh;
-    const double dk = 2.0 * M_PI / RMAX;
     for (int j = 0; j <= NK; ++j) h_start[j] = 0;
     auto fold = [](int i, int n) { return i <= (n - 1) / 2 ? i : i - n; };
     for (int px = 0; px < nx; ++px)
@@ -111,12 +111,9 @@ int sort_chunks(const SysDev &S) {
                 const bool qx = (nx % 2 == 0) && (x == nx / 2), qy = (ny % 2 == 0) && (y == ny / 2);
                 const bool qz = (nz % 2 == 0) && (kz == nz / 2);
                 const int mz = qz ? -kz : kz;
-                const double cx = qx ? 0.0 : mx, cy = qy ? 0.0 : my, cz = qz ? 0.0 : mz;
-                double k2 = S.g[0] * mx * mx + S.g[1] * (double)my * my + S.g[2] * (double)mz * mz +
-                            2.0 * (S.g[3] * cx * cy + S.g[4] * cx * cz + S.g[5] * cy * cz);
-                if (k2 < 0) k2 = 0;
-                long j = (long)(std::sqrt(k2) / dk);
-                if (j > NK - 1) j = NK - 1;
+                int j;                           // the FP32 decision the contraction repeats
+                float tt;
+                kpoint_interval32(S.gf, mx, my, mz, qx, qy, qz, j, tt);
                 const size_t idx = ((size_t)px * ny + py) * nzh + kz;
                 h_bin[idx] = (int)j;
                 ++h_start[j + 1];

@@ -1034,27 +1034,17 @@ __device__ __forceinline__ void c32_produce(const SysDev *__restrict__ sys, cons
 
 // |k| of half-spectrum index idx (positions of the x / y passes mapped to
 // frequencies, Nyquist planes with the convention of the FP64 path) as table
-// interval j and offset tt in [0, 1); weight 1 on the kz = 0 and Nyquist
-// planes, 2 elsewhere (the other half of the spectrum)
-__device__ __forceinline__ void c32_kpoint(const SysDev &S, unsigned idx, float inv_dk, int &j, float &tt,
-                                           float &weight) {
+// interval j and offset tt in [0, 1), exactly as the host sorted it; weight
+// 1 on the kz = 0 and Nyquist planes, 2 elsewhere (the other half of the
+// spectrum)
+__device__ __forceinline__ void c32_kpoint(const SysDev &S, unsigned idx, int &j, float &tt, float &weight) {
     const int nx = S.nx, ny = S.ny, nz = S.nz, nzh = S.nzh;
     const int kz = (int)(idx % (unsigned)nzh);
     const int rest = (int)(idx / (unsigned)nzh);
     const int y = axis_freq(rest % ny, ny, S.sy1), x = axis_freq(rest / ny, nx, S.sx1);
-    const int mx = fold(x, nx), my = fold(y, ny);
-    const bool nyq_x = (nx % 2 == 0) && (x == nx / 2);
-    const bool nyq_y = (ny % 2 == 0) && (y == ny / 2);
     const bool nyq_z = (nz % 2 == 0) && (kz == nz / 2);
-    const int mz = nyq_z ? -kz : kz;
-    const float fx = (float)mx, fy = (float)my, fz = (float)mz;
-    const float cxv = nyq_x ? 0.f : fx, cyv = nyq_y ? 0.f : fy, czv = nyq_z ? 0.f : fz;
-    float k2 = S.gf[0] * fx * fx + S.gf[1] * fy * fy + S.gf[2] * fz * fz +
-               2.f * (S.gf[3] * cxv * cyv + S.gf[4] * cxv * czv + S.gf[5] * cyv * czv);
-    k2 = k2 > 0.f ? k2 : 0.f;
-    const float xk = sqrtf(k2) * inv_dk;
-    j = (int)xk;
-    tt = xk - (float)j;
+    kpoint_interval32(S.gf, fold(x, nx), fold(y, ny), nyq_z ? -kz : kz, (nx % 2 == 0) && (x == nx / 2),
+                      (ny % 2 == 0) && (y == ny / 2), nyq_z, j, tt);
     weight = (kz == 0 || nyq_z) ? 1.f : 2.f;
 }
 
@@ -1108,7 +1098,6 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
     } else {
         const int cw = (threadIdx.x >> 5) - 1;   // consumer warp
         const int lane = threadIdx.x & 31;
-        const float inv_dk = (float)(RMAX / (2.0 * 3.14159265358979323846));
         int i = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
             const int b = i & 1;
@@ -1128,20 +1117,21 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
                 const unsigned idx = m.idx[b * CHUNK32 + k];
                 int j;
                 float tt, w;
-                c32_kpoint(S, idx, inv_dk, j, tt, w);
+                c32_kpoint(S, idx, j, tt, w);
                 f2_t th[NQ], F[NQ];
                 load_rec_f2(m.th + ((size_t)b * CHUNK32 + k) * 10, th);
 #pragma unroll
                 for (int a = 0; a < NQ; ++a) F[a] = 0ull;
+                // the interval's row is staged: the host sorted this k-point into
+                // the chunk with the same FP32 decision (j = NK - 1: beyond the
+                // table).  A row outside the staged range would break that
+                // invariant: skipped and reported (status 2), never read.
                 if (j < NK - 1) {
-                    // the interval's row: staged, else (rounding at a chunk edge) global
-                    // (two copies of the loop, so that the staged one compiles to
-                    // shared-memory loads rather than generic ones)
-                    const int span = min(mt.z, SPAN32);
-                    if (span > 0 && j >= mt.y && j < mt.y + span)
-                        contract_row<false>(m.rows + ((size_t)b * SPAN32 + (j - mt.y)) * NPAIR, tt, th, F);
+                    const int r = j - mt.y;
+                    if (r >= 0 && r < min(mt.z, SPAN32))
+                        contract_row<false>(m.rows + ((size_t)b * SPAN32 + r) * NPAIR, tt, th, F);
                     else
-                        contract_row<true>(tab + (size_t)j * NPAIR, tt, th, F);
+                        atomicExch(err, 2);
                 }
                 eacc = w * energy_f2(th, F);
                 store_rec_f2(reinterpret_cast<float4 *>(S.spec) + (size_t)idx * 10, F);

@@ -105,3 +105,23 @@ def test_set_tiles_rejects_bad_shapes_and_held_handles(table):
         _close(f.calculate(s.n.numpy(), s.sigma.numpy()), ref, 1)
     finally:
         f.close()
+
+
+def test_fp32_interval_decision_random_triclinic_cells(table):
+    """The host sorts k-points into kernel-table intervals with the same FP32
+    arithmetic as the contraction kernel; a disagreement would surface as a
+    VDWGB_ECUDA status from the host-array call.  Random triclinic cells put
+    many |k| near interval boundaries."""
+    rng = np.random.default_rng(1234)
+    for case in range(8):
+        shape = tuple(int(v) for v in rng.choice([12, 15, 16, 18, 20, 24], 3))
+        a = np.diag(rng.uniform(5.0, 9.0, 3)) + np.tril(rng.uniform(-1.5, 1.5, (3, 3)), -1)
+        centre = tuple(a.sum(axis=0) / 2)
+        s = inputs.make_system(shape, a, [(3.0, 1.4, centre)], 1 + case % 2)
+        n, sg = s.n.numpy(), s.sigma.numpy()
+        ref = vdw.Oracle().energy_potential(n, sg, s.cell, s.functional)
+        f = B.Functional(s.shape, s.cell, s.functional, B.FP32_MIXED)
+        try:
+            _close(f.calculate(n, sg), ref, 1)
+        finally:
+            f.close()
