@@ -228,7 +228,12 @@ int vdwgb_batch_calculate_device(vdwgb_batch b, const double *const *d_rho,
 int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double *const *sigma,
                           double *const *dedrho, double *const *dedsigma, double *energy);
 
-/* Kernel launches one evaluation of the batch enqueues. */
+/* Kernel launches one evaluation of the batch enqueues.  A batch of two or
+ * more systems runs as two halves (split by grid points) whose stage chains
+ * are independent branches of the captured graph, so their stages overlap;
+ * each half launches its own stages.  VDWGB_BATCH_SPLIT=0 in the environment
+ * keeps one launch per stage for the whole batch.  Results are the same
+ * either way. */
 int vdwgb_batch_launches(vdwgb_batch b);
 
 /* Stage timing: with timing enabled, each batch evaluation records CUDA

@@ -1157,7 +1157,37 @@ struct vdwgb_batch_s {
     std::vector<std::vector<cudaEvent_t>> spare;
     double *d_energy = nullptr;                        // host-pointer path
     cudaStream_t own = nullptr;
+    // software pipeline of two halves in the graph: systems [0, split) and
+    // [split, n), the second half one stage behind the first (0: one set)
+    int split = 0;
+    LaunchSet half[2];
+    int *dprefix2 = nullptr;
+    cudaStream_t cap2 = nullptr;
+    cudaEvent_t cev[NSTAGE + 2] = {};
 };
+
+// Split point of a batch for the two-half pipeline: the prefix of systems
+// whose grid points come closest to half the total (0: no split).
+static int batch_split_point(vdwgb_data *const *hs, int count) {
+    if (count < 2) return 0;
+    {
+        const char *e = std::getenv("VDWGB_BATCH_SPLIT");
+        if (e && e[0] == '0') return 0;
+    }
+    double total = 0.0;
+    for (int i = 0; i < count; ++i) total += (double)hs[i]->nx * hs[i]->ny * hs[i]->nz;
+    double acc = 0.0, best = 1e300;
+    int h = 1;
+    for (int i = 1; i < count; ++i) {
+        acc += (double)hs[i - 1]->nx * hs[i - 1]->ny * hs[i - 1]->nz;
+        const double d = acc > total / 2 ? acc - total / 2 : total / 2 - acc;
+        if (d < best) {
+            best = d;
+            h = i;
+        }
+    }
+    return h;
+}
 
 }  // extern "C"
 
@@ -1249,9 +1279,27 @@ int vdwgb_batch_new(vdwgb_handle *handles, int count, vdwgb_batch *out) {
         if (e == cudaSuccess) e = cudaMemcpy(b->dsys, b->host.data(), count * sizeof(SysDev), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) rc = cuda_fail(e, "batch setup");
     }
+    const int h = rc == 0 ? batch_split_point(handles, count) : 0;
+    if (h > 0) {
+        // launch sets of the two halves over the same descriptors, own tile prefix sums
+        const size_t na = (size_t)NKIND * (h + 1), nb = (size_t)NKIND * (count - h + 1);
+        std::vector<int> p2(na + nb, 0);
+        e = cudaMalloc(&b->dprefix2, (na + nb) * sizeof(int));
+        if (e != cudaSuccess) rc = cuda_fail(e, "batch setup");
+        if (rc == 0) rc = batch_launchset(handles, h, b->host.data(), p2.data(), b->dsys, b->dprefix2, b->half[0]);
+        if (rc == 0)
+            rc = batch_launchset(handles + h, count - h, b->host.data() + h, p2.data() + na, b->dsys + h,
+                                 b->dprefix2 + na, b->half[1]);
+        if (rc == 0) {
+            e = cudaMemcpy(b->dprefix2, p2.data(), (na + nb) * sizeof(int), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) rc = cuda_fail(e, "batch setup");
+        }
+        if (rc == 0) b->split = h;
+    }
     if (rc) {
         cudaFree(b->dsys);
         cudaFree(b->dprefix);
+        cudaFree(b->dprefix2);
         delete b;
         return rc;
     }
@@ -1304,10 +1352,30 @@ int vdwgb_batch_calculate_device(vdwgb_batch b, const double *const *d_rho, cons
         return 0;
     }
     if (!b->exec) {
-        // capture the stage launches once; replays read the descriptors above
+        // capture the stage launches once; replays read the descriptors above.
+        // Split batch: the two halves' stage chains are independent branches
+        // of the graph, so a compute-bound stage of one half can run beside
+        // a memory-bound stage of the other
         CK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "capture stream");
+        if (b->split) {
+            CK(cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking), "capture stream");
+            for (int k = 0; k < NSTAGE + 2; ++k)
+                CK(cudaEventCreateWithFlags(&b->cev[k], cudaEventDisableTiming), "event");
+        }
         CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
-        cudaError_t le = launch_all(b->ls, b->prec, b->cap);
+        cudaError_t le = cudaSuccess;
+        if (b->split) {
+            le = cudaEventRecord(b->cev[0], b->cap);
+            if (le == cudaSuccess) le = cudaStreamWaitEvent(b->cap2, b->cev[0], 0);
+            for (int k = 0; k < NSTAGE && le == cudaSuccess; ++k) {
+                le = launch_stage(b->half[0], b->prec, k, b->cap);
+                if (le == cudaSuccess) le = launch_stage(b->half[1], b->prec, k, b->cap2);
+            }
+            if (le == cudaSuccess) le = cudaEventRecord(b->cev[NSTAGE + 1], b->cap2);
+            if (le == cudaSuccess) le = cudaStreamWaitEvent(b->cap, b->cev[NSTAGE + 1], 0);
+        } else {
+            le = launch_all(b->ls, b->prec, b->cap);
+        }
         cudaError_t ce = cudaStreamEndCapture(b->cap, &b->graph);
         if (le != cudaSuccess) return cuda_fail(le, "capture launch");
         if (ce != cudaSuccess) return cuda_fail(ce, "end capture");
@@ -1383,6 +1451,7 @@ int vdwgb_batch_stage_ms(vdwgb_batch b, double *ms, int *ncalls) {
 
 int vdwgb_batch_launches(vdwgb_batch b) {
     if (!b) return 0;
+    if (b->split) return count_launches(b->half[0]) + count_launches(b->half[1]);
     return count_launches(b->ls);
 }
 
@@ -1405,8 +1474,12 @@ int vdwgb_batch_free(vdwgb_batch *bp) {
         cudaFree(b->d_energy);
         if (b->graph) cudaGraphDestroy(b->graph);
         if (b->cap) cudaStreamDestroy(b->cap);
+        if (b->cap2) cudaStreamDestroy(b->cap2);
+        for (auto ev : b->cev)
+            if (ev) cudaEventDestroy(ev);
         cudaFree(b->dsys);
         cudaFree(b->dprefix);
+        cudaFree(b->dprefix2);
         delete b;
     }
     *bp = nullptr;

@@ -80,7 +80,9 @@ def test_plane_kernel_in_a_mixed_batch(oracle_default):
         alone = [(float(en[i]), dn[i].cpu().numpy(), ds[i].cpu().numpy()) for i in range(len(fs))]
         bt = B.vdwgb_batch_new([f.h for f in fs])
         try:
-            assert B.vdwgb_batch_launches(bt) == 9
+            # fused and unfused systems together use all nine stage kinds (a
+            # batch split into two halves launches the stages of each half)
+            assert B.vdwgb_batch_launches(bt) >= 9
             en.zero_()
             B.vdwgb_batch_calculate_device(bt, ns, ss, dn, ds, en, stream)
             torch.cuda.synchronize()
