@@ -41,8 +41,10 @@ enum { VDWGB_DF1 = 1, VDWGB_DF2 = 2 };
  *   VDWGB_FP64        every step in FP64 (the paper computes in double
  *                     precision, Sec. 6).
  *   VDWGB_FP32_MIXED  theta fields, FFTs and kernel contraction in FP32;
- *                     q0, saturation and spline coefficients in FP64; the
- *                     energy sum in FP64. */
+ *                     q0 and the saturation in double-float (pairs of FP32,
+ *                     about 46 significant bits: the GPU's FP64 rate is
+ *                     1/64 of its FP32 rate); energy partials summed with
+ *                     compensated (error-free) sums in a fixed order. */
 enum { VDWGB_FP64 = 0, VDWGB_FP32_MIXED = 1 };
 
 /* Kernel interpolation in |k| (Sec. 3, procedure step 3a): the paper
@@ -224,7 +226,10 @@ int vdwgb_batch_calculate_device(vdwgb_batch b, const double *const *d_rho,
                                  double *const *d_dedsigma, double *d_energy, void *cuda_stream);
 /* The same from HOST arrays: copies in through per-handle device staging,
  * evaluates, copies dedrho, dedsigma and the `count` energies back, and waits.
- * Blocking. */
+ * Blocking.  A split batch (see vdwgb_batch_launches) runs each half as its
+ * own copy-in / stages / copy-out chain on its own stream, so one half's
+ * copies overlap the other half's kernels; pinned host arrays let the copies
+ * run asynchronously (pageable ones work, at the speed of staged copies). */
 int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double *const *sigma,
                           double *const *dedrho, double *const *dedsigma, double *energy);
 

@@ -1163,6 +1163,11 @@ struct vdwgb_batch_s {
     LaunchSet half[2];
     int *dprefix2 = nullptr;
     cudaStream_t cap2 = nullptr;
+    cudaStream_t own2 = nullptr;                       // host-pointer path, second half
+    cudaGraph_t hgraph[2] = {nullptr, nullptr};        // host-pointer path: one stage chain per half
+    cudaGraphExec_t hexec[2] = {nullptr, nullptr};
+    double *h_energy = nullptr;                        // pinned staging of the energies (the caller's
+                                                       // array may be pageable: a copy into it would block)
     cudaEvent_t cev[NSTAGE + 2] = {};
 };
 
@@ -1408,8 +1413,76 @@ int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double 
         dsg[i] = d + N;
         odn[i] = d + 2 * N;
         ods[i] = d + 3 * N;
-        CK(cudaMemcpyAsync(d, rho[i], N * sizeof(double), cudaMemcpyHostToDevice, b->own), "copy rho");
-        CK(cudaMemcpyAsync(d + N, sigma[i], N * sizeof(double), cudaMemcpyHostToDevice, b->own), "copy sigma");
+    }
+    if (b->split && !b->timing) {
+        // two halves on two streams: a half's copies in, its stages, its copies
+        // out; the upload of one half overlaps the other half's kernels, and
+        // so does the download
+        if (!b->own2) CK(cudaStreamCreateWithFlags(&b->own2, cudaStreamNonBlocking), "stream");
+        if (!b->h_energy) CK(cudaMallocHost(&b->h_energy, n * sizeof(double)), "pinned energies");
+        for (int hh = 0; hh < 2; ++hh) {
+            if (b->hexec[hh]) continue;
+            // each half's stage chain captured once (replays read the descriptors)
+            CK(cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal), "begin capture");
+            cudaError_t le = cudaSuccess;
+            for (int k = 0; k < NSTAGE && le == cudaSuccess; ++k) le = launch_stage(b->half[hh], b->prec, k, b->own);
+            cudaError_t ce = cudaStreamEndCapture(b->own, &b->hgraph[hh]);
+            if (le != cudaSuccess) return cuda_fail(le, "capture launch");
+            if (ce != cudaSuccess) return cuda_fail(ce, "end capture");
+            CK(cudaGraphInstantiate(&b->hexec[hh], b->hgraph[hh], 0), "instantiate graph");
+        }
+        bool changed = false;
+        for (int i = 0; i < n; ++i) {
+            SysDev &S = b->host[i];
+            if (S.n != dr[i] || S.sigma != dsg[i] || S.dedn != odn[i] || S.dedsigma != ods[i] ||
+                S.energy != b->d_energy + i) {
+                S.n = dr[i];
+                S.sigma = dsg[i];
+                S.dedn = odn[i];
+                S.dedsigma = ods[i];
+                S.energy = b->d_energy + i;
+                changed = true;
+            }
+        }
+        if (changed) {
+            // no evaluation of this batch may still read the descriptors
+            CK(cudaDeviceSynchronize(), "synchronize");
+            CK(cudaMemcpy(b->dsys, b->host.data(), n * sizeof(SysDev), cudaMemcpyHostToDevice), "descriptors");
+            for (auto &p : b->last) p = nullptr;   // the graph path re-uploads its own pointers
+        }
+        for (int hh = 0; hh < 2; ++hh) {
+            cudaStream_t st = hh ? b->own2 : b->own;
+            const int lo = hh ? b->split : 0, hi = hh ? n : b->split;
+            for (int i = lo; i < hi; ++i) {
+                const size_t N = (size_t)b->hs[i]->nx * b->hs[i]->ny * b->hs[i]->nz;
+                CK(cudaMemcpyAsync(const_cast<double *>(dr[i]), rho[i], N * sizeof(double), cudaMemcpyHostToDevice, st),
+                   "copy rho");
+                CK(cudaMemcpyAsync(const_cast<double *>(dsg[i]), sigma[i], N * sizeof(double), cudaMemcpyHostToDevice,
+                                   st),
+                   "copy sigma");
+            }
+            CK(cudaGraphLaunch(b->hexec[hh], st), "graph launch");
+            for (int i = lo; i < hi; ++i) {
+                const size_t N = (size_t)b->hs[i]->nx * b->hs[i]->ny * b->hs[i]->nz;
+                CK(cudaMemcpyAsync(dedrho[i], odn[i], N * sizeof(double), cudaMemcpyDeviceToHost, st), "copy dedrho");
+                CK(cudaMemcpyAsync(dedsigma[i], ods[i], N * sizeof(double), cudaMemcpyDeviceToHost, st),
+                   "copy dedsigma");
+            }
+            CK(cudaMemcpyAsync(b->h_energy + lo, b->d_energy + lo, (hi - lo) * sizeof(double), cudaMemcpyDeviceToHost,
+                               st),
+               "copy energy");
+        }
+        CK(cudaStreamSynchronize(b->own), "synchronize");
+        CK(cudaStreamSynchronize(b->own2), "synchronize");
+        std::memcpy(energy, b->h_energy, n * sizeof(double));
+        return vdwgb_device_status(b->device);
+    }
+    for (int i = 0; i < n; ++i) {
+        const size_t N = (size_t)b->hs[i]->nx * b->hs[i]->ny * b->hs[i]->nz;
+        CK(cudaMemcpyAsync(const_cast<double *>(dr[i]), rho[i], N * sizeof(double), cudaMemcpyHostToDevice, b->own),
+           "copy rho");
+        CK(cudaMemcpyAsync(const_cast<double *>(dsg[i]), sigma[i], N * sizeof(double), cudaMemcpyHostToDevice, b->own),
+           "copy sigma");
     }
     int rc = vdwgb_batch_calculate_device(b, dr.data(), dsg.data(), odn.data(), ods.data(), b->d_energy, b->own);
     if (rc) return rc;
@@ -1471,6 +1544,12 @@ int vdwgb_batch_free(vdwgb_batch *bp) {
         for (auto &v : b->spare)
             for (auto e : v) cudaEventDestroy(e);
         if (b->own) cudaStreamDestroy(b->own);
+        if (b->own2) cudaStreamDestroy(b->own2);
+        if (b->h_energy) cudaFreeHost(b->h_energy);
+        for (int hh = 0; hh < 2; ++hh) {
+            if (b->hexec[hh]) cudaGraphExecDestroy(b->hexec[hh]);
+            if (b->hgraph[hh]) cudaGraphDestroy(b->hgraph[hh]);
+        }
         cudaFree(b->d_energy);
         if (b->graph) cudaGraphDestroy(b->graph);
         if (b->cap) cudaStreamDestroy(b->cap);
