@@ -226,19 +226,20 @@ int vdwgb_batch_calculate_device(vdwgb_batch b, const double *const *d_rho,
                                  double *const *d_dedsigma, double *d_energy, void *cuda_stream);
 /* The same from HOST arrays: copies in through per-handle device staging,
  * evaluates, copies dedrho, dedsigma and the `count` energies back, and waits.
- * Blocking.  A split batch (see vdwgb_batch_launches) runs each half as its
- * own copy-in / stages / copy-out chain on its own stream, so one half's
- * copies overlap the other half's kernels; pinned host arrays let the copies
+ * Blocking.  A split batch (see vdwgb_batch_launches) runs each part as its
+ * own copy-in / stages / copy-out chain on its own stream, so one part's
+ * copies overlap the other parts' kernels; pinned host arrays let the copies
  * run asynchronously (pageable ones work, at the speed of staged copies). */
 int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double *const *sigma,
                           double *const *dedrho, double *const *dedsigma, double *energy);
 
 /* Kernel launches one evaluation of the batch enqueues.  A batch of two or
- * more systems runs as two halves (split by grid points) whose stage chains
- * are independent branches of the captured graph, so their stages overlap;
- * each half launches its own stages.  VDWGB_BATCH_SPLIT=0 in the environment
- * keeps one launch per stage for the whole batch.  Results are the same
- * either way. */
+ * more systems runs as K parts (consecutive systems, split by grid points)
+ * whose stage chains are independent branches of the captured graph, so
+ * their stages overlap; each part launches its own stages.  K comes from
+ * VDWGB_BATCH_SPLIT in the environment when the batch is created (0 or 1:
+ * one launch per stage for the whole batch; 2..4; default 4), capped by the
+ * number of systems.  Results are the same either way. */
 int vdwgb_batch_launches(vdwgb_batch b);
 
 /* Stage timing: with timing enabled, each batch evaluation records CUDA

@@ -1157,41 +1157,49 @@ struct vdwgb_batch_s {
     std::vector<std::vector<cudaEvent_t>> spare;
     double *d_energy = nullptr;                        // host-pointer path
     cudaStream_t own = nullptr;
-    // software pipeline of two halves in the graph: systems [0, split) and
-    // [split, n), the second half one stage behind the first (0: one set)
-    int split = 0;
-    LaunchSet half[2];
+    // the batch as parts (systems [pstart[p], pstart[p + 1])) whose stage
+    // chains are independent branches (nparts = 0: one launch set for all)
+    static constexpr int MAXPARTS = 4;
+    int nparts = 0;
+    int pstart[MAXPARTS + 1] = {};
+    LaunchSet part[MAXPARTS];
     int *dprefix2 = nullptr;
-    cudaStream_t cap2 = nullptr;
-    cudaStream_t own2 = nullptr;                       // host-pointer path, second half
-    cudaGraph_t hgraph[2] = {nullptr, nullptr};        // host-pointer path: one stage chain per half
-    cudaGraphExec_t hexec[2] = {nullptr, nullptr};
+    cudaStream_t capp[MAXPARTS] = {};                  // capture streams of parts 1.. (part 0: cap)
+    cudaStream_t hst[MAXPARTS] = {};                   // host-pointer path streams of parts 1.. (part 0: own)
+    cudaGraph_t hgraph[MAXPARTS] = {};                 // host-pointer path: one stage chain per part
+    cudaGraphExec_t hexec[MAXPARTS] = {};
     double *h_energy = nullptr;                        // pinned staging of the energies (the caller's
                                                        // array may be pageable: a copy into it would block)
-    cudaEvent_t cev[NSTAGE + 2] = {};
+    cudaEvent_t cev[2 * MAXPARTS] = {};
 };
 
-// Split point of a batch for the two-half pipeline: the prefix of systems
-// whose grid points come closest to half the total (0: no split).
-static int batch_split_point(vdwgb_data *const *hs, int count) {
-    if (count < 2) return 0;
+// Parts of a batch: K = VDWGB_BATCH_SPLIT (0 or 1: none; 2..4; default 4:
+// measured on 8 x 96^3 systems, the kernels alone run alike with 2-4 parts,
+// and 4 parts leave the least copy time exposed in the host-array call)
+// capped by the system count; boundary p at the system prefix whose grid
+// points come closest to p/K of the total (boundaries strictly increasing).
+// Returns the number of parts (0: no split) and fills start[0..parts].
+static int batch_parts(vdwgb_data *const *hs, int count, int *start) {
+    int K = vdwgb_batch_s::MAXPARTS;
     {
         const char *e = std::getenv("VDWGB_BATCH_SPLIT");
-        if (e && e[0] == '0') return 0;
+        if (e && e[0] >= '0' && e[0] <= '9') K = e[0] - '0';
     }
-    double total = 0.0;
-    for (int i = 0; i < count; ++i) total += (double)hs[i]->nx * hs[i]->ny * hs[i]->nz;
-    double acc = 0.0, best = 1e300;
-    int h = 1;
-    for (int i = 1; i < count; ++i) {
-        acc += (double)hs[i - 1]->nx * hs[i - 1]->ny * hs[i - 1]->nz;
-        const double d = acc > total / 2 ? acc - total / 2 : total / 2 - acc;
-        if (d < best) {
-            best = d;
-            h = i;
-        }
+    if (K > vdwgb_batch_s::MAXPARTS) K = vdwgb_batch_s::MAXPARTS;
+    if (K > count) K = count;
+    if (K < 2) return 0;
+    std::vector<double> acc(count + 1, 0.0);
+    for (int i = 0; i < count; ++i) acc[i + 1] = acc[i] + (double)hs[i]->nx * hs[i]->ny * hs[i]->nz;
+    start[0] = 0;
+    for (int p = 1; p < K; ++p) {
+        const double target = acc[count] * p / K;
+        int best = start[p - 1] + 1;
+        for (int i = best; i <= count - (K - p); ++i)
+            if (std::fabs(acc[i] - target) < std::fabs(acc[best] - target)) best = i;
+        start[p] = best;
     }
-    return h;
+    start[K] = count;
+    return K;
 }
 
 }  // extern "C"
@@ -1284,22 +1292,27 @@ int vdwgb_batch_new(vdwgb_handle *handles, int count, vdwgb_batch *out) {
         if (e == cudaSuccess) e = cudaMemcpy(b->dsys, b->host.data(), count * sizeof(SysDev), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) rc = cuda_fail(e, "batch setup");
     }
-    const int h = rc == 0 ? batch_split_point(handles, count) : 0;
-    if (h > 0) {
-        // launch sets of the two halves over the same descriptors, own tile prefix sums
-        const size_t na = (size_t)NKIND * (h + 1), nb = (size_t)NKIND * (count - h + 1);
-        std::vector<int> p2(na + nb, 0);
-        e = cudaMalloc(&b->dprefix2, (na + nb) * sizeof(int));
+    int ps[vdwgb_batch_s::MAXPARTS + 1];
+    const int np = rc == 0 ? batch_parts(handles, count, ps) : 0;
+    if (np > 0) {
+        // launch sets of the parts over the same descriptors, own tile prefix sums
+        size_t off[vdwgb_batch_s::MAXPARTS + 1];
+        off[0] = 0;
+        for (int p = 0; p < np; ++p) off[p + 1] = off[p] + (size_t)NKIND * (ps[p + 1] - ps[p] + 1);
+        std::vector<int> p2(off[np], 0);
+        e = cudaMalloc(&b->dprefix2, off[np] * sizeof(int));
         if (e != cudaSuccess) rc = cuda_fail(e, "batch setup");
-        if (rc == 0) rc = batch_launchset(handles, h, b->host.data(), p2.data(), b->dsys, b->dprefix2, b->half[0]);
-        if (rc == 0)
-            rc = batch_launchset(handles + h, count - h, b->host.data() + h, p2.data() + na, b->dsys + h,
-                                 b->dprefix2 + na, b->half[1]);
+        for (int p = 0; p < np && rc == 0; ++p)
+            rc = batch_launchset(handles + ps[p], ps[p + 1] - ps[p], b->host.data() + ps[p], p2.data() + off[p],
+                                 b->dsys + ps[p], b->dprefix2 + off[p], b->part[p]);
         if (rc == 0) {
-            e = cudaMemcpy(b->dprefix2, p2.data(), (na + nb) * sizeof(int), cudaMemcpyHostToDevice);
+            e = cudaMemcpy(b->dprefix2, p2.data(), off[np] * sizeof(int), cudaMemcpyHostToDevice);
             if (e != cudaSuccess) rc = cuda_fail(e, "batch setup");
         }
-        if (rc == 0) b->split = h;
+        if (rc == 0) {
+            b->nparts = np;
+            for (int p = 0; p <= np; ++p) b->pstart[p] = ps[p];
+        }
     }
     if (rc) {
         cudaFree(b->dsys);
@@ -1358,26 +1371,31 @@ int vdwgb_batch_calculate_device(vdwgb_batch b, const double *const *d_rho, cons
     }
     if (!b->exec) {
         // capture the stage launches once; replays read the descriptors above.
-        // Split batch: the two halves' stage chains are independent branches
-        // of the graph, so a compute-bound stage of one half can run beside
-        // a memory-bound stage of the other
+        // Split batch: the parts' stage chains are independent branches of
+        // the graph, so a compute-bound stage of one part can run beside a
+        // memory-bound stage of another
         CK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "capture stream");
-        if (b->split) {
-            CK(cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking), "capture stream");
-            for (int k = 0; k < NSTAGE + 2; ++k)
-                CK(cudaEventCreateWithFlags(&b->cev[k], cudaEventDisableTiming), "event");
+        const int np = b->nparts;
+        for (int p = 1; p < np; ++p) {
+            CK(cudaStreamCreateWithFlags(&b->capp[p], cudaStreamNonBlocking), "capture stream");
+            CK(cudaEventCreateWithFlags(&b->cev[2 * p], cudaEventDisableTiming), "event");
+            CK(cudaEventCreateWithFlags(&b->cev[2 * p + 1], cudaEventDisableTiming), "event");
         }
         CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
         cudaError_t le = cudaSuccess;
-        if (b->split) {
-            le = cudaEventRecord(b->cev[0], b->cap);
-            if (le == cudaSuccess) le = cudaStreamWaitEvent(b->cap2, b->cev[0], 0);
-            for (int k = 0; k < NSTAGE && le == cudaSuccess; ++k) {
-                le = launch_stage(b->half[0], b->prec, k, b->cap);
-                if (le == cudaSuccess) le = launch_stage(b->half[1], b->prec, k, b->cap2);
+        if (np) {
+            // fork: parts 1.. branch off the capture stream, join at the end
+            for (int p = 1; p < np && le == cudaSuccess; ++p) {
+                le = cudaEventRecord(b->cev[2 * p], b->cap);
+                if (le == cudaSuccess) le = cudaStreamWaitEvent(b->capp[p], b->cev[2 * p], 0);
             }
-            if (le == cudaSuccess) le = cudaEventRecord(b->cev[NSTAGE + 1], b->cap2);
-            if (le == cudaSuccess) le = cudaStreamWaitEvent(b->cap, b->cev[NSTAGE + 1], 0);
+            for (int k = 0; k < NSTAGE && le == cudaSuccess; ++k)
+                for (int p = 0; p < np && le == cudaSuccess; ++p)
+                    le = launch_stage(b->part[p], b->prec, k, p ? b->capp[p] : b->cap);
+            for (int p = 1; p < np && le == cudaSuccess; ++p) {
+                le = cudaEventRecord(b->cev[2 * p + 1], b->capp[p]);
+                if (le == cudaSuccess) le = cudaStreamWaitEvent(b->cap, b->cev[2 * p + 1], 0);
+            }
         } else {
             le = launch_all(b->ls, b->prec, b->cap);
         }
@@ -1414,22 +1432,23 @@ int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double 
         odn[i] = d + 2 * N;
         ods[i] = d + 3 * N;
     }
-    if (b->split && !b->timing) {
-        // two halves on two streams: a half's copies in, its stages, its copies
-        // out; the upload of one half overlaps the other half's kernels, and
-        // so does the download
-        if (!b->own2) CK(cudaStreamCreateWithFlags(&b->own2, cudaStreamNonBlocking), "stream");
+    if (b->nparts && !b->timing) {
+        // each part on its own stream: its copies in, its stage graph, its
+        // copies out; the copies of one part overlap the kernels of the others
+        const int np = b->nparts;
+        for (int p = 1; p < np; ++p)
+            if (!b->hst[p]) CK(cudaStreamCreateWithFlags(&b->hst[p], cudaStreamNonBlocking), "stream");
         if (!b->h_energy) CK(cudaMallocHost(&b->h_energy, n * sizeof(double)), "pinned energies");
-        for (int hh = 0; hh < 2; ++hh) {
-            if (b->hexec[hh]) continue;
-            // each half's stage chain captured once (replays read the descriptors)
+        for (int p = 0; p < np; ++p) {
+            if (b->hexec[p]) continue;
+            // each part's stage chain captured once (replays read the descriptors)
             CK(cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal), "begin capture");
             cudaError_t le = cudaSuccess;
-            for (int k = 0; k < NSTAGE && le == cudaSuccess; ++k) le = launch_stage(b->half[hh], b->prec, k, b->own);
-            cudaError_t ce = cudaStreamEndCapture(b->own, &b->hgraph[hh]);
+            for (int k = 0; k < NSTAGE && le == cudaSuccess; ++k) le = launch_stage(b->part[p], b->prec, k, b->own);
+            cudaError_t ce = cudaStreamEndCapture(b->own, &b->hgraph[p]);
             if (le != cudaSuccess) return cuda_fail(le, "capture launch");
             if (ce != cudaSuccess) return cuda_fail(ce, "end capture");
-            CK(cudaGraphInstantiate(&b->hexec[hh], b->hgraph[hh], 0), "instantiate graph");
+            CK(cudaGraphInstantiate(&b->hexec[p], b->hgraph[p], 0), "instantiate graph");
         }
         bool changed = false;
         for (int i = 0; i < n; ++i) {
@@ -1448,11 +1467,11 @@ int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double 
             // no evaluation of this batch may still read the descriptors
             CK(cudaDeviceSynchronize(), "synchronize");
             CK(cudaMemcpy(b->dsys, b->host.data(), n * sizeof(SysDev), cudaMemcpyHostToDevice), "descriptors");
-            for (auto &p : b->last) p = nullptr;   // the graph path re-uploads its own pointers
+            for (auto &q : b->last) q = nullptr;   // the graph path re-uploads its own pointers
         }
-        for (int hh = 0; hh < 2; ++hh) {
-            cudaStream_t st = hh ? b->own2 : b->own;
-            const int lo = hh ? b->split : 0, hi = hh ? n : b->split;
+        for (int p = 0; p < np; ++p) {
+            cudaStream_t st = p ? b->hst[p] : b->own;
+            const int lo = b->pstart[p], hi = b->pstart[p + 1];
             for (int i = lo; i < hi; ++i) {
                 const size_t N = (size_t)b->hs[i]->nx * b->hs[i]->ny * b->hs[i]->nz;
                 CK(cudaMemcpyAsync(const_cast<double *>(dr[i]), rho[i], N * sizeof(double), cudaMemcpyHostToDevice, st),
@@ -1461,7 +1480,7 @@ int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double 
                                    st),
                    "copy sigma");
             }
-            CK(cudaGraphLaunch(b->hexec[hh], st), "graph launch");
+            CK(cudaGraphLaunch(b->hexec[p], st), "graph launch");
             for (int i = lo; i < hi; ++i) {
                 const size_t N = (size_t)b->hs[i]->nx * b->hs[i]->ny * b->hs[i]->nz;
                 CK(cudaMemcpyAsync(dedrho[i], odn[i], N * sizeof(double), cudaMemcpyDeviceToHost, st), "copy dedrho");
@@ -1472,8 +1491,7 @@ int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double 
                                st),
                "copy energy");
         }
-        CK(cudaStreamSynchronize(b->own), "synchronize");
-        CK(cudaStreamSynchronize(b->own2), "synchronize");
+        for (int p = 0; p < np; ++p) CK(cudaStreamSynchronize(p ? b->hst[p] : b->own), "synchronize");
         std::memcpy(energy, b->h_energy, n * sizeof(double));
         return vdwgb_device_status(b->device);
     }
@@ -1524,7 +1542,11 @@ int vdwgb_batch_stage_ms(vdwgb_batch b, double *ms, int *ncalls) {
 
 int vdwgb_batch_launches(vdwgb_batch b) {
     if (!b) return 0;
-    if (b->split) return count_launches(b->half[0]) + count_launches(b->half[1]);
+    if (b->nparts) {
+        int total = 0;
+        for (int p = 0; p < b->nparts; ++p) total += count_launches(b->part[p]);
+        return total;
+    }
     return count_launches(b->ls);
 }
 
@@ -1544,16 +1566,16 @@ int vdwgb_batch_free(vdwgb_batch *bp) {
         for (auto &v : b->spare)
             for (auto e : v) cudaEventDestroy(e);
         if (b->own) cudaStreamDestroy(b->own);
-        if (b->own2) cudaStreamDestroy(b->own2);
         if (b->h_energy) cudaFreeHost(b->h_energy);
-        for (int hh = 0; hh < 2; ++hh) {
-            if (b->hexec[hh]) cudaGraphExecDestroy(b->hexec[hh]);
-            if (b->hgraph[hh]) cudaGraphDestroy(b->hgraph[hh]);
+        for (int p = 0; p < vdwgb_batch_s::MAXPARTS; ++p) {
+            if (b->hst[p]) cudaStreamDestroy(b->hst[p]);
+            if (b->capp[p]) cudaStreamDestroy(b->capp[p]);
+            if (b->hexec[p]) cudaGraphExecDestroy(b->hexec[p]);
+            if (b->hgraph[p]) cudaGraphDestroy(b->hgraph[p]);
         }
         cudaFree(b->d_energy);
         if (b->graph) cudaGraphDestroy(b->graph);
         if (b->cap) cudaStreamDestroy(b->cap);
-        if (b->cap2) cudaStreamDestroy(b->cap2);
         for (auto ev : b->cev)
             if (ev) cudaEventDestroy(ev);
         cudaFree(b->dsys);

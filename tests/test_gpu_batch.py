@@ -1,11 +1,11 @@
 """GPU: the batch calls against single evaluations, bit for bit.
 
 A system's arithmetic does not depend on the systems beside it, so the
-host-array batch call (vdwgb_batch_calculate, two halves pipelined on two
-streams), the device-pointer call (captured graph, two independent halves)
+host-array batch call (vdwgb_batch_calculate, parts pipelined on their own
+streams), the device-pointer call (captured graph, independent parts)
 and the unsplit batch (VDWGB_BATCH_SPLIT=0) must all reproduce each system's
 single evaluation exactly, in both precisions, on repeated calls and when
-the two paths alternate on one batch."""
+the two paths alternate on one batch; with 2 and 4 parts."""
 import os
 
 import numpy as np
@@ -30,7 +30,7 @@ def table():
     return B.vdwgb_kernel_table(0)
 
 
-@pytest.mark.parametrize("split", ["1", "0"])
+@pytest.mark.parametrize("split", ["2", "4", "0"])
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
 def test_batch_paths_match_single_evaluations(table, prec, split):
     import torch
@@ -70,7 +70,7 @@ def test_batch_paths_match_single_evaluations(table, prec, split):
         e = B.vdwgb_batch_calculate(bt, hn, hs, hdn, hds)
         assert all(e[i] == alone[i][0] for i in range(len(fs)))
         assert all(np.array_equal(hdn[i], alone[i][1]) for i in range(len(fs)))
-        assert B.vdwgb_batch_launches(bt) == (16 if split == "1" else 8)
+        assert B.vdwgb_batch_launches(bt) == 8 * max(int(split), 1)
     finally:
         if bt is not None:
             B.vdwgb_batch_free(bt)

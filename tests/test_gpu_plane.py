@@ -81,7 +81,7 @@ def test_plane_kernel_in_a_mixed_batch(oracle_default):
         bt = B.vdwgb_batch_new([f.h for f in fs])
         try:
             # fused and unfused systems together use all nine stage kinds (a
-            # batch split into two halves launches the stages of each half)
+            # batch split into parts launches the stages of each part)
             assert B.vdwgb_batch_launches(bt) >= 9
             en.zero_()
             B.vdwgb_batch_calculate_device(bt, ns, ss, dn, ds, en, stream)
