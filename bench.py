@@ -158,7 +158,6 @@ def stage_bytes(shape, prec_bytes):
 # such systems (profiles/fp32_kernels_dimer96_batch2.md); a launch over nb
 # systems moves nb times this.  Clear an entry when its kernel changes.
 MEASURED_TRAFFIC_PER_SYSTEM = {
-    "zfwd": (28.770048e6 + 113.816832e6) / 2,
     "yfwd": (144.588544e6 + 84.737792e6) / 2,
     "xfwd": (144.602880e6 + 84.997632e6) / 2,
     "xinv": (144.595200e6 + 84.561920e6) / 2,

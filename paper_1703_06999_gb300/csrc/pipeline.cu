@@ -436,10 +436,43 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zfwd(const SysD
             // points i = li * nz + z, walked without division
             const int dz = nt % nz, dli = nt / nz;
             int z = threadIdx.x % nz, li = threadIdx.x / nz;
+            {
+                // the next tile's n and sigma lines into L2 while this tile runs
+                const int tn = t + gridDim.x;
+                if (tn < total && tn < tbase + S.tiles[0]) {
+                    const int l0n = (tn - tbase) * LZ;
+                    const int nln = min(LZ, nlines_tot - l0n);
+                    const size_t bytes = (size_t)nln * nz * sizeof(double);
+                    const char *pn = reinterpret_cast<const char *>(S.n + (size_t)l0n * nz);
+                    const char *ps = reinterpret_cast<const char *>(S.sigma + (size_t)l0n * nz);
+                    for (size_t o = (size_t)threadIdx.x * 128; o < bytes; o += (size_t)nt * 128) {
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(pn + o));
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(ps + o));
+                    }
+                }
+            }
+            // n and sigma are loaded one point ahead, so that the global-memory
+            // latency of the next point overlaps q0 of this one
+            double n_next = 0.0, s_next = 0.0;
+            if (li < nl) {
+                n_next = gn[li * nz + z];
+                s_next = gs[li * nz + z];
+            }
             for (; li < nl;) {
                 const int i = li * nz + z;
-                const double n = gn[i];
-                const double sg = gs[i];
+                const double n = n_next;
+                const double sg = s_next;
+                {
+                    int z2 = z + dz, li2 = li + dli;   // the walk's next point
+                    if (z2 >= nz) {
+                        z2 -= nz;
+                        ++li2;
+                    }
+                    if (li2 < nl) {
+                        n_next = gn[li2 * nz + z2];
+                        s_next = gs[li2 * nz + z2];
+                    }
+                }
                 Rec<T> r;
                 int j = -1;
                 T B = (T)0, ndqn = (T)0, ndqs = (T)0, nn = (T)0;
