@@ -153,16 +153,19 @@ def stage_bytes(shape, prec_bytes):
     }
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch and per
-# 96^3 dimer system, from one full ncu capture of the current kernels on two
-# such systems (profiles/fp32_kernels_dimer96_batch2.md); a launch over nb
-# systems moves nb times this.  Clear an entry when its kernel changes.
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
+# each stage kernel, per 96^3 dimer system: a single-pass ncu capture of the
+# benchmarked 8-system launches themselves (one launch per stage,
+# VDWGB_BATCH_SPLIT=0), divided by 8 (profiles/dram_traffic_dimer96_batch8_fp32.md).
+# Clear an entry when its kernel changes.
 MEASURED_TRAFFIC_PER_SYSTEM = {
-    "yfwd": (144.588544e6 + 84.737792e6) / 2,
-    "xfwd": (144.602880e6 + 84.997632e6) / 2,
-    "xinv": (144.595200e6 + 84.561920e6) / 2,
-    "yinv": (144.596480e6 + 84.507648e6) / 2,
-    "zinv": (173.128960e6 + 18.168832e6) / 2,
+    "zfwd": 746.3e6 / 8,
+    "yfwd": 1092.1e6 / 8,
+    "xfwd": 1093.8e6 / 8,
+    "contract": 1115.1e6 / 8,
+    "xinv": 1093.4e6 / 8,
+    "yinv": 1092.8e6 / 8,
+    "zinv": 793.8e6 / 8,
 }
 
 
@@ -459,7 +462,8 @@ def main():
     roof = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": pk["hbm_gbs"],
             "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
             "peak_source": pk_kind,
-            "traffic_source": "ncu capture on 2 systems, scaled per system" if traffic is not None else None,
+            "traffic_source": "single-pass ncu capture of the 8-system launch (per system x systems)"
+                              if traffic is not None else None,
             "stage_timing": "each stage launched on its own between CUDA events, outside the timed steps "
                             "(the timed steps replay the captured graph, where the two halves of the "
                             "batch overlap)",
