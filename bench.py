@@ -162,7 +162,6 @@ MEASURED_TRAFFIC_PER_SYSTEM = {
     "zfwd": 746.3e6 / 8,
     "yfwd": 1092.1e6 / 8,
     "xfwd": 1093.8e6 / 8,
-    "contract": 1115.1e6 / 8,
     "xinv": 1093.4e6 / 8,
     "yinv": 1092.8e6 / 8,
     "zinv": 793.8e6 / 8,

@@ -969,8 +969,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_contract(const 
 // warp: warp 0 walks the chunk list (system, chunk record, k-point order) and
 // issues the loads of the next chunk — ten 16-byte cp.async copies per k-point
 // record and one bulk copy of the chunk's table rows — into the free half of
-// a double buffer, while warps 1..11 compute the current chunk entirely from
-// shared memory (one k-point per thread, up to CHUNK32 = 352 per chunk).
+// a double buffer, while the consumer warps compute the current chunk entirely
+// from shared memory (one k-point per thread, up to CHUNK32 = 320 per chunk).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
@@ -984,9 +984,10 @@ __device__ __forceinline__ void mbar_arrive_local(unsigned long long *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-constexpr int C32_THREADS = 32 * (1 + C32_CWARPS);   // warp 0 producer, warps 1.. consumers
-static_assert(CHUNK32 == C32_THREADS - 32, "one k-point per consumer thread");
-constexpr int C32_ARRIVALS = 33;            // 32 cp.async arrivals + the row copy's expect-tx arrive
+constexpr int C32_PWARPS = 2;               // producer warps (0..): record gathers split between them
+constexpr int C32_THREADS = 32 * (C32_PWARPS + C32_CWARPS);   // producer warps first, then consumers
+static_assert(CHUNK32 == 32 * C32_CWARPS, "one k-point per consumer thread");
+constexpr int C32_ARRIVALS = 32 * C32_PWARPS + 1;   // cp.async arrivals of every producer lane + the row copy's
 
 struct C32Smem {
     unsigned long long *full;   // [2] chunk landed
@@ -1017,32 +1018,34 @@ __device__ __forceinline__ C32Smem c32_smem(unsigned char *smem) {
     return m;
 }
 
-// producer warp: loads of global chunk t into buffer half b
+// producer warp pw: loads of global chunk t into buffer half b (warp 0 also
+// the descriptor, the chunk record and the table rows; the record gathers
+// are split between the producer warps, 32-record row r to warp r mod C32_PWARPS)
 __device__ __forceinline__ void c32_produce(const SysDev *__restrict__ sys, const int *__restrict__ prefix, int nsys,
                                             int t, int b, int &psi, const C32Smem &m, const float4 *__restrict__ tab) {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, pw = threadIdx.x >> 5;
     psi = advance_sys(prefix, nsys, t, psi);
     const SysDev &S = sys[psi];
     const int lt = t - prefix[psi];
     const int4 c = S.chunks[lt];
-    // descriptor copy for the consumers
-    {
+    if (pw == 0) {
+        // descriptor copy for the consumers
         const int *src = reinterpret_cast<const int *>(&S);
         int *dst = reinterpret_cast<int *>(&m.sys[b]);
         for (int i = lane; i < (int)(sizeof(SysDev) / sizeof(int)); i += 32) dst[i] = src[i];
+        if (lane == 0) m.meta[b] = make_int4(c.y, c.z, c.w, lt);
     }
-    if (lane == 0) m.meta[b] = make_int4(c.y, c.z, c.w, lt);
     const float4 *spec = reinterpret_cast<const float4 *>(S.spec);
     unsigned kidx[CHUNK32 / 32];
 #pragma unroll
     for (int r = 0; r < CHUNK32 / 32; ++r) {
         const int k = lane + 32 * r;
-        kidx[r] = k < c.y ? S.kidx[c.x + k] : 0u;
+        kidx[r] = (k < c.y && r % C32_PWARPS == pw) ? S.kidx[c.x + k] : 0u;
     }
 #pragma unroll
     for (int r = 0; r < CHUNK32 / 32; ++r) {
         const int k = lane + 32 * r;
-        if (k < c.y) {
+        if (k < c.y && r % C32_PWARPS == pw) {
             m.idx[b * CHUNK32 + k] = kidx[r];
             const float4 *src = spec + (size_t)kidx[r] * 10;
             float4 *dst = m.th + ((size_t)b * CHUNK32 + k) * 10;
@@ -1052,7 +1055,7 @@ __device__ __forceinline__ void c32_produce(const SysDev *__restrict__ sys, cons
     }
     cp_async_arrive(&m.full[b]);
     __syncwarp();                                  // descriptor, meta and indices written
-    if (lane == 0) {
+    if (pw == 0 && lane == 0) {
         const int span = min(c.w, SPAN32);
         if (span > 0) {
             const unsigned bytes = (unsigned)(span * NPAIR * sizeof(float4));
@@ -1081,7 +1084,7 @@ __device__ __forceinline__ void c32_kpoint(const SysDev &S, unsigned idx, int &j
     weight = (kz == 0 || nyq_z) ? 1.f : 2.f;
 }
 
-// Warp 0 fills the two buffer halves in turn (chunk i into half i & 1, after
+// The producer warps fill the two buffer halves in turn (chunk i into half i & 1, after
 // every consumer warp has released that half's previous chunk); the consumer
 // warps run through the chunks without block-wide barriers, each writing one
 // energy partial per chunk (epart[chunk * C32_CWARPS + warp]).
@@ -1100,8 +1103,8 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
         fence_mbar_init();
     }
     __syncthreads();
-    if (threadIdx.x < 32) {
-        // producer
+    if (threadIdx.x < 32 * C32_PWARPS) {
+        // producers
         int psi = -1;
         int last0 = -1, last1 = -1;   // last chunk (local count) issued into each half
         int i = 0;
@@ -1111,7 +1114,7 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
                 // chunk i - 2 released: completion (i - 2) / 2 of empty[b]
                 const bool ok = mbar_wait(&m.empty[b], ((i >> 1) + 1) & 1u);
                 if (!__all_sync(0xffffffffu, ok) || *(volatile int *)&s_failed) {
-                    if (threadIdx.x == 0) {
+                    if ((threadIdx.x & 31) == 0) {
                         atomicExch(err, 1);
                         s_failed = 1;
                     }
@@ -1129,7 +1132,7 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
             if (last1 >= 0) mbar_wait(&m.full[1], (last1 >> 1) & 1u);
         }
     } else {
-        const int cw = (threadIdx.x >> 5) - 1;   // consumer warp
+        const int cw = (threadIdx.x >> 5) - C32_PWARPS;   // consumer warp
         const int lane = threadIdx.x & 31;
         int i = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
@@ -1144,7 +1147,7 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
             }
             float eacc = 0.f;
             const int4 mt = m.meta[b];
-            const int k = threadIdx.x - 32;
+            const int k = threadIdx.x - 32 * C32_PWARPS;
             if (k < mt.x) {
                 const SysDev &S = m.sys[b];
                 const unsigned idx = m.idx[b * CHUNK32 + k];

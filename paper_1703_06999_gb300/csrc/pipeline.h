@@ -34,7 +34,7 @@ __host__ __device__ inline int z_ld(int nl) { return 10 * nl + 1; }
 
 // contraction chunks: at most CHUNK k-points spanning at most SPAN table
 // intervals (FP32-mixed: one k-point per consumer thread, 15 consumer warps)
-constexpr int C32_CWARPS = 11;  // FP32 contraction: consumer warps per block (one energy partial each per chunk)
+constexpr int C32_CWARPS = 10;  // FP32 contraction: consumer warps per block (one energy partial each per chunk)
 constexpr int CHUNK32 = 32 * C32_CWARPS, SPAN32 = 8, CHUNK64 = 256, SPAN64 = 8;
 
 // Shared memory of an x / y pass block: barriers and twiddles, then nbuf
