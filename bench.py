@@ -5,7 +5,9 @@ FP64 plain form, with latency, roofline and a CPU (oracle) baseline.
 Workload (default): a batch of 8 dimer-like systems on 96^3 grids in an
 18 x 18 x 24 bohr cell (seeds 0-3, vdW-DF1 and vdW-DF2), synthetic densities.
 One step = the whole hot path (q0/theta, forward FFTs, kernel contraction and
-energy, inverse FFTs, potential) over the batch, one launch per stage.
+energy, inverse FFTs, potential) over the batch: the library's batch graph,
+one launch per stage for each of its parts (the batch runs as four parts
+whose stage chains overlap).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload dimer96_batch8|cubic24|shell192|uneven64]

@@ -206,21 +206,24 @@ int vdwgb_plan_info(vdwgb_handle h, int *info);
 /* Seconds spent building the table on `device` (0 if not built). */
 double vdwgb_table_build_seconds(int device);
 
-/* ---- batched form: many independent systems, one launch per stage ----- */
+/* ---- batched form: many independent systems, one launch per stage and part */
 
 typedef struct vdwgb_batch_s *vdwgb_batch;
 
 /* Create a batch of `count` initialised handles (same device and precision,
- * any grids).  The batch owns a launch plan over all systems and a CUDA
- * graph of its stages; the handles stay owned by the caller and must
- * outlive the batch. */
+ * any grids).  The batch owns a launch plan over all systems, one per part
+ * (see vdwgb_batch_launches), and a CUDA graph of their stages; the handles
+ * stay owned by the caller and must outlive the batch.  While a batch holds
+ * a handle, vdwgb_set_tiles refuses it. */
 int vdwgb_batch_new(vdwgb_handle *handles, int count, vdwgb_batch *out);
 
 /* Evaluate every system of the batch from DEVICE arrays enqueued on
  * cuda_stream: d_rho[i], d_sigma[i], d_dedrho[i], d_dedsigma[i] point to the
  * arrays of system i, d_energy to `count` device doubles.  One launch per
- * stage covers all systems (persistent tile loop), replayed from a CUDA
- * graph when the pointer set repeats. */
+ * stage covers all systems of a part (persistent tile loop); the parts'
+ * stage chains are independent branches of one CUDA graph, captured on the
+ * first call and replayed (a changed pointer set is uploaded to the
+ * descriptors before the replay). */
 int vdwgb_batch_calculate_device(vdwgb_batch b, const double *const *d_rho,
                                  const double *const *d_sigma, double *const *d_dedrho,
                                  double *const *d_dedsigma, double *d_energy, void *cuda_stream);
