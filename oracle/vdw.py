@@ -27,8 +27,8 @@ Where each function comes from:
 * ``energy_potential``  theta (Eq. theta), E via Eq. (enlk), F_alpha,
                         dE/dn (Eq. dedn) and dE/dsigma (Eq. dedsigma).
 
-Readings where the paper is silent, garbled or ambiguous are listed in
-the design doc and restated next to the code they affect.
+Readings where the paper is silent, garbled or ambiguous are stated next to
+the code they affect.
 """
 from __future__ import annotations
 
