@@ -166,7 +166,6 @@ MEASURED_TRAFFIC_PER_SYSTEM = {
     "xfwd": 1093.8e6 / 8,
     "xinv": 1093.4e6 / 8,
     "yinv": 1092.8e6 / 8,
-    "zinv": 793.8e6 / 8,
 }
 
 

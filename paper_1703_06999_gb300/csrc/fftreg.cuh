@@ -314,4 +314,101 @@ __device__ __forceinline__ void fft_ip_auto(cx<T> *a, int n, int nlines, int ld,
     }
 }
 
+// Inverse in-place permuted transform of a z tile whose input is the staged
+// half spectrum of the 20 real fields, packed into complex lines on the fly:
+// line l = 10 li + c holds Z(f) = X_2c(f) + i X_2c+1(f) for f < nzh (the
+// imaginary parts of the f = 0 and Nyquist bins dropped) and the Hermitian
+// mirror conj(X_2c(nz - f)) + i conj(X_2c+1(nz - f)) above.  spec: [li][kz][20]
+// complex (16-byte aligned).  The first (block) pass reads its N2 inputs at
+// frequencies q + N1 j2 straight from spec and writes positions q N2 + j2 of
+// a; the second pass is that of fft_ip.  Natural order in a at the end;
+// ends with a barrier.
+template <int N1, int N2, typename T>
+__device__ __noinline__ void fft_ip_inv_packed(cx<T> *a, const cx<T> *spec, int nlines, int ld, int nzh,
+                                               const cx<T> *tw) {
+    constexpr int N = N1 * N2;
+    const int nt = blockDim.x;
+    const int dl = nt % nlines, dj = nt / nlines;
+    {
+        int l = threadIdx.x % nlines, q = threadIdx.x / nlines;
+        for (; q < N1;) {                     // item (l, q): positions q N2 + j2
+            const int li = l / 10, c = l - 10 * li;
+            const cx<T> *sl = spec + (size_t)li * nzh * NQ + 2 * c;
+            cx<T> v[N2];
+#pragma unroll
+            for (int j2 = 0; j2 < N2; ++j2) {
+                const int f = q + N1 * j2;
+                const bool mirror = f >= nzh;
+                const int kz = mirror ? N - f : f;
+                cx<T> x0 = sl[(size_t)kz * NQ], x1 = sl[(size_t)kz * NQ + 1];
+                if (f == 0 || ((N & 1) == 0 && f == N / 2)) {
+                    x0.y = (T)0;
+                    x1.y = (T)0;
+                }
+                v[j2] = mirror ? cx<T>{x0.x + x1.y, x1.x - x0.y} : cx<T>{x0.x - x1.y, x0.y + x1.x};
+            }
+            dftr<N2, true>(v);
+#pragma unroll
+            for (int j2 = 1; j2 < N2; ++j2) {
+                cx<T> w = tw[q * j2];
+                w.y = -w.y;
+                v[j2] = cmul(v[j2], w);
+            }
+            cx<T> *p = a + (size_t)q * N2 * ld + l;
+#pragma unroll
+            for (int j2 = 0; j2 < N2; ++j2) p[(size_t)j2 * ld] = v[j2];
+            l += dl;
+            q += dj;
+            if (l >= nlines) {
+                l -= nlines;
+                ++q;
+            }
+        }
+    }
+    __syncthreads();
+    {
+        int l = threadIdx.x % nlines, q = threadIdx.x / nlines;
+        for (; q < N2;) {                     // item (l, j2): positions j1 N2 + j2
+            cx<T> v[N1];
+            cx<T> *p = a + (size_t)q * ld + l;
+#pragma unroll
+            for (int j1 = 0; j1 < N1; ++j1) v[j1] = p[(size_t)j1 * N2 * ld];
+            dftr<N1, true>(v);
+#pragma unroll
+            for (int j1 = 0; j1 < N1; ++j1) p[(size_t)j1 * N2 * ld] = v[j1];
+            l += dl;
+            q += dj;
+            if (l >= nlines) {
+                l -= nlines;
+                ++q;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void fft_ip_inv_packed_auto(cx<T> *a, const cx<T> *spec, int n, int nlines, int ld,
+                                                       int nzh, const cx<T> *tw) {
+    switch (n) {
+        case 16: fft_ip_inv_packed<4, 4>(a, spec, nlines, ld, nzh, tw); break;
+        case 24: fft_ip_inv_packed<8, 3>(a, spec, nlines, ld, nzh, tw); break;
+        case 32: fft_ip_inv_packed<8, 4>(a, spec, nlines, ld, nzh, tw); break;
+        case 40: fft_ip_inv_packed<8, 5>(a, spec, nlines, ld, nzh, tw); break;
+        case 48: fft_ip_inv_packed<8, 6>(a, spec, nlines, ld, nzh, tw); break;
+        case 64: fft_ip_inv_packed<8, 8>(a, spec, nlines, ld, nzh, tw); break;
+        case 72: fft_ip_inv_packed<8, 9>(a, spec, nlines, ld, nzh, tw); break;
+        case 80: fft_ip_inv_packed<10, 8>(a, spec, nlines, ld, nzh, tw); break;
+        case 96: fft_ip_inv_packed<12, 8>(a, spec, nlines, ld, nzh, tw); break;
+        case 112: fft_ip_inv_packed<14, 8>(a, spec, nlines, ld, nzh, tw); break;
+        case 128: fft_ip_inv_packed<16, 8>(a, spec, nlines, ld, nzh, tw); break;
+        case 144: fft_ip_inv_packed<12, 12>(a, spec, nlines, ld, nzh, tw); break;
+        case 160: fft_ip_inv_packed<16, 10>(a, spec, nlines, ld, nzh, tw); break;
+        case 192: fft_ip_inv_packed<16, 12>(a, spec, nlines, ld, nzh, tw); break;
+        case 224: fft_ip_inv_packed<16, 14>(a, spec, nlines, ld, nzh, tw); break;
+        case 256: fft_ip_inv_packed<16, 16>(a, spec, nlines, ld, nzh, tw); break;
+        default: break;
+    }
+}
+
 }  // namespace vdwgb

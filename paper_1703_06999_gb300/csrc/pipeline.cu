@@ -1267,11 +1267,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zinv(const SysD
         const cx<T> *spec = ins[cur];
         const bool even = (nz % 2) == 0;
         const int ld = z_ld(nl);
-        // FP32 with a split: packed at permuted positions, transformed in place
+        // FP32 with a split: transformed in place, the first pass reading the
+        // complex lines straight from the staged half spectrum; other axes:
+        // packed into the tile buffer first, then transformed
         const int zs = sizeof(T) == 4 ? S.sz1 : 0, zs2 = zs ? nz / zs : 0;
         // Z_c[kz] = X_{2c}[kz] + i X_{2c+1}[kz]; Z_c[nz-kz] = conj(X_{2c}) + i conj(X_{2c+1});
         // one thread handles half h (c = 5h .. 5h+4) of one (line, kz)
-        {
+        if (!zs) {
             const int half = threadIdx.x & 1;
             const int step = blockDim.x >> 1;
             const int dk = step % nzh, dli = step / nzh;
@@ -1311,12 +1313,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zinv(const SysD
                 }
             }
         }
-        __syncthreads();
         cx<T> *R;
         if (zs) {
-            fft_ip_auto<true>(bufA, nz, L, ld, tw);
+            fft_ip_inv_packed_auto<T>(bufA, spec, nz, L, ld, nzh, tw);
             R = bufA;
         } else {
+            __syncthreads();
             R = fft_auto<true>(bufA, bufB, S.ax[2], L, ld, tw);
         }
         const Rec<T> *rec = recs[cur];
