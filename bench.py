@@ -161,7 +161,6 @@ def stage_bytes(shape, prec_bytes):
 # VDWGB_BATCH_SPLIT=0), divided by 8 (profiles/dram_traffic_dimer96_batch8_fp32.md).
 # Clear an entry when its kernel changes.
 MEASURED_TRAFFIC_PER_SYSTEM = {
-    "zfwd": 746.3e6 / 8,
     "yfwd": 1092.1e6 / 8,
     "xfwd": 1093.8e6 / 8,
     "xinv": 1093.4e6 / 8,

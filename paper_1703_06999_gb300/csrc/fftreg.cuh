@@ -387,6 +387,125 @@ __device__ __noinline__ void fft_ip_inv_packed(cx<T> *a, const cx<T> *spec, int 
     __syncthreads();
 }
 
+// Forward in-place transform of a z tile of complex lines l = 10 li + c
+// (Z = theta_2c + i theta_2c+1, natural order in a) whose second pass writes
+// the two real spectra straight to the half spectrum out ([li][kz][20]
+// complex, global): item (l, k1) transforms the blocks k1 and N1 - k1 together,
+// whose frequencies k1 + N1 k2 and N1 - k1 + N1 k2' are each other's mirrors
+// nz - f, and writes X_2c(f) = (Z(f) + conj Z(-f)) / 2 and
+// X_2c+1(f) = (Z(f) - conj Z(-f)) / 2i for every f < nzh of the two blocks.
+// a is left in an intermediate state; ends without a barrier (the caller
+// synchronises before a is reused).
+template <typename T>
+__device__ __forceinline__ void unpack_store(cx<T> *out, cx<T> z, cx<T> zm) {
+    const T ex = (T)0.5 * (z.x + zm.x), ey = (T)0.5 * (z.y - zm.y);
+    const T ox = (T)0.5 * (z.y + zm.y), oy = (T)-0.5 * (z.x - zm.x);
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(out) = make_float4(ex, ey, ox, oy);
+    } else {
+        out[0] = cx<T>{ex, ey};
+        out[1] = cx<T>{ox, oy};
+    }
+}
+
+template <int N1, int N2, typename T>
+__device__ __noinline__ void fft_ip_fwd_unpack(cx<T> *a, cx<T> *out, int nlines, int ld, int nzh, const cx<T> *tw) {
+    const int nt = blockDim.x;
+    const int dl = nt % nlines, dj = nt / nlines;
+    {
+        // first pass as fft_ip (forward: strided, then twiddles)
+        int l = threadIdx.x % nlines, q = threadIdx.x / nlines;
+        for (; q < N2;) {
+            cx<T> v[N1];
+            cx<T> *p = a + (size_t)q * ld + l;
+#pragma unroll
+            for (int j1 = 0; j1 < N1; ++j1) v[j1] = p[(size_t)j1 * N2 * ld];
+            dftr<N1, false>(v);
+#pragma unroll
+            for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul(v[k1], tw[q * k1]);
+#pragma unroll
+            for (int j1 = 0; j1 < N1; ++j1) p[(size_t)j1 * N2 * ld] = v[j1];
+            l += dl;
+            q += dj;
+            if (l >= nlines) {
+                l -= nlines;
+                ++q;
+            }
+        }
+    }
+    __syncthreads();
+    constexpr int NH = N1 / 2 + 1;   // block pairs (k1, N1 - k1), k1 = 0 .. N1/2
+    int l = threadIdx.x % nlines, q = threadIdx.x / nlines;
+    for (; q < NH;) {
+        const int k1 = q, k1p = (N1 - k1) % N1;
+        const int li = l / 10, c = l - 10 * li;
+        cx<T> *ol = out + (size_t)li * nzh * NQ + 2 * c;
+        cx<T> u[N2], w[N2];
+        {
+            const cx<T> *p = a + (size_t)k1 * N2 * ld + l;
+#pragma unroll
+            for (int j2 = 0; j2 < N2; ++j2) u[j2] = p[(size_t)j2 * ld];
+            dftr<N2, false>(u);                  // u[k2] = Z(k1 + N1 k2)
+        }
+        if (k1 == 0) {
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) {
+                const int f = N1 * k2;
+                if (f < nzh) unpack_store(ol + (size_t)f * NQ, u[k2], u[(N2 - k2) % N2]);
+            }
+        } else if (k1p == k1) {                  // k1 = N1 / 2
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) {
+                const int f = k1 + N1 * k2;
+                if (f < nzh) unpack_store(ol + (size_t)f * NQ, u[k2], u[N2 - 1 - k2]);
+            }
+        } else {
+            {
+                const cx<T> *p = a + (size_t)k1p * N2 * ld + l;
+#pragma unroll
+                for (int j2 = 0; j2 < N2; ++j2) w[j2] = p[(size_t)j2 * ld];
+                dftr<N2, false>(w);              // w[k2] = Z(N1 - k1 + N1 k2)
+            }
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) {
+                const int f = k1 + N1 * k2, fp = k1p + N1 * k2;
+                if (f < nzh) unpack_store(ol + (size_t)f * NQ, u[k2], w[N2 - 1 - k2]);
+                if (fp < nzh) unpack_store(ol + (size_t)fp * NQ, w[k2], u[N2 - 1 - k2]);
+            }
+        }
+        l += dl;
+        q += dj;
+        if (l >= nlines) {
+            l -= nlines;
+            ++q;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void fft_ip_fwd_unpack_auto(cx<T> *a, cx<T> *out, int n, int nlines, int ld, int nzh,
+                                                       const cx<T> *tw) {
+    switch (n) {
+        case 16: fft_ip_fwd_unpack<4, 4>(a, out, nlines, ld, nzh, tw); break;
+        case 24: fft_ip_fwd_unpack<8, 3>(a, out, nlines, ld, nzh, tw); break;
+        case 32: fft_ip_fwd_unpack<8, 4>(a, out, nlines, ld, nzh, tw); break;
+        case 40: fft_ip_fwd_unpack<8, 5>(a, out, nlines, ld, nzh, tw); break;
+        case 48: fft_ip_fwd_unpack<8, 6>(a, out, nlines, ld, nzh, tw); break;
+        case 64: fft_ip_fwd_unpack<8, 8>(a, out, nlines, ld, nzh, tw); break;
+        case 72: fft_ip_fwd_unpack<8, 9>(a, out, nlines, ld, nzh, tw); break;
+        case 80: fft_ip_fwd_unpack<10, 8>(a, out, nlines, ld, nzh, tw); break;
+        case 96: fft_ip_fwd_unpack<12, 8>(a, out, nlines, ld, nzh, tw); break;
+        case 112: fft_ip_fwd_unpack<14, 8>(a, out, nlines, ld, nzh, tw); break;
+        case 128: fft_ip_fwd_unpack<16, 8>(a, out, nlines, ld, nzh, tw); break;
+        case 144: fft_ip_fwd_unpack<12, 12>(a, out, nlines, ld, nzh, tw); break;
+        case 160: fft_ip_fwd_unpack<16, 10>(a, out, nlines, ld, nzh, tw); break;
+        case 192: fft_ip_fwd_unpack<16, 12>(a, out, nlines, ld, nzh, tw); break;
+        case 224: fft_ip_fwd_unpack<16, 14>(a, out, nlines, ld, nzh, tw); break;
+        case 256: fft_ip_fwd_unpack<16, 16>(a, out, nlines, ld, nzh, tw); break;
+        default: break;
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void fft_ip_inv_packed_auto(cx<T> *a, const cx<T> *spec, int n, int nlines, int ld,
                                                        int nzh, const cx<T> *tw) {

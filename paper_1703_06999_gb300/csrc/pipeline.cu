@@ -527,30 +527,25 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zfwd(const SysD
             }
         }
         __syncthreads();
-        // FP32 with a split: in place, frequency f at position fft_perm_pos(f)
+        // the two real transforms of each line: X_{2c}(kz) = (Z(kz) + conj Z(-kz)) / 2,
+        // X_{2c+1}(kz) = (Z(kz) - conj Z(-kz)) / 2i.  FP32 with a split: in
+        // place, the second pass writing them straight to the spectrum; other
+        // axes: transform, then one thread writes the 10 outputs of half h
+        // (c = 5h .. 5h+4) of one (line, kz)
         const int zs = sizeof(T) == 4 ? S.sz1 : 0;
-        cx<T> *R;
-        if (zs) {
-            fft_ip_auto<false>(bufA, nz, L, ld, tw);
-            R = bufA;
-        } else {
-            R = fft_auto<false>(bufA, bufB, S.ax[2], L, ld, tw);
-        }
-        const int zs2 = zs ? nz / zs : 0;
-        // unpack the two real transforms: X_{2c}(kz) = (Z(kz) + conj Z(-kz)) / 2,
-        // X_{2c+1}(kz) = (Z(kz) - conj Z(-kz)) / 2i; one thread writes the 10
-        // outputs of half h (c = 5h .. 5h+4) of one (line, kz)
         cx<T> *spec = reinterpret_cast<cx<T> *>(S.spec) + (size_t)l0 * nzh * NQ;
-        {
+        cx<T> *R = bufA;
+        if (zs) fft_ip_fwd_unpack_auto<T>(bufA, spec, nz, L, ld, nzh, tw);
+        else R = fft_auto<false>(bufA, bufB, S.ax[2], L, ld, tw);
+        if (!zs) {
             const int half = threadIdx.x & 1;
             const int step = nt >> 1;
             const int dk = step % nzh, dli = step / nzh;
             int kz = (threadIdx.x >> 1) % nzh, li = (threadIdx.x >> 1) / nzh;
             for (; li < nl;) {
                 const int km = kz == 0 ? 0 : nz - kz;
-                const int pk = zs ? fft_perm_pos(kz, zs, zs2) : kz, pm = zs ? fft_perm_pos(km, zs, zs2) : km;
-                const cx<T> *zk = R + (size_t)pk * ld + li * 10 + 5 * half;
-                const cx<T> *zm = R + (size_t)pm * ld + li * 10 + 5 * half;
+                const cx<T> *zk = R + (size_t)kz * ld + li * 10 + 5 * half;
+                const cx<T> *zm = R + (size_t)km * ld + li * 10 + 5 * half;
                 cx<T> *out = spec + ((size_t)li * nzh + kz) * NQ + 10 * half;
 #pragma unroll
                 for (int c = 0; c < 5; ++c) {
