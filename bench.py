@@ -161,10 +161,13 @@ def stage_bytes(shape, prec_bytes):
 # VDWGB_BATCH_SPLIT=0), divided by 8 (profiles/dram_traffic_dimer96_batch8_fp32.md).
 # Clear an entry when its kernel changes.
 MEASURED_TRAFFIC_PER_SYSTEM = {
-    "yfwd": 1092.1e6 / 8,
-    "xfwd": 1093.8e6 / 8,
-    "xinv": 1093.4e6 / 8,
-    "yinv": 1092.8e6 / 8,
+    "zfwd": 755.6e6 / 8,
+    "yfwd": 1097.2e6 / 8,
+    "xfwd": 1093.0e6 / 8,
+    "contract": 1116.7e6 / 8,
+    "xinv": 1092.8e6 / 8,
+    "yinv": 1097.6e6 / 8,
+    "zinv": 794.6e6 / 8,
 }
 
 
