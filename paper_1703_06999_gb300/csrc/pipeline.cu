@@ -605,29 +605,6 @@ __device__ __forceinline__ dvec4 ld_row(const dvec4 *p) {
 
 __device__ __forceinline__ int fold(int i, int n) { return i <= (n - 1) / 2 ? i : i - n; }
 
-// Block sum of per-thread FP32 terms without the FP64 pipe: FP32 sums within
-// each warp, then the warp sums added as a double-float pair by thread 0,
-// whose result (valid in thread 0 only) is widened on the integer pipe.
-__device__ __forceinline__ double block_sum_f(float v, float *red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) red[w] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0) {
-        const int nw = (blockDim.x + 31) >> 5;
-        float hi = 0.f, lo = 0.f;
-        for (int i = 0; i < nw; ++i) {
-            float e;
-            two_sum(hi, red[i], hi, e);
-            lo += e;
-        }
-        s = f2d_bits(hi) + f2d_bits(lo);
-    }
-    __syncthreads();
-    return s;
-}
-
 template <typename T>
 __device__ __forceinline__ double block_sum(double v, double *red) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
