@@ -146,3 +146,65 @@ def test_spline_basis_c2_at_nodes():
         pr, dpr = vdw.spline_basis(np.array([q[i] + eps]), q, d2)
         assert np.allclose(pl, pr, atol=1e-7)
         assert np.allclose(dpl, dpr, atol=1e-5)
+
+
+def _q0_dion_route(n, sigma, Z):
+    """q0 built the other way the appendix gives it: q0 = (eps_xc^0 / eps_x^LDA) k_F,
+    where eps_xc^0 is the LDA exchange-correlation energy per particle with
+    the screened-exchange gradient correction of Dion et al. (the reference
+    the appendix cites): eps_xc^0 = eps_x^LDA + eps_c^LDA - eps_x^LDA (Z_ab / 9) s^2,
+    eps_x^LDA = -3 k_F / (4 pi), s = |grad n| / (2 k_F n).  No term of the
+    oracle's closed form is reused: the exchange energy, the reduced gradient
+    and the ratio are formed from their definitions."""
+    kF = (3.0 * np.pi ** 2 * n) ** (1.0 / 3.0)
+    rs = (3.0 / (4.0 * np.pi * n)) ** (1.0 / 3.0)
+    eps_c, _ = vdw.pw92_eps_c(rs)
+    eps_x = -3.0 * kF / (4.0 * np.pi)
+    s = np.sqrt(sigma) / (2.0 * kF * n)
+    eps_xc0 = eps_x + eps_c - eps_x * (Z / 9.0) * s * s
+    return eps_xc0 / eps_x * kF
+
+
+@pytest.mark.parametrize("functional", [vdw.DF1, vdw.DF2])
+def test_q0_gradient_term_matches_dion_definition(functional):
+    # Appendix (q0): the closed form k_F - (4 pi/3) eps_c - (Z_ab/36) sigma/(k_F n^2)
+    # must equal the ratio form (eps_xc^0 / eps_x^LDA) k_F with Dion's gradient
+    # correction.  Inputs span densities 1e-4..10 and reduced gradients
+    # s = 0..3, so the gradient term ranges from nothing to dominant; the
+    # saturation (pinned separately) is applied to both sides.
+    rng = np.random.default_rng(17)
+    n = 10 ** rng.uniform(-4, 1, 500)
+    kF = (3 * np.pi ** 2 * n) ** (1 / 3)
+    s_red = rng.uniform(0.0, 3.0, 500)
+    sigma = (2 * kF * n * s_red) ** 2
+    Z = vdw.Z_AB[functional]
+    want, _ = vdw.saturate(_q0_dion_route(n, sigma, Z), 5.0)
+    got, _, _ = vdw.q0_of(n, sigma, functional)
+    assert np.allclose(got, want, rtol=1e-12, atol=0)
+    # the plausible misreadings of the gradient term all miss by far more
+    base = kF - 4 * np.pi / 3 * vdw.pw92_eps_c((9 * np.pi / 4) ** (1 / 3) / kF)[0]
+    for wrong in (-(Z / 9) * sigma / (kF * n * n),          # /9 instead of /36
+                  -(Z / 36) * sigma / (kF * kF * n * n),    # k_F^2 (the commented-out form)
+                  -(Z / 36) * sigma / (kF * n),             # n instead of n^2
+                  (Z / 36) * sigma / (kF * n * n)):         # sign
+        bad, _ = vdw.saturate(base + wrong, 5.0)
+        sel = s_red > 0.5
+        assert np.max(np.abs(bad[sel] / got[sel] - 1)) > 1e-3
+
+
+def test_q0_gradient_term_ratio_df2_over_df1():
+    # Only Z_ab differs between the functionals (appendix), and the gradient
+    # term is linear in Z_ab: below saturation (h(x) = x to 1e-12 for x < 0.5)
+    # the sigma-dependent part of q0 scales by exactly 1.887 / 0.8491.
+    n = np.array([1e-5, 3e-5, 1e-4])
+    kF = (3 * np.pi ** 2 * n) ** (1 / 3)
+    sigma = (2 * kF * n * 1.2) ** 2                 # s = 1.2
+    g = {}
+    for fn in (vdw.DF1, vdw.DF2):
+        q_s, _, _ = vdw.q0_of(n, sigma, fn)
+        q_0, _, _ = vdw.q0_of(n, np.zeros_like(n), fn)
+        assert np.all(q_s < 0.5)
+        g[fn] = q_s - q_0
+    assert np.allclose(g[vdw.DF2] / g[vdw.DF1], 1.887 / 0.8491, rtol=1e-9)
+    # and its size: (|Z_ab| / 9) s^2 k_F with s = 1.2
+    assert np.allclose(g[vdw.DF1], 0.8491 / 9 * 1.44 * kF, rtol=1e-9)
