@@ -160,8 +160,9 @@ int vdwgb_phi(int device, int npts, const double *d1, const double *d2, double *
 /* q0(n, sigma) and its partial derivatives (appendix, q0 with PW92
  * correlation and the saturation h_5) exactly as the given precision form
  * evaluates them inside vdwgb_calculate (FP64 values either way; the
- * FP32-mixed form reaches them with FP32-seeded FP64 iterations and forms
- * the derivatives in FP32).  Host arrays of npts doubles. */
+ * FP32-mixed form evaluates q0 in double-float arithmetic, pairs of FP32
+ * with about 46 significant bits, and forms the derivatives in FP32).  Host
+ * arrays of npts doubles. */
 int vdwgb_q0(int device, int precision, int functional, int npts, const double *n, const double *sigma,
              double *q0, double *dq0dn, double *dq0dsigma);
 
@@ -321,18 +322,23 @@ int vdwgb_server_free(vdwgb_server *s);
  * ESTATE if the device has no resident kernel table yet: call
  * vdwgb_kernel_table(device, NULL, NULL, NULL) once before (that call
  * allocates).  The first call on a device looks up the device address of the
- * fixed array, with the device made current; make that first call before any
- * stream capture.
+ * fixed array, with the device made current.
  *
  * Arguments: cell9 as in vdwgb_set_unit_cell (host, row-major lattice
  * vectors, Bohr); d_rho, d_sigma (read), d_dedrho, d_dedsigma (written) are
  * DEVICE arrays of nx*ny*nz doubles in C order, d_energy one device double;
- * all enqueued on cuda_stream (NULL = legacy default stream), nothing waits.
- * All calls on one device share its fixed array and leave their data in it
- * (nothing needs clearing: each call overwrites what it reads).  Calls on one
- * device whose GPU work overlaps (on two streams, say) race on the array and
- * give wrong results: order them, e.g. on one stream.  Each device has its
- * own array. */
+ * all enqueued on cuda_stream (NULL = legacy default stream).  The plan data
+ * (k-point order, twiddles, descriptors) are copied into the fixed array
+ * from pageable host memory, so the call may wait for the stream's earlier
+ * work before it returns, and it cannot be captured into a CUDA graph: on a
+ * stream that is being captured it returns ESTATE without enqueuing
+ * anything.  All calls on one device share its fixed array and leave their
+ * data in it (nothing needs clearing: each call overwrites what it reads).
+ * Calls on one device whose GPU work overlaps (on two streams, say) race on
+ * the array and give wrong results: order them, e.g. on one stream.  Each
+ * device has its own array.  A kernel whose bounded wait for staged data ran
+ * out sets the device's status flag: after synchronising, check
+ * vdwgb_device_status(device) (0: the results are valid). */
 int vdwgb_calculate_noalloc(int device, int functional, int nx, int ny, int nz, const double *cell9,
                             const double *d_rho, const double *d_sigma, double *d_dedrho,
                             double *d_dedsigma, double *d_energy, void *cuda_stream);

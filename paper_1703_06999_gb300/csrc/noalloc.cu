@@ -12,7 +12,11 @@
 // call before the first finished) race on it.  Host code cannot use the
 // array's name as a device address: the first call on a device (with that
 // device current) asks the runtime for the array's device address once and
-// caches it; make that first call before any stream capture.
+// caches it.  The plan data reach the array by copies from pageable host
+// memory, so a call may wait for the stream's earlier work before it
+// returns, and a call on a stream that is being captured is refused
+// (ESTATE): a captured pageable copy would replay from host memory that a
+// later call has overwritten.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -222,6 +226,14 @@ extern "C" int vdwgb_calculate_noalloc(int device, int functional, int nx, int n
     std::lock_guard<std::mutex> lk(g_na_mu);
     cudaError_t e = cudaSetDevice(device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        e = cudaStreamIsCapturing(st, &cs);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+        if (cs != cudaStreamCaptureStatusNone)
+            return fail(VDWGB_ESTATE, "vdwgb_calculate_noalloc cannot run on a stream that is being captured");
+    }
     if (!g_na_dev[device]) {
         // once per device, with the device current: the array's device address
         void *ptr = nullptr;
@@ -294,7 +306,6 @@ extern "C" int vdwgb_calculate_noalloc(int device, int functional, int nx, int n
         L.grid[k] = L.total[k] < sms * per_sm ? L.total[k] : sms * per_sm;
     }
     // uploads from host staging (pageable: each copy has read its source when it returns)
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     const size_t nk = (size_t)nx * ny * nzh;
     e = cudaMemcpyAsync(base + OFF_KIDX, h_kidx, nk * sizeof(unsigned), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)

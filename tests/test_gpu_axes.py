@@ -1,0 +1,138 @@
+"""GPU parity on the axis lengths the workloads use, on inputs at the edges
+of the method's domain, and on the 192^3 ligand-shell workload.
+
+* Every FFT length with a compiled register codelet above 64 (72, 128, 144,
+  160, 192, 224, 256) is put on x, on y and on z of a thin grid, in both
+  precisions.  The other two axes are short, so the oracle stays cheap.
+* A density with exact zeros, negative values and values just below and
+  above the low-density cut-off n_min = 1e-12, negative sigma entries and
+  saturating densities, compared element by element.
+* The 192^3 ligand-shell-like system (200 exponentials, vacuum near 1e-8)
+  against the oracle in both precisions (slow: the oracle takes about a
+  minute on one core).
+
+Tolerances as in test_gpu_parity: FP64 energy 1e-10 relative and potential
+1e-9 of its max norm; FP32-mixed |dE| <= 1e-6 Ha and potential 1e-5 of its
+max norm."""
+import numpy as np
+import pytest
+
+from oracle import vdw
+from paper_1703_06999_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+B = pytest.importorskip("paper_1703_06999_gb300.binding")
+
+TOL = {0: (1e-10, 1e-9), 1: (1e-6, 1e-5)}
+
+
+def _check(res, ref, prec):
+    e, dn, ds = res
+    etol, ptol = TOL[prec]
+    assert np.isfinite(e) and np.all(np.isfinite(dn)) and np.all(np.isfinite(ds))
+    if prec == B.FP64:
+        assert abs(e - ref.energy) <= etol * max(abs(ref.energy), 1e-3), (e, ref.energy)
+    else:
+        assert abs(e - ref.energy) <= etol, (e, ref.energy)
+    assert np.max(np.abs(dn - ref.dedn)) <= ptol * max(np.max(np.abs(ref.dedn)), 1e-300)
+    assert np.max(np.abs(ds - ref.dedsigma)) <= ptol * max(np.max(np.abs(ref.dedsigma)), 1e-300)
+
+
+def _thin(L, axis):
+    shape = [6, 8, 10]
+    shape[axis] = L
+    lengths = [3.0, 4.0, 4.5]
+    lengths[axis] = 0.2 * L
+    atoms = []
+    g = np.random.default_rng(L + 7 * axis)
+    for _ in range(3):
+        c = g.uniform(0, 1, 3) * lengths
+        atoms.append((float(g.uniform(1, 6)), float(g.uniform(1.0, 2.5)), tuple(c)))
+    return inputs.make_system(tuple(shape), np.diag(lengths), atoms, 1 + axis % 2)
+
+
+LENGTHS = [72, 128, 144, 160, 192, 224, 256]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("axis", [0, 1, 2], ids=["x", "y", "z"])
+@pytest.mark.parametrize("L", LENGTHS)
+def test_codelet_lengths_on_each_axis(oracle_default, L, axis, prec):
+    s = _thin(L, axis)
+    n, sg = s.n.numpy(), s.sigma.numpy()
+    ref = oracle_default.energy_potential(n, sg, s.cell, s.functional)
+    f = B.Functional(s.shape, s.cell, s.functional, prec)
+    try:
+        _check(f.calculate(n, sg), ref, prec)
+    finally:
+        f.close()
+
+
+def _edge_system():
+    """A small density pushed to the edges of the method's domain: exact
+    zeros, negative values (numerical noise a host code may pass), values
+    just below and just above n_min = 1e-12, a few large densities whose q0
+    saturates at q_cut = 5, and negative sigma entries."""
+    s = inputs.make_system((24, 20, 18), np.diag([8.0, 7.0, 6.5]),
+                           [(4.0, 1.6, (2.0, 2.0, 2.0)), (2.0, 1.1, (6.0, 5.0, 4.0))], 2)
+    n = s.n.numpy().copy()
+    sg = s.sigma.numpy().copy()
+    g = np.random.default_rng(3)
+    flat_n, flat_s = n.reshape(-1), sg.reshape(-1)
+    n[:, :, 12:15] = 0.0                              # an exactly empty slab
+    idx = g.choice(flat_n.size, 510, replace=False)
+    vals = np.concatenate([np.full(100, -1e-14), np.full(100, 1e-13), np.full(100, 1e-12),
+                           np.full(100, 1.0000001e-12), np.full(100, 3e-12),
+                           np.full(10, 15.0)])      # q_raw / q_cut > 1.5: q0 = q_cut to FP64 precision
+    flat_n[idx] = vals
+    neg = g.choice(flat_s.size, 400, replace=False)
+    flat_s[neg] = -np.abs(flat_s[neg]) - 1e-9        # negative sigma: treated as 0
+    return s, n, sg
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_low_density_and_saturation_edges(oracle_default, prec):
+    s, n, sg = _edge_system()
+    ref = oracle_default.energy_potential(n, sg, s.cell, s.functional)
+    f = B.Functional(s.shape, s.cell, s.functional, prec)
+    try:
+        got = f.calculate(n, sg)
+    finally:
+        f.close()
+    _check(got, ref, prec)
+    dead = n <= 1e-12
+    assert np.all(got[1][dead] == 0.0) and np.all(got[2][dead] == 0.0)
+    # the q0 < q_min clamp cannot be reached by a live point: k_F(n_min) is
+    # about 3.1e-4 > q_min = 1e-5 and the other two terms are non-negative
+    q0, _, _ = vdw.q0_of(np.array([1.0000001e-12]), np.array([0.0]), 1)
+    assert q0[0] > 3e-4
+
+
+def test_sigma_sign_only_enters_as_zero(oracle_default):
+    # sigma < 0 means sigma = 0 on both sides: replacing every negative entry
+    # by 0 gives the same GPU result bit for bit
+    s, n, sg = _edge_system()
+    clipped = np.maximum(sg, 0.0)
+    for prec in (0, 1):
+        f = B.Functional(s.shape, s.cell, s.functional, prec)
+        try:
+            a = f.calculate(n, sg)
+            b = f.calculate(n, clipped)
+        finally:
+            f.close()
+        assert a[0] == b[0] and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+@pytest.mark.slow
+def test_ligand_shell_192_against_oracle(oracle_default):
+    import torch
+    s = inputs.ligand_shell(0, device=torch.device("cuda:0"))
+    n, sg = s.n.cpu().numpy(), s.sigma.cpu().numpy()
+    ref = oracle_default.energy_potential(n, sg, s.cell, s.functional)
+    for prec in (B.FP32_MIXED, B.FP64):
+        f = B.Functional(s.shape, s.cell, s.functional, prec)
+        try:
+            _check(f.calculate(n, sg), ref, prec)
+        finally:
+            f.close()

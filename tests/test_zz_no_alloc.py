@@ -48,6 +48,7 @@ def _noalloc(dev, s, n, sg):
     B.vdwgb_calculate_noalloc(0, s.functional, s.shape, s.cell, n, sg, dn, ds, e,
                               torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
+    B.vdwgb_device_status(0)       # raises if a bounded wait ran out (results invalid)
     return float(e[0]), dn.cpu().numpy(), ds.cpu().numpy()
 
 
@@ -100,3 +101,25 @@ def test_noalloc_rejects_beyond_limits(dev, shape):
     with pytest.raises(B.VdwgbError) as ei:
         B.vdwgb_calculate_noalloc(0, B.DF1, shape, np.diag([8.0, 8.0, 8.0]), n, n, out, out, e, 0)
     assert ei.value.code == -1
+
+
+def test_noalloc_refuses_a_capturing_stream(dev):
+    # the plan data are copied from pageable host memory: the call cannot be
+    # captured and must say so instead of recording those copies
+    import torch
+    s = inputs.small_cubic(4, ngrid=16)
+    n, sg = _to(dev, s)
+    out = torch.empty_like(n)
+    e = torch.zeros(1, dtype=torch.float64, device=dev)
+    st = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    code = None
+    with torch.cuda.graph(g, stream=st):
+        try:
+            B.vdwgb_calculate_noalloc(0, s.functional, s.shape, s.cell, n, sg, out, out, e, st.cuda_stream)
+        except B.VdwgbError as err:
+            code = err.code
+        e.add_(0.0)                # keep the captured graph non-empty
+    assert code == -4
+    torch.cuda.synchronize()
+    _close(_noalloc(dev, s, n, sg), _handle(dev, s, n, sg))   # the array is still usable
