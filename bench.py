@@ -1,31 +1,36 @@
 """Benchmark: grid points per second of the vdW-DF nonlocal-correlation
 evaluation (E_c^nl and its potential), FP32-mixed batched form against the
-FP64 plain form, with latency, roofline and a CPU (oracle) baseline.
+FP64 plain form, with latency, rooflines, errors against the FP64 oracle and
+the oracle timed on the host cores.
 
-Workload (default): a batch of 8 dimer-like systems on 96^3 grids in an
-18 x 18 x 24 bohr cell (seeds 0-3, vdW-DF1 and vdW-DF2), synthetic densities.
-One step = the whole hot path (q0/theta, forward FFTs, kernel contraction and
-energy, inverse FFTs, potential) over the batch: the library's batch graph,
-one launch per stage for each of its parts (the batch runs as four parts
-whose stage chains overlap).
+Workload (default, ``uneven64``): a batch of 64 independent systems whose
+grid axes are drawn from {32, 48, 64, 80, 96, 128} (non-cubic mixes), grid
+spacing 0.15-0.30 bohr, 4-60 exponentials each, vdW-DF1 and vdW-DF2 mixed
+(25.8 M grid points), synthetic densities.  One step = the whole hot path
+(q0/theta, forward FFTs, kernel contraction and energy, inverse FFTs,
+potential) over the batch: the library's batch graph, one persistent launch
+per stage for each of its parts, autotuned tile shapes.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload dimer96_batch8|cubic24|shell192|uneven64]
+                  [--workload uneven64|dimer96_batch8|cubic24|shell192]
 
-The other workloads (the small 24^3 case, one 192^3 ligand-shell-like system,
-a batch of 64 uneven grids) measure the same quantities for the record; they
-skip the serving stream, and the CPU baseline runs only on the default and
-the 24^3 workload.
+The default run also times the 8-system 96^3 dimer batch (``extra``), the
+serving stream (Poisson arrivals, continuous batching) and the FP64 oracle
+on every system of the batch on all host cores (errors of both GPU forms
+against it, and the CPU baseline).  The other workloads measure the timed
+quantities for the record.
 
 N > 1: run under torch.distributed.run; each rank evaluates its own batch
 (independent systems, no data-path collective), weak scaling.
 """
 import argparse
+import ctypes
 import json
 import os
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -34,10 +39,13 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-WORKLOAD = "dimer96_batch8"
-SHAPE = (96, 96, 96)
-CELL = (18.0, 18.0, 24.0)
+WORKLOAD = "uneven64"
+DIMER_SHAPE = (96, 96, 96)
+DIMER_CELL = (18.0, 18.0, 24.0)
 METRIC = "grid pts/s for E_c^nl+potential, FP32 batched vs FP64 plain; p50/p99 latency"
+PRECISION_NOTE = ("FP32 theta fields, FFTs and kernel contraction; q0 and saturation in double-float "
+                  "(FP32 pairs, ~46 significant bits); per-warp energy sums in FP64, energy finish in "
+                  "compensated FP32 pairs; outputs FP64")
 
 
 def parse():
@@ -46,18 +54,18 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--batch", type=int, default=8)
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "cubic24", "shell192", "uneven64"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "dimer96_batch8", "cubic24", "shell192"])
+    ap.add_argument("--no-oracle", action="store_true", help="skip the oracle errors and the CPU baseline")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-stream measurement")
+    ap.add_argument("--no-extra", action="store_true", help="skip the extra 96^3 dimer batch")
     ap.add_argument("--only-timed", action="store_true",
                     help="stop after the timed batched steps (for profiler launch lists)")
     return ap.parse_args()
 
 
 def rank_seeds(rank, nb):
-    """Seeds of the systems rank `rank` evaluates: independent systems per
-    rank (weak scaling, no data exchange between ranks)."""
+    """Seeds of the dimer systems rank `rank` evaluates: independent systems
+    per rank (weak scaling, no data exchange between ranks)."""
     return [rank * 1000 + i // 2 for i in range(nb)]
 
 
@@ -77,50 +85,107 @@ def dist_env():
     return rank, world, local
 
 
+def make_workload(name, rank, device):
+    """The systems of a workload (synthetic densities, built on `device`)."""
+    from paper_1703_06999_gb300 import inputs
+    if name == "dimer96_batch8":
+        seeds = rank_seeds(rank, 8)
+        return [inputs.dimer(seeds[i], shape=DIMER_SHAPE, cell_lengths=DIMER_CELL, functional=1 + i % 2,
+                             device=device) for i in range(8)]
+    if name == "cubic24":
+        return [inputs.small_cubic(rank, ngrid=24, device=device)]
+    if name == "shell192":
+        return [inputs.ligand_shell(rank, device=device)]
+    return inputs.uneven_batch(rank, count=64, device=device)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """SM clock and clock-event (throttle) reasons sampled during the timed
+    region: NVML every 5 ms from a thread (read-only queries), else
+    nvidia-smi every 50 ms."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
     def __init__(self, index):
         self.index = index
+        self.sm, self.smax, self.reasons = [], [], set()
+        self.stop_flag = False
+        self.mode = None
+        try:
+            self.nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.nv.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit")
+            self.h = ctypes.c_void_p()
+            if self.nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h)) != 0:
+                raise OSError("handle")
+            self.mode = "nvml"
+            self.t = threading.Thread(target=self._loop, daemon=True)
+            self.t.start()
+        except (OSError, AttributeError):
+            self._start_smi()
+
+    def _loop(self):
+        clk, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        get_r = getattr(self.nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop_flag:
+            if self.nv.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(clk)) == 0:
+                self.sm.append(float(clk.value))
+            if self.nv.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) == 0:
+                self.smax.append(float(mx.value))
+            if get_r(self.h, ctypes.byref(rs)) == 0:
+                for bit, nm in self.REASONS.items():
+                    if rs.value & bit:
+                        self.reasons.add(nm)
+            time.sleep(0.005)
+
+    def _start_smi(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
-            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.Q,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
+            self.mode = "nvidia-smi"
         except OSError:
             self.p = None
 
     def stop(self):
-        if self.p is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.p.terminate()
-        try:
-            self.p.wait(5)
-        except subprocess.TimeoutExpired:
-            self.p.kill()
-        self.f.flush()
-        self.f.seek(0)
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.f.read().splitlines():
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
-                continue
+        if self.mode == "nvml":
+            self.stop_flag = True
+            self.t.join(2)
+        elif self.mode == "nvidia-smi" and self.p is not None:
+            self.p.terminate()
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        os.unlink(self.f.name)
-        return {"sm_mhz": float(np.median(sm)) if sm else None,
-                "sm_max_mhz": float(max(smax)) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                self.p.wait(5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+            self.f.flush()
+            self.f.seek(0)
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for line in self.f.read().splitlines():
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    self.sm.append(float(parts[1]))
+                    self.smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        self.reasons.add(nm)
+            os.unlink(self.f.name)
+        else:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no clock source"], "samples": 0}
+        return {"sm_mhz": float(np.median(self.sm)) if self.sm else None,
+                "sm_max_mhz": float(max(self.smax)) if self.smax else None,
+                "reasons": sorted(self.reasons), "samples": len(self.sm), "source": self.mode}
 
 
 def peaks():
@@ -131,6 +196,9 @@ def peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
+# ---------------------------------------------------------------------------
+# algorithmic work per stage
+# ---------------------------------------------------------------------------
 def stage_bytes(shape, prec_bytes):
     """Algorithmic DRAM bytes per launch of each stage for one system.
     c = complex element size; the half spectrum holds 20 * nx * ny * (nz/2+1)
@@ -155,55 +223,147 @@ def stage_bytes(shape, prec_bytes):
     }
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
-# each stage kernel, per 96^3 dimer system: a single-pass ncu capture of the
-# benchmarked 8-system launches themselves (one launch per stage,
-# VDWGB_BATCH_SPLIT=0), divided by 8 (profiles/dram_traffic_dimer96_batch8_fp32.md).
-# Clear an entry when its kernel changes.
-MEASURED_TRAFFIC_PER_SYSTEM = {
-    "zfwd": 755.6e6 / 8,
-    "yfwd": 1097.2e6 / 8,
-    "xfwd": 1093.0e6 / 8,
-    "contract": 1116.7e6 / 8,
-    "xinv": 1092.8e6 / 8,
-    "yinv": 1097.6e6 / 8,
-    "zinv": 794.6e6 / 8,
+# Fused multiply-adds per half-spectrum k-point of the contraction: 210
+# cubic evaluations (three per two pairs: 315), 400 complex multiply-adds by
+# the real phi (one two-lane FMA each) and 20 for the energy, all two-lane
+# FP32 FMAs (two FMAs, four flops each).
+CONTRACT_FMA2_PER_KPOINT = 315 + 400 + 20
+# FP64 form: 210 cubic evaluations (3 FMAs each), 400 complex multiply-adds
+# (2 FMAs each) and 20 energy terms (2 each).
+CONTRACT_FMA64_PER_KPOINT = 630 + 800 + 40
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a
+# stage kernel, per workload: single-pass ncu captures of the benchmarked
+# launches themselves (one launch per stage, VDWGB_BATCH_SPLIT=0).  An entry
+# is removed when its kernel changes.
+MEASURED_TRAFFIC = {
+    "dimer96_batch8": {"zfwd": 755.6e6, "yfwd": 1097.2e6, "xfwd": 1093.0e6, "xinv": 1092.8e6,
+                       "yinv": 1097.6e6, "zinv": 794.6e6},
 }
 
 
+# ---------------------------------------------------------------------------
+# oracle legs (FP64 CPU, test infrastructure): process pool started with spawn
+# ---------------------------------------------------------------------------
+def _oracle_job(args):
+    """One oracle evaluation in a worker process: (index, E, dedn, dedsigma, s)."""
+    i, n, sg, cell, fn = args
+    from oracle import vdw
+    o = _oracle_job.o = getattr(_oracle_job, "o", None) or vdw.Oracle()
+    t0 = time.perf_counter()
+    r = o.energy_potential(n, sg, cell, fn)
+    return i, r.energy, r.dedn, r.dedsigma, time.perf_counter() - t0
+
+
+def oracle_workers(max_points):
+    """Worker count for the oracle pool: every host core, bounded by the host
+    memory the largest system needs (about 1.5 kB per grid point)."""
+    cores = os.cpu_count() or 1
+    try:
+        with open("/proc/meminfo") as f:
+            avail = next(int(l.split()[1]) * 1024 for l in f if l.startswith("MemAvailable"))
+    except (OSError, StopIteration):
+        avail = 16 << 30
+    per = 1500 * max_points + (256 << 20)
+    return max(1, min(cores, int(0.5 * avail // per)))
+
+
+class OraclePool:
+    """`workers` spawned processes evaluating the oracle, one system per job.
+    The kernel table is built (or loaded from its cache) once in this
+    process and then loaded by each worker in an untimed warm-up job."""
+
+    def __init__(self, workers):
+        import multiprocessing as mp
+        from oracle import vdw
+        vdw.Oracle()                       # build the table cache once, here
+        self.workers = workers
+        old = os.environ.get("OMP_NUM_THREADS")
+        os.environ["OMP_NUM_THREADS"] = "1"
+        try:
+            self.pool = mp.get_context("spawn").Pool(workers)
+        finally:
+            if old is None:
+                os.environ.pop("OMP_NUM_THREADS", None)
+            else:
+                os.environ["OMP_NUM_THREADS"] = old
+        tiny = np.full((4, 4, 4), 0.01)
+        self.pool.map(_oracle_job, [(-1, tiny, tiny * 0, np.eye(3) * 4, 1)] * workers, chunksize=1)
+
+    def run(self, jobs):
+        """Results by job index and the wall time of the whole set."""
+        order = sorted(range(len(jobs)), key=lambda k: -jobs[k][1].size)   # largest first
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_job, [jobs[k] for k in order], chunksize=1)
+        wall = time.perf_counter() - t0
+        return {r[0]: r for r in res}, wall
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def errors_vs_oracle(gpu, ref):
+    """Per system: |dE| (Ha) and max-norm relative errors of dedn, dedsigma."""
+    out = []
+    for i, (e, dn, ds) in enumerate(gpu):
+        _, re, rdn, rds, _ = ref[i]
+        out.append((abs(e - re), float(np.max(np.abs(dn - rdn)) / max(np.max(np.abs(rdn)), 1e-300)),
+                    float(np.max(np.abs(ds - rds)) / max(np.max(np.abs(rds)), 1e-300))))
+    a = np.array(out)
+    return {"systems": len(out), "max_abs_dE_Ha": float(a[:, 0].max()), "dedn_maxnorm_rel": float(a[:, 1].max()),
+            "dedsigma_maxnorm_rel": float(a[:, 2].max()), "median_abs_dE_Ha": float(np.median(a[:, 0]))}
+
+
 def run_reference(args, rank):
-    """The oracle (FP64 CPU, test infrastructure) timed on the host cores on a
-    bounded sample of the workload: one 48^3 grid of the same dimer density
-    per step (the full 96^3 batch would take minutes per step)."""
+    """The reference arm: the oracle (FP64 CPU, test infrastructure, as it
+    stands) on the host cores.  Each step evaluates a bounded sample of the
+    workload on a process pool: the 16 smallest systems of the 64-grid batch
+    (about 1.7 M grid points), or one 48^3 grid of a dimer density for the
+    dimer workload."""
     if rank != 0:
         return
     from paper_1703_06999_gb300 import inputs
-    from oracle import vdw
-    o = vdw.Oracle()
-    s = inputs.dimer(0, shape=(48, 48, 48), cell_lengths=CELL, functional=1)
-    n, sg = s.n.numpy(), s.sigma.numpy()
-    for _ in range(args.warmup):
-        o.energy_potential(n, sg, s.cell, 1)
-    t = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        o.energy_potential(n, sg, s.cell, 1)
-        t.append(time.perf_counter() - t0)
-    tot = sum(t)
-    val = s.npts * args.steps / tot
-    sample = "oracle on one 48^3 grid of the 96^3 dimer workload's density (18x18x24 bohr, seed 0, vdW-DF1) per step"
+    if args.workload == "dimer96_batch8":
+        systems = [inputs.dimer(0, shape=(48, 48, 48), cell_lengths=DIMER_CELL, functional=1)]
+        sample = "oracle on one 48^3 grid of the dimer density (18x18x24 bohr, seed 0) per step"
+    elif args.workload == WORKLOAD:
+        allsys = inputs.uneven_batch(0, count=64)
+        systems = sorted(allsys, key=lambda s: s.npts)[:16]
+        sample = ("oracle on the 16 smallest systems of the 64-grid batch (%d grid points) per step, one "
+                  "system per worker process" % sum(s.npts for s in systems))
+    else:
+        systems = make_workload(args.workload, 0, "cpu")
+        sample = "oracle on the whole workload per step"
+    jobs = [(i, s.n.numpy(), s.sigma.numpy(), s.cell, s.functional) for i, s in enumerate(systems)]
+    pts = sum(s.npts for s in systems)
+    workers = min(len(jobs), oracle_workers(max(s.npts for s in systems)))
+    pool = OraclePool(workers)
+    try:
+        for _ in range(args.warmup):
+            pool.run(jobs)
+        t = 0.0
+        for _ in range(args.steps):
+            _, w = pool.run(jobs)
+            t += w
+    finally:
+        pool.close()
+    val = pts * args.steps / t
     out = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": "grid pts/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD + " (oracle sample: 48^3)", "grid": [48, 48, 48]},
-        "cpu_baseline": {"value": val, "unit": "grid pts/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "data": "synthetic", "config": {"workload": args.workload + " (oracle sample)"},
+        "cpu_baseline": {"value": val, "unit": "grid pts/s", "cores": workers, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": "grid pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# serving stream
+# ---------------------------------------------------------------------------
 def serve_bench(B, inputs, torch, dev, local, seconds=3.0, rate=200.0, pool_entries=16):
     """Served form: Poisson arrivals (mean `rate` per second) of evaluations
     with grids from 48^3 to 160x192x224 (10-400 exponentials), FP32-mixed,
@@ -270,30 +430,51 @@ def serve_bench(B, inputs, torch, dev, local, seconds=3.0, rate=200.0, pool_entr
             "grids": sorted({tuple(p[0].shape) for p in pool})}
 
 
-def cpu_baseline():
-    """Oracle (as it stands) on one 96^3 system of the workload, on the host."""
-    from paper_1703_06999_gb300 import inputs
-    from oracle import vdw
-    o = vdw.Oracle()                      # table setup not timed
-    s = inputs.dimer(0, shape=SHAPE, cell_lengths=CELL, functional=1)
-    n, sg = s.n.numpy(), s.sigma.numpy()
-    t0 = time.perf_counter()
-    o.energy_potential(n, sg, s.cell, 1)
-    dt = time.perf_counter() - t0
-    return {"value": s.npts / dt, "unit": "grid pts/s", "cores": 1, "kind": "oracle",
-            "sample": "one 96^3 dimer system (seed 0, vdW-DF1), %.1f s" % dt}
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def timed_batch(B, torch, bt, ns, ss, dn, ds, en, sp, stream, steps, warmup, flush, world, dev, local):
+    """Warm-up, then exactly `steps` timed replays of the batch graph
+    (barrier + synchronize on both sides, L2 flushed between steps outside
+    the events); returns per-step ms, total ms (max over ranks) and clocks."""
+    for _ in range(warmup):
+        B.vdwgb_batch_calculate_device(bt, ns, ss, dn, ds, en, sp)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    torch.cuda.profiler.start()             # profilers started with capture off record the timed steps only
+    for k in range(steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        B.vdwgb_batch_calculate_device(bt, ns, ss, dn, ds, en, sp)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    clocks = clk.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = np.array([a.elapsed_time(b) for a, b in evs])
+    tot = float(step_ms.sum())
+    if world > 1:
+        tot = reduce_max(tot, dev)
+    return step_ms, tot, clocks
 
 
-def cpu_baseline_small(s):
-    """Oracle (as it stands) on the whole (small) workload system, on the host."""
-    from oracle import vdw
-    o = vdw.Oracle()
-    n, sg = s.n.cpu().numpy(), s.sigma.cpu().numpy()
-    t0 = time.perf_counter()
-    o.energy_potential(n, sg, s.cell, s.functional)
-    dt = time.perf_counter() - t0
-    return {"value": s.npts / dt, "unit": "grid pts/s", "cores": 1, "kind": "oracle",
-            "sample": "the whole %s system, %.2f s" % ("x".join(map(str, s.shape)), dt)}
+def stage_breakdown(B, torch, bt, ns, ss, dn, ds, en, sp, flush, steps):
+    """The same evaluation with each stage launched on its own between CUDA
+    events (one launch per stage over the whole batch), outside the timed
+    steps: per-launch ms of every stage."""
+    B.vdwgb_batch_set_timing(bt, True)
+    for _ in range(steps):
+        flush.zero_()
+        B.vdwgb_batch_calculate_device(bt, ns, ss, dn, ds, en, sp)
+    torch.cuda.synchronize()
+    stage_ms, ncalls = B.vdwgb_batch_stage_ms(bt)
+    B.vdwgb_batch_set_timing(bt, False)
+    return stage_ms / max(ncalls, 1)
 
 
 def main():
@@ -315,26 +496,15 @@ def main():
     B.vdwgb_set_autotune(True)   # tile shapes measured once per grid at init (outside the timed region)
 
     default = args.workload == WORKLOAD
-    if default:
-        nb = args.batch
-        seeds = rank_seeds(rank, nb)
-        systems = [inputs.dimer(seeds[i], shape=SHAPE, cell_lengths=CELL, functional=1 + i % 2,
-                                device=dev) for i in range(nb)]
-    elif args.workload == "cubic24":
-        systems = [inputs.small_cubic(rank, ngrid=24, device=dev)]
-    elif args.workload == "shell192":
-        systems = [inputs.ligand_shell(rank, device=dev)]
-    else:
-        systems = inputs.uneven_batch(rank, count=64, device=dev)
-    if not default:
-        nb = len(systems)
-        args.no_serve = True
-        if args.workload != "cubic24":
-            args.no_cpu_baseline = True
+    systems = make_workload(args.workload, rank, dev)
+    nb = len(systems)
     pts = sum(s.npts for s in systems)
+    if not default:
+        args.no_serve = True
+        args.no_extra = True
 
-    def make(prec):
-        return [B.Functional(s.shape, s.cell, s.functional, prec, device=local) for s in systems]
+    def make(prec, syss):
+        return [B.Functional(s.shape, s.cell, s.functional, prec, device=local) for s in syss]
 
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
@@ -342,58 +512,30 @@ def main():
     ds = [torch.empty_like(s.n) for s in systems]
     en = torch.zeros(nb, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 2x L2
-
-    f32 = make(B.FP32_MIXED)
-    plan_info = B.vdwgb_plan_info(f32[0].h)
-    bt = B.vdwgb_batch_new([f.h for f in f32])
     ns = [s.n for s in systems]
     ss = [s.sigma for s in systems]
-    for _ in range(args.warmup):
-        B.vdwgb_batch_calculate_device(bt, ns, ss, dn, ds, en, sp)
-    torch.cuda.synchronize()
+
+    f32 = make(B.FP32_MIXED, systems)
+    plan_info = B.vdwgb_plan_info(f32[0].h)
+    bt = B.vdwgb_batch_new([f.h for f in f32])
 
     # ---- timed region: FP32-mixed batched (the captured graph) ----------------
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    clk = ClockSampler(local)
-    torch.cuda.profiler.start()             # profilers started with capture off record the timed steps only
-    for k in range(args.steps):
-        flush.zero_()                       # L2 flushed between timed steps (outside the events)
-        evs[k][0].record(stream)
-        B.vdwgb_batch_calculate_device(bt, ns, ss, dn, ds, en, sp)
-        evs[k][1].record(stream)
-    torch.cuda.synchronize()
-    torch.cuda.profiler.stop()
-    clocks = clk.stop()
-    if world > 1:
-        torch.distributed.barrier()
-    step_ms = np.array([a.elapsed_time(b) for a, b in evs])
-    # per-stage breakdown, outside the timed region: the same steps with each
-    # stage launched on its own between CUDA events (one stage at a time, so
-    # each kernel's duration is its own)
-    B.vdwgb_batch_set_timing(bt, True)
-    for k in range(args.steps):
-        flush.zero_()
-        B.vdwgb_batch_calculate_device(bt, ns, ss, dn, ds, en, sp)
-    torch.cuda.synchronize()
-    stage_ms, ncalls = B.vdwgb_batch_stage_ms(bt)
-    B.vdwgb_batch_set_timing(bt, False)
-    tot_ms = float(step_ms.sum())
-    if world > 1:
-        tot_ms = reduce_max(tot_ms, dev)
+    step_ms, tot_ms, clocks = timed_batch(B, torch, bt, ns, ss, dn, ds, en, sp, stream, args.steps, args.warmup,
+                                          flush, world, dev, local)
     value = pts * world * args.steps / (tot_ms / 1000.0)
+    per_launch_ms = stage_breakdown(B, torch, bt, ns, ss, dn, ds, en, sp, flush, args.steps)
     if args.only_timed:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "grid pts/s", "n_gpus": world,
                               "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
                               "partial": "only the timed batched steps were run",
-                              "stage_ms_per_launch": (stage_ms / max(ncalls, 1)).tolist()}), flush=True)
+                              "stage_ms_per_launch": per_launch_ms.tolist()}), flush=True)
         return
-    e32 = en.cpu().numpy().copy()
-    dn32 = [x.clone() for x in dn]
-    ds32 = [x.clone() for x in ds]
+    # results of the FP32-mixed batch (the last timed call)
+    B.vdwgb_batch_calculate_device(bt, ns, ss, dn, ds, en, sp)
+    torch.cuda.synchronize()
+    B.vdwgb_device_status(local)
+    g32 = [(float(en[i]), dn[i].cpu().numpy(), ds[i].cpu().numpy()) for i in range(nb)]
 
     # ---- latency of single FP32 evaluations (one system at a time) -----------
     lat = []
@@ -407,30 +549,6 @@ def main():
         if i >= 20:
             lat.append(e1[0].elapsed_time(e1[1]))
     lat = np.array(lat)
-
-    # ---- FP64 plain, one system at a time, same inputs ------------------------
-    f64 = make(B.FP64)
-    k64 = max(2, args.steps // 4)
-    for i, f in enumerate(f64):
-        f.calculate_device(ns[i], ss[i], dn[i], ds[i], en[i:i + 1], sp)
-    torch.cuda.synchronize()
-    t64 = 0.0
-    for _ in range(k64):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for i, f in enumerate(f64):
-            f.calculate_device(ns[i], ss[i], dn[i], ds[i], en[i:i + 1], sp)
-        b.record(stream)
-        b.synchronize()
-        t64 += a.elapsed_time(b)
-    fp64_value = pts * k64 / (t64 / 1000.0)
-    e64 = en.cpu().numpy().copy()
-    err_e = float(np.max(np.abs(e32 - e64)))
-    err_n = max(float((dn32[i] - dn[i]).abs().max() / dn[i].abs().max()) for i in range(nb))
-    err_s = max(float((ds32[i] - ds[i]).abs().max() / ds[i].abs().max()) for i in range(nb))
-    for f in f64:
-        f.close()
 
     # ---- end to end through the host-pointer batch API ------------------------
     hn = [s.n.cpu().pin_memory().numpy() for s in systems]
@@ -448,48 +566,142 @@ def main():
         e2e_val = pts * world * ke / reduce_max(e2e_s, dev)
     h2d = sum(2 * s.npts * 8 for s in systems)
     d2h = sum(2 * s.npts * 8 for s in systems) + 8 * nb
-
-    # ---- roofline of the dominant stage --------------------------------------
-    names = [B.vdwgb_stage_name(i) for i in range(B.vdwgb_num_stages())]
-    per_launch_ms = stage_ms / max(ncalls, 1)
-    dom = int(np.argmax(per_launch_ms))
-    sb = {k: 0 for k in names}
-    for s in systems:
-        for k, v in stage_bytes(s.shape, 4).items():
-            sb[k] += v
-    pk, pk_kind = peaks()
-    achieved = sb[names[dom]] / (per_launch_ms[dom] / 1000.0) / 1e9
-    tps = MEASURED_TRAFFIC_PER_SYSTEM.get(names[dom]) if default else None
-    traffic = tps * nb if tps is not None else None
-    roof = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": pk["hbm_gbs"],
-            "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
-            "peak_source": pk_kind,
-            "traffic_source": "single-pass ncu capture of the 8-system launch (per system x systems)"
-                              if traffic is not None else None,
-            "stage_timing": "each stage launched on its own between CUDA events, outside the timed steps "
-                            "(the timed steps replay the captured graph, where the two halves of the "
-                            "batch overlap)",
-            "stages": {n: {"ms_per_launch": float(m), "alg_bytes": int(sb[n]),
-                           "GBps": (sb[n] / (m / 1000.0) / 1e9) if m > 0 else None}
-                       for n, m in zip(names, per_launch_ms)}}
-
     launches_per_step = B.vdwgb_batch_launches(bt)
     for f in f32:
         f.close()
     B.vdwgb_batch_free(bt)
+
+    # ---- FP64 plain, one system at a time, same inputs ------------------------
+    f64 = make(B.FP64, systems)
+    k64 = max(2, args.steps // 4)
+    for i, f in enumerate(f64):
+        f.calculate_device(ns[i], ss[i], dn[i], ds[i], en[i:i + 1], sp)
+    torch.cuda.synchronize()
+    B.vdwgb_device_status(local)
+    g64 = [(float(en[i]), dn[i].cpu().numpy(), ds[i].cpu().numpy()) for i in range(nb)]
+    t64 = 0.0
+    for _ in range(k64):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for i, f in enumerate(f64):
+            f.calculate_device(ns[i], ss[i], dn[i], ds[i], en[i:i + 1], sp)
+        b.record(stream)
+        b.synchronize()
+        t64 += a.elapsed_time(b)
+    fp64_value = pts * k64 / (t64 / 1000.0)
+    # FP64 stage breakdown (one launch per stage over the batch)
+    bt64 = B.vdwgb_batch_new([f.h for f in f64])
+    per_launch64 = stage_breakdown(B, torch, bt64, ns, ss, dn, ds, en, sp, flush, max(2, args.steps // 4))
+    B.vdwgb_batch_free(bt64)
+    for f in f64:
+        f.close()
+    err_32_64 = {"max_abs_dE_Ha": max(abs(a[0] - b[0]) for a, b in zip(g32, g64)),
+                 "dedn_maxnorm_rel": max(float(np.max(np.abs(a[1] - b[1])) / np.max(np.abs(b[1])))
+                                         for a, b in zip(g32, g64)),
+                 "dedsigma_maxnorm_rel": max(float(np.max(np.abs(a[2] - b[2])) / np.max(np.abs(b[2])))
+                                             for a, b in zip(g32, g64))}
+
+    # ---- rooflines of the stages ----------------------------------------------
+    names = [B.vdwgb_stage_name(i) for i in range(B.vdwgb_num_stages())]
+    dom = int(np.argmax(per_launch_ms))
+    sb = {k: 0 for k in names}
+    sb64 = {k: 0 for k in names}
+    nk_total = sum(s.shape[0] * s.shape[1] * (s.shape[2] // 2 + 1) for s in systems)
+    for s in systems:
+        for k, v in stage_bytes(s.shape, 4).items():
+            sb[k] += v
+        for k, v in stage_bytes(s.shape, 8).items():
+            sb64[k] += v
+    pk, pk_kind = peaks()
+    hbm = pk["hbm_gbs"]
+    achieved = sb[names[dom]] / (per_launch_ms[dom] / 1000.0) / 1e9
+    traffic = MEASURED_TRAFFIC.get(args.workload, {}).get(names[dom])
+    fp32x2_peak = B.vdwgb_alu_peak(1, local)
+    fp32_peak = B.vdwgb_alu_peak(0, local)
+    fp64_peak = B.vdwgb_alu_peak(2, local)
+    ic = names.index("contract")
+    c_gflops = 4.0 * CONTRACT_FMA2_PER_KPOINT * nk_total / (per_launch_ms[ic] / 1000.0) / 1e9
+    c64_gflops = 2.0 * CONTRACT_FMA64_PER_KPOINT * nk_total / (per_launch64[ic] / 1000.0) / 1e9
+    roof = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": hbm,
+            "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+            "peak_source": pk_kind + " (copy bandwidth, MEASURED_PEAKS.json hbm_gbs)",
+            "traffic_source": ("single-pass ncu capture of this launch" if traffic is not None
+                               else "no capture of the current kernel on this workload"),
+            "stage_timing": "each stage launched on its own between CUDA events (one launch over the whole "
+                            "batch), outside the timed steps; the timed steps replay the captured graph, where "
+                            "the batch runs as overlapping parts",
+            "stages": {n: {"ms_per_launch": float(m), "alg_bytes": int(sb[n]),
+                           "GBps": (sb[n] / (m / 1000.0) / 1e9) if m > 0 else None,
+                           "frac_hbm": (sb[n] / (m / 1000.0) / 1e9 / hbm) if m > 0 else None}
+                       for n, m in zip(names, per_launch_ms)}}
+    alu = {"peaks_gflops": {"fp32": fp32_peak, "fp32x2": fp32x2_peak, "fp64": fp64_peak,
+                            "source": "vdwgb_alu_peak: FMA chains, CUDA events, timed alone"},
+           "contract_fp32": {"achieved_gflops": c_gflops, "peak_gflops": fp32x2_peak,
+                             "frac": c_gflops / fp32x2_peak,
+                             "flops_per_kpoint": 4 * CONTRACT_FMA2_PER_KPOINT},
+           "contract_fp64": {"achieved_gflops": c64_gflops, "peak_gflops": fp64_peak,
+                             "frac": c64_gflops / fp64_peak, "ms_per_launch": float(per_launch64[ic]),
+                             "flops_per_kpoint": 2 * CONTRACT_FMA64_PER_KPOINT},
+           "fp64_stages_ms_per_launch": {n: float(m) for n, m in zip(names, per_launch64)}}
+
+    # ---- extra workload: the 8-system 96^3 dimer batch ------------------------
+    extra = None
+    if not args.no_extra:
+        dsys = make_workload("dimer96_batch8", rank, dev)
+        fd = make(B.FP32_MIXED, dsys)
+        btd = B.vdwgb_batch_new([f.h for f in fd])
+        dnd = [torch.empty_like(s.n) for s in dsys]
+        dsd = [torch.empty_like(s.n) for s in dsys]
+        end = torch.zeros(len(dsys), dtype=torch.float64, device=dev)
+        nsd, ssd = [s.n for s in dsys], [s.sigma for s in dsys]
+        stepd, totd, clkd = timed_batch(B, torch, btd, nsd, ssd, dnd, dsd, end, sp, stream, args.steps,
+                                        args.warmup, flush, world, dev, local)
+        pld = stage_breakdown(B, torch, btd, nsd, ssd, dnd, dsd, end, sp, flush, args.steps)
+        ptsd = sum(s.npts for s in dsys)
+        sbd = {k: 0 for k in names}
+        for s in dsys:
+            for k, v in stage_bytes(s.shape, 4).items():
+                sbd[k] += v
+        extra = {"dimer96_batch8": {
+            "value": ptsd * world * args.steps / (totd / 1000.0), "unit": "grid pts/s",
+            "ms_per_step": totd / args.steps, "clocks": clkd,
+            "stages": {n: {"ms_per_launch": float(m), "frac_hbm": (sbd[n] / (m / 1000.0) / 1e9 / hbm)
+                           if m > 0 else None} for n, m in zip(names, pld)}}}
+        B.vdwgb_batch_free(btd)
+        for f in fd:
+            f.close()
+
     serving = None if args.no_serve else serve_bench(B, inputs, torch, dev, local)
+
+    # ---- oracle: errors of both forms and the CPU baseline (all host cores) ---
+    err32 = err64 = cpu = None
+    if not args.no_oracle and rank == 0 and world == 1:
+        jobs = [(i, s.n.cpu().numpy(), s.sigma.cpu().numpy(), s.cell, s.functional) for i, s in enumerate(systems)]
+        workers = oracle_workers(max(s.npts for s in systems))
+        pool = OraclePool(workers)
+        try:
+            ref, wall = pool.run(jobs)
+        finally:
+            pool.close()
+        err32 = errors_vs_oracle(g32, ref)
+        err64 = errors_vs_oracle(g64, ref)
+        one = float(np.mean([ref[i][4] / systems[i].npts for i in ref]))    # seconds per point, one core
+        cpu = {"value": pts / wall, "unit": "grid pts/s", "cores": workers, "kind": "oracle",
+               "sample": "the whole %s workload (%d systems, %d grid points), one system per worker process"
+                         % (args.workload, nb, pts),
+               "one_core_value": 1.0 / one, "host_cores": os.cpu_count(),
+               "kernel_table": "built or loaded before timing"}
 
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "grid pts/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32-mixed (f64 q0 and energy sum)",
-            "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload,
-                       "grid": list(SHAPE) if default else sorted({tuple(s.shape) for s in systems}),
-                       "cell_bohr": list(CELL) if default else None, "systems": nb,
-                       "functionals": sorted({int(s.functional) for s in systems}), "precision": "fp32_mixed",
-                       "parallelism": "replicas", "plan": plan_info,
+                       "grids": sorted({tuple(s.shape) for s in systems}), "systems": nb, "grid_points": pts,
+                       "functionals": sorted({int(s.functional) for s in systems}), "precision": PRECISION_NOTE,
+                       "parallelism": "replicas", "plan_first_system": plan_info,
                        "l2": "flushed between timed steps (256 MB write); working set %.0f MB"
                              % (sum(s.shape[0] * s.shape[1] * (s.shape[2] // 2 + 1) * 160 + 48 * s.npts
                                     for s in systems) / 1e6)},
@@ -500,19 +712,22 @@ def main():
                                                   "p99": float(np.percentile(lat, 99)), "n": int(lat.size)},
                            "batch_step": {"p50": float(np.percentile(step_ms, 50)),
                                           "p99": float(np.percentile(step_ms, 99))}},
-            "error_fp32_vs_fp64": {"max_abs_dE_Ha": err_e, "dedn_maxnorm_rel": err_n,
-                                   "dedsigma_maxnorm_rel": err_s},
+            "error_vs_oracle": {"fp32_mixed": err32, "fp64": err64},
+            "error_fp32_vs_fp64": err_32_64,
             "roofline": roof,
+            "alu": alu,
             "e2e": {"value": e2e_val, "unit": "grid pts/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "api": "vdwgb_batch_calculate (host arrays, pinned)"},
             "gpu_launches": int(args.steps * launches_per_step),
             "clocks": clocks,
             "table_build_s": B.vdwgb_table_build_seconds(local),
         }
+        if cpu is not None:
+            out["cpu_baseline"] = cpu
+        if extra is not None:
+            out["extra"] = extra
         if serving is not None:
             out["serving"] = serving
-        if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline() if default else cpu_baseline_small(systems[0])
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -143,6 +143,18 @@ int vdwgb_device_status(int device);
  * work for this handle are not launched). */
 int vdwgb_launches_per_call(vdwgb_handle h);
 
+/* Measured arithmetic peak of the CUDA cores of `device` (the paper has no
+ * counterpart; this is the denominator of the ALU rooflines of the FP32
+ * stage kernels and of the FP64 form).  kind 0: scalar FP32 fused
+ * multiply-add; 1: two-lane FP32 fused multiply-add (fma.rn.f32x2, the form
+ * the FP32 contraction uses); 2: FP64 fused multiply-add.  *gflops receives
+ * 2 x (fused multiply-adds per second) / 1e9 from CUDA events around one
+ * launch of eight independent FMA chains per thread, eight 256-thread blocks
+ * per SM, after a warm-up launch (about 10 ms each).  Allocates 4 bytes of
+ * device memory for the duration of the call.  EINVAL for another kind or
+ * device. */
+int vdwgb_alu_peak(int device, int kind, double *gflops);
+
 /* ---- kernel table (setup, resident per device) ------------------------ */
 
 /* Copy the resident FP64 tables of `device` to host memory (building them if

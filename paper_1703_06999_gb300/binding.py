@@ -85,6 +85,7 @@ _SIGS.update({
     "vdwgb_server_free": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p)]),
     "vdwgb_calculate_noalloc": (ctypes.c_int, [ctypes.c_int] * 5 + [ctypes.c_void_p] * 7),
     "vdwgb_set_fused": (ctypes.c_int, [ctypes.c_int]),
+    "vdwgb_alu_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
 })
 
 
@@ -206,6 +207,13 @@ def vdwgb_footprint_bytes(shape, precision):
 
 def vdwgb_device_status(device=0):
     _ck(lib().vdwgb_device_status(int(device)), "vdwgb_device_status")
+
+
+def vdwgb_alu_peak(kind, device=0):
+    """Measured GFLOP/s of the CUDA cores: kind 0 FP32, 1 FP32x2, 2 FP64."""
+    g = ctypes.c_double(0.0)
+    _ck(lib().vdwgb_alu_peak(int(device), int(kind), ctypes.byref(g)), "vdwgb_alu_peak")
+    return g.value
 
 
 def vdwgb_batch_launches(b):

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvdwgb.so")
-SOURCES = ["capi.cu", "pipeline.cu", "table.cu", "serve.cu", "noalloc.cu", "plane.cu"]
+SOURCES = ["capi.cu", "pipeline.cu", "table.cu", "serve.cu", "noalloc.cu", "plane.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

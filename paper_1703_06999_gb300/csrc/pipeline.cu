@@ -1144,8 +1144,11 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
                 eacc = w * energy_f2(th, F);
                 store_rec_f2(reinterpret_cast<float4 *>(S.spec) + (size_t)idx * 10, F);
             }
-            for (int o = 16; o > 0; o >>= 1) eacc += __shfl_down_sync(0xffffffffu, eacc, o);
-            if (lane == 0) m.sys[b].epart[(size_t)mt.w * C32_CWARPS + cw] = f2d_bits(eacc);
+            // the warp's 32 k-point energies widened exactly (integer pipe) and
+            // summed in FP64: five FP64 additions per warp and chunk
+            double ed = f2d_bits(eacc);
+            for (int o = 16; o > 0; o >>= 1) ed += __shfl_down_sync(0xffffffffu, ed, o);
+            if (lane == 0) m.sys[b].epart[(size_t)mt.w * C32_CWARPS + cw] = ed;
             __syncwarp();                        // the warp's reads of half b are done
             if (lane == 0) mbar_arrive_local(&m.empty[b]);
         }
@@ -1378,11 +1381,12 @@ __device__ __forceinline__ void neumaier_add_f(float &s, float &c, float v) {
     s = t;
 }
 
-// T = double: FP64 partials, FP64 compensated sums.  T = float: the partials
-// (FP32 values widened exactly, one per chunk and consumer warp; or doubles
-// from the plane kernel, split into FP32 pairs) are summed as compensated
-// FP32 pairs on the FP32 pipe (GB300's FP64 pipe runs at 1/64 of the FP32
-// rate) and widened on the integer pipe at the end.
+// T = double: FP64 partials, FP64 compensated sums.  T = float: the FP64
+// partials (one per chunk and consumer warp: FP64 sums of the warp's FP32
+// k-point energies; or one per plane and cluster rank from the plane kernel)
+// are split into FP32 pairs and summed as compensated FP32 pairs on the FP32
+// pipe (GB300's FP64 pipe runs at 1/64 of the FP32 rate), then widened on
+// the integer pipe.
 template <typename T>
 __global__ void __launch_bounds__(EF_THREADS) k_efinish(const SysDev *__restrict__ sys, int nsys) {
     // one block per system: each thread sums a strided share of the partials,
@@ -1408,7 +1412,7 @@ __global__ void __launch_bounds__(EF_THREADS) k_efinish(const SysDev *__restrict
                 if constexpr (sizeof(T) == 8) {
                     neumaier_add(s, c, v[u]);
                 } else {
-                    const dfl d = df_from_bits(v[u]);   // lo = 0 for widened FP32 partials
+                    const dfl d = df_from_bits(v[u]);   // hi + lo: 48 of the partial's bits
                     neumaier_add_f(s, c, d.hi);
                     c += d.lo;
                 }
