@@ -517,6 +517,7 @@ def main():
 
     f32 = make(B.FP32_MIXED, systems)
     plan_info = B.vdwgb_plan_info(f32[0].h)
+    fused = any(B.vdwgb_plan_info(f.h)["cluster"] for f in f32)   # plane kernel in use
     bt = B.vdwgb_batch_new([f.h for f in f32])
 
     # ---- timed region: FP32-mixed batched (the captured graph) ----------------
@@ -613,6 +614,9 @@ def main():
             sb[k] += v
         for k, v in stage_bytes(s.shape, 8).items():
             sb64[k] += v
+    if not fused:
+        sb["plane"] = 0                   # not launched: separate y, x and contraction passes
+    sb64["plane"] = 0
     pk, pk_kind = peaks()
     hbm = pk["hbm_gbs"]
     achieved = sb[names[dom]] / (per_launch_ms[dom] / 1000.0) / 1e9
@@ -663,6 +667,8 @@ def main():
         for s in dsys:
             for k, v in stage_bytes(s.shape, 4).items():
                 sbd[k] += v
+        if not any(B.vdwgb_plan_info(f.h)["cluster"] for f in fd):
+            sbd["plane"] = 0
         extra = {"dimer96_batch8": {
             "value": ptsd * world * args.steps / (totd / 1000.0), "unit": "grid pts/s",
             "ms_per_step": totd / args.steps, "clocks": clkd,

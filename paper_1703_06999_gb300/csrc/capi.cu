@@ -415,9 +415,7 @@ static void set_tiles(vdwgb_data *h, int LZ, int LZi, int Wy, int Wx, int nby, i
     L.smem[1] = stage_smem(1, prec, ny, Wy, nby + L.work[1]);
     L.smem[2] = stage_smem(1, prec, nx, Wx, nbx + L.work[2]);
     for (int s = 0; s < 4; ++s) {
-        int per_sm = (int)((228 * 1024) / (L.smem[s] + 1024));
-        per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
-        const int cap = di.sms * per_sm;
+        const int cap = di.sms * stage_blocks_per_sm(s, prec, L.smem[s]);
         L.grid[s] = L.total[s] < cap ? L.total[s] : cap;
     }
 }
@@ -729,7 +727,9 @@ static int plan(vdwgb_data *h) {
         CK(dalloc(h, &h->kord, kord.size() * sizeof(unsigned short)), "plane k-point order");
         CK(dupload(h, h->kord, kord.data(), kord.size() * sizeof(unsigned short)), "plane k-point order");
     } else {
-        CK(dalloc(h, &h->kidx, kidx.size() * sizeof(unsigned)), "k-point order");
+        // four spare entries: the FP32 contraction copies 16-byte aligned
+        // supersets of a chunk's indices
+        CK(dalloc(h, &h->kidx, (kidx.size() + 4) * sizeof(unsigned)), "k-point order");
         CK(dupload(h, h->kidx, kidx.data(), kidx.size() * sizeof(unsigned)), "k-point order");
         CK(dalloc(h, &h->chunks, chunks.size() * sizeof(int4)), "chunks");
         CK(dupload(h, h->chunks, chunks.data(), chunks.size() * sizeof(int4)), "chunks");
@@ -769,9 +769,8 @@ static int plan(vdwgb_data *h) {
     L.total[4] = S.tiles[4];
     L.prefix[4] = h->dprefix + 8;
     {
-        int per_sm = (int)((228 * 1024) / (L.smem[4] + 1024));
-        per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
-        L.grid[4] = L.total[4] < di.sms * per_sm ? L.total[4] : di.sms * per_sm;
+        const int cap = di.sms * stage_blocks_per_sm(4, prec, L.smem[4]);
+        L.grid[4] = L.total[4] < cap ? L.total[4] : cap;
     }
     L.prefix[5] = h->dprefix + 10;
     L.total[5] = S.tiles[5];
@@ -1240,9 +1239,7 @@ int vdwgb::batch_launchset(vdwgb_data *const *hs, int count, SysDev *hdesc, int 
     for (int s = 0; s < NKIND; ++s) {
         L.prefix[s] = dprefix + s * (count + 1);
         L.total[s] = pre[s * (count + 1) + count];
-        int per_sm = (int)((228 * 1024) / (L.smem[s] + 1024));
-        per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
-        const int cap = di.sms * per_sm;
+        const int cap = di.sms * stage_blocks_per_sm(s, prec, L.smem[s]);
         L.grid[s] = L.total[s] < cap ? L.total[s] : cap;
     }
     // plane kernel: one cluster size per launch; grid in clusters

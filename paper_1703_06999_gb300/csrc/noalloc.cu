@@ -41,7 +41,7 @@ constexpr size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 constexpr size_t OFF_SPEC = 0;
 constexpr size_t OFF_REC = al256(OFF_SPEC + NA_MAX_KPOINTS * NQ * sizeof(cx<float>));
 constexpr size_t OFF_KIDX = al256(OFF_REC + NA_MAX_POINTS * sizeof(Rec<float>));
-constexpr size_t OFF_CHUNK = al256(OFF_KIDX + NA_MAX_KPOINTS * sizeof(unsigned));
+constexpr size_t OFF_CHUNK = al256(OFF_KIDX + (NA_MAX_KPOINTS + 4) * sizeof(unsigned));   // 4 spare entries
 constexpr size_t OFF_EPART = al256(OFF_CHUNK + NA_MAX_CHUNKS * sizeof(int4));
 constexpr size_t OFF_TW = al256(OFF_EPART + NA_MAX_CHUNKS * C32_CWARPS * sizeof(double));
 constexpr size_t OFF_DESC = al256(OFF_TW + 3 * NA_MAX_AXIS * sizeof(cx<float>));
@@ -301,9 +301,8 @@ extern "C" int vdwgb_calculate_noalloc(int device, int functional, int nx, int n
     L.smem[4] = contract_smem(1, NA_MAXSPAN);
     for (int k = 0; k < NKIND; ++k) {
         if (L.smem[k] > maxsmem - 1024) return fail(VDWGB_EINVAL, "tile does not fit shared memory");
-        int per_sm = (int)((228 * 1024) / (L.smem[k] + 1024));
-        per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
-        L.grid[k] = L.total[k] < sms * per_sm ? L.total[k] : sms * per_sm;
+        const int cap = sms * stage_blocks_per_sm(k, 1, L.smem[k]);
+        L.grid[k] = L.total[k] < cap ? L.total[k] : cap;
     }
     // uploads from host staging (pageable: each copy has read its source when it returns)
     const size_t nk = (size_t)nx * ny * nzh;

@@ -937,107 +937,49 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_contract(const 
 }
 
 // ---------------------------------------------------------------------------
-// FP32-mixed contraction (procedure step 3, as k_contract) with a producer
-// warp: warp 0 walks the chunk list (system, chunk record, k-point order) and
-// issues the loads of the next chunk — ten 16-byte cp.async copies per k-point
-// record and one bulk copy of the chunk's table rows — into the free half of
-// a double buffer, while the consumer warps compute the current chunk entirely
-// from shared memory (one k-point per thread, up to CHUNK32 = 320 per chunk).
+// FP32-mixed contraction (procedure step 3, as k_contract).  One producer
+// warp and C32_CWARPS consumer warps per block, one block per SM.  The
+// producer walks the block's chunks up to C32_RING - 1 chunks ahead of the
+// consumers; for each it writes a small descriptor (the system's grid and
+// metric, the chunk record) into a ring slot and issues two bulk copies into
+// the slot: the chunk's k-point indices and its kernel-table rows.  Each
+// consumer thread owns one k-point of a chunk and gathers that k-point's 20
+// theta values (one 160-byte record) straight from global memory into
+// registers one chunk ahead, so the gather of chunk i + 1 is in flight while
+// chunk i is computed.  Shared memory holds only the table rows (read by all
+// lanes of a warp at once), the indices and the descriptors.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-// arrive on bar when all earlier cp.async copies of this thread have landed
-__device__ __forceinline__ void cp_async_arrive(unsigned long long *bar) {
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __device__ __forceinline__ void mbar_arrive_local(unsigned long long *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-constexpr int C32_PWARPS = 2;               // producer warps (0..): record gathers split between them
-constexpr int C32_THREADS = 32 * (C32_PWARPS + C32_CWARPS);   // producer warps first, then consumers
+constexpr int C32_RING = 4;                                  // chunks in flight per block
+constexpr int C32_THREADS = 32 * (1 + C32_CWARPS);           // producer warp first, then the consumers
 static_assert(CHUNK32 == 32 * C32_CWARPS, "one k-point per consumer thread");
-constexpr int C32_ARRIVALS = 32 * C32_PWARPS + 1;   // cp.async arrivals of every producer lane + the row copy's
+constexpr int C32_KSLOT = CHUNK32 + 4;                       // indices per slot (a 16-byte aligned superset)
 
-struct C32Smem {
-    unsigned long long *full;   // [2] chunk landed
-    unsigned long long *empty;  // [2] chunk released by every consumer warp
-    SysDev *sys;                // [2] descriptor of the buffered chunk's system
-    int4 *meta;                 // [2] {count, first interval, intervals, chunk index in its system}
-    unsigned *idx;              // [2][CHUNK32] k-point indices
-    float4 *th;                 // [2][CHUNK32][10] theta records
-    float4 *rows;               // [2][SPAN32][NPAIR] table rows
+// What the consumers need of a chunk: its system's grid and metric, output
+// pointers, and the chunk record.
+struct __align__(16) C32Desc {
+    int nx, ny, nz, nzh, sx1, sy1;
+    int count;       // k-points in the chunk
+    int first;       // first kernel-table interval of the chunk
+    int span;        // staged intervals (0: the chunk lies beyond the table)
+    int lt;          // chunk index within its system (energy partials)
+    int koff;        // position of the chunk's first index in the slot's copy
+    int pad;
+    float gf[6];
+    const float4 *spec;
+    double *epart;
 };
 
-__host__ __device__ inline size_t c32_off_sys() { return 64; }
-__host__ __device__ inline size_t c32_off_meta() { return c32_off_sys() + 2 * ((sizeof(SysDev) + 15) / 16) * 16; }
-__host__ __device__ inline size_t c32_off_idx() { return c32_off_meta() + 2 * sizeof(int4); }
-__host__ __device__ inline size_t c32_off_th() { return c32_off_idx() + 2 * CHUNK32 * sizeof(unsigned); }
-__host__ __device__ inline size_t c32_off_rows() { return c32_off_th() + 2 * (size_t)CHUNK32 * 10 * sizeof(float4); }
-__host__ __device__ inline size_t c32_smem_bytes() { return c32_off_rows() + 2 * (size_t)SPAN32 * NPAIR * sizeof(float4); }
-
-__device__ __forceinline__ C32Smem c32_smem(unsigned char *smem) {
-    C32Smem m;
-    m.full = reinterpret_cast<unsigned long long *>(smem);
-    m.empty = m.full + 2;
-    m.sys = reinterpret_cast<SysDev *>(smem + c32_off_sys());
-    m.meta = reinterpret_cast<int4 *>(smem + c32_off_meta());
-    m.idx = reinterpret_cast<unsigned *>(smem + c32_off_idx());
-    m.th = reinterpret_cast<float4 *>(smem + c32_off_th());
-    m.rows = reinterpret_cast<float4 *>(smem + c32_off_rows());
-    return m;
+__host__ __device__ inline size_t c32_off_desc() { return 2 * C32_RING * sizeof(unsigned long long); }
+__host__ __device__ inline size_t c32_off_kidx() { return c32_off_desc() + C32_RING * sizeof(C32Desc); }
+__host__ __device__ inline size_t c32_off_rows() {
+    return (c32_off_kidx() + (size_t)C32_RING * C32_KSLOT * sizeof(unsigned) + 127) / 128 * 128;
 }
-
-// producer warp pw: loads of global chunk t into buffer half b (warp 0 also
-// the descriptor, the chunk record and the table rows; the record gathers
-// are split between the producer warps, 32-record row r to warp r mod C32_PWARPS)
-__device__ __forceinline__ void c32_produce(const SysDev *__restrict__ sys, const int *__restrict__ prefix, int nsys,
-                                            int t, int b, int &psi, const C32Smem &m, const float4 *__restrict__ tab) {
-    const int lane = threadIdx.x & 31, pw = threadIdx.x >> 5;
-    psi = advance_sys(prefix, nsys, t, psi);
-    const SysDev &S = sys[psi];
-    const int lt = t - prefix[psi];
-    const int4 c = S.chunks[lt];
-    if (pw == 0) {
-        // descriptor copy for the consumers
-        const int *src = reinterpret_cast<const int *>(&S);
-        int *dst = reinterpret_cast<int *>(&m.sys[b]);
-        for (int i = lane; i < (int)(sizeof(SysDev) / sizeof(int)); i += 32) dst[i] = src[i];
-        if (lane == 0) m.meta[b] = make_int4(c.y, c.z, c.w, lt);
-    }
-    const float4 *spec = reinterpret_cast<const float4 *>(S.spec);
-    unsigned kidx[CHUNK32 / 32];
-#pragma unroll
-    for (int r = 0; r < CHUNK32 / 32; ++r) {
-        const int k = lane + 32 * r;
-        kidx[r] = (k < c.y && r % C32_PWARPS == pw) ? S.kidx[c.x + k] : 0u;
-    }
-#pragma unroll
-    for (int r = 0; r < CHUNK32 / 32; ++r) {
-        const int k = lane + 32 * r;
-        if (k < c.y && r % C32_PWARPS == pw) {
-            m.idx[b * CHUNK32 + k] = kidx[r];
-            const float4 *src = spec + (size_t)kidx[r] * 10;
-            float4 *dst = m.th + ((size_t)b * CHUNK32 + k) * 10;
-#pragma unroll
-            for (int a = 0; a < 10; ++a) cp_async16(dst + a, src + a);
-        }
-    }
-    cp_async_arrive(&m.full[b]);
-    __syncwarp();                                  // descriptor, meta and indices written
-    if (pw == 0 && lane == 0) {
-        const int span = min(c.w, SPAN32);
-        if (span > 0) {
-            const unsigned bytes = (unsigned)(span * NPAIR * sizeof(float4));
-            fence_proxy_async();
-            mbar_expect_tx(&m.full[b], bytes);
-            bulk_g2s(m.rows + (size_t)b * SPAN32 * NPAIR, tab + (size_t)c.z * NPAIR, bytes, &m.full[b]);
-        } else {
-            mbar_arrive_local(&m.full[b]);
-        }
-    }
+__host__ __device__ inline size_t c32_smem_bytes() {
+    return c32_off_rows() + (size_t)C32_RING * SPAN32 * NPAIR * sizeof(float4);
 }
 
 // |k| of half-spectrum index idx (positions of the x / y passes mapped to
@@ -1045,89 +987,162 @@ __device__ __forceinline__ void c32_produce(const SysDev *__restrict__ sys, cons
 // interval j and offset tt in [0, 1), exactly as the host sorted it; weight
 // 1 on the kz = 0 and Nyquist planes, 2 elsewhere (the other half of the
 // spectrum)
-__device__ __forceinline__ void c32_kpoint(const SysDev &S, unsigned idx, int &j, float &tt, float &weight) {
-    const int nx = S.nx, ny = S.ny, nz = S.nz, nzh = S.nzh;
+__device__ __forceinline__ void c32_kpoint(const C32Desc &D, unsigned idx, int &j, float &tt, float &weight) {
+    const int nx = D.nx, ny = D.ny, nz = D.nz, nzh = D.nzh;
     const int kz = (int)(idx % (unsigned)nzh);
     const int rest = (int)(idx / (unsigned)nzh);
-    const int y = axis_freq(rest % ny, ny, S.sy1), x = axis_freq(rest / ny, nx, S.sx1);
+    const int y = axis_freq(rest % ny, ny, D.sy1), x = axis_freq(rest / ny, nx, D.sx1);
     const bool nyq_z = (nz % 2 == 0) && (kz == nz / 2);
-    kpoint_interval32(S.gf, fold(x, nx), fold(y, ny), nyq_z ? -kz : kz, (nx % 2 == 0) && (x == nx / 2),
+    kpoint_interval32(D.gf, fold(x, nx), fold(y, ny), nyq_z ? -kz : kz, (nx % 2 == 0) && (x == nx / 2),
                       (ny % 2 == 0) && (y == ny / 2), nyq_z, j, tt);
     weight = (kz == 0 || nyq_z) ? 1.f : 2.f;
 }
 
-// The producer warps fill the two buffer halves in turn (chunk i into half i & 1, after
-// every consumer warp has released that half's previous chunk); the consumer
-// warps run through the chunks without block-wide barriers, each writing one
-// energy partial per chunk (epart[chunk * C32_CWARPS + warp]).
+// consumer side: wait (bounded) for chunk i's slot b, then gather this
+// thread's k-point record of that chunk (consumer thread k) into nxt and
+// its index into idx_n; false if the wait ran out (flag and status set)
+__device__ __forceinline__ bool c32_gather(int i, int b, int k, int lane, unsigned long long *full, const C32Desc *desc,
+                                           const unsigned *kslot, int *err, int *s_failed, f2_t (&nxt)[NQ],
+                                           unsigned &idx_n) {
+    const bool ok = !*(volatile int *)s_failed && mbar_wait(&full[b], (i / C32_RING) & 1);
+    if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) {
+            atomicExch(err, 1);
+            *s_failed = 1;
+        }
+        return false;
+    }
+    const C32Desc &D = desc[b];
+    if (k < D.count) {
+        idx_n = kslot[(size_t)b * C32_KSLOT + D.koff + k];
+        const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(D.spec + (size_t)idx_n * 10);
+#pragma unroll
+        for (int m = 0; m < NQ / 2; ++m) {
+            const ulonglong2 q = src[m];
+            nxt[2 * m] = q.x;
+            nxt[2 * m + 1] = q.y;
+        }
+    }
+    return true;
+}
+
 __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__restrict__ sys, const int *__restrict__ prefix,
                                                              int nsys, int total, const float4 *__restrict__ tab,
                                                              int *__restrict__ err) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const C32Smem m = c32_smem(smem);
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(smem);
+    unsigned long long *empty = full + C32_RING;
+    C32Desc *desc = reinterpret_cast<C32Desc *>(smem + c32_off_desc());
+    unsigned *kslot = reinterpret_cast<unsigned *>(smem + c32_off_kidx());
+    float4 *rows = reinterpret_cast<float4 *>(smem + c32_off_rows());
     __shared__ int s_failed;
+    const int lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         s_failed = 0;
-        for (int h = 0; h < 2; ++h) {
-            mbar_init(&m.full[h], C32_ARRIVALS);
-            mbar_init(&m.empty[h], C32_CWARPS);
+        for (int r = 0; r < C32_RING; ++r) {
+            mbar_init(&full[r], 1);
+            mbar_init(&empty[r], C32_CWARPS);
         }
         fence_mbar_init();
     }
     __syncthreads();
-    if (threadIdx.x < 32 * C32_PWARPS) {
-        // producers
-        int psi = -1;
-        int last0 = -1, last1 = -1;   // last chunk (local count) issued into each half
-        int i = 0;
-        for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
-            const int b = i & 1;
-            if (i >= 2) {
-                // chunk i - 2 released: completion (i - 2) / 2 of empty[b]
-                const bool ok = mbar_wait(&m.empty[b], ((i >> 1) + 1) & 1u);
+    if (threadIdx.x < 32) {
+        // ---- producer warp: descriptors and bulk copies, C32_RING - 1 chunks ahead
+        int4 cl = make_int4(0, 0, 0, 0);   // this lane's share of the next 32 chunk records
+        int sl = 0, ltl = 0;
+        int psi = -1;                      // system of the cached fields below (lane 0)
+        C32Desc d;
+        const unsigned *gkidx = nullptr;
+        int issued = 0;
+        for (int t = blockIdx.x, i = 0, b = 0; t < total; t += gridDim.x, ++i, b = b + 1 == C32_RING ? 0 : b + 1) {
+            if ((i & 31) == 0) {
+                // chunk records of chunks i .. i + 31 of this block, one per lane
+                const int tl = t + lane * gridDim.x;
+                if (tl < total) {
+                    sl = find_sys(prefix, nsys, tl);
+                    ltl = tl - prefix[sl];
+                    cl = sys[sl].chunks[ltl];
+                }
+            }
+            const int src = i & 31;
+            const int s = __shfl_sync(0xffffffffu, sl, src);
+            const int lt = __shfl_sync(0xffffffffu, ltl, src);
+            const int cx = __shfl_sync(0xffffffffu, cl.x, src), cy = __shfl_sync(0xffffffffu, cl.y, src);
+            const int cz = __shfl_sync(0xffffffffu, cl.z, src), cwv = __shfl_sync(0xffffffffu, cl.w, src);
+            if (i >= C32_RING) {
+                // slot b released by every consumer warp (its previous use, chunk i - C32_RING)
+                const bool ok = mbar_wait(&empty[b], ((i / C32_RING) - 1) & 1);
                 if (!__all_sync(0xffffffffu, ok) || *(volatile int *)&s_failed) {
-                    if ((threadIdx.x & 31) == 0) {
+                    if (lane == 0) {
                         atomicExch(err, 1);
                         s_failed = 1;
                     }
                     break;
                 }
             }
-            c32_produce(sys, prefix, nsys, t, b, psi, m, tab);
-            if (b) last1 = i;
-            else last0 = i;
-        }
-        // every copy issued has landed before the block exits
-        cp_async_wait_all();
-        if (threadIdx.x == 0) {
-            if (last0 >= 0) mbar_wait(&m.full[0], (last0 >> 1) & 1u);
-            if (last1 >= 0) mbar_wait(&m.full[1], (last1 >> 1) & 1u);
-        }
-    } else {
-        const int cw = (threadIdx.x >> 5) - C32_PWARPS;   // consumer warp
-        const int lane = threadIdx.x & 31;
-        int i = 0;
-        for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
-            const int b = i & 1;
-            const bool ok = !*(volatile int *)&s_failed && mbar_wait(&m.full[b], (i >> 1) & 1u);
-            if (!__all_sync(0xffffffffu, ok)) {
-                if (lane == 0) {
-                    atomicExch(err, 1);
-                    s_failed = 1;
+            if (lane == 0) {
+                if (s != psi) {
+                    const SysDev &S = sys[s];
+                    d.nx = S.nx;
+                    d.ny = S.ny;
+                    d.nz = S.nz;
+                    d.nzh = S.nzh;
+                    d.sx1 = S.sx1;
+                    d.sy1 = S.sy1;
+                    for (int q = 0; q < 6; ++q) d.gf[q] = S.gf[q];
+                    d.spec = reinterpret_cast<const float4 *>(S.spec);
+                    d.epart = S.epart;
+                    gkidx = S.kidx;
+                    psi = s;
                 }
-                break;
+                const int koff = cx & 3;
+                d.count = cy;
+                d.first = cz;
+                d.span = min(cwv, SPAN32);
+                d.lt = lt;
+                d.koff = koff;
+                d.pad = 0;
+                desc[b] = d;
+                // indices: a 16-byte aligned superset of [cx, cx + cy) (the
+                // k-point order is allocated with 4 spare entries)
+                const unsigned kbytes = (unsigned)(((koff + cy) * 4 + 15) & ~15);
+                const unsigned rbytes = (unsigned)(d.span * NPAIR * sizeof(float4));
+                fence_proxy_async();
+                mbar_expect_tx(&full[b], kbytes + rbytes);
+                bulk_g2s(kslot + (size_t)b * C32_KSLOT, gkidx + (cx - koff), kbytes, &full[b]);
+                if (rbytes) bulk_g2s(rows + (size_t)b * SPAN32 * NPAIR, tab + (size_t)cz * NPAIR, rbytes, &full[b]);
             }
-            float eacc = 0.f;
-            const int4 mt = m.meta[b];
-            const int k = threadIdx.x - 32 * C32_PWARPS;
-            if (k < mt.x) {
-                const SysDev &S = m.sys[b];
-                const unsigned idx = m.idx[b * CHUNK32 + k];
+            issued = i + 1;
+            __syncwarp();
+        }
+        // every copy issued has landed before the block exits (the last use of each slot)
+        if (lane == 0)
+            for (int i = issued - C32_RING > 0 ? issued - C32_RING : 0; i < issued; ++i)
+                mbar_wait(&full[i % C32_RING], (i / C32_RING) & 1);
+    } else {
+        // ---- consumer warps: one k-point per thread
+        const int cw = (threadIdx.x >> 5) - 1;
+        const int k = threadIdx.x - 32;
+        f2_t th[NQ];
+        unsigned idx = 0;
+        bool have = false;
+        bool running = blockIdx.x < total && c32_gather(0, 0, k, lane, full, desc, kslot, err, &s_failed, th, idx);
+        for (int t = blockIdx.x, i = 0, b = 0; running && t < total;
+             t += gridDim.x, ++i, b = b + 1 == C32_RING ? 0 : b + 1) {
+            have = k < desc[b].count;
+            const unsigned idx_c = idx;
+            // the next chunk's records, in flight while this chunk is computed
+            f2_t nx[NQ];
+            const int bn = b + 1 == C32_RING ? 0 : b + 1;
+            if (t + gridDim.x < total)
+                running = c32_gather(i + 1, bn, k, lane, full, desc, kslot, err, &s_failed, nx, idx);
+            const C32Desc &D = desc[b];
+            double ed = 0.0;
+            if (have) {
                 int j;
                 float tt, w;
-                c32_kpoint(S, idx, j, tt, w);
-                f2_t th[NQ], F[NQ];
-                load_rec_f2(m.th + ((size_t)b * CHUNK32 + k) * 10, th);
+                c32_kpoint(D, idx_c, j, tt, w);
+                f2_t F[NQ];
 #pragma unroll
                 for (int a = 0; a < NQ; ++a) F[a] = 0ull;
                 // the interval's row is staged: the host sorted this k-point into
@@ -1135,29 +1150,30 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
                 // table).  A row outside the staged range would break that
                 // invariant: skipped and reported (status 2), never read.
                 if (j < NK - 1) {
-                    const int r = j - mt.y;
-                    if (r >= 0 && r < min(mt.z, SPAN32))
-                        contract_row<false>(m.rows + ((size_t)b * SPAN32 + r) * NPAIR, tt, th, F);
+                    const int r = j - D.first;
+                    if (r >= 0 && r < D.span)
+                        contract_row<false>(rows + ((size_t)b * SPAN32 + r) * NPAIR, tt, th, F);
                     else
                         atomicExch(err, 2);
                 }
-                eacc = w * energy_f2(th, F);
-                store_rec_f2(reinterpret_cast<float4 *>(S.spec) + (size_t)idx * 10, F);
+                ed = f2d_bits(w * energy_f2(th, F));
+                store_rec_f2(const_cast<float4 *>(D.spec) + (size_t)idx_c * 10, F);
             }
-            // the warp's 32 k-point energies widened exactly (integer pipe) and
+            // the warp's k-point energies widened exactly (integer pipe) and
             // summed in FP64: five FP64 additions per warp and chunk
-            double ed = f2d_bits(eacc);
             for (int o = 16; o > 0; o >>= 1) ed += __shfl_down_sync(0xffffffffu, ed, o);
-            if (lane == 0) m.sys[b].epart[(size_t)mt.w * C32_CWARPS + cw] = ed;
-            __syncwarp();                        // the warp's reads of half b are done
-            if (lane == 0) mbar_arrive_local(&m.empty[b]);
+            if (lane == 0) D.epart[(size_t)D.lt * C32_CWARPS + cw] = ed;
+            __syncwarp();                        // the warp's reads of slot b are done
+            if (lane == 0) mbar_arrive_local(&empty[b]);
+#pragma unroll
+            for (int a = 0; a < NQ; ++a) th[a] = nx[a];
         }
     }
     __syncthreads();
     if (threadIdx.x == 0)
-        for (int h = 0; h < 2; ++h) {
-            mbar_inval(&m.full[h]);
-            mbar_inval(&m.empty[h]);
+        for (int r = 0; r < C32_RING; ++r) {
+            mbar_inval(&full[r]);
+            mbar_inval(&empty[r]);
         }
 }
 
