@@ -398,8 +398,11 @@ static void set_tiles(vdwgb_data *h, int LZ, int LZi, int Wy, int Wx, int nby, i
     L.twmax[1] = ny;
     L.twmax[2] = nx;
     L.bufelems[0] = 0;
-    L.bufelems[3] = LZi * nzh * NQ;
-    L.recelems = LZi * nz;
+    // z-inverse: FP32 axes with an in-place split read the spectrum and the
+    // records straight from global memory (nothing staged); others stage tiles
+    const bool zdirect = prec == VDWGB_FP32_MIXED && S.sz1;
+    L.bufelems[3] = zdirect ? 0 : LZi * nzh * NQ;
+    L.recelems = zdirect ? 0 : LZi * nz;
     L.abelems = nz * z_ld(LZi);
     L.bufelems[1] = ny * Wy * NQ;
     L.bufelems[2] = nx * Wx * NQ;
@@ -727,9 +730,7 @@ static int plan(vdwgb_data *h) {
         CK(dalloc(h, &h->kord, kord.size() * sizeof(unsigned short)), "plane k-point order");
         CK(dupload(h, h->kord, kord.data(), kord.size() * sizeof(unsigned short)), "plane k-point order");
     } else {
-        // four spare entries: the FP32 contraction copies 16-byte aligned
-        // supersets of a chunk's indices
-        CK(dalloc(h, &h->kidx, (kidx.size() + 4) * sizeof(unsigned)), "k-point order");
+        CK(dalloc(h, &h->kidx, kidx.size() * sizeof(unsigned)), "k-point order");
         CK(dupload(h, h->kidx, kidx.data(), kidx.size() * sizeof(unsigned)), "k-point order");
         CK(dalloc(h, &h->chunks, chunks.size() * sizeof(int4)), "chunks");
         CK(dupload(h, h->chunks, chunks.data(), chunks.size() * sizeof(int4)), "chunks");
@@ -1206,23 +1207,39 @@ static int batch_parts(vdwgb_data *const *hs, int count, int *start) {
 int vdwgb::batch_launchset(vdwgb_data *const *hs, int count, SysDev *hdesc, int *pre, const SysDev *ddesc,
                            const int *dprefix, LaunchSet &L) {
     std::memset(&L, 0, sizeof L);
-    for (int s = 0; s < NKIND; ++s) pre[s * (count + 1)] = 0;
-    for (int i = 0; i < count; ++i) {
-        hdesc[i] = hs[i]->hsys;
-        for (int s = 0; s < NKIND; ++s) {
-            pre[s * (count + 1) + i + 1] = pre[s * (count + 1) + i] + hs[i]->hsys.tiles[s];
-            if (hs[i]->ls.smem[s] > L.smem[s]) L.smem[s] = hs[i]->ls.smem[s];
-            if (hs[i]->ls.twmax[s] > L.twmax[s]) L.twmax[s] = hs[i]->ls.twmax[s];
-            if (hs[i]->ls.bufelems[s] > L.bufelems[s]) L.bufelems[s] = hs[i]->ls.bufelems[s];
-            if (i == 0 || hs[i]->ls.nbuf[s] < L.nbuf[s]) L.nbuf[s] = hs[i]->ls.nbuf[s];
-            if (hs[i]->ls.work[s] > L.work[s]) L.work[s] = hs[i]->ls.work[s];
-        }
-        if (hs[i]->ls.recelems > L.recelems) L.recelems = hs[i]->ls.recelems;
-        if (hs[i]->ls.abelems > L.abelems) L.abelems = hs[i]->ls.abelems;
-    }
     const int device = hs[0]->device;
     const int prec = hs[0]->prec;
     DevInfo &di = g_dev[device];
+    const size_t lim = di.maxsmem - 1024;
+    // z-inverse: the launch runs the direct form only if every system does;
+    // otherwise the direct systems' tiles are staged too, with their lines
+    // per tile lowered (in the batch's copies of the descriptors) until a
+    // staged tile fits shared memory
+    bool zdirect = true;
+    for (int i = 0; i < count; ++i) zdirect = zdirect && hs[i]->ls.bufelems[3] == 0;
+    for (int i = 0; i < count; ++i) {
+        hdesc[i] = hs[i]->hsys;
+        SysDev &D = hdesc[i];
+        if (!zdirect && hs[i]->ls.bufelems[3] == 0) {
+            int l = D.LZi;
+            while (l > 1 && zinv_smem(prec, D.nz, l * D.nzh * NQ, l * D.nz, D.nz * z_ld(l), 1) > lim) --l;
+            D.LZi = l;
+            D.tiles[3] = (D.nx * D.ny + l - 1) / l;
+        }
+        for (int s = 0; s < NKIND; ++s) {
+            pre[s * (count + 1) + i + 1] = pre[s * (count + 1) + i] + D.tiles[s];
+            if (hs[i]->ls.smem[s] > L.smem[s]) L.smem[s] = hs[i]->ls.smem[s];
+            if (hs[i]->ls.twmax[s] > L.twmax[s]) L.twmax[s] = hs[i]->ls.twmax[s];
+            if (s != 3 && hs[i]->ls.bufelems[s] > L.bufelems[s]) L.bufelems[s] = hs[i]->ls.bufelems[s];
+            if (i == 0 || hs[i]->ls.nbuf[s] < L.nbuf[s]) L.nbuf[s] = hs[i]->ls.nbuf[s];
+            if (hs[i]->ls.work[s] > L.work[s]) L.work[s] = hs[i]->ls.work[s];
+        }
+        if (!zdirect) {
+            L.bufelems[3] = std::max(L.bufelems[3], D.LZi * D.nzh * NQ);
+            L.recelems = std::max(L.recelems, D.LZi * D.nz);
+        }
+        L.abelems = std::max(L.abelems, D.nz * z_ld(D.LZi));
+    }
     L.sys = ddesc;
     L.nsys = count;
     L.err = hs[0]->ls.err;
@@ -1233,7 +1250,6 @@ int vdwgb::batch_launchset(vdwgb_data *const *hs, int count, SysDev *hdesc, int 
     for (int s = 1; s <= 2; ++s)
         L.smem[s] = xy_smem_bytes(L.twmax[s], L.bufelems[s], L.nbuf[s] + L.work[s], c);
     L.smem[3] = zinv_smem(prec, L.twmax[3], L.bufelems[3], L.recelems, L.abelems, 1 + L.work[3]);
-    const size_t lim = di.maxsmem - 1024;
     if (L.smem[1] > lim || L.smem[2] > lim || L.smem[3] > lim)
         return fail(VDWGB_EINVAL, "batch: combined row tiles exceed shared memory");
     for (int s = 0; s < NKIND; ++s) {

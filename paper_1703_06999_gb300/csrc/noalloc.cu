@@ -41,7 +41,7 @@ constexpr size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 constexpr size_t OFF_SPEC = 0;
 constexpr size_t OFF_REC = al256(OFF_SPEC + NA_MAX_KPOINTS * NQ * sizeof(cx<float>));
 constexpr size_t OFF_KIDX = al256(OFF_REC + NA_MAX_POINTS * sizeof(Rec<float>));
-constexpr size_t OFF_CHUNK = al256(OFF_KIDX + (NA_MAX_KPOINTS + 4) * sizeof(unsigned));   // 4 spare entries
+constexpr size_t OFF_CHUNK = al256(OFF_KIDX + NA_MAX_KPOINTS * sizeof(unsigned));
 constexpr size_t OFF_EPART = al256(OFF_CHUNK + NA_MAX_CHUNKS * sizeof(int4));
 constexpr size_t OFF_TW = al256(OFF_EPART + NA_MAX_CHUNKS * C32_CWARPS * sizeof(double));
 constexpr size_t OFF_DESC = al256(OFF_TW + 3 * NA_MAX_AXIS * sizeof(cx<float>));
@@ -284,8 +284,8 @@ extern "C" int vdwgb_calculate_noalloc(int device, int functional, int nx, int n
     L.twmax[0] = L.twmax[3] = nz;
     L.twmax[1] = ny;
     L.twmax[2] = nx;
-    L.bufelems[3] = S.LZi * nzh * NQ;
-    L.recelems = S.LZi * nz;
+    L.bufelems[3] = S.sz1 ? 0 : S.LZi * nzh * NQ;     // split z axes: direct z-inverse, nothing staged
+    L.recelems = S.sz1 ? 0 : S.LZi * nz;
     L.abelems = nz * z_ld(S.LZi);
     L.bufelems[1] = ny * S.Wy * NQ;
     L.bufelems[2] = nx * S.Wx * NQ;

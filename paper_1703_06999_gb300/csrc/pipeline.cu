@@ -939,24 +939,25 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_contract(const 
 // ---------------------------------------------------------------------------
 // FP32-mixed contraction (procedure step 3, as k_contract).  One producer
 // warp and C32_CWARPS consumer warps per block, one block per SM.  The
-// producer walks the block's chunks up to C32_RING - 1 chunks ahead of the
-// consumers; for each it writes a small descriptor (the system's grid and
-// metric, the chunk record) into a ring slot and issues two bulk copies into
-// the slot: the chunk's k-point indices and its kernel-table rows.  Each
-// consumer thread owns one k-point of a chunk and gathers that k-point's 20
-// theta values (one 160-byte record) straight from global memory into
-// registers one chunk ahead, so the gather of chunk i + 1 is in flight while
-// chunk i is computed.  Shared memory holds only the table rows (read by all
-// lanes of a warp at once), the indices and the descriptors.
+// producer stages the block's chunks into a double buffer: for each chunk a
+// small descriptor (the system's grid and metric, the chunk record), the
+// k-point indices, one 160-byte bulk copy per k-point record (the 20 theta
+// values) and one bulk copy of the chunk's kernel-table rows.  It reads the
+// chunk records of its next 32 chunks at once (one per lane) and the indices
+// of the next chunk into registers before that chunk's buffer is free, so a
+// freed buffer is refilled by bulk copies alone.  Each consumer thread
+// computes one k-point from shared memory and writes F over theta in global
+// memory.  Records sit 176 bytes apart in shared memory, so the ten 16-byte
+// loads of a warp's records are free of bank conflicts.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void mbar_arrive_local(unsigned long long *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-constexpr int C32_RING = 4;                                  // chunks in flight per block
 constexpr int C32_THREADS = 32 * (1 + C32_CWARPS);           // producer warp first, then the consumers
 static_assert(CHUNK32 == 32 * C32_CWARPS, "one k-point per consumer thread");
-constexpr int C32_KSLOT = CHUNK32 + 4;                       // indices per slot (a 16-byte aligned superset)
+constexpr int C32_KPL = CHUNK32 / 32;                        // k-points per producer lane and chunk
+constexpr int C32_RSTRIDE = 11;                              // float4 per staged record (10 used)
 
 // What the consumers need of a chunk: its system's grid and metric, output
 // pointers, and the chunk record.
@@ -966,21 +967,19 @@ struct __align__(16) C32Desc {
     int first;       // first kernel-table interval of the chunk
     int span;        // staged intervals (0: the chunk lies beyond the table)
     int lt;          // chunk index within its system (energy partials)
-    int koff;        // position of the chunk's first index in the slot's copy
-    int pad;
+    int pad0, pad1;
     float gf[6];
-    const float4 *spec;
+    float4 *spec;
     double *epart;
 };
 
-__host__ __device__ inline size_t c32_off_desc() { return 2 * C32_RING * sizeof(unsigned long long); }
-__host__ __device__ inline size_t c32_off_kidx() { return c32_off_desc() + C32_RING * sizeof(C32Desc); }
+__host__ __device__ inline size_t c32_off_desc() { return 64; }
+__host__ __device__ inline size_t c32_off_idx() { return c32_off_desc() + 2 * sizeof(C32Desc); }
+__host__ __device__ inline size_t c32_off_rec() { return (c32_off_idx() + 2 * CHUNK32 * sizeof(unsigned) + 127) / 128 * 128; }
 __host__ __device__ inline size_t c32_off_rows() {
-    return (c32_off_kidx() + (size_t)C32_RING * C32_KSLOT * sizeof(unsigned) + 127) / 128 * 128;
+    return c32_off_rec() + 2 * (size_t)CHUNK32 * C32_RSTRIDE * sizeof(float4);
 }
-__host__ __device__ inline size_t c32_smem_bytes() {
-    return c32_off_rows() + (size_t)C32_RING * SPAN32 * NPAIR * sizeof(float4);
-}
+__host__ __device__ inline size_t c32_smem_bytes() { return c32_off_rows() + 2 * (size_t)SPAN32 * NPAIR * sizeof(float4); }
 
 // |k| of half-spectrum index idx (positions of the x / y passes mapped to
 // frequencies, Nyquist planes with the convention of the FP64 path) as table
@@ -998,65 +997,39 @@ __device__ __forceinline__ void c32_kpoint(const C32Desc &D, unsigned idx, int &
     weight = (kz == 0 || nyq_z) ? 1.f : 2.f;
 }
 
-// consumer side: wait (bounded) for chunk i's slot b, then gather this
-// thread's k-point record of that chunk (consumer thread k) into nxt and
-// its index into idx_n; false if the wait ran out (flag and status set)
-__device__ __forceinline__ bool c32_gather(int i, int b, int k, int lane, unsigned long long *full, const C32Desc *desc,
-                                           const unsigned *kslot, int *err, int *s_failed, f2_t (&nxt)[NQ],
-                                           unsigned &idx_n) {
-    const bool ok = !*(volatile int *)s_failed && mbar_wait(&full[b], (i / C32_RING) & 1);
-    if (!__all_sync(0xffffffffu, ok)) {
-        if (lane == 0) {
-            atomicExch(err, 1);
-            *s_failed = 1;
-        }
-        return false;
-    }
-    const C32Desc &D = desc[b];
-    if (k < D.count) {
-        idx_n = kslot[(size_t)b * C32_KSLOT + D.koff + k];
-        const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(D.spec + (size_t)idx_n * 10);
-#pragma unroll
-        for (int m = 0; m < NQ / 2; ++m) {
-            const ulonglong2 q = src[m];
-            nxt[2 * m] = q.x;
-            nxt[2 * m + 1] = q.y;
-        }
-    }
-    return true;
-}
-
 __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__restrict__ sys, const int *__restrict__ prefix,
                                                              int nsys, int total, const float4 *__restrict__ tab,
                                                              int *__restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
-    unsigned long long *full = reinterpret_cast<unsigned long long *>(smem);
-    unsigned long long *empty = full + C32_RING;
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(smem);   // [2]
+    unsigned long long *empty = full + 2;                                    // [2]
     C32Desc *desc = reinterpret_cast<C32Desc *>(smem + c32_off_desc());
-    unsigned *kslot = reinterpret_cast<unsigned *>(smem + c32_off_kidx());
+    unsigned *sidx = reinterpret_cast<unsigned *>(smem + c32_off_idx());
+    float4 *srec = reinterpret_cast<float4 *>(smem + c32_off_rec());
     float4 *rows = reinterpret_cast<float4 *>(smem + c32_off_rows());
     __shared__ int s_failed;
     const int lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         s_failed = 0;
-        for (int r = 0; r < C32_RING; ++r) {
-            mbar_init(&full[r], 1);
-            mbar_init(&empty[r], C32_CWARPS);
+        for (int h = 0; h < 2; ++h) {
+            mbar_init(&full[h], 1);
+            mbar_init(&empty[h], C32_CWARPS);
         }
         fence_mbar_init();
     }
     __syncthreads();
     if (threadIdx.x < 32) {
-        // ---- producer warp: descriptors and bulk copies, C32_RING - 1 chunks ahead
-        int4 cl = make_int4(0, 0, 0, 0);   // this lane's share of the next 32 chunk records
+        // ---- producer warp
+        int4 cl = make_int4(0, 0, 0, 0);   // this lane's chunk record among the next 32 chunks
         int sl = 0, ltl = 0;
-        int psi = -1;                      // system of the cached fields below (lane 0)
+        int psi = -1;                      // system of the cached fields below
         C32Desc d;
         const unsigned *gkidx = nullptr;
+        unsigned kn[C32_KPL];              // indices of the chunk about to be staged, k = lane + 32 r
         int issued = 0;
-        for (int t = blockIdx.x, i = 0, b = 0; t < total; t += gridDim.x, ++i, b = b + 1 == C32_RING ? 0 : b + 1) {
+        for (int t = blockIdx.x, i = 0; t < total; t += gridDim.x, ++i) {
+            const int b = i & 1;
             if ((i & 31) == 0) {
-                // chunk records of chunks i .. i + 31 of this block, one per lane
                 const int tl = t + lane * gridDim.x;
                 if (tl < total) {
                     sl = find_sys(prefix, nsys, tl);
@@ -1069,9 +1042,30 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
             const int lt = __shfl_sync(0xffffffffu, ltl, src);
             const int cx = __shfl_sync(0xffffffffu, cl.x, src), cy = __shfl_sync(0xffffffffu, cl.y, src);
             const int cz = __shfl_sync(0xffffffffu, cl.z, src), cwv = __shfl_sync(0xffffffffu, cl.w, src);
-            if (i >= C32_RING) {
-                // slot b released by every consumer warp (its previous use, chunk i - C32_RING)
-                const bool ok = mbar_wait(&empty[b], ((i / C32_RING) - 1) & 1);
+            if (s != psi) {                // every lane keeps the system's fields
+                const SysDev &S = sys[s];
+                d.nx = S.nx;
+                d.ny = S.ny;
+                d.nz = S.nz;
+                d.nzh = S.nzh;
+                d.sx1 = S.sx1;
+                d.sy1 = S.sy1;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) d.gf[q] = S.gf[q];
+                d.spec = reinterpret_cast<float4 *>(S.spec);
+                d.epart = S.epart;
+                gkidx = S.kidx;
+                psi = s;
+            }
+            // the chunk's indices into registers (coalesced) before its buffer is free
+#pragma unroll
+            for (int r = 0; r < C32_KPL; ++r) {
+                const int k = lane + 32 * r;
+                kn[r] = k < cy ? gkidx[cx + k] : 0u;
+            }
+            if (i >= 2) {
+                // buffer b released by every consumer warp (chunk i - 2)
+                const bool ok = mbar_wait(&empty[b], ((i >> 1) + 1) & 1u);
                 if (!__all_sync(0xffffffffu, ok) || *(volatile int *)&s_failed) {
                     if (lane == 0) {
                         atomicExch(err, 1);
@@ -1080,69 +1074,66 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
                     break;
                 }
             }
+            const int span = min(cwv, SPAN32);
+            // descriptor and indices (generic stores), published to the
+            // consumers by lane 0's arrive on full[b] after the warp barrier
+#pragma unroll
+            for (int r = 0; r < C32_KPL; ++r) {
+                const int k = lane + 32 * r;
+                if (k < cy) sidx[b * CHUNK32 + k] = kn[r];
+            }
             if (lane == 0) {
-                if (s != psi) {
-                    const SysDev &S = sys[s];
-                    d.nx = S.nx;
-                    d.ny = S.ny;
-                    d.nz = S.nz;
-                    d.nzh = S.nzh;
-                    d.sx1 = S.sx1;
-                    d.sy1 = S.sy1;
-                    for (int q = 0; q < 6; ++q) d.gf[q] = S.gf[q];
-                    d.spec = reinterpret_cast<const float4 *>(S.spec);
-                    d.epart = S.epart;
-                    gkidx = S.kidx;
-                    psi = s;
-                }
-                const int koff = cx & 3;
                 d.count = cy;
                 d.first = cz;
-                d.span = min(cwv, SPAN32);
+                d.span = span;
                 d.lt = lt;
-                d.koff = koff;
-                d.pad = 0;
+                d.pad0 = d.pad1 = 0;
                 desc[b] = d;
-                // indices: a 16-byte aligned superset of [cx, cx + cy) (the
-                // k-point order is allocated with 4 spare entries)
-                const unsigned kbytes = (unsigned)(((koff + cy) * 4 + 15) & ~15);
-                const unsigned rbytes = (unsigned)(d.span * NPAIR * sizeof(float4));
+            }
+            __syncwarp();
+            if (lane == 0) {
                 fence_proxy_async();
-                mbar_expect_tx(&full[b], kbytes + rbytes);
-                bulk_g2s(kslot + (size_t)b * C32_KSLOT, gkidx + (cx - koff), kbytes, &full[b]);
-                if (rbytes) bulk_g2s(rows + (size_t)b * SPAN32 * NPAIR, tab + (size_t)cz * NPAIR, rbytes, &full[b]);
+                mbar_expect_tx(&full[b], (unsigned)(cy * 160 + span * NPAIR * (int)sizeof(float4)));
+                if (span > 0)
+                    bulk_g2s(rows + (size_t)b * SPAN32 * NPAIR, tab + (size_t)cz * NPAIR,
+                             (unsigned)(span * NPAIR * sizeof(float4)), &full[b]);
+            }
+            __syncwarp();                  // the expected bytes are registered before any record lands
+#pragma unroll
+            for (int r = 0; r < C32_KPL; ++r) {
+                const int k = lane + 32 * r;
+                if (k < cy)
+                    bulk_g2s(srec + ((size_t)b * CHUNK32 + k) * C32_RSTRIDE, d.spec + (size_t)kn[r] * 10, 160u,
+                             &full[b]);
             }
             issued = i + 1;
-            __syncwarp();
         }
-        // every copy issued has landed before the block exits (the last use of each slot)
+        // every copy issued has landed before the block exits (the last use of each buffer)
         if (lane == 0)
-            for (int i = issued - C32_RING > 0 ? issued - C32_RING : 0; i < issued; ++i)
-                mbar_wait(&full[i % C32_RING], (i / C32_RING) & 1);
+            for (int i = issued - 2 > 0 ? issued - 2 : 0; i < issued; ++i) mbar_wait(&full[i & 1], (i >> 1) & 1u);
     } else {
         // ---- consumer warps: one k-point per thread
         const int cw = (threadIdx.x >> 5) - 1;
         const int k = threadIdx.x - 32;
-        f2_t th[NQ];
-        unsigned idx = 0;
-        bool have = false;
-        bool running = blockIdx.x < total && c32_gather(0, 0, k, lane, full, desc, kslot, err, &s_failed, th, idx);
-        for (int t = blockIdx.x, i = 0, b = 0; running && t < total;
-             t += gridDim.x, ++i, b = b + 1 == C32_RING ? 0 : b + 1) {
-            have = k < desc[b].count;
-            const unsigned idx_c = idx;
-            // the next chunk's records, in flight while this chunk is computed
-            f2_t nx[NQ];
-            const int bn = b + 1 == C32_RING ? 0 : b + 1;
-            if (t + gridDim.x < total)
-                running = c32_gather(i + 1, bn, k, lane, full, desc, kslot, err, &s_failed, nx, idx);
+        for (int t = blockIdx.x, i = 0; t < total; t += gridDim.x, ++i) {
+            const int b = i & 1;
+            const bool ok = !*(volatile int *)&s_failed && mbar_wait(&full[b], (i >> 1) & 1u);
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) {
+                    atomicExch(err, 1);
+                    s_failed = 1;
+                }
+                break;
+            }
             const C32Desc &D = desc[b];
             double ed = 0.0;
-            if (have) {
+            if (k < D.count) {
+                const unsigned idx = sidx[b * CHUNK32 + k];
                 int j;
                 float tt, w;
-                c32_kpoint(D, idx_c, j, tt, w);
-                f2_t F[NQ];
+                c32_kpoint(D, idx, j, tt, w);
+                f2_t th[NQ], F[NQ];
+                load_rec_f2(srec + ((size_t)b * CHUNK32 + k) * C32_RSTRIDE, th);
 #pragma unroll
                 for (int a = 0; a < NQ; ++a) F[a] = 0ull;
                 // the interval's row is staged: the host sorted this k-point into
@@ -1157,23 +1148,21 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
                         atomicExch(err, 2);
                 }
                 ed = f2d_bits(w * energy_f2(th, F));
-                store_rec_f2(const_cast<float4 *>(D.spec) + (size_t)idx_c * 10, F);
+                store_rec_f2(D.spec + (size_t)idx * 10, F);
             }
             // the warp's k-point energies widened exactly (integer pipe) and
             // summed in FP64: five FP64 additions per warp and chunk
             for (int o = 16; o > 0; o >>= 1) ed += __shfl_down_sync(0xffffffffu, ed, o);
             if (lane == 0) D.epart[(size_t)D.lt * C32_CWARPS + cw] = ed;
-            __syncwarp();                        // the warp's reads of slot b are done
+            __syncwarp();                        // the warp's reads of buffer b are done
             if (lane == 0) mbar_arrive_local(&empty[b]);
-#pragma unroll
-            for (int a = 0; a < NQ; ++a) th[a] = nx[a];
         }
     }
     __syncthreads();
     if (threadIdx.x == 0)
-        for (int r = 0; r < C32_RING; ++r) {
-            mbar_inval(&full[r]);
-            mbar_inval(&empty[r]);
+        for (int h = 0; h < 2; ++h) {
+            mbar_inval(&full[h]);
+            mbar_inval(&empty[h]);
         }
 }
 
@@ -1201,6 +1190,67 @@ __device__ __forceinline__ void zinv_issue(const SysDev *__restrict__ sys, const
     bulk_g2s(rbuf, reinterpret_cast<const Rec<T> *>(S.rec) + (size_t)l0 * S.nz, rb, bar);
 }
 
+// Potential of the z-inverse tile's nl lines (Eq. dedn, Eq. dedsigma):
+// dE/dtheta_a = dV F_a; dedn = sum_a F_a (p_a + n p_a' dq0/dn), dedsigma =
+// sum_a F_a n p_a' dq0/dsigma (the 1/N of the inverse transform folded in).
+// R: the transformed lines in shared memory ([z][ld], line li * 10 + c holds
+// F_2c + i F_2c+1); rec: the tile's point records (shared or global memory).
+// With D_j = sum_a F_a d2_a[j]:
+//   sum_a F_a p_a  = A F_j + B F_{j+1} + cA D_j + cB D_{j+1},
+//   sum_a F_a p_a' = (F_{j+1} - F_j) / h + dA D_j + dB D_{j+1}.
+template <typename T>
+__device__ __forceinline__ void zinv_potential(const SysDev &S, const QShared<T> *qs, const cx<T> *R,
+                                               const Rec<T> *rec, int l0, int nl, int ld) {
+    const int nz = S.nz;
+    const size_t p0 = (size_t)l0 * nz;
+    const T invN = sizeof(T) == 4 ? (T)S.invNf : (T)S.invN;
+    const int dz = blockDim.x % nz, dli = blockDim.x / nz;
+    int z = threadIdx.x % nz, li = threadIdx.x / nz;
+    double *gdn = S.dedn + p0, *gds = S.dedsigma + p0;
+    for (; li < nl;) {
+        const int i = li * nz + z;
+        const Rec<T> r = rec[i];
+        double dn = 0.0, ds = 0.0;
+        if (r.j >= 0) {
+            const int j = r.j;
+            T r0[NQ], r1[NQ];
+            d2_rows<T>(j, qs->d2, r0, r1);
+            const cx<T> *src = R + (size_t)z * ld + li * 10;
+            T D0 = (T)0, D1 = (T)0;
+#pragma unroll
+            for (int c = 0; c < 10; ++c) {
+                const cx<T> v = src[c];
+                D0 += v.x * r0[2 * c] + v.y * r0[2 * c + 1];
+                D1 += v.x * r1[2 * c] + v.y * r1[2 * c + 1];
+            }
+            const T *ft = reinterpret_cast<const T *>(src);
+            const T Fj = ft[j], Fj1 = ft[j + 1];
+            const T hh6 = qs->hh6[j], h6 = qs->h6[j], B = r.B, A = (T)1 - B;
+            const T cA = (A * A * A - A) * hh6;
+            const T cB = (B * B * B - B) * hh6;
+            const T dA = -((T)3 * A * A - (T)1) * h6;
+            const T dB = ((T)3 * B * B - (T)1) * h6;
+            const T s0 = (A * Fj + B * Fj1 + cA * D0 + cB * D1) * invN;
+            const T s1 = ((Fj1 - Fj) * qs->ih[j] + dA * D0 + dB * D1) * invN;
+            if (sizeof(T) == 4) {
+                dn = f2d_bits((float)(s0 + r.ndqn * s1));
+                ds = f2d_bits((float)(r.ndqs * s1));
+            } else {
+                dn = (double)(s0 + r.ndqn * s1);
+                ds = (double)(r.ndqs * s1);
+            }
+        }
+        gdn[i] = dn;
+        gds[i] = ds;
+        z += dz;
+        li += dli;
+        if (z >= nz) {
+            z -= nz;
+            ++li;
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zinv(const SysDev *__restrict__ sys, const int *__restrict__ prefix,
                                               int nsys, int total, int nzmax, int inelems, int recelems,
@@ -1215,6 +1265,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zinv(const SysD
     Rec<T> *recs[2] = {rec0, rec0 + recelems};
     cx<T> *bufA = reinterpret_cast<cx<T> *>(rec0 + 2 * (size_t)recelems);
     cx<T> *bufB = bufA + abelems;
+    __shared__ SysDev sS;                    // descriptor of the current tile's system
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -1222,10 +1273,44 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zinv(const SysD
     }
     load_qshared(qs);
     __syncthreads();
+    if (inelems == 0) {
+        // direct form (every system of the launch transforms in place, FP32):
+        // the first transform pass reads the tile's half spectrum straight
+        // from global memory (each ten consecutive threads read one k-point's
+        // 160 contiguous bytes) and the potential reads the point records
+        // from global memory; nothing is staged, so the block needs only the
+        // transform buffer and runs at the occupancy its registers allow
+        int cur_sys = -1, tbase = 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x) {
+            const int nsi = advance_sys(prefix, nsys, t, cur_sys);
+            if (nsi != cur_sys) {
+                __syncthreads();             // readers of the previous descriptor are done
+                copy_sys(&sS, &sys[nsi]);
+                __syncthreads();
+                const cx<T> *twg = reinterpret_cast<const cx<T> *>(sS.tw[2]);
+                for (int i = threadIdx.x; i < sS.nz; i += blockDim.x) tw[i] = twg[i];
+                __syncthreads();
+                cur_sys = nsi;
+                tbase = prefix[nsi];
+            }
+            const SysDev &S = sS;
+            const int l0 = (t - tbase) * S.LZi;
+            const int nl = min(S.LZi, S.nx * S.ny - l0);
+            const int ld = z_ld(nl);
+            const cx<T> *gspec = reinterpret_cast<const cx<T> *>(S.spec) + (size_t)l0 * S.nzh * NQ;
+            fft_ip_inv_packed_auto<T>(bufA, gspec, S.nz, 10 * nl, ld, S.nzh, tw);
+            zinv_potential<T>(S, qs, bufA, reinterpret_cast<const Rec<T> *>(S.rec) + (size_t)l0 * S.nz, l0, nl, ld);
+            __syncthreads();                 // bufA is rewritten by the next tile
+        }
+        if (threadIdx.x == 0) {
+            mbar_inval(&bar[0]);
+            mbar_inval(&bar[1]);
+        }
+        return;
+    }
     unsigned ph[2] = {0u, 0u};
     int t = blockIdx.x;
     if (t < total && threadIdx.x == 0) zinv_issue<T>(sys, prefix, nsys, t, ins[0], recs[0], &bar[0]);
-    __shared__ SysDev sS;                    // descriptor of the current tile's system
     int cur_sys = -1, tbase = 0;
     for (int it = 0; t < total; ++it, t += gridDim.x) {
         const int cur = it & 1;
@@ -1312,61 +1397,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zinv(const SysD
             __syncthreads();
             R = fft_auto<true>(bufA, bufB, S.ax[2], L, ld, tw);
         }
-        const Rec<T> *rec = recs[cur];
-        const size_t p0 = (size_t)l0 * nz;
-        const T invN = sizeof(T) == 4 ? (T)S.invNf : (T)S.invN;
-        {
-            // dE/dtheta_a = dV F_a; dedn = sum_a F_a (p_a + n p_a' dq0/dn),
-            // dedsigma = sum_a F_a n p_a' dq0/dsigma (the 1/N of the inverse
-            // transform folded in).  With D_j = sum_a F_a d2_a[j]:
-            //   sum_a F_a p_a  = A F_j + B F_{j+1} + cA D_j + cB D_{j+1},
-            //   sum_a F_a p_a' = (F_{j+1} - F_j) / h + dA D_j + dB D_{j+1}.
-            const int dz = blockDim.x % nz, dli = blockDim.x / nz;
-            int z = threadIdx.x % nz, li = threadIdx.x / nz;
-            double *gdn = S.dedn + p0, *gds = S.dedsigma + p0;
-            for (; li < nl;) {
-                const int i = li * nz + z;
-                const Rec<T> r = rec[i];
-                double dn = 0.0, ds = 0.0;
-                if (r.j >= 0) {
-                    const int j = r.j;
-                    T r0[NQ], r1[NQ];
-                    d2_rows<T>(j, qs->d2, r0, r1);
-                    const cx<T> *src = R + (size_t)z * ld + li * 10;
-                    T D0 = (T)0, D1 = (T)0;
-#pragma unroll
-                    for (int c = 0; c < 10; ++c) {
-                        const cx<T> v = src[c];
-                        D0 += v.x * r0[2 * c] + v.y * r0[2 * c + 1];
-                        D1 += v.x * r1[2 * c] + v.y * r1[2 * c + 1];
-                    }
-                    const T *ft = reinterpret_cast<const T *>(src);
-                    const T Fj = ft[j], Fj1 = ft[j + 1];
-                    const T hh6 = qs->hh6[j], h6 = qs->h6[j], B = r.B, A = (T)1 - B;
-                    const T cA = (A * A * A - A) * hh6;
-                    const T cB = (B * B * B - B) * hh6;
-                    const T dA = -((T)3 * A * A - (T)1) * h6;
-                    const T dB = ((T)3 * B * B - (T)1) * h6;
-                    const T s0 = (A * Fj + B * Fj1 + cA * D0 + cB * D1) * invN;
-                    const T s1 = ((Fj1 - Fj) * qs->ih[j] + dA * D0 + dB * D1) * invN;
-                    if (sizeof(T) == 4) {
-                        dn = f2d_bits((float)(s0 + r.ndqn * s1));
-                        ds = f2d_bits((float)(r.ndqs * s1));
-                    } else {
-                        dn = (double)(s0 + r.ndqn * s1);
-                        ds = (double)(r.ndqs * s1);
-                    }
-                }
-                gdn[i] = dn;
-                gds[i] = ds;
-                z += dz;
-                li += dli;
-                if (z >= nz) {
-                    z -= nz;
-                    ++li;
-                }
-            }
-        }
+        zinv_potential<T>(S, qs, R, recs[cur], l0, nl, ld);
         fence_proxy_async();
         __syncthreads();
     }
@@ -1509,8 +1540,13 @@ size_t smem_xy(int n, int W, int nslots) {
     return xy_smem_bytes(n, n * NQ * W, nslots, sizeof(cx<T>));
 }
 
+size_t zinv_smem(int prec, int nzmax, int inelems, int recelems, int abelems, int nab);
+
+// z-inverse block: FP32 axes with an in-place split run the direct form (no
+// staging: transform buffer only), all others stage two tiles of input
 template <typename T>
 size_t smem_zinv(int nz, int LZ) {
+    if (sizeof(T) == 4 && fft_split(nz)) return zinv_smem(1, nz, 0, 0, nz * z_ld(LZ), 1);
     const size_t nzh = nz / 2 + 1;
     return 16 + ((sizeof(QShared<T>) + 15) / 16) * 16 +
            sizeof(cx<T>) * ((size_t)((nz + 7) & ~7) + 2 * (size_t)LZ * nzh * NQ + z_nbuf<T>(nz) * nz * z_ld(LZ)) +
@@ -1562,6 +1598,30 @@ cudaError_t init_kernels(size_t maxsmem) {
     if (e != cudaSuccess) return e;
     if ((e = init_plane_kernel(maxsmem)) != cudaSuccess) return e;
     return init_kernels_t<double>(maxsmem);
+}
+
+template <typename T>
+static const void *kind_kernel(int kind) {
+    switch (kind) {
+        case 0: return (const void *)k_zfwd<T>;
+        case 1: return (const void *)k_xy<T, 0>;
+        case 2: return (const void *)k_xy<T, 2>;
+        case 3: return (const void *)k_zinv<T>;
+        default:
+            if (sizeof(T) == 4) return (const void *)k_contract32;
+            return (const void *)k_contract<T>;
+    }
+}
+
+int stage_blocks_per_sm(int kind, int prec, size_t smem) {
+    const void *fn = prec == 1 ? kind_kernel<float>(kind) : kind_kernel<double>(kind);
+    const int threads = (kind == 4 && prec == 1) ? C32_THREADS : 256;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        n = 1;
+    }
+    return n < 1 ? 1 : (n > 8 ? 8 : n);
 }
 
 // stage -> tile kind (-1: efinish)

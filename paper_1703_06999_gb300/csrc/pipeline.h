@@ -34,8 +34,7 @@ __host__ __device__ inline int z_ld(int nl) { return 10 * nl + 1; }
 
 // contraction chunks: at most CHUNK k-points spanning at most SPAN table
 // intervals (FP32-mixed: one k-point per consumer thread)
-constexpr int C32_CWARPS = 7;   // FP32 contraction: consumer warps per block (one energy partial each per chunk; with
-                                // the producer warp, two warps per SM sub-partition)
+constexpr int C32_CWARPS = 11;  // FP32 contraction: consumer warps per block (one energy partial each per chunk)
 constexpr int CHUNK32 = 32 * C32_CWARPS, SPAN32 = 8, CHUNK64 = 256, SPAN64 = 8;
 
 // Shared memory of an x / y pass block: barriers and twiddles, then nbuf
@@ -58,14 +57,10 @@ size_t stage_smem(int stage, int prec, int n, int tile, int nbuf = 3);
 // nab: z-inverse tile buffers (1 when every system of the launch transforms in place)
 size_t zinv_smem(int prec, int nzmax, int inelems, int recelems, int abelems, int nab);
 size_t contract_smem(int prec, int maxspan);
-// Resident blocks per SM a stage's grid is sized for: as many as its shared
-// memory allows (1..8), except the FP32 contraction, which is built for one
-// block per SM (its registers allow no second one).
-inline int stage_blocks_per_sm(int kind, int prec, size_t smem) {
-    if (kind == 4 && prec == 1) return 1;
-    const int per_sm = (int)((228 * 1024) / (smem + 1024));
-    return per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
-}
+// Resident blocks per SM a stage's grid is sized for (tile kinds 0..4 as in
+// LaunchSet): what the kernel's registers and `smem` bytes of dynamic shared
+// memory allow, from the runtime's occupancy calculator (1..8).
+int stage_blocks_per_sm(int kind, int prec, size_t smem);
 cudaError_t init_kernels(size_t maxsmem);
 constexpr int NSTAGE = 9;   // stages per evaluation (stages without tiles are not launched)
 constexpr int NKIND = 6;    // tile kinds
