@@ -1207,6 +1207,7 @@ static int batch_parts(vdwgb_data *const *hs, int count, int *start) {
 int vdwgb::batch_launchset(vdwgb_data *const *hs, int count, SysDev *hdesc, int *pre, const SysDev *ddesc,
                            const int *dprefix, LaunchSet &L) {
     std::memset(&L, 0, sizeof L);
+    for (int s = 0; s < NKIND; ++s) pre[s * (count + 1)] = 0;   // the caller's array may hold an older launch
     const int device = hs[0]->device;
     const int prec = hs[0]->prec;
     DevInfo &di = g_dev[device];

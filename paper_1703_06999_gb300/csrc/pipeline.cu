@@ -1099,6 +1099,7 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
                              (unsigned)(span * NPAIR * sizeof(float4)), &full[b]);
             }
             __syncwarp();                  // the expected bytes are registered before any record lands
+            fence_proxy_async();           // the consumers' reads of buffer b before these copies overwrite it
 #pragma unroll
             for (int r = 0; r < C32_KPL; ++r) {
                 const int k = lane + 32 * r;
