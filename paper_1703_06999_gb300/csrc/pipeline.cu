@@ -939,25 +939,33 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_contract(const 
 // ---------------------------------------------------------------------------
 // FP32-mixed contraction (procedure step 3, as k_contract).  One producer
 // warp and C32_CWARPS consumer warps per block, one block per SM.  The
-// producer stages the block's chunks into a double buffer: for each chunk a
-// small descriptor (the system's grid and metric, the chunk record), the
-// k-point indices, one 160-byte bulk copy per k-point record (the 20 theta
-// values) and one bulk copy of the chunk's kernel-table rows.  It reads the
-// chunk records of its next 32 chunks at once (one per lane) and the indices
-// of the next chunk into registers before that chunk's buffer is free, so a
-// freed buffer is refilled by bulk copies alone.  Each consumer thread
-// computes one k-point from shared memory and writes F over theta in global
-// memory.  Records sit 176 bytes apart in shared memory, so the ten 16-byte
-// loads of a warp's records are free of bank conflicts.
+// producer stages the block's chunks into a ring of C32_RING slots: for each
+// chunk a small descriptor (the system's grid and metric, the chunk record),
+// its k-point indices and one bulk copy of its kernel-table rows.  It reads
+// the chunk records of its next 32 chunks at once (one per lane) and a
+// chunk's indices before the chunk's slot is free.  Each consumer thread owns
+// one k-point of a chunk and fetches that k-point's 20 theta values (one
+// 160-byte record) itself, with ten 16-byte cp.async copies into its own
+// record slot, one chunk ahead: the copies of chunk i + 1 are in flight while
+// chunk i is computed, and no thread waits for another thread's copies.
+// Records sit 176 bytes apart in shared memory, so a warp's 16-byte loads of
+// its records are free of bank conflicts.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void mbar_arrive_local(unsigned long long *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 constexpr int C32_THREADS = 32 * (1 + C32_CWARPS);           // producer warp first, then the consumers
 static_assert(CHUNK32 == 32 * C32_CWARPS, "one k-point per consumer thread");
-constexpr int C32_KPL = CHUNK32 / 32;                        // k-points per producer lane and chunk
-constexpr int C32_RSTRIDE = 11;                              // float4 per staged record (10 used)
+constexpr int C32_KPL = CHUNK32 / 32;                        // indices per producer lane and chunk
+constexpr int C32_RING = 3;                                  // staged chunks (descriptor, indices, rows)
+constexpr int C32_RSTRIDE = 11;                              // float4 per record slot (10 used)
 
 // What the consumers need of a chunk: its system's grid and metric, output
 // pointers, and the chunk record.
@@ -974,12 +982,16 @@ struct __align__(16) C32Desc {
 };
 
 __host__ __device__ inline size_t c32_off_desc() { return 64; }
-__host__ __device__ inline size_t c32_off_idx() { return c32_off_desc() + 2 * sizeof(C32Desc); }
-__host__ __device__ inline size_t c32_off_rec() { return (c32_off_idx() + 2 * CHUNK32 * sizeof(unsigned) + 127) / 128 * 128; }
+__host__ __device__ inline size_t c32_off_idx() { return c32_off_desc() + C32_RING * sizeof(C32Desc); }
+__host__ __device__ inline size_t c32_off_rec() {
+    return (c32_off_idx() + (size_t)C32_RING * CHUNK32 * sizeof(unsigned) + 127) / 128 * 128;
+}
 __host__ __device__ inline size_t c32_off_rows() {
     return c32_off_rec() + 2 * (size_t)CHUNK32 * C32_RSTRIDE * sizeof(float4);
 }
-__host__ __device__ inline size_t c32_smem_bytes() { return c32_off_rows() + 2 * (size_t)SPAN32 * NPAIR * sizeof(float4); }
+__host__ __device__ inline size_t c32_smem_bytes() {
+    return c32_off_rows() + (size_t)C32_RING * SPAN32 * NPAIR * sizeof(float4);
+}
 
 // |k| of half-spectrum index idx (positions of the x / y passes mapped to
 // frequencies, Nyquist planes with the convention of the FP64 path) as table
@@ -997,12 +1009,38 @@ __device__ __forceinline__ void c32_kpoint(const C32Desc &D, unsigned idx, int &
     weight = (kz == 0 || nyq_z) ? 1.f : 2.f;
 }
 
+// consumer thread k: wait (bounded) for chunk i's slot b, then start the ten
+// 16-byte copies of its record of that chunk into record buffer rb (one
+// commit group); its index into idx.  False if the wait ran out.
+__device__ __forceinline__ bool c32_fetch(int i, int b, int rb, int k, int lane, unsigned long long *full,
+                                          const C32Desc *desc, const unsigned *sidx, float4 *srec, int *err,
+                                          int *s_failed, unsigned &idx) {
+    const bool ok = !*(volatile int *)s_failed && mbar_wait(&full[b], (unsigned)((i / C32_RING) & 1));
+    if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) {
+            atomicExch(err, 1);
+            *s_failed = 1;
+        }
+        return false;
+    }
+    const C32Desc &D = desc[b];
+    if (k < D.count) {
+        idx = sidx[b * CHUNK32 + k];
+        const float4 *src = D.spec + (size_t)idx * 10;
+        float4 *dst = srec + ((size_t)rb * CHUNK32 + k) * C32_RSTRIDE;
+#pragma unroll
+        for (int a = 0; a < 10; ++a) cp_async16(dst + a, src + a);
+    }
+    cp_async_commit();
+    return true;
+}
+
 __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__restrict__ sys, const int *__restrict__ prefix,
                                                              int nsys, int total, const float4 *__restrict__ tab,
                                                              int *__restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
-    unsigned long long *full = reinterpret_cast<unsigned long long *>(smem);   // [2]
-    unsigned long long *empty = full + 2;                                    // [2]
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(smem);   // [C32_RING]
+    unsigned long long *empty = full + C32_RING;                             // [C32_RING]
     C32Desc *desc = reinterpret_cast<C32Desc *>(smem + c32_off_desc());
     unsigned *sidx = reinterpret_cast<unsigned *>(smem + c32_off_idx());
     float4 *srec = reinterpret_cast<float4 *>(smem + c32_off_rec());
@@ -1011,24 +1049,23 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
     const int lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         s_failed = 0;
-        for (int h = 0; h < 2; ++h) {
-            mbar_init(&full[h], 1);
-            mbar_init(&empty[h], C32_CWARPS);
+        for (int r = 0; r < C32_RING; ++r) {
+            mbar_init(&full[r], 1);
+            mbar_init(&empty[r], C32_CWARPS);
         }
         fence_mbar_init();
     }
     __syncthreads();
     if (threadIdx.x < 32) {
-        // ---- producer warp
+        // ---- producer warp: descriptors, indices and table rows, C32_RING - 1 chunks ahead
         int4 cl = make_int4(0, 0, 0, 0);   // this lane's chunk record among the next 32 chunks
         int sl = 0, ltl = 0;
         int psi = -1;                      // system of the cached fields below
         C32Desc d;
         const unsigned *gkidx = nullptr;
-        unsigned kn[C32_KPL];              // indices of the chunk about to be staged, k = lane + 32 r
+        unsigned kn[C32_KPL];
         int issued = 0;
-        for (int t = blockIdx.x, i = 0; t < total; t += gridDim.x, ++i) {
-            const int b = i & 1;
+        for (int t = blockIdx.x, i = 0, b = 0; t < total; t += gridDim.x, ++i, b = b + 1 == C32_RING ? 0 : b + 1) {
             if ((i & 31) == 0) {
                 const int tl = t + lane * gridDim.x;
                 if (tl < total) {
@@ -1057,15 +1094,15 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
                 gkidx = S.kidx;
                 psi = s;
             }
-            // the chunk's indices into registers (coalesced) before its buffer is free
+            // the chunk's indices into registers (coalesced) before its slot is free
 #pragma unroll
             for (int r = 0; r < C32_KPL; ++r) {
                 const int k = lane + 32 * r;
                 kn[r] = k < cy ? gkidx[cx + k] : 0u;
             }
-            if (i >= 2) {
-                // buffer b released by every consumer warp (chunk i - 2)
-                const bool ok = mbar_wait(&empty[b], ((i >> 1) + 1) & 1u);
+            if (i >= C32_RING) {
+                // slot b released by every consumer warp (its previous use, chunk i - C32_RING)
+                const bool ok = mbar_wait(&empty[b], (unsigned)(((i / C32_RING) - 1) & 1));
                 if (!__all_sync(0xffffffffu, ok) || *(volatile int *)&s_failed) {
                     if (lane == 0) {
                         atomicExch(err, 1);
@@ -1093,48 +1130,44 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
             __syncwarp();
             if (lane == 0) {
                 fence_proxy_async();
-                mbar_expect_tx(&full[b], (unsigned)(cy * 160 + span * NPAIR * (int)sizeof(float4)));
+                mbar_expect_tx(&full[b], (unsigned)(span * NPAIR * (int)sizeof(float4)));
                 if (span > 0)
                     bulk_g2s(rows + (size_t)b * SPAN32 * NPAIR, tab + (size_t)cz * NPAIR,
                              (unsigned)(span * NPAIR * sizeof(float4)), &full[b]);
             }
-            __syncwarp();                  // the expected bytes are registered before any record lands
-            fence_proxy_async();           // the consumers' reads of buffer b before these copies overwrite it
-#pragma unroll
-            for (int r = 0; r < C32_KPL; ++r) {
-                const int k = lane + 32 * r;
-                if (k < cy)
-                    bulk_g2s(srec + ((size_t)b * CHUNK32 + k) * C32_RSTRIDE, d.spec + (size_t)kn[r] * 10, 160u,
-                             &full[b]);
-            }
             issued = i + 1;
         }
-        // every copy issued has landed before the block exits (the last use of each buffer)
+        // every copy issued has landed before the block exits (the last use of each slot)
         if (lane == 0)
-            for (int i = issued - 2 > 0 ? issued - 2 : 0; i < issued; ++i) mbar_wait(&full[i & 1], (i >> 1) & 1u);
+            for (int i = issued - C32_RING > 0 ? issued - C32_RING : 0; i < issued; ++i)
+                mbar_wait(&full[i % C32_RING], (unsigned)((i / C32_RING) & 1));
     } else {
         // ---- consumer warps: one k-point per thread
         const int cw = (threadIdx.x >> 5) - 1;
         const int k = threadIdx.x - 32;
-        for (int t = blockIdx.x, i = 0; t < total; t += gridDim.x, ++i) {
-            const int b = i & 1;
-            const bool ok = !*(volatile int *)&s_failed && mbar_wait(&full[b], (i >> 1) & 1u);
-            if (!__all_sync(0xffffffffu, ok)) {
-                if (lane == 0) {
-                    atomicExch(err, 1);
-                    s_failed = 1;
-                }
-                break;
+        unsigned idx = 0;
+        bool running = blockIdx.x < total &&
+                       c32_fetch(0, 0, 0, k, lane, full, desc, sidx, srec, err, &s_failed, idx);
+        for (int t = blockIdx.x, i = 0, b = 0; running && t < total;
+             t += gridDim.x, ++i, b = b + 1 == C32_RING ? 0 : b + 1) {
+            const unsigned idx_c = idx;
+            // the next chunk's record copies, in flight while this chunk is computed
+            const bool more = t + gridDim.x < total;
+            if (more) {
+                const int bn = b + 1 == C32_RING ? 0 : b + 1;
+                running = c32_fetch(i + 1, bn, (i + 1) & 1, k, lane, full, desc, sidx, srec, err, &s_failed, idx);
+                cp_async_wait<1>();                  // this thread's copies of chunk i have landed
+            } else {
+                cp_async_wait<0>();
             }
             const C32Desc &D = desc[b];
             double ed = 0.0;
             if (k < D.count) {
-                const unsigned idx = sidx[b * CHUNK32 + k];
                 int j;
                 float tt, w;
-                c32_kpoint(D, idx, j, tt, w);
+                c32_kpoint(D, idx_c, j, tt, w);
                 f2_t th[NQ], F[NQ];
-                load_rec_f2(srec + ((size_t)b * CHUNK32 + k) * C32_RSTRIDE, th);
+                load_rec_f2(srec + ((size_t)(i & 1) * CHUNK32 + k) * C32_RSTRIDE, th);
 #pragma unroll
                 for (int a = 0; a < NQ; ++a) F[a] = 0ull;
                 // the interval's row is staged: the host sorted this k-point into
@@ -1149,21 +1182,22 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
                         atomicExch(err, 2);
                 }
                 ed = f2d_bits(w * energy_f2(th, F));
-                store_rec_f2(D.spec + (size_t)idx * 10, F);
+                store_rec_f2(D.spec + (size_t)idx_c * 10, F);
             }
             // the warp's k-point energies widened exactly (integer pipe) and
             // summed in FP64: five FP64 additions per warp and chunk
             for (int o = 16; o > 0; o >>= 1) ed += __shfl_down_sync(0xffffffffu, ed, o);
             if (lane == 0) D.epart[(size_t)D.lt * C32_CWARPS + cw] = ed;
-            __syncwarp();                        // the warp's reads of buffer b are done
+            __syncwarp();                        // the warp's reads of slot b are done
             if (lane == 0) mbar_arrive_local(&empty[b]);
         }
+        cp_async_wait<0>();                      // no copy of this thread is in flight at exit
     }
     __syncthreads();
     if (threadIdx.x == 0)
-        for (int h = 0; h < 2; ++h) {
-            mbar_inval(&full[h]);
-            mbar_inval(&empty[h]);
+        for (int r = 0; r < C32_RING; ++r) {
+            mbar_inval(&full[r]);
+            mbar_inval(&empty[r]);
         }
 }
 
