@@ -364,14 +364,19 @@ def run_reference(args, rank):
 # ---------------------------------------------------------------------------
 # serving stream
 # ---------------------------------------------------------------------------
-def serve_bench(B, inputs, torch, dev, local, seconds=3.0, rate=200.0, pool_entries=16):
-    """Served form: Poisson arrivals (mean `rate` per second) of evaluations
-    with grids from 48^3 to 160x192x224 (10-400 exponentials), FP32-mixed,
-    admitted by footprint into an 8 GiB pool, continuous batching; against
-    the same evaluations one at a time in FP64.  Inputs come from a pool of
-    `pool_entries` distinct requests reused across arrivals (host arrays,
-    page-locked)."""
-    reqs = inputs.serving_requests(seed=0, count=pool_entries, rate=rate)
+def serve_bench(B, inputs, torch, dev, local, rate=200.0, count=2000, distinct=128,
+                sweep=(400.0, 800.0, 1600.0, 3200.0), sweep_seconds=2.5):
+    """Served form (the Poisson serving stream): arrivals with mean `rate`
+    per second of evaluations with grids from 48^3 to 160x192x224 (sorted
+    axes, 10-400 exponentials, spacing 0.15-0.30 bohr), FP32-mixed, admitted
+    by footprint into a 64 GiB pool where plans stay resident, continuous
+    batching (up to 16 requests per batch, 3 batches in flight).  `distinct`
+    different requests (density, cell, grid) are drawn from the stream's
+    distribution and the `count` arrivals cycle through them in a random
+    order (host arrays, page-locked).  Reported against the same requests
+    one at a time in FP64.  Then a sweep of higher rates (`sweep_seconds`
+    each) up to saturation."""
+    reqs = inputs.serving_requests(seed=0, count=distinct, rate=rate)
     pool = []
     for r in reqs:
         sy = inputs.realise(r, device=dev)
@@ -380,9 +385,9 @@ def serve_bench(B, inputs, torch, dev, local, seconds=3.0, rate=200.0, pool_entr
         dn = torch.empty(sy.shape, dtype=torch.float64).pin_memory().numpy()
         ds = torch.empty(sy.shape, dtype=torch.float64).pin_memory().numpy()
         pool.append((sy, hn, hs, dn, ds))
-    # FP64 one at a time (plain form), device-resident inputs
+    # FP64 one at a time (plain form), device-resident inputs, on a sample of 32
     lat64, pts64 = [], 0
-    for sy, *_ in pool:
+    for sy, *_ in pool[:32]:
         f = B.Functional(sy.shape, sy.cell, sy.functional, B.FP64, device=local)
         o1, o2 = torch.empty_like(sy.n), torch.empty_like(sy.n)
         en = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -397,37 +402,52 @@ def serve_bench(B, inputs, torch, dev, local, seconds=3.0, rate=200.0, pool_entr
         pts64 += sy.npts
         f.close()
     fp64_rate = pts64 / sum(lat64)
-    sv = B.vdwgb_server_new(local, B.FP32_MIXED, pool_bytes=8 << 30, max_batch=16, max_inflight=3)
-    try:
-        # warm-up: every pool entry once
-        for sy, hn, hs, dn, ds in pool:
-            B.vdwgb_server_wait(sv, B.vdwgb_server_submit(sv, sy.functional, sy.shape, sy.cell, hn, hs, dn, ds), 120)
-        B.vdwgb_server_free(sv)
-        sv = B.vdwgb_server_new(local, B.FP32_MIXED, pool_bytes=8 << 30, max_batch=16, max_inflight=3)
-        g = np.random.default_rng(1)
-        arrivals = np.cumsum(g.exponential(1.0 / rate, int(rate * seconds * 1.5)))
-        arrivals = arrivals[arrivals < seconds]
-        ids = []
-        t0 = time.perf_counter()
-        for k, ta in enumerate(arrivals):
-            while time.perf_counter() - t0 < ta:
-                time.sleep(0.0002)
-            sy, hn, hs, dn, ds = pool[k % len(pool)]
-            ids.append(B.vdwgb_server_submit(sv, sy.functional, sy.shape, sy.cell, hn, hs, dn, ds))
-        for rid in ids:
-            B.vdwgb_server_wait(sv, rid, 300.0)
-        wall = time.perf_counter() - t0
-        st = B.vdwgb_server_stats(sv)
-    finally:
-        B.vdwgb_server_free(sv)
-    return {"requests": len(ids), "rate_req_s": rate, "seconds": seconds, "value": st["pts_per_s"],
-            "unit": "grid pts/s", "p50_ms": 1000 * st["p50_s"], "p99_ms": 1000 * st["p99_s"],
-            "mean_batch": st["mean_batch"], "batches": st["batches"], "failed": st["failed"],
-            "wall_s": wall, "pool_peak_GB": st["pool_used_peak"] / 1e9,
-            "fp64_one_at_a_time": {"value": fp64_rate, "unit": "grid pts/s",
-                                   "p50_ms": 1000 * float(np.median(lat64)),
-                                   "p99_ms": 1000 * float(np.percentile(lat64, 99))},
-            "grids": sorted({tuple(p[0].shape) for p in pool})}
+    for sy, *_ in pool:
+        sy.n = sy.sigma = None                      # device copies no longer needed
+    torch.cuda.empty_cache()
+    g = np.random.default_rng(1)
+
+    def stream(rate_s, n_arrivals):
+        sv = B.vdwgb_server_new(local, B.FP32_MIXED, pool_bytes=64 << 30, max_batch=16, max_inflight=3)
+        try:
+            for k in range(len(pool)):              # warm-up: every request once (plans built, resident)
+                sy, hn, hs, dn, ds = pool[k]
+                B.vdwgb_server_wait(sv, B.vdwgb_server_submit(sv, sy.functional, sy.shape, sy.cell, hn, hs, dn, ds),
+                                    300.0)
+            warm = B.vdwgb_server_stats(sv)
+            arrivals = np.cumsum(g.exponential(1.0 / rate_s, n_arrivals))
+            order = g.integers(0, len(pool), n_arrivals)
+            ids, pts = [], 0
+            t0 = time.perf_counter()
+            for k, ta in enumerate(arrivals):
+                while time.perf_counter() - t0 < ta:
+                    time.sleep(0.0002)
+                sy, hn, hs, dn, ds = pool[order[k]]
+                ids.append(B.vdwgb_server_submit(sv, sy.functional, sy.shape, sy.cell, hn, hs, dn, ds))
+                pts += sy.npts
+            lat = [B.vdwgb_server_wait(sv, rid, 300.0)[1] for rid in ids]
+            wall = time.perf_counter() - t0
+            st = B.vdwgb_server_stats(sv)
+        finally:
+            B.vdwgb_server_free(sv)
+        lat = np.array(lat)
+        batches = st["batches"] - warm["batches"]
+        return {"requests": len(ids), "rate_req_s": rate_s, "offered_s": float(arrivals[-1]),
+                "value": pts / wall, "unit": "grid pts/s", "wall_s": wall,
+                "p50_ms": 1000 * float(np.percentile(lat, 50)), "p99_ms": 1000 * float(np.percentile(lat, 99)),
+                "mean_batch": (st["completed"] - warm["completed"]) / max(batches, 1), "batches": batches,
+                "failed": st["failed"], "plans_reused": st["plans_reused"] - warm["plans_reused"],
+                "plans_built": st["plans_built"] - warm["plans_built"], "pool_peak_GB": st["pool_used_peak"] / 1e9}
+
+    main = stream(rate, count)
+    main["fp64_one_at_a_time"] = {"value": fp64_rate, "unit": "grid pts/s", "requests": len(lat64),
+                                  "p50_ms": 1000 * float(np.median(lat64)),
+                                  "p99_ms": 1000 * float(np.percentile(lat64, 99))}
+    main["distinct_requests"] = len(pool)
+    main["grids"] = len({tuple(p[0].shape) for p in pool})
+    main["grid_points_mean"] = float(np.mean([p[0].npts for p in pool]))
+    main["sweep"] = [stream(r, int(r * sweep_seconds)) for r in sweep]
+    return main
 
 
 # ---------------------------------------------------------------------------

@@ -280,12 +280,18 @@ typedef struct {
     double pts_per_s;        /* grid points of completed requests / (last completion - first submit) */
     double p50_s, p99_s;     /* latency quantiles (completion - submission) of completed requests */
     size_t pool_bytes, pool_used_peak;
+    long long plans_reused;  /* requests that re-planned a resident plan of their grid */
+    long long plans_built;   /* requests that built a new plan */
 } vdwgb_server_stats_t;
 
 /* Create a server on `device` for `precision`.  pool_bytes: device-memory
- * budget for admitted requests (work buffer, records, staging of each); a
- * request is admitted, in arrival order, when its footprint fits what is
- * left.  max_batch (1..256): most requests per batched launch (one launch per
+ * budget for admitted requests and resident plans (work buffer, records,
+ * k-point order, staging of each); a request is admitted, in arrival order,
+ * when a resident plan of its grid is idle, or its footprint fits what is
+ * left after evicting idle plans (least recently used first).  A finished
+ * request's plan stays resident; the next request of the same grid re-plans
+ * only its cell-dependent parts (reciprocal metric, k-point order sorted on
+ * the device, chunks).  max_batch (1..256): most requests per batched launch (one launch per
  * stage over all of them); max_inflight (1..8): batches on the GPU at once,
  * each on its own stream, so later requests are admitted and planned while
  * earlier ones run.  Worker threads plan requests (FFT plans, k-point order),

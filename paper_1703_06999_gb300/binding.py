@@ -65,7 +65,8 @@ class ServerStats(ctypes.Structure):
                 ("failed", ctypes.c_longlong), ("batches", ctypes.c_longlong),
                 ("mean_batch", ctypes.c_double), ("pts_per_s", ctypes.c_double),
                 ("p50_s", ctypes.c_double), ("p99_s", ctypes.c_double),
-                ("pool_bytes", ctypes.c_size_t), ("pool_used_peak", ctypes.c_size_t)]
+                ("pool_bytes", ctypes.c_size_t), ("pool_used_peak", ctypes.c_size_t),
+                ("plans_reused", ctypes.c_longlong), ("plans_built", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

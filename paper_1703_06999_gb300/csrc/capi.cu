@@ -211,77 +211,116 @@ static void choose_tiles(int prec, int nx, int ny, int nz, int nzh, size_t lim, 
     Wx = best_w(prec, nx, nzh, nbuf + workx);
 }
 
-// Sort the half-spectrum k-points of a system by kernel-table interval
-// j = floor(|k| / dk) (|k| with the same Nyquist convention as the kernels;
-// intervals beyond the table form their own group) and cut the order into
-// chunks of at most `chunkmax` k-points spanning at most `maxspan` intervals.
-// chunk = {first index into kidx, count, first interval, intervals (0 beyond)}.
-// FP32-mixed (f32): intervals from kpoint_interval32, the decision the
-// contraction kernel repeats; FP64: |k| in FP64.
-static void build_chunks(const SysDev &S, bool f32, int maxspan, int chunkmax, std::vector<unsigned> &kidx,
-                         std::vector<int4> &chunks) {
-    const int nx = S.nx, ny = S.ny, nz = S.nz, nzh = S.nzh;
-    const size_t nk = (size_t)nx * ny * nzh;
-    const double dk = 2.0 * M_PI / RMAX;
-    std::vector<int> bin(nk);
-    std::vector<size_t> count(NK + 1, 0);
-    auto fold = [](int i, int n) { return i <= (n - 1) / 2 ? i : i - n; };
-    for (int px = 0; px < nx; ++px) {
-        const int x = axis_freq(px, nx, S.sx1);          // frequency at this position
-        const int mx = fold(x, nx);
-        const bool qx = (nx % 2 == 0) && (x == nx / 2);
-        for (int py = 0; py < ny; ++py) {
-            const int y = axis_freq(py, ny, S.sy1);
-            const int my = fold(y, ny);
-            const bool qy = (ny % 2 == 0) && (y == ny / 2);
-            for (int kz = 0; kz < nzh; ++kz) {
-                const bool qz = (nz % 2 == 0) && (kz == nz / 2);
-                const int mz = qz ? -kz : kz;
-                long j;
-                if (f32) {
-                    int j32;
-                    float tt;
-                    kpoint_interval32(S.gf, mx, my, mz, qx, qy, qz, j32, tt);
-                    j = j32;
-                } else {
-                    const double cx = qx ? 0.0 : mx, cy = qy ? 0.0 : my, cz = qz ? 0.0 : mz;
-                    double k2 = S.g[0] * mx * mx + S.g[1] * (double)my * my + S.g[2] * (double)mz * mz +
-                                2.0 * (S.g[3] * cx * cy + S.g[4] * cx * cz + S.g[5] * cy * cz);
-                    if (k2 < 0) k2 = 0;
-                    j = (long)(std::sqrt(k2) / dk);
-                    if (j > NK - 1) j = NK - 1;
-                }
-                const size_t idx = ((size_t)px * ny + py) * nzh + kz;
-                bin[idx] = (int)j;
-                ++count[j];
+// Contraction chunks of a system from the k-points per kernel-table interval
+// of its sorted order (the order is interval by interval, so the counts fix
+// it): chunks of at most `chunkmax` k-points spanning at most `maxspan`
+// intervals; k-points beyond the table (interval NK - 1) form their own
+// chunks.  chunk = {first index into the order, count, first interval,
+// intervals staged (0 beyond the table)}.
+static void chunks_from_counts(const std::vector<int> &count, int maxspan, int chunkmax, std::vector<int4> &chunks) {
+    chunks.clear();
+    int j = 0;
+    while (j < NK && count[j] == 0) ++j;
+    int left = j < NK ? count[j] : 0;   // k-points of interval j not yet in a chunk
+    size_t pos = 0;
+    while (j < NK) {
+        const int j0 = j;
+        int n = 0, jl = j0;
+        while (j < NK && n < chunkmax) {
+            if (j0 == NK - 1 ? j != NK - 1 : (j == NK - 1 || j - j0 >= maxspan)) break;
+            const int take = std::min(left, chunkmax - n);
+            n += take;
+            left -= take;
+            jl = j;
+            if (left == 0) {
+                ++j;
+                while (j < NK && count[j] == 0) ++j;
+                left = j < NK ? count[j] : 0;
             }
         }
+        chunks.push_back(make_int4((int)pos, n, j0, j0 == NK - 1 ? 0 : jl - j0 + 1));
+        pos += (size_t)n;
     }
-    std::vector<size_t> start(NK + 1, 0);
-    for (int j = 1; j <= NK; ++j) start[j] = start[j - 1] + count[j - 1];
-    kidx.assign(nk, 0);
-    std::vector<size_t> pos(start.begin(), start.end());
-    for (size_t i = 0; i < nk; ++i) kidx[pos[bin[i]]++] = (unsigned)i;
-    chunks.clear();
-    size_t i = 0;
-    while (i < nk) {
-        const int j0 = bin[kidx[i]];
-        int4 c;
-        c.x = (int)i;
-        c.z = j0;
-        size_t n = 0;
-        int jl = j0;
-        while (i + n < nk && n < (size_t)chunkmax) {
-            const int jb = bin[kidx[i + n]];
-            if (j0 == NK - 1 ? jb != NK - 1 : (jb == NK - 1 || jb - j0 >= maxspan)) break;
-            jl = jb;
-            ++n;
-        }
-        c.y = (int)n;
-        c.w = j0 == NK - 1 ? 0 : jl - j0 + 1;
-        chunks.push_back(c);
-        i += n;
-    }
+}
+
+// Upper bound of the chunk count of any system of nk k-points.
+static size_t max_chunks(size_t nk, int chunkmax) { return (nk + chunkmax - 1) / chunkmax + NK + 1; }
+
+// Reciprocal metric, energy scale and functional constants of the handle's
+// cell and functional in its descriptor.
+static void set_metric(vdwgb_data *h) {
+    SysDev &S = h->hsys;
+    const double *c = h->cell;
+    const double det = c[0] * (c[4] * c[8] - c[5] * c[7]) - c[1] * (c[3] * c[8] - c[5] * c[6]) +
+                       c[2] * (c[3] * c[7] - c[4] * c[6]);
+    double inv[9];   // inverse of C
+    inv[0] = (c[4] * c[8] - c[5] * c[7]) / det;
+    inv[1] = (c[2] * c[7] - c[1] * c[8]) / det;
+    inv[2] = (c[1] * c[5] - c[2] * c[4]) / det;
+    inv[3] = (c[5] * c[6] - c[3] * c[8]) / det;
+    inv[4] = (c[0] * c[8] - c[2] * c[6]) / det;
+    inv[5] = (c[2] * c[3] - c[0] * c[5]) / det;
+    inv[6] = (c[3] * c[7] - c[4] * c[6]) / det;
+    inv[7] = (c[1] * c[6] - c[0] * c[7]) / det;
+    inv[8] = (c[0] * c[4] - c[1] * c[3]) / det;
+    double B[9];   // reciprocal lattice, B = 2 pi C^{-T} (rows b_j): B[j][k] = 2 pi inv[k][j]
+    for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k) B[j * 3 + k] = 2.0 * M_PI * inv[k * 3 + j];
+    double g[3][3];  // g = B B^T: |k|^2 = m^T g m
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            g[i][j] = B[i * 3] * B[j * 3] + B[i * 3 + 1] * B[j * 3 + 1] + B[i * 3 + 2] * B[j * 3 + 2];
+    S.g[0] = g[0][0];
+    S.g[1] = g[1][1];
+    S.g[2] = g[2][2];
+    S.g[3] = g[0][1];
+    S.g[4] = g[0][2];
+    S.g[5] = g[1][2];
+    for (int i = 0; i < 6; ++i) S.gf[i] = (float)S.g[i];
+    const double N = (double)S.nx * S.ny * S.nz;
+    S.escale = 0.5 * std::fabs(det) / (N * N);
+    S.invN = 1.0 / N;
+    S.Z = h->functional == VDWGB_DF2 ? -1.887 : -0.8491;
+    const double zc = -S.Z / 36.0;
+    S.zc[0] = (float)zc;
+    S.zc[1] = (float)(zc - (double)S.zc[0]);
+    S.invNf = (float)S.invN;
+}
+
+// The k-point order of the handle's current cell, sorted on the device into
+// h->kidx (stream st, spec buffer as scratch when large enough), and its
+// chunks uploaded to h->chunks (capacity max_chunks).  Sets tiles[4] and
+// nepart.  Waits for st (the interval counts come back to the host).
+static int sort_kpoints(vdwgb_data *h, cudaStream_t st) {
+    SysDev &S = h->hsys;
+    const bool f32 = h->prec == VDWGB_FP32_MIXED;
+    const int maxspan = f32 ? SPAN32 : SPAN64;
+    const int chunkmax = f32 ? CHUNK32 : CHUNK64;
+    const size_t nk = (size_t)S.nx * S.ny * S.nzh;
+    const size_t need = ksort_scratch_ints(nk) * sizeof(int);
+    const size_t specbytes = nk * NQ * elem_bytes(h->prec);
+    int *scratch = nullptr;
+    if (need <= specbytes) scratch = static_cast<int *>(h->spec);
+    else CK(dalloc(h, &scratch, need), "k-point sort scratch");
+    std::vector<int> count(NK, 0);
+    cudaError_t e = launch_ksort(S, f32, h->kidx, scratch, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(count.data(), scratch + (need / sizeof(int) - NK), NK * sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (scratch != h->spec) dfree(h, scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "k-point sort");
+    std::vector<int4> chunks;
+    chunks_from_counts(count, maxspan, chunkmax, chunks);
+    if (chunks.size() > max_chunks(nk, chunkmax)) return fail(VDWGB_ECUDA, "k-point sort: chunk bound exceeded");
+    CK(cudaMemcpyAsync(h->chunks, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice, st), "chunks");
+    CK(cudaStreamSynchronize(st), "chunks");   // the host vector is released on return
+    S.tiles[4] = (int)chunks.size();
+    S.nepart = S.tiles[4] * (f32 ? C32_CWARPS : 1);   // FP32: one per consumer warp
+    LaunchSet &L = h->ls;
+    L.total[4] = S.tiles[4];
+    const int cap = g_dev[h->device].sms * stage_blocks_per_sm(4, h->prec, L.smem[4]);
+    L.grid[4] = L.total[4] < cap ? L.total[4] : cap;
+    return 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -661,79 +700,39 @@ static int plan(vdwgb_data *h) {
         stage_smem(1, prec, ny, S.Wy, nbuf + worky) > lim || stage_smem(3, prec, nz, S.LZi) > lim)
         return fail(VDWGB_EINVAL, "grid %dx%dx%d too large for one block per pencil in this precision",
                     nx, ny, nz);
-    // reciprocal metric g = B B^T, B = 2 pi C^{-T} (rows b_j)
-    const double *c = h->cell;
-    const double det = c[0] * (c[4] * c[8] - c[5] * c[7]) - c[1] * (c[3] * c[8] - c[5] * c[6]) +
-                       c[2] * (c[3] * c[7] - c[4] * c[6]);
-    double inv[9];   // inverse of C
-    inv[0] = (c[4] * c[8] - c[5] * c[7]) / det;
-    inv[1] = (c[2] * c[7] - c[1] * c[8]) / det;
-    inv[2] = (c[1] * c[5] - c[2] * c[4]) / det;
-    inv[3] = (c[5] * c[6] - c[3] * c[8]) / det;
-    inv[4] = (c[0] * c[8] - c[2] * c[6]) / det;
-    inv[5] = (c[2] * c[3] - c[0] * c[5]) / det;
-    inv[6] = (c[3] * c[7] - c[4] * c[6]) / det;
-    inv[7] = (c[1] * c[6] - c[0] * c[7]) / det;
-    inv[8] = (c[0] * c[4] - c[1] * c[3]) / det;
-    double B[9];   // B[j][k] = 2 pi inv[k][j]
-    for (int j = 0; j < 3; ++j)
-        for (int k = 0; k < 3; ++k) B[j * 3 + k] = 2.0 * M_PI * inv[k * 3 + j];
-    double g[3][3];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-            g[i][j] = B[i * 3] * B[j * 3] + B[i * 3 + 1] * B[j * 3 + 1] + B[i * 3 + 2] * B[j * 3 + 2];
-    S.g[0] = g[0][0];
-    S.g[1] = g[1][1];
-    S.g[2] = g[2][2];
-    S.g[3] = g[0][1];
-    S.g[4] = g[0][2];
-    S.g[5] = g[1][2];
-    for (int i = 0; i < 6; ++i) S.gf[i] = (float)S.g[i];
-    const double N = (double)nx * ny * nz;
-    const double omega = std::fabs(det);
-    S.escale = 0.5 * omega / (N * N);
-    S.invN = 1.0 / N;
-    S.Z = h->functional == VDWGB_DF2 ? -1.887 : -0.8491;
-    {
-        const double zc = -S.Z / 36.0;
-        S.zc[0] = (float)zc;
-        S.zc[1] = (float)(zc - (double)S.zc[0]);
-    }
-    S.invNf = (float)S.invN;
-    // half-spectrum k-points sorted by kernel-table interval, cut into chunks
-    // (or, for the plane kernel, per plane and cluster rank)
+    set_metric(h);
+    // half-spectrum k-points sorted by kernel-table interval on the device and
+    // cut into chunks (below), or, for the plane kernel, per plane and cluster rank
     const int maxspan = prec == VDWGB_FP32_MIXED ? SPAN32 : SPAN64;
     const int chunkmax = prec == VDWGB_FP32_MIXED ? CHUNK32 : CHUNK64;
-    std::vector<unsigned> kidx;
-    std::vector<int4> chunks;
+    const size_t nk = (size_t)nx * ny * nzh;
     std::vector<unsigned short> kord;
     int maxcl = 0;
     const int C = fused_cluster(h, di.maxsmem - 1024, maxcl);
     S.fused = C;
+    size_t nchunk_cap = 0, nepart_cap = 0;
     if (C) {
         build_kord(S, C, kord, S.kstride);
         S.tiles[4] = 0;
         S.tiles[5] = nzh;
         S.nepart = nzh * C;
+        nepart_cap = S.nepart;
     } else {
-        build_chunks(S, prec == VDWGB_FP32_MIXED, maxspan, chunkmax, kidx, chunks);
-        S.tiles[4] = (int)chunks.size();
         S.tiles[5] = 0;
-        S.nepart = S.tiles[4] * (prec == VDWGB_FP32_MIXED ? C32_CWARPS : 1);   // FP32: one per consumer warp
+        nchunk_cap = max_chunks(nk, chunkmax);
+        nepart_cap = nchunk_cap * (prec == VDWGB_FP32_MIXED ? C32_CWARPS : 1);
     }
     // memory
-    const size_t nspec = (size_t)nx * ny * nzh * NQ;
+    const size_t nspec = nk * NQ;
     CK(dalloc(h, &h->spec, nspec * elem_bytes(prec)), "work buffer");
     CK(dalloc(h, &h->rec, (size_t)nx * ny * nz * rec_bytes(prec)), "point records");
-    CK(dalloc(h, &h->epart, (size_t)S.nepart * sizeof(double)), "energy partials");
+    CK(dalloc(h, &h->epart, nepart_cap * sizeof(double)), "energy partials");
     if (C) {
         CK(dalloc(h, &h->kord, kord.size() * sizeof(unsigned short)), "plane k-point order");
         CK(dupload(h, h->kord, kord.data(), kord.size() * sizeof(unsigned short)), "plane k-point order");
     } else {
-        CK(dalloc(h, &h->kidx, kidx.size() * sizeof(unsigned)), "k-point order");
-        CK(dupload(h, h->kidx, kidx.data(), kidx.size() * sizeof(unsigned)), "k-point order");
-        CK(dalloc(h, &h->chunks, chunks.size() * sizeof(int4)), "chunks");
-        CK(dupload(h, h->chunks, chunks.data(), chunks.size() * sizeof(int4)), "chunks");
+        CK(dalloc(h, &h->kidx, nk * sizeof(unsigned)), "k-point order");
+        CK(dalloc(h, &h->chunks, nchunk_cap * sizeof(int4)), "chunks");
     }
     S.kidx = h->kidx;
     S.chunks = h->chunks;
@@ -754,8 +753,8 @@ static int plan(vdwgb_data *h) {
     S.spec = h->spec;
     S.rec = h->rec;
     S.epart = h->epart;
-    h->bytes = nspec * elem_bytes(prec) + (size_t)nx * ny * nz * rec_bytes(prec) + S.nepart * sizeof(double) +
-               kidx.size() * sizeof(unsigned) + chunks.size() * sizeof(int4) + kord.size() * sizeof(unsigned short);
+    h->bytes = nspec * elem_bytes(prec) + (size_t)nx * ny * nz * rec_bytes(prec) + nepart_cap * sizeof(double) +
+               (C ? 0 : nk * sizeof(unsigned)) + nchunk_cap * sizeof(int4) + kord.size() * sizeof(unsigned short);
     CK(dalloc(h, &h->dsys, sizeof(SysDev)), "descriptor");
     CK(dalloc(h, &h->dprefix, 2 * NKIND * sizeof(int)), "prefix");
     if (prec == VDWGB_FP32_MIXED) CK(dalloc(h, &h->tmap, 2 * sizeof(CUtensorMap)), "tensor maps");
@@ -769,10 +768,7 @@ static int plan(vdwgb_data *h) {
     L.twmax[4] = L.bufelems[4] = L.nbuf[4] = 0;
     L.total[4] = S.tiles[4];
     L.prefix[4] = h->dprefix + 8;
-    {
-        const int cap = di.sms * stage_blocks_per_sm(4, prec, L.smem[4]);
-        L.grid[4] = L.total[4] < cap ? L.total[4] : cap;
-    }
+    L.grid[4] = 0;
     L.prefix[5] = h->dprefix + 10;
     L.total[5] = S.tiles[5];
     L.cluster = C;
@@ -787,6 +783,10 @@ static int plan(vdwgb_data *h) {
         L.table = h->interp == VDWGB_INTERP_LINEAR ? (const void *)tr.lin64 : (const void *)tr.cub64;
     h->table = L.table;
     if (!h->alloc_stream) CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "stream");
+    if (!C) {
+        const int rc = sort_kpoints(h, h->alloc_stream ? h->alloc_stream : h->stream);
+        if (rc) return rc;
+    }
     {
         int rc = apply_tuned(h);          // cached or measured tile choices
         if (rc) return rc;
@@ -875,6 +875,18 @@ int vdwgb::handle_init(vdwgb_data *h, int device, int precision, cudaStream_t al
 }
 
 void vdwgb::handle_release(vdwgb_data *h) { release(h); }
+
+int vdwgb::handle_replan(vdwgb_data *h, const double *cell9, int functional) {
+    if (!h || !h->inited) return fail(VDWGB_ESTATE, "re-plan of an uninitialised handle");
+    if (h->hsys.fused) return fail(VDWGB_ESTATE, "re-plan of a plane-kernel plan");
+    std::memcpy(h->cell, cell9, sizeof h->cell);
+    h->functional = functional;
+    set_metric(h);
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    int rc = sort_kpoints(h, h->alloc_stream ? h->alloc_stream : h->stream);
+    if (rc) return rc;
+    return upload_plan(h);
+}
 
 size_t vdwgb::handle_io_bytes(const vdwgb_data *h) { return h->bytes; }
 
@@ -1018,7 +1030,10 @@ size_t vdwgb_footprint_bytes(int nx, int ny, int nz, int precision) {
     const size_t nzh = (size_t)nz / 2 + 1;
     const size_t N = (size_t)nx * ny * nz;
     const size_t nk = (size_t)nx * ny * nzh;
-    return nk * NQ * elem_bytes(p) + N * rec_bytes(p) + nk * sizeof(unsigned) + (nk / 64 + NK) * (sizeof(int4) + sizeof(double));
+    const size_t chunks = max_chunks(nk, p == VDWGB_FP32_MIXED ? CHUNK32 : CHUNK64);
+    const size_t parts = chunks * (p == VDWGB_FP32_MIXED ? C32_CWARPS : 1);
+    return nk * NQ * elem_bytes(p) + N * rec_bytes(p) + nk * sizeof(unsigned) + chunks * sizeof(int4) +
+           parts * sizeof(double);
 }
 
 int vdwgb_launches_per_call(vdwgb_handle h) {

@@ -49,6 +49,11 @@ bool device_peek(int device, int *sms, size_t *maxsmem, int **err);
 // every allocation and upload stream-ordered on it
 int handle_init(vdwgb_data *h, int device, int precision, cudaStream_t alloc_stream);
 void handle_release(vdwgb_data *h);
+// re-plan an initialised handle for another cell and functional of the same
+// grid and precision: metric, k-point order and chunks (on the device),
+// descriptor; buffers, twiddles, tiles and tensor maps are kept.  Waits for
+// the handle's stream (alloc_stream for server handles).
+int handle_replan(vdwgb_data *h, const double *cell9, int functional);
 size_t handle_io_bytes(const vdwgb_data *h);
 // launch set over n handles: fills hdesc[n] (copies of the handles'
 // descriptors; the caller sets I/O pointers), hprefix[NKIND * (n + 1)] and L,

@@ -1038,7 +1038,7 @@ __device__ __forceinline__ bool c32_fetch(int i, int b, int rb, int k, int lane,
 __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__restrict__ sys, const int *__restrict__ prefix,
                                                              int nsys, int total, const float4 *__restrict__ tab,
                                                              int *__restrict__ err) {
-    extern __shared__ __align__(128) unsigned char smem[];
+    extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long *full = reinterpret_cast<unsigned long long *>(smem);   // [C32_RING]
     unsigned long long *empty = full + C32_RING;                             // [C32_RING]
     C32Desc *desc = reinterpret_cast<C32Desc *>(smem + c32_off_desc());
@@ -1554,6 +1554,138 @@ cudaError_t launch_q0(int prec, int npts, const double *n, const double *s, doub
     const int blocks = (npts + 255) / 256;
     if (prec == 1) k_q0<float><<<blocks, 256>>>(npts, n, s, Z, q0, dqdn, dqds);
     else k_q0<double><<<blocks, 256>>>(npts, n, s, Z, q0, dqdn, dqds);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// k-point order (plan step): the half-spectrum k-points of a system sorted by
+// kernel-table interval j = floor(|k| / dk), stably (equal intervals keep
+// index order), for the contraction's chunks.  Each warp owns a range of
+// KSORT_RANGE consecutive k-points: k_ksort_hist counts its range's intervals,
+// k_ksort_scan turns the counts into each range's first position per
+// interval, and k_ksort_scatter walks the range again in index order, 32 at a
+// time, placing each k-point at its interval's next position (the rank among
+// equal intervals of the same step from a warp match).  The result is the
+// order of a sequential stable counting sort.
+// ---------------------------------------------------------------------------
+// interval of half-spectrum index idx: FP32-mixed as the contraction decides
+// it (kpoint_interval32); FP64 from |k| in FP64 with every rounding explicit
+template <bool F32>
+__device__ __forceinline__ int ksort_bin(const SysDev &S, unsigned idx) {
+    const int nx = S.nx, ny = S.ny, nz = S.nz, nzh = S.nzh;
+    const int kz = (int)(idx % (unsigned)nzh);
+    const int rest = (int)(idx / (unsigned)nzh);
+    const int x = axis_freq(rest / ny, nx, S.sx1), y = axis_freq(rest % ny, ny, S.sy1);
+    const int mx = fold(x, nx), my = fold(y, ny);
+    const bool qx = (nx % 2 == 0) && (x == nx / 2), qy = (ny % 2 == 0) && (y == ny / 2);
+    const bool qz = (nz % 2 == 0) && (kz == nz / 2);
+    const int mz = qz ? -kz : kz;
+    if constexpr (F32) {
+        int j;
+        float tt;
+        kpoint_interval32(S.gf, mx, my, mz, qx, qy, qz, j, tt);
+        return j;
+    } else {
+        const double fx = (double)mx, fy = (double)my, fz = (double)mz;
+        const double cx = qx ? 0.0 : fx, cy = qy ? 0.0 : fy, cz = qz ? 0.0 : fz;
+        const double diag = __dadd_rn(__dadd_rn(__dmul_rn(__dmul_rn(S.g[0], fx), fx), __dmul_rn(__dmul_rn(S.g[1], fy), fy)),
+                                      __dmul_rn(__dmul_rn(S.g[2], fz), fz));
+        const double cross = __dadd_rn(__dadd_rn(__dmul_rn(__dmul_rn(S.g[3], cx), cy), __dmul_rn(__dmul_rn(S.g[4], cx), cz)),
+                                       __dmul_rn(__dmul_rn(S.g[5], cy), cz));
+        double k2 = __dadd_rn(diag, __dmul_rn(2.0, cross));
+        k2 = k2 > 0.0 ? k2 : 0.0;
+        const double q = __ddiv_rn(__dsqrt_rn(k2), 2.0 * 3.14159265358979323846 / RMAX);
+        return q < (double)(NK - 1) ? (int)q : NK - 1;
+    }
+}
+
+constexpr int KSORT_WARPS = 8;
+
+template <bool F32>
+__global__ void __launch_bounds__(32 * KSORT_WARPS) k_ksort_hist(SysDev S, int nranges, int *__restrict__ hist) {
+    __shared__ int h[KSORT_WARPS][NK];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.x * KSORT_WARPS + w;
+    if (r >= nranges) return;              // warps work alone: no block barrier below
+    for (int i = lane; i < NK; i += 32) h[w][i] = 0;
+    __syncwarp();
+    const size_t nk = (size_t)S.nx * S.ny * S.nzh;
+    const size_t b0 = (size_t)r * KSORT_RANGE;
+    const size_t b1 = b0 + KSORT_RANGE < nk ? b0 + KSORT_RANGE : nk;
+    for (size_t i = b0 + lane; i < b1; i += 32) atomicAdd(&h[w][ksort_bin<F32>(S, (unsigned)i)], 1);
+    __syncwarp();
+    for (int i = lane; i < NK; i += 32) hist[(size_t)r * NK + i] = h[w][i];
+}
+
+// one block of NK threads: thread j turns the counts of interval j into
+// each range's first position (in place) and writes the interval's total
+__global__ void __launch_bounds__(NK) k_ksort_scan(int nranges, int *__restrict__ hist, int *__restrict__ counts) {
+    __shared__ int tot[NK], start[NK];
+    const int j = threadIdx.x;
+    int run = 0;
+    for (int r = 0; r < nranges; ++r) {
+        const int v = hist[(size_t)r * NK + j];
+        hist[(size_t)r * NK + j] = run;
+        run += v;
+    }
+    counts[j] = run;
+    tot[j] = run;
+    __syncthreads();
+    if (j == 0) {
+        int s0 = 0;
+        for (int q = 0; q < NK; ++q) {
+            start[q] = s0;
+            s0 += tot[q];
+        }
+    }
+    __syncthreads();
+    const int st = start[j];
+    for (int r = 0; r < nranges; ++r) hist[(size_t)r * NK + j] += st;
+}
+
+template <bool F32>
+__global__ void __launch_bounds__(32 * KSORT_WARPS) k_ksort_scatter(SysDev S, int nranges, const int *__restrict__ off,
+                                                                  unsigned *__restrict__ kidx) {
+    __shared__ int so[KSORT_WARPS][NK];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.x * KSORT_WARPS + w;
+    if (r >= nranges) return;
+    for (int i = lane; i < NK; i += 32) so[w][i] = off[(size_t)r * NK + i];
+    __syncwarp();
+    const size_t nk = (size_t)S.nx * S.ny * S.nzh;
+    const size_t b0 = (size_t)r * KSORT_RANGE;
+    const size_t b1 = b0 + KSORT_RANGE < nk ? b0 + KSORT_RANGE : nk;
+    for (size_t base = b0; base < b1; base += 32) {
+        const size_t i = base + lane;
+        const bool in = i < b1;
+        const unsigned mask = __ballot_sync(0xffffffffu, in);
+        if (in) {
+            const int j = ksort_bin<F32>(S, (unsigned)i);
+            const unsigned peers = __match_any_sync(mask, j);
+            const int rank = __popc(peers & ((1u << lane) - 1u));
+            kidx[so[w][j] + rank] = (unsigned)i;
+            __syncwarp(mask);
+            if (lane == __ffs(peers) - 1) so[w][j] += __popc(peers);
+        }
+        __syncwarp();
+    }
+}
+
+size_t ksort_scratch_ints(size_t nk) {
+    const size_t nranges = (nk + KSORT_RANGE - 1) / KSORT_RANGE;
+    return (nranges + 1) * (size_t)NK;
+}
+
+cudaError_t launch_ksort(const SysDev &S, bool f32, unsigned *kidx, int *scratch, cudaStream_t st) {
+    const size_t nk = (size_t)S.nx * S.ny * S.nzh;
+    const int nranges = (int)((nk + KSORT_RANGE - 1) / KSORT_RANGE);
+    int *hist = scratch, *counts = scratch + (size_t)nranges * NK;
+    const int blocks = (nranges + KSORT_WARPS - 1) / KSORT_WARPS;
+    if (f32) k_ksort_hist<true><<<blocks, 32 * KSORT_WARPS, 0, st>>>(S, nranges, hist);
+    else k_ksort_hist<false><<<blocks, 32 * KSORT_WARPS, 0, st>>>(S, nranges, hist);
+    k_ksort_scan<<<1, NK, 0, st>>>(nranges, hist, counts);
+    if (f32) k_ksort_scatter<true><<<blocks, 32 * KSORT_WARPS, 0, st>>>(S, nranges, hist, kidx);
+    else k_ksort_scatter<false><<<blocks, 32 * KSORT_WARPS, 0, st>>>(S, nranges, hist, kidx);
     return cudaGetLastError();
 }
 

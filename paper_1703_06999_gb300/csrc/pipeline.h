@@ -77,6 +77,14 @@ cudaError_t init_plane_kernel(size_t maxsmem);
 int plane_max_clusters(int C, size_t smem);
 const char *stage_name(int i);
 cudaError_t upload_qmesh(const QMeshDev &q);
+// k-point order on the device (plan step): a stable counting sort of the
+// half-spectrum k-points of system S (grid, splits and metric set) by
+// kernel-table interval into kidx[nx ny (nz/2+1)], with the FP32 interval
+// decision of the contraction (f32) or FP64 |k|.  scratch: ksort_scratch_ints
+// ints of device memory; its last NK ints receive the k-points per interval.
+constexpr int KSORT_RANGE = 16384;   // k-points per warp in the sort
+size_t ksort_scratch_ints(size_t nk);
+cudaError_t launch_ksort(const SysDev &S, bool f32, unsigned *kidx, int *scratch, cudaStream_t st);
 cudaError_t launch_q0(int prec, int npts, const double *n, const double *s, double Z, double *q0, double *dqdn,
                       double *dqds);
 

@@ -1,13 +1,20 @@
 // Serving loop: evaluations of different grids arrive over time; each is
 // admitted when its device-memory footprint fits the server's budget,
-// planned on a host thread (FFT plans, k-point order, stream-ordered
-// allocations, input upload), and joins the next batched launch (one launch
+// planned on a host thread, and joins the next batched launch (one launch
 // per stage over all systems of the batch).  Up to max_inflight batches run
 // at once on their own streams, so requests that arrive while others are on
 // the GPU are admitted and overlap with them (continuous batching).  The
-// kernel table stays resident on the device for the server's lifetime.
+// kernel table stays resident on the device for the server's lifetime, and
+// so do plans: a finished request's handle (buffers, FFT twiddles, tile
+// shapes, tensor maps) stays on the device, counted against the pool, and
+// the next request of the same grid re-plans only what depends on its cell
+// and functional (metric and k-point order, sorted on the device).  Idle
+// plans are evicted, least recently used first, when an admission needs
+// their memory.
 #include <algorithm>
 #include <atomic>
+#include <list>
+#include <tuple>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -72,6 +79,14 @@ struct vdwgb_server_s {
     std::vector<std::thread> workers;
     bool stop = false;
     long long next_id = 1;
+    // resident plans not in use, most recently used first: (grid, handle, footprint)
+    struct Idle {
+        std::tuple<int, int, int> grid;
+        vdwgb_data *h;
+        size_t footprint;
+    };
+    std::list<Idle> idle;
+    long long plans_reused = 0, plans_built = 0;
     // statistics
     long long submitted = 0, completed = 0, failed = 0, batches = 0, batched_reqs = 0;
     double t_first = 0, t_last = 0;
@@ -84,28 +99,75 @@ static size_t request_footprint(int nx, int ny, int nz, int prec) {
     return vdwgb_footprint_bytes(nx, ny, nz, prec) + (4 * N + 1) * sizeof(double) + (1u << 20);
 }
 
-// planner: admit in arrival order while the footprint fits, plan, upload inputs
+// an idle resident plan of this grid, or nullptr (under the lock)
+static vdwgb_data *take_idle(vdwgb_server_s *s, const Req *r) {
+    const auto key = std::make_tuple(r->nx, r->ny, r->nz);
+    for (auto it = s->idle.begin(); it != s->idle.end(); ++it)
+        if (it->grid == key) {
+            vdwgb_data *h = it->h;
+            s->idle.erase(it);
+            return h;
+        }
+    return nullptr;
+}
+
+static size_t idle_bytes(const vdwgb_server_s *s) {
+    size_t b = 0;
+    for (const auto &x : s->idle) b += x.footprint;
+    return b;
+}
+
+// planner: admit in arrival order while the footprint fits (a resident plan
+// of the same grid, the free pool, or the free pool after evicting idle
+// plans), plan or re-plan, upload inputs
 static void planner_loop(vdwgb_server_s *s, int k) {
     cudaSetDevice(s->device);
     cudaStream_t st = s->plan_streams[k];
     for (;;) {
         Req *r = nullptr;
+        vdwgb_data *reuse = nullptr;
+        std::vector<vdwgb_data *> evict;
         {
             std::unique_lock<std::mutex> lk(s->mu);
             s->cv.wait(lk, [&] {
-                return s->stop || (!s->pending.empty() && s->pending.front()->footprint <= s->pool - s->used);
+                if (s->stop) return true;
+                if (s->pending.empty()) return false;
+                const Req *f = s->pending.front();
+                const auto key = std::make_tuple(f->nx, f->ny, f->nz);
+                for (const auto &x : s->idle)
+                    if (x.grid == key) return true;
+                return f->footprint <= s->pool - s->used + idle_bytes(s);
             });
             if (s->stop) return;
             r = s->pending.front();
             s->pending.pop_front();
-            s->used += r->footprint;
+            reuse = take_idle(s, r);
+            if (reuse) {
+                ++s->plans_reused;             // its footprint stays counted in used
+            } else {
+                while (r->footprint > s->pool - s->used && !s->idle.empty()) {
+                    evict.push_back(s->idle.back().h);   // least recently used
+                    s->used -= s->idle.back().footprint;
+                    s->idle.pop_back();
+                }
+                s->used += r->footprint;
+                ++s->plans_built;
+            }
             s->peak = std::max(s->peak, s->used);
         }
-        int rc = vdwgb_new(r->functional, &r->h);
-        if (!rc)
-            rc = vdwgb_set_unit_cell(r->h, r->nx, r->ny, r->nz, r->cell[0], r->cell[1], r->cell[2], r->cell[3],
-                                     r->cell[4], r->cell[5], r->cell[6], r->cell[7], r->cell[8]);
-        if (!rc) rc = handle_init(r->h, s->device, s->prec, st);
+        for (vdwgb_data *h : evict) vdwgb_finalize(&h);   // stream-ordered frees
+        int rc = 0;
+        if (reuse) {
+            r->h = reuse;
+            r->h->alloc_stream = st;           // this planner's stream orders its work from now on
+            rc = handle_replan(r->h, r->cell, r->functional);
+        } else {
+            rc = vdwgb_new(r->functional, &r->h);
+            if (!rc)
+                rc = vdwgb_set_unit_cell(r->h, r->nx, r->ny, r->nz, r->cell[0], r->cell[1], r->cell[2], r->cell[3],
+                                         r->cell[4], r->cell[5], r->cell[6], r->cell[7], r->cell[8]);
+            if (!rc) rc = handle_init(r->h, s->device, s->prec, st);
+        }
         if (!rc) {
             const size_t N = r->npts;
             cudaError_t e = cudaMemcpyAsync(r->h->d_io, r->rho, N * sizeof(double), cudaMemcpyHostToDevice, st);
@@ -235,7 +297,9 @@ static void complete_slot(vdwgb_server_s *s, Slot *slot, int dev_rc, cudaStream_
         }
         if (r->ready) cudaEventDestroy(r->ready);
         r->ready = nullptr;
-        if (r->h) vdwgb_finalize(&r->h);   // stream-ordered frees on its planner stream
+        // failed requests release their plan (stream-ordered frees); finished
+        // ones keep it resident for the next request of the same grid
+        if (r->h && st[i] != 0) vdwgb_finalize(&r->h);
     }
     const double t = now_s();
     std::lock_guard<std::mutex> lk(s->mu);
@@ -243,7 +307,12 @@ static void complete_slot(vdwgb_server_s *s, Slot *slot, int dev_rc, cudaStream_
         Req *r = reqs[i];
         r->energy = en[i];
         r->t_done = t;
-        s->used -= r->footprint;
+        if (r->h) {
+            s->idle.push_front({std::make_tuple(r->nx, r->ny, r->nz), r->h, r->footprint});
+            r->h = nullptr;
+        } else {
+            s->used -= r->footprint;
+        }
         if (st[i] == 0) {
             ++s->completed;
             s->pts_done += (double)r->npts;
@@ -431,6 +500,8 @@ int vdwgb_server_stats(vdwgb_server s, vdwgb_server_stats_t *out) {
     out->mean_batch = s->batches ? (double)s->batched_reqs / (double)s->batches : 0.0;
     out->pool_bytes = s->pool;
     out->pool_used_peak = s->peak;
+    out->plans_reused = s->plans_reused;
+    out->plans_built = s->plans_built;
     const double span = s->t_last - s->t_first;
     out->pts_per_s = span > 0 ? s->pts_done / span : 0.0;
     if (!s->lat.empty()) {
@@ -473,6 +544,8 @@ int vdwgb_server_free(vdwgb_server *sp) {
         if (r->ready) cudaEventDestroy(r->ready);
         delete r;
     }
+    for (auto &x : s->idle) vdwgb_finalize(&x.h);
+    s->idle.clear();
     for (auto &sl : s->slots) {
         if (sl.st) cudaStreamSynchronize(sl.st);
         if (sl.st) cudaStreamDestroy(sl.st);

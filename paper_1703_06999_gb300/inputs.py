@@ -51,32 +51,49 @@ def _grid_coords(shape, cell, device):
 
 def density(shape, cell, atoms: Sequence[Atom], floor: float = 1e-10,
             device="cpu", cutoff: float = 30.0) -> torch.Tensor:
-    """n(r) on the grid (float64, [nx][ny][nz], z contiguous)."""
+    """n(r) on the grid (float64, [nx][ny][nz], z contiguous).  Every periodic
+    image of an atom that can come within zeta |r - R| <= cutoff of the cell
+    contributes; the images are evaluated in groups (one pass over the grid
+    per group) to keep the number of device operations small.  On a GPU the
+    distances and exponentials are evaluated in FP32 (the GPU's FP64 rate is
+    a small fraction of its FP32 rate; the density then differs from the FP64
+    evaluation by about 1e-5 relative) and summed in FP64."""
     cell = np.asarray(cell, dtype=np.float64)
-    r = _grid_coords(shape, cell, device)
-    n = torch.full(tuple(shape), float(floor), dtype=torch.float64, device=device)
+    r = _grid_coords(shape, cell, device).reshape(-1, 3)
+    npts = r.shape[0]
     # shortest distance between opposite faces, for the image range
     vol = abs(np.linalg.det(cell))
     heights = [vol / np.linalg.norm(np.cross(cell[(i + 1) % 3], cell[(i + 2) % 3])) for i in range(3)]
-    cell_t = torch.as_tensor(cell, device=device)
     mid = 0.5 * cell.sum(axis=0)
     half_diag = 0.5 * max(np.linalg.norm(cell[0] * sx + cell[1] * sy + cell[2] * sz)
                           for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1))
+    centres, zetas, prefs = [], [], []
     for Z, zeta, centre in atoms:
         reach = cutoff / zeta
         nimg = [int(math.ceil(reach / h)) + 1 for h in heights]
         pref = Z * zeta ** 3 / (8.0 * math.pi)
-        c = torch.as_tensor(np.asarray(centre, dtype=np.float64), device=device)
         for i in range(-nimg[0], nimg[0] + 1):
             for j in range(-nimg[1], nimg[1] + 1):
                 for k in range(-nimg[2], nimg[2] + 1):
-                    shift_np = np.asarray(centre) + i * cell[0] + j * cell[1] + k * cell[2]
-                    if (np.linalg.norm(shift_np - mid) - half_diag) * zeta > cutoff:
+                    shift = np.asarray(centre) + i * cell[0] + j * cell[1] + k * cell[2]
+                    if (np.linalg.norm(shift - mid) - half_diag) * zeta > cutoff:
                         continue          # this image cannot reach the cell
-                    shift = c + i * cell_t[0] + j * cell_t[1] + k * cell_t[2]
-                    d = torch.linalg.vector_norm(r - shift, dim=-1)
-                    n += pref * torch.exp(-zeta * d)
-    return n
+                    centres.append(shift)
+                    zetas.append(zeta)
+                    prefs.append(pref)
+    n = torch.full((npts,), float(floor), dtype=torch.float64, device=device)
+    if centres:
+        fdt = torch.float32 if torch.device(device).type == "cuda" else torch.float64
+        c = torch.as_tensor(np.asarray(centres), dtype=fdt, device=device)
+        zt = torch.as_tensor(np.asarray(zetas), dtype=fdt, device=device)
+        pf = torch.as_tensor(np.asarray(prefs), dtype=torch.float64, device=device)
+        rr = r.to(fdt)
+        group = max(1, (1 << 25) // max(npts, 1))          # about 128-256 MB of distances per group
+        for g0 in range(0, len(centres), group):
+            g1 = min(len(centres), g0 + group)
+            d = torch.cdist(c[g0:g1], rr, compute_mode="donot_use_mm_for_euclid_dist")   # (group, npts)
+            n += (pf[g0:g1, None] * torch.exp(-zt[g0:g1, None] * d).to(torch.float64)).sum(dim=0)
+    return n.reshape(tuple(shape))
 
 
 def spectral_sigma(n: torch.Tensor, cell) -> torch.Tensor:

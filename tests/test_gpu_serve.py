@@ -78,3 +78,61 @@ def test_server_rejects_oversized_and_bad_requests():
             B.vdwgb_server_poll(sv, 123456)      # unknown id
     finally:
         B.vdwgb_server_free(sv)
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_resident_plans_are_replanned_for_new_cells(prec):
+    # Requests of one grid but different cells and functionals, one after the
+    # other: from the second on, each re-plans the resident plan of its grid
+    # (metric, k-point order sorted on the device, chunks) and must give the
+    # result of a fresh handle bit for bit.
+    systems = []
+    for i in range(6):
+        sh = (24, 20, 30) if i % 2 == 0 else (32, 32, 16)
+        g = np.random.default_rng(300 + i)
+        L = np.array(sh) * g.uniform(0.18, 0.32)
+        cell = np.diag(L)
+        if i == 4:                                   # a triclinic cell too
+            cell = np.array([[L[0], 0, 0], [0.7, L[1], 0], [-0.4, 0.9, L[2]]])
+        atoms = [(float(g.uniform(1, 6)), float(g.uniform(1, 2.5)), tuple(g.uniform(0, 1, 3) @ cell))
+                 for _ in range(3)]
+        systems.append(inputs.make_system(sh, cell, atoms, 1 + (i // 2) % 2))
+    alone = []
+    for s in systems:
+        f = B.Functional(s.shape, s.cell, s.functional, prec)
+        alone.append(f.calculate(s.n.numpy(), s.sigma.numpy()))
+        f.close()
+    sv = B.vdwgb_server_new(0, prec, pool_bytes=1 << 30, max_batch=4, max_inflight=2)
+    try:
+        for s, a in zip(systems, alone):
+            dn, ds = np.empty(s.shape), np.empty(s.shape)
+            rid = B.vdwgb_server_submit(sv, s.functional, s.shape, s.cell, s.n.numpy(), s.sigma.numpy(), dn, ds)
+            e, _ = B.vdwgb_server_wait(sv, rid, 120.0)
+            assert e == a[0] and np.array_equal(dn, a[1]) and np.array_equal(ds, a[2])
+        st = B.vdwgb_server_stats(sv)
+        assert st["plans_built"] == 2 and st["plans_reused"] == 4 and st["failed"] == 0
+    finally:
+        B.vdwgb_server_free(sv)
+
+
+def test_idle_plans_are_evicted_when_the_pool_is_full():
+    # a pool that holds one plan of each grid at a time: alternating grids
+    # evict the other grid's idle plan, and every request still completes
+    g1, g2 = (48, 48, 40), (40, 48, 48)
+    foot = max(B.vdwgb_footprint_bytes(g1, B.FP32_MIXED), B.vdwgb_footprint_bytes(g2, B.FP32_MIXED))
+    npts = 48 * 48 * 40
+    pool = int(1.5 * (foot + 32 * npts + (1 << 20)))
+    sv = B.vdwgb_server_new(0, B.FP32_MIXED, pool_bytes=pool, max_batch=1, max_inflight=1)
+    try:
+        for i in range(4):
+            sh = g1 if i % 2 == 0 else g2
+            x = np.full(sh, 0.02)
+            dn, ds = np.empty(sh), np.empty(sh)
+            rid = B.vdwgb_server_submit(sv, 1, sh, np.diag(np.array(sh) * 0.25), x, x * 0.0, dn, ds)
+            e, _ = B.vdwgb_server_wait(sv, rid, 120.0)
+            assert np.isfinite(e)
+        st = B.vdwgb_server_stats(sv)
+        assert st["completed"] == 4 and st["plans_built"] == 4 and st["plans_reused"] == 0
+        assert st["pool_used_peak"] <= pool
+    finally:
+        B.vdwgb_server_free(sv)
