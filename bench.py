@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "dimer96_batch8", "cubic24", "shell192"])
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "dimer96_batch8", "cubic24", "shell192", "shell640"])
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle errors and the CPU baseline")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-stream measurement")
     ap.add_argument("--no-extra", action="store_true", help="skip the extra 96^3 dimer batch")
@@ -96,7 +97,41 @@ def make_workload(name, rank, device):
         return [inputs.small_cubic(rank, ngrid=24, device=device)]
     if name == "shell192":
         return [inputs.ligand_shell(rank, device=device)]
+    if name == "shell640":
+        return [shell640(rank, device)]
     return inputs.uneven_batch(rank, count=64, device=device)
+
+
+def shell160(seed, device):
+    """A ligand-shell-like density on 160^3 points in a 27.4 bohr cell: a core
+    of 12 exponentials and 8 radial chains of 4 (one quarter of the paper's
+    (58 Angstrom)^3 box along each axis)."""
+    from paper_1703_06999_gb300 import inputs
+    g = np.random.default_rng(640 + seed)
+    L = 109.6 / 4
+    c0 = np.array([L / 2] * 3)
+    atoms = []
+    for _ in range(12):
+        v = g.normal(size=3)
+        v *= g.uniform(0, 3.0) / np.linalg.norm(v)
+        atoms.append((float(g.uniform(6, 8)), float(g.uniform(2, 3)), tuple(c0 + v)))
+    for _ in range(8):
+        u = g.normal(size=3)
+        u /= np.linalg.norm(u)
+        for k in range(4):
+            atoms.append((float(g.uniform(1, 6)), float(g.uniform(1, 2.5)), tuple(c0 + (4.0 + 1.2 * k) * u)))
+    return inputs.make_system((160, 160, 160), np.diag([L, L, L]), atoms, 1, device=device, name="shell160")
+
+
+def shell640(seed, device):
+    """The paper's density-grid size: 640^3 points in a (58 Angstrom)^3 =
+    109.6 bohr cubic box, the 4 x 4 x 4 supercell of shell160 (so that its
+    energy is 64 times the 160^3 system's, a check at a size no oracle run
+    reaches)."""
+    from paper_1703_06999_gb300 import inputs
+    b = shell160(seed, device)
+    return inputs.System((640, 640, 640), 4 * b.cell, 1, b.n.repeat(4, 4, 4).contiguous(),
+                         b.sigma.repeat(4, 4, 4).contiguous(), [], "shell640")
 
 
 # ---------------------------------------------------------------------------
@@ -593,35 +628,55 @@ def main():
     B.vdwgb_batch_free(bt)
 
     # ---- FP64 plain, one system at a time, same inputs ------------------------
-    f64 = make(B.FP64, systems)
-    k64 = max(2, args.steps // 4)
-    for i, f in enumerate(f64):
-        f.calculate_device(ns[i], ss[i], dn[i], ds[i], en[i:i + 1], sp)
-    torch.cuda.synchronize()
-    B.vdwgb_device_status(local)
-    g64 = [(float(en[i]), dn[i].cpu().numpy(), ds[i].cpu().numpy()) for i in range(nb)]
-    t64 = 0.0
-    for _ in range(k64):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
+    try:
+        f64 = make(B.FP64, systems)
+    except B.VdwgbError:
+        f64 = None                        # grids whose FP64 tiles do not fit shared memory (640 axes)
+    supercell = None
+    if f64 is None:
+        fp64_value, k64, t64, g64, per_launch64, err_32_64 = None, 0, 0.0, None, None, None
+        if args.workload == "shell640":
+            # the 160^3 cell of the supercell in FP64: E(640^3) = 64 E(160^3), tiled potentials
+            b = shell160(rank, dev)
+            fb = B.Functional(b.shape, b.cell, 1, B.FP64, device=local)
+            eb, dnb, dsb = fb.calculate(b.n.cpu().numpy(), b.sigma.cpu().numpy())
+            fb.close()
+            tile = lambda x: np.tile(x, (4, 4, 4))
+            supercell = {"fp64_160cubed_energy_Ha": eb, "fp32_640cubed_energy_over_64_Ha": g32[0][0] / 64,
+                         "abs_dE_per_160cubed_cell_Ha": abs(g32[0][0] / 64 - eb),
+                         "rel_dE": abs(g32[0][0] / 64 - eb) / abs(eb),
+                         "dedn_maxnorm_rel": float(np.max(np.abs(g32[0][1] - tile(dnb))) / np.max(np.abs(dnb))),
+                         "dedsigma_maxnorm_rel": float(np.max(np.abs(g32[0][2] - tile(dsb))) / np.max(np.abs(dsb)))}
+    else:
+        k64 = max(2, args.steps // 4)
+    if f64 is not None:
         for i, f in enumerate(f64):
             f.calculate_device(ns[i], ss[i], dn[i], ds[i], en[i:i + 1], sp)
-        b.record(stream)
-        b.synchronize()
-        t64 += a.elapsed_time(b)
-    fp64_value = pts * k64 / (t64 / 1000.0)
-    # FP64 stage breakdown (one launch per stage over the batch)
-    bt64 = B.vdwgb_batch_new([f.h for f in f64])
-    per_launch64 = stage_breakdown(B, torch, bt64, ns, ss, dn, ds, en, sp, flush, max(2, args.steps // 4))
-    B.vdwgb_batch_free(bt64)
-    for f in f64:
-        f.close()
-    err_32_64 = {"max_abs_dE_Ha": max(abs(a[0] - b[0]) for a, b in zip(g32, g64)),
-                 "dedn_maxnorm_rel": max(float(np.max(np.abs(a[1] - b[1])) / np.max(np.abs(b[1])))
-                                         for a, b in zip(g32, g64)),
-                 "dedsigma_maxnorm_rel": max(float(np.max(np.abs(a[2] - b[2])) / np.max(np.abs(b[2])))
-                                             for a, b in zip(g32, g64))}
+        torch.cuda.synchronize()
+        B.vdwgb_device_status(local)
+        g64 = [(float(en[i]), dn[i].cpu().numpy(), ds[i].cpu().numpy()) for i in range(nb)]
+        t64 = 0.0
+        for _ in range(k64):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for i, f in enumerate(f64):
+                f.calculate_device(ns[i], ss[i], dn[i], ds[i], en[i:i + 1], sp)
+            b.record(stream)
+            b.synchronize()
+            t64 += a.elapsed_time(b)
+        fp64_value = pts * k64 / (t64 / 1000.0)
+        # FP64 stage breakdown (one launch per stage over the batch)
+        bt64 = B.vdwgb_batch_new([f.h for f in f64])
+        per_launch64 = stage_breakdown(B, torch, bt64, ns, ss, dn, ds, en, sp, flush, max(2, args.steps // 4))
+        B.vdwgb_batch_free(bt64)
+        for f in f64:
+            f.close()
+        err_32_64 = {"max_abs_dE_Ha": max(abs(a[0] - b[0]) for a, b in zip(g32, g64)),
+                     "dedn_maxnorm_rel": max(float(np.max(np.abs(a[1] - b[1])) / np.max(np.abs(b[1])))
+                                             for a, b in zip(g32, g64)),
+                     "dedsigma_maxnorm_rel": max(float(np.max(np.abs(a[2] - b[2])) / np.max(np.abs(b[2])))
+                                                 for a, b in zip(g32, g64))}
 
     # ---- rooflines of the stages ----------------------------------------------
     names = [B.vdwgb_stage_name(i) for i in range(B.vdwgb_num_stages())]
@@ -646,7 +701,8 @@ def main():
     fp64_peak = B.vdwgb_alu_peak(2, local)
     ic = names.index("contract")
     c_gflops = 4.0 * CONTRACT_FMA2_PER_KPOINT * nk_total / (per_launch_ms[ic] / 1000.0) / 1e9
-    c64_gflops = 2.0 * CONTRACT_FMA64_PER_KPOINT * nk_total / (per_launch64[ic] / 1000.0) / 1e9
+    c64_gflops = (2.0 * CONTRACT_FMA64_PER_KPOINT * nk_total / (per_launch64[ic] / 1000.0) / 1e9
+                  if per_launch64 is not None else None)
     roof = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": hbm,
             "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
             "peak_source": pk_kind + " (copy bandwidth, MEASURED_PEAKS.json hbm_gbs)",
@@ -664,10 +720,12 @@ def main():
            "contract_fp32": {"achieved_gflops": c_gflops, "peak_gflops": fp32x2_peak,
                              "frac": c_gflops / fp32x2_peak,
                              "flops_per_kpoint": 4 * CONTRACT_FMA2_PER_KPOINT},
-           "contract_fp64": {"achieved_gflops": c64_gflops, "peak_gflops": fp64_peak,
+           "contract_fp64": None if per_launch64 is None else
+                            {"achieved_gflops": c64_gflops, "peak_gflops": fp64_peak,
                              "frac": c64_gflops / fp64_peak, "ms_per_launch": float(per_launch64[ic]),
                              "flops_per_kpoint": 2 * CONTRACT_FMA64_PER_KPOINT},
-           "fp64_stages_ms_per_launch": {n: float(m) for n, m in zip(names, per_launch64)}}
+           "fp64_stages_ms_per_launch": None if per_launch64 is None else
+                                        {n: float(m) for n, m in zip(names, per_launch64)}}
 
     # ---- extra workload: the 8-system 96^3 dimer batch ------------------------
     extra = None
@@ -702,7 +760,7 @@ def main():
 
     # ---- oracle: errors of both forms and the CPU baseline (all host cores) ---
     err32 = err64 = cpu = None
-    if not args.no_oracle and rank == 0 and world == 1:
+    if not args.no_oracle and rank == 0 and world == 1 and args.workload != "shell640":
         jobs = [(i, s.n.cpu().numpy(), s.sigma.cpu().numpy(), s.cell, s.functional) for i, s in enumerate(systems)]
         workers = oracle_workers(max(s.npts for s in systems))
         pool = OraclePool(workers)
@@ -711,7 +769,7 @@ def main():
         finally:
             pool.close()
         err32 = errors_vs_oracle(g32, ref)
-        err64 = errors_vs_oracle(g64, ref)
+        err64 = errors_vs_oracle(g64, ref) if g64 is not None else None
         one = float(np.mean([ref[i][4] / systems[i].npts for i in ref]))    # seconds per point, one core
         cpu = {"value": pts / wall, "unit": "grid pts/s", "cores": workers, "kind": "oracle",
                "sample": "the whole %s workload (%d systems, %d grid points), one system per worker process"
@@ -731,9 +789,10 @@ def main():
                        "l2": "flushed between timed steps (256 MB write); working set %.0f MB"
                              % (sum(s.shape[0] * s.shape[1] * (s.shape[2] // 2 + 1) * 160 + 48 * s.npts
                                     for s in systems) / 1e6)},
-            "fp64_plain": {"value": fp64_value, "unit": "grid pts/s", "steps": k64,
+            "fp64_plain": None if fp64_value is None else
+                          {"value": fp64_value, "unit": "grid pts/s", "steps": k64,
                            "ms_per_step": t64 / k64, "form": "one system at a time"},
-            "speedup_fp32_batched_vs_fp64_plain": value / (fp64_value * world),
+            "speedup_fp32_batched_vs_fp64_plain": None if fp64_value is None else value / (fp64_value * world),
             "latency_ms": {"single_system_fp32": {"p50": float(np.percentile(lat, 50)),
                                                   "p99": float(np.percentile(lat, 99)), "n": int(lat.size)},
                            "batch_step": {"p50": float(np.percentile(step_ms, 50)),
@@ -750,6 +809,8 @@ def main():
         }
         if cpu is not None:
             out["cpu_baseline"] = cpu
+        if supercell is not None:
+            out["supercell_check"] = supercell
         if extra is not None:
             out["extra"] = extra
         if serving is not None:

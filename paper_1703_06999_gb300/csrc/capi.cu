@@ -437,9 +437,9 @@ static void set_tiles(vdwgb_data *h, int LZ, int LZi, int Wy, int Wx, int nby, i
     L.twmax[1] = ny;
     L.twmax[2] = nx;
     L.bufelems[0] = 0;
-    // z-inverse: FP32 axes with an in-place split read the spectrum and the
-    // records straight from global memory (nothing staged); others stage tiles
-    const bool zdirect = prec == VDWGB_FP32_MIXED && S.sz1;
+    // z-inverse: FP32 reads the spectrum and the records straight from
+    // global memory (nothing staged); FP64 stages tiles
+    const bool zdirect = prec == VDWGB_FP32_MIXED;
     L.bufelems[3] = zdirect ? 0 : LZi * nzh * NQ;
     L.recelems = zdirect ? 0 : LZi * nz;
     L.abelems = nz * z_ld(LZi);
@@ -1227,21 +1227,12 @@ int vdwgb::batch_launchset(vdwgb_data *const *hs, int count, SysDev *hdesc, int 
     const int prec = hs[0]->prec;
     DevInfo &di = g_dev[device];
     const size_t lim = di.maxsmem - 1024;
-    // z-inverse: the launch runs the direct form only if every system does;
-    // otherwise the direct systems' tiles are staged too, with their lines
-    // per tile lowered (in the batch's copies of the descriptors) until a
-    // staged tile fits shared memory
-    bool zdirect = true;
-    for (int i = 0; i < count; ++i) zdirect = zdirect && hs[i]->ls.bufelems[3] == 0;
+    // z-inverse: the direct form (nothing staged) is the FP32 one; a batch
+    // holds one precision
+    const bool zdirect = prec == VDWGB_FP32_MIXED;
     for (int i = 0; i < count; ++i) {
         hdesc[i] = hs[i]->hsys;
-        SysDev &D = hdesc[i];
-        if (!zdirect && hs[i]->ls.bufelems[3] == 0) {
-            int l = D.LZi;
-            while (l > 1 && zinv_smem(prec, D.nz, l * D.nzh * NQ, l * D.nz, D.nz * z_ld(l), 1) > lim) --l;
-            D.LZi = l;
-            D.tiles[3] = (D.nx * D.ny + l - 1) / l;
-        }
+        const SysDev &D = hdesc[i];
         for (int s = 0; s < NKIND; ++s) {
             pre[s * (count + 1) + i + 1] = pre[s * (count + 1) + i] + D.tiles[s];
             if (hs[i]->ls.smem[s] > L.smem[s]) L.smem[s] = hs[i]->ls.smem[s];

@@ -284,8 +284,8 @@ extern "C" int vdwgb_calculate_noalloc(int device, int functional, int nx, int n
     L.twmax[0] = L.twmax[3] = nz;
     L.twmax[1] = ny;
     L.twmax[2] = nx;
-    L.bufelems[3] = S.sz1 ? 0 : S.LZi * nzh * NQ;     // split z axes: direct z-inverse, nothing staged
-    L.recelems = S.sz1 ? 0 : S.LZi * nz;
+    L.bufelems[3] = 0;                               // FP32: direct z-inverse, nothing staged
+    L.recelems = 0;
     L.abelems = nz * z_ld(S.LZi);
     L.bufelems[1] = ny * S.Wy * NQ;
     L.bufelems[2] = nx * S.Wx * NQ;

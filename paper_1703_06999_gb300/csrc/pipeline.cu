@@ -1225,6 +1225,53 @@ __device__ __forceinline__ void zinv_issue(const SysDev *__restrict__ sys, const
     bulk_g2s(rbuf, reinterpret_cast<const Rec<T> *>(S.rec) + (size_t)l0 * S.nz, rb, bar);
 }
 
+// Pack the staged (or global) half spectra of nl z-lines into complex
+// lines of the transform buffer a ([z][ld], line li * 10 + c):
+// Z_c[kz] = X_2c[kz] + i X_2c+1[kz] and, for the mirror, Z_c[nz - kz] =
+// conj(X_2c[kz]) + i conj(X_2c+1[kz]); the imaginary parts of the kz = 0 and
+// Nyquist bins are dropped (complex-to-real semantics).  One thread handles
+// half h (c = 5h .. 5h + 4) of one (line, kz).  No barrier at the end.
+template <typename T>
+__device__ __forceinline__ void zinv_pack(cx<T> *a, const cx<T> *spec, int nl, int nz, int nzh, int ld) {
+    const bool even = (nz % 2) == 0;
+    const int half = threadIdx.x & 1;
+    const int step = blockDim.x >> 1;
+    const int dk = step % nzh, dli = step / nzh;
+    int kz = (threadIdx.x >> 1) % nzh, li = (threadIdx.x >> 1) / nzh;
+    for (; li < nl;) {
+        const cx<T> *in = spec + ((size_t)li * nzh + kz) * NQ + 10 * half;
+        const int km = nz - kz;
+        const bool mirror = kz > 0 && km >= nzh;
+        const bool realbin = kz == 0 || (even && kz == nz / 2);
+        cx<T> *o1 = a + (size_t)kz * ld + li * 10 + 5 * half;
+        cx<T> *o2 = a + (size_t)(mirror ? km : 0) * ld + li * 10 + 5 * half;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            cx<T> x0, x1;
+            if constexpr (sizeof(T) == 4) {
+                const float4 v = *reinterpret_cast<const float4 *>(in + 2 * c);
+                x0 = cx<T>{v.x, v.y};
+                x1 = cx<T>{v.z, v.w};
+            } else {
+                x0 = in[2 * c];
+                x1 = in[2 * c + 1];
+            }
+            if (realbin) {
+                x0.y = (T)0;
+                x1.y = (T)0;
+            }
+            o1[c] = cx<T>{x0.x - x1.y, x0.y + x1.x};
+            if (mirror) o2[c] = cx<T>{x0.x + x1.y, x1.x - x0.y};
+        }
+        kz += dk;
+        li += dli;
+        if (kz >= nzh) {
+            kz -= nzh;
+            ++li;
+        }
+    }
+}
+
 // Potential of the z-inverse tile's nl lines (Eq. dedn, Eq. dedsigma):
 // dE/dtheta_a = dV F_a; dedn = sum_a F_a (p_a + n p_a' dq0/dn), dedsigma =
 // sum_a F_a n p_a' dq0/dsigma (the 1/N of the inverse transform folded in).
@@ -1309,12 +1356,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zinv(const SysD
     load_qshared(qs);
     __syncthreads();
     if (inelems == 0) {
-        // direct form (every system of the launch transforms in place, FP32):
-        // the first transform pass reads the tile's half spectrum straight
-        // from global memory (each ten consecutive threads read one k-point's
-        // 160 contiguous bytes) and the potential reads the point records
-        // from global memory; nothing is staged, so the block needs only the
-        // transform buffer and runs at the occupancy its registers allow
+        // direct form (FP32): the first transform pass (or, on axes without
+        // an in-place split, the packing of the complex lines) reads the
+        // tile's half spectrum straight from global memory (each ten
+        // consecutive threads read one k-point's 160 contiguous bytes) and
+        // the potential reads the point records from global memory; nothing
+        // is staged, so the block needs only its transform buffers and runs
+        // at the occupancy its registers allow
         int cur_sys = -1, tbase = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x) {
             const int nsi = advance_sys(prefix, nsys, t, cur_sys);
@@ -1333,8 +1381,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zinv(const SysD
             const int nl = min(S.LZi, S.nx * S.ny - l0);
             const int ld = z_ld(nl);
             const cx<T> *gspec = reinterpret_cast<const cx<T> *>(S.spec) + (size_t)l0 * S.nzh * NQ;
-            fft_ip_inv_packed_auto<T>(bufA, gspec, S.nz, 10 * nl, ld, S.nzh, tw);
-            zinv_potential<T>(S, qs, bufA, reinterpret_cast<const Rec<T> *>(S.rec) + (size_t)l0 * S.nz, l0, nl, ld);
+            cx<T> *R = bufA;
+            if (sizeof(T) == 4 && S.sz1) {
+                fft_ip_inv_packed_auto<T>(bufA, gspec, S.nz, 10 * nl, ld, S.nzh, tw);
+            } else {
+                zinv_pack<T>(bufA, gspec, nl, S.nz, S.nzh, ld);
+                __syncthreads();
+                R = fft_auto<true>(bufA, bufB, S.ax[2], 10 * nl, ld, tw);
+            }
+            zinv_potential<T>(S, qs, R, reinterpret_cast<const Rec<T> *>(S.rec) + (size_t)l0 * S.nz, l0, nl, ld);
             __syncthreads();                 // bufA is rewritten by the next tile
         }
         if (threadIdx.x == 0) {
@@ -1382,48 +1437,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zinv(const SysD
         // complex lines straight from the staged half spectrum; other axes:
         // packed into the tile buffer first, then transformed
         const int zs = sizeof(T) == 4 ? S.sz1 : 0, zs2 = zs ? nz / zs : 0;
-        // Z_c[kz] = X_{2c}[kz] + i X_{2c+1}[kz]; Z_c[nz-kz] = conj(X_{2c}) + i conj(X_{2c+1});
-        // one thread handles half h (c = 5h .. 5h+4) of one (line, kz)
-        if (!zs) {
-            const int half = threadIdx.x & 1;
-            const int step = blockDim.x >> 1;
-            const int dk = step % nzh, dli = step / nzh;
-            int kz = (threadIdx.x >> 1) % nzh, li = (threadIdx.x >> 1) / nzh;
-            for (; li < nl;) {
-                const cx<T> *in = spec + ((size_t)li * nzh + kz) * NQ + 10 * half;
-                const int km = nz - kz;
-                const bool mirror = kz > 0 && km >= nzh;
-                const bool realbin = kz == 0 || (even && kz == nz / 2);
-                const int pk = zs ? fft_perm_pos(kz, zs, zs2) : kz;
-                const int pm = mirror ? (zs ? fft_perm_pos(km, zs, zs2) : km) : 0;
-                cx<T> *o1 = bufA + (size_t)pk * ld + li * 10 + 5 * half;
-                cx<T> *o2 = bufA + (size_t)pm * ld + li * 10 + 5 * half;
-#pragma unroll
-                for (int c = 0; c < 5; ++c) {
-                    cx<T> a, b;
-                    if constexpr (sizeof(T) == 4) {
-                        const float4 v = *reinterpret_cast<const float4 *>(in + 2 * c);
-                        a = cx<T>{v.x, v.y};
-                        b = cx<T>{v.z, v.w};
-                    } else {
-                        a = in[2 * c];
-                        b = in[2 * c + 1];
-                    }
-                    if (realbin) {
-                        a.y = (T)0;
-                        b.y = (T)0;
-                    }
-                    o1[c] = cx<T>{a.x - b.y, a.y + b.x};
-                    if (mirror) o2[c] = cx<T>{a.x + b.y, b.x - a.y};
-                }
-                kz += dk;
-                li += dli;
-                if (kz >= nzh) {
-                    kz -= nzh;
-                    ++li;
-                }
-            }
-        }
+        // axes without an in-place split: the complex lines packed into the
+        // transform buffer first (zinv_pack), then transformed
+        if (!zs) zinv_pack<T>(bufA, spec, nl, nz, nzh, ld);
         cx<T> *R;
         if (zs) {
             fft_ip_inv_packed_auto<T>(bufA, spec, nz, L, ld, nzh, tw);
@@ -1709,11 +1725,11 @@ size_t smem_xy(int n, int W, int nslots) {
 
 size_t zinv_smem(int prec, int nzmax, int inelems, int recelems, int abelems, int nab);
 
-// z-inverse block: FP32 axes with an in-place split run the direct form (no
-// staging: transform buffer only), all others stage two tiles of input
+// z-inverse block: FP32 runs the direct form (no staging: one transform
+// buffer with an in-place split, else two), FP64 stages two tiles of input
 template <typename T>
 size_t smem_zinv(int nz, int LZ) {
-    if (sizeof(T) == 4 && fft_split(nz)) return zinv_smem(1, nz, 0, 0, nz * z_ld(LZ), 1);
+    if (sizeof(T) == 4) return zinv_smem(1, nz, 0, 0, nz * z_ld(LZ), fft_split(nz) ? 1 : 2);
     const size_t nzh = nz / 2 + 1;
     return 16 + ((sizeof(QShared<T>) + 15) / 16) * 16 +
            sizeof(cx<T>) * ((size_t)((nz + 7) & ~7) + 2 * (size_t)LZ * nzh * NQ + z_nbuf<T>(nz) * nz * z_ld(LZ)) +

@@ -136,3 +136,67 @@ def test_ligand_shell_192_against_oracle(oracle_default):
             _check(f.calculate(n, sg), ref, prec)
         finally:
             f.close()
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2], ids=["x", "y", "z"])
+def test_axis_640_fp32_and_fp64_limit(oracle_default, axis):
+    # 640 points, the paper's density-grid axis (performance section): the
+    # FP32-mixed form takes it on any axis (generic Stockham stages); the FP64
+    # form's tiles of one 640-point pencil of 20 complex fields do not fit
+    # shared memory, and it says so (EINVAL) instead of running
+    s = _thin(640, axis)
+    n, sg = s.n.numpy(), s.sigma.numpy()
+    ref = oracle_default.energy_potential(n, sg, s.cell, s.functional)
+    f = B.Functional(s.shape, s.cell, s.functional, B.FP32_MIXED)
+    try:
+        _check(f.calculate(n, sg), ref, B.FP32_MIXED)
+    finally:
+        f.close()
+    with pytest.raises(B.VdwgbError) as ei:
+        B.Functional(s.shape, s.cell, s.functional, B.FP64)
+    assert ei.value.code == -1
+
+
+def _shell160():
+    """A ligand-shell-like density on 160^3 points in a 27.4 bohr cell (one
+    quarter of the paper's (58 Angstrom)^3 box along each axis)."""
+    g = np.random.default_rng(640)
+    L = 109.6 / 4
+    c0 = np.array([L / 2] * 3)
+    atoms = []
+    for _ in range(12):
+        v = g.normal(size=3)
+        v *= g.uniform(0, 3.0) / np.linalg.norm(v)
+        atoms.append((float(g.uniform(6, 8)), float(g.uniform(2, 3)), tuple(c0 + v)))
+    for _ in range(8):
+        u = g.normal(size=3)
+        u /= np.linalg.norm(u)
+        for k in range(4):
+            atoms.append((float(g.uniform(1, 6)), float(g.uniform(1, 2.5)), tuple(c0 + (4.0 + 1.2 * k) * u)))
+    import torch
+    dev = torch.device("cuda:0")
+    return inputs.make_system((160, 160, 160), np.diag([L, L, L]), atoms, 1, device=dev)
+
+
+@pytest.mark.slow
+def test_grid_640_cubed_supercell_of_160_cubed():
+    # The paper's 640^3 density grid in one FP32-mixed evaluation: the density
+    # is the 4 x 4 x 4 supercell of a 160^3 system, so E(640^3) = 64 E(160^3)
+    # and the potentials are the small system's, tiled (extensivity of the
+    # periodic energy); the 160^3 reference is the FP64 form.
+    s = _shell160()
+    n, sg = s.n.cpu().numpy(), s.sigma.cpu().numpy()
+    f = B.Functional(s.shape, s.cell, 1, B.FP64)
+    try:
+        e64, dn64, ds64 = f.calculate(n, sg)
+    finally:
+        f.close()
+    nb, sgb = np.tile(n, (4, 4, 4)), np.tile(sg, (4, 4, 4))
+    f = B.Functional((640, 640, 640), 4 * s.cell, 1, B.FP32_MIXED)
+    try:
+        e, dn, ds = f.calculate(nb, sgb)
+    finally:
+        f.close()
+    assert abs(e / 64 - e64) <= 1e-6, (e / 64, e64)
+    assert np.max(np.abs(dn - np.tile(dn64, (4, 4, 4)))) <= 1e-5 * np.max(np.abs(dn64))
+    assert np.max(np.abs(ds - np.tile(ds64, (4, 4, 4)))) <= 1e-5 * np.max(np.abs(ds64))
