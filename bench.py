@@ -79,6 +79,15 @@ def reduce_max(x, device):
     return float(t.item())
 
 
+_T0 = time.perf_counter()
+
+
+def log(msg):
+    """Progress of the run on stderr (the JSON line goes to stdout)."""
+    sys.stderr.write("[bench %7.1f s] %s\n" % (time.perf_counter() - _T0, msg))
+    sys.stderr.flush()
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -412,6 +421,7 @@ def serve_bench(B, inputs, torch, dev, local, rate=200.0, count=2000, distinct=1
     one at a time in FP64.  Then a sweep of higher rates (`sweep_seconds`
     each) up to saturation."""
     reqs = inputs.serving_requests(seed=0, count=distinct, rate=rate)
+    log("serving: %d distinct requests" % distinct)
     pool = []
     for r in reqs:
         sy = inputs.realise(r, device=dev)
@@ -443,6 +453,7 @@ def serve_bench(B, inputs, torch, dev, local, rate=200.0, count=2000, distinct=1
     g = np.random.default_rng(1)
 
     def stream(rate_s, n_arrivals):
+        log("serving: %g req/s, %d arrivals" % (rate_s, n_arrivals))
         sv = B.vdwgb_server_new(local, B.FP32_MIXED, pool_bytes=64 << 30, max_batch=16, max_inflight=3)
         try:
             for k in range(len(pool)):              # warm-up: every request once (plans built, resident)
@@ -551,6 +562,7 @@ def main():
     B.vdwgb_set_autotune(True)   # tile shapes measured once per grid at init (outside the timed region)
 
     default = args.workload == WORKLOAD
+    log("building the %s workload" % args.workload)
     systems = make_workload(args.workload, rank, dev)
     nb = len(systems)
     pts = sum(s.npts for s in systems)
@@ -570,12 +582,14 @@ def main():
     ns = [s.n for s in systems]
     ss = [s.sigma for s in systems]
 
+    log("planning %d FP32-mixed handles (autotuned tiles)" % nb)
     f32 = make(B.FP32_MIXED, systems)
     plan_info = B.vdwgb_plan_info(f32[0].h)
     fused = any(B.vdwgb_plan_info(f.h)["cluster"] for f in f32)   # plane kernel in use
     bt = B.vdwgb_batch_new([f.h for f in f32])
 
     # ---- timed region: FP32-mixed batched (the captured graph) ----------------
+    log("timed batched steps")
     step_ms, tot_ms, clocks = timed_batch(B, torch, bt, ns, ss, dn, ds, en, sp, stream, args.steps, args.warmup,
                                           flush, world, dev, local)
     value = pts * world * args.steps / (tot_ms / 1000.0)
@@ -594,6 +608,7 @@ def main():
     g32 = [(float(en[i]), dn[i].cpu().numpy(), ds[i].cpu().numpy()) for i in range(nb)]
 
     # ---- latency of single FP32 evaluations (one system at a time) -----------
+    log("single-system latency")
     lat = []
     e1 = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     for i in range(220):
@@ -607,6 +622,7 @@ def main():
     lat = np.array(lat)
 
     # ---- end to end through the host-pointer batch API ------------------------
+    log("end to end through host arrays")
     hn = [s.n.cpu().pin_memory().numpy() for s in systems]
     hs = [s.sigma.cpu().pin_memory().numpy() for s in systems]
     hdn = [torch.empty(s.shape, dtype=torch.float64).pin_memory().numpy() for s in systems]
@@ -628,6 +644,7 @@ def main():
     B.vdwgb_batch_free(bt)
 
     # ---- FP64 plain, one system at a time, same inputs ------------------------
+    log("FP64 plain form")
     try:
         f64 = make(B.FP64, systems)
     except B.VdwgbError:
@@ -730,6 +747,7 @@ def main():
     # ---- extra workload: the 8-system 96^3 dimer batch ------------------------
     extra = None
     if not args.no_extra:
+        log("extra workload: 8 x 96^3 dimers")
         dsys = make_workload("dimer96_batch8", rank, dev)
         fd = make(B.FP32_MIXED, dsys)
         btd = B.vdwgb_batch_new([f.h for f in fd])
@@ -756,6 +774,8 @@ def main():
         for f in fd:
             f.close()
 
+    if not args.no_serve:
+        log("serving stream")
     serving = None if args.no_serve else serve_bench(B, inputs, torch, dev, local)
 
     # ---- oracle: errors of both forms and the CPU baseline (all host cores) ---
@@ -763,6 +783,7 @@ def main():
     if not args.no_oracle and rank == 0 and world == 1 and args.workload != "shell640":
         jobs = [(i, s.n.cpu().numpy(), s.sigma.cpu().numpy(), s.cell, s.functional) for i, s in enumerate(systems)]
         workers = oracle_workers(max(s.npts for s in systems))
+        log("oracle on %d host processes" % workers)
         pool = OraclePool(workers)
         try:
             ref, wall = pool.run(jobs)

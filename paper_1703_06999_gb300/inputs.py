@@ -72,21 +72,19 @@ def density(shape, cell, atoms: Sequence[Atom], floor: float = 1e-10,
         reach = cutoff / zeta
         nimg = [int(math.ceil(reach / h)) + 1 for h in heights]
         pref = Z * zeta ** 3 / (8.0 * math.pi)
-        for i in range(-nimg[0], nimg[0] + 1):
-            for j in range(-nimg[1], nimg[1] + 1):
-                for k in range(-nimg[2], nimg[2] + 1):
-                    shift = np.asarray(centre) + i * cell[0] + j * cell[1] + k * cell[2]
-                    if (np.linalg.norm(shift - mid) - half_diag) * zeta > cutoff:
-                        continue          # this image cannot reach the cell
-                    centres.append(shift)
-                    zetas.append(zeta)
-                    prefs.append(pref)
+        ijk = np.stack(np.meshgrid(*[np.arange(-m, m + 1) for m in nimg], indexing="ij"), axis=-1).reshape(-1, 3)
+        shifts = np.asarray(centre, dtype=np.float64) + ijk @ cell
+        keep = (np.linalg.norm(shifts - mid, axis=1) - half_diag) * zeta <= cutoff   # images that reach the cell
+        centres.append(shifts[keep])
+        zetas.append(np.full(int(keep.sum()), zeta))
+        prefs.append(np.full(int(keep.sum()), pref))
     n = torch.full((npts,), float(floor), dtype=torch.float64, device=device)
-    if centres:
+    centres = np.concatenate(centres) if centres else np.zeros((0, 3))
+    if len(centres):
         fdt = torch.float32 if torch.device(device).type == "cuda" else torch.float64
-        c = torch.as_tensor(np.asarray(centres), dtype=fdt, device=device)
-        zt = torch.as_tensor(np.asarray(zetas), dtype=fdt, device=device)
-        pf = torch.as_tensor(np.asarray(prefs), dtype=torch.float64, device=device)
+        c = torch.as_tensor(centres, dtype=fdt, device=device)
+        zt = torch.as_tensor(np.concatenate(zetas), dtype=fdt, device=device)
+        pf = torch.as_tensor(np.concatenate(prefs), dtype=torch.float64, device=device)
         rr = r.to(fdt)
         group = max(1, (1 << 25) // max(npts, 1))          # about 128-256 MB of distances per group
         for g0 in range(0, len(centres), group):
