@@ -55,9 +55,10 @@ def density(shape, cell, atoms: Sequence[Atom], floor: float = 1e-10,
     image of an atom that can come within zeta |r - R| <= cutoff of the cell
     contributes; the images are evaluated in groups (one pass over the grid
     per group) to keep the number of device operations small.  On a GPU the
-    distances and exponentials are evaluated in FP32 (the GPU's FP64 rate is
-    a small fraction of its FP32 rate; the density then differs from the FP64
-    evaluation by about 1e-5 relative) and summed in FP64."""
+    distances, exponentials and the sum over a group's images are evaluated
+    in FP32 (the GPU's FP64 rate is a small fraction of its FP32 rate; the
+    density then differs from an FP64 evaluation by about 1e-5 relative), and
+    the groups are summed in FP64."""
     cell = np.asarray(cell, dtype=np.float64)
     r = _grid_coords(shape, cell, device).reshape(-1, 3)
     npts = r.shape[0]
@@ -81,16 +82,23 @@ def density(shape, cell, atoms: Sequence[Atom], floor: float = 1e-10,
     n = torch.full((npts,), float(floor), dtype=torch.float64, device=device)
     centres = np.concatenate(centres) if centres else np.zeros((0, 3))
     if len(centres):
-        fdt = torch.float32 if torch.device(device).type == "cuda" else torch.float64
+        gpu = torch.device(device).type == "cuda"
+        fdt = torch.float32 if gpu else torch.float64
         c = torch.as_tensor(centres, dtype=fdt, device=device)
         zt = torch.as_tensor(np.concatenate(zetas), dtype=fdt, device=device)
-        pf = torch.as_tensor(np.concatenate(prefs), dtype=torch.float64, device=device)
-        rr = r.to(fdt)
-        group = max(1, (1 << 25) // max(npts, 1))          # about 128-256 MB of distances per group
+        pf = torch.as_tensor(np.concatenate(prefs), dtype=fdt, device=device)
+        rx, ry, rz = (r[:, q].to(fdt).contiguous() for q in range(3))
+        group = max(1, (1 << 26) // max(npts, 1))          # about 256 MB per intermediate
         for g0 in range(0, len(centres), group):
             g1 = min(len(centres), g0 + group)
-            d = torch.cdist(c[g0:g1], rr, compute_mode="donot_use_mm_for_euclid_dist")   # (group, npts)
-            n += (pf[g0:g1, None] * torch.exp(-zt[g0:g1, None] * d).to(torch.float64)).sum(dim=0)
+            d2 = rx[None, :] - c[g0:g1, 0:1]
+            d2.square_()
+            t = ry[None, :] - c[g0:g1, 1:2]
+            d2.addcmul_(t, t)
+            t = rz[None, :] - c[g0:g1, 2:3]
+            d2.addcmul_(t, t)
+            d2.sqrt_().mul_(-zt[g0:g1, None]).exp_()       # exp(-zeta |r - R|) per image and point
+            n += (pf[None, g0:g1] @ d2).reshape(-1).to(torch.float64)
     return n.reshape(tuple(shape))
 
 
