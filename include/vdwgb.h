@@ -178,6 +178,19 @@ int vdwgb_phi(int device, int npts, const double *d1, const double *d2, double *
 int vdwgb_q0(int device, int precision, int functional, int npts, const double *n, const double *sigma,
              double *q0, double *dq0dn, double *dq0dsigma);
 
+/* Fault injection for testing the error paths without a GPU fault (off by
+ * default; the paper has no counterpart).  kind VDWGB_FAULT_ALLOC: the next
+ * `count` device allocations the library makes (handle plans, batches,
+ * server requests and slots) fail as if the device were out of memory, so
+ * the call that needed them returns VDWGB_ENOMEM.  kind VDWGB_FAULT_WAIT: the
+ * next `count` calls of vdwgb_device_status (made by the host-array calls,
+ * the batch host-array call and the server after each batch) first set the
+ * device's status flag, as a kernel whose bounded wait ran out leaves it, so
+ * they report VDWGB_ETIMEDOUT.  kind VDWGB_FAULT_NONE disarms both.  EINVAL
+ * for another kind or a negative count.  Process-wide, thread-safe. */
+enum { VDWGB_FAULT_NONE = 0, VDWGB_FAULT_ALLOC = 1, VDWGB_FAULT_WAIT = 2 };
+int vdwgb_inject_fault(int kind, int count);
+
 /* Plane kernel on (1) or off (0, default) for handles initialised after the
  * call.  On: FP32-mixed handles whose x and y lengths are multiples of 16
  * with a compiled two-pass split (16..256) and whose kz-plane fits the shared

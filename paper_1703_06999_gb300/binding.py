@@ -87,6 +87,7 @@ _SIGS.update({
     "vdwgb_calculate_noalloc": (ctypes.c_int, [ctypes.c_int] * 5 + [ctypes.c_void_p] * 7),
     "vdwgb_set_fused": (ctypes.c_int, [ctypes.c_int]),
     "vdwgb_alu_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "vdwgb_inject_fault": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
 })
 
 
@@ -208,6 +209,16 @@ def vdwgb_footprint_bytes(shape, precision):
 
 def vdwgb_device_status(device=0):
     _ck(lib().vdwgb_device_status(int(device)), "vdwgb_device_status")
+
+
+FAULT_NONE, FAULT_ALLOC, FAULT_WAIT = 0, 1, 2
+
+
+def vdwgb_inject_fault(kind, count=1):
+    """Arm a fault for tests: FAULT_ALLOC (next `count` device allocations
+    fail: ENOMEM), FAULT_WAIT (next `count` status checks find the device's
+    timeout flag set: ETIMEDOUT), FAULT_NONE (disarm)."""
+    _ck(lib().vdwgb_inject_fault(int(kind), int(count)), "vdwgb_inject_fault")
 
 
 def vdwgb_alu_peak(kind, device=0):

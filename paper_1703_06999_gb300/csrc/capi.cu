@@ -12,6 +12,7 @@
 #include <tuple>
 #include <cstdlib>
 #include <algorithm>
+#include <atomic>
 
 #include <cuda.h>
 
@@ -130,7 +131,32 @@ static std::vector<double> twiddles(int n) {
 // handle (struct vdwgb_data in internal.h)
 // ---------------------------------------------------------------------------
 
+// ---------------------------------------------------------------------------
+// Fault injection (vdwgb_inject_fault): armed counts, taken one at a time
+// ---------------------------------------------------------------------------
+static std::atomic<int> g_inj_alloc{0}, g_inj_wait{0};
+
+static bool take_injection(std::atomic<int> &c) {
+    int v = c.load();
+    while (v > 0)
+        if (c.compare_exchange_weak(v, v - 1)) return true;
+    return false;
+}
+
+// cudaMalloc, or the out-of-memory error an armed injection asks for
+cudaError_t vdwgb::device_malloc(void **p, size_t bytes) {
+    if (take_injection(g_inj_alloc)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
 static cudaError_t dalloc(vdwgb_data *h, void **p, size_t bytes) {
+    if (take_injection(g_inj_alloc)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
     if (h->alloc_stream) return cudaMallocAsync(p, bytes, h->alloc_stream);
     return cudaMalloc(p, bytes);
 }
@@ -613,7 +639,7 @@ static int apply_tuned(vdwgb_data *h) {
     std::vector<double> host(2 * N, 0.0);
     for (size_t i = 0; i < N; ++i) host[i] = 0.01;
     double *tmp = nullptr;
-    CK(cudaMalloc(&tmp, (4 * N + 1) * sizeof(double)), "tune buffers");
+    CK(device_malloc(reinterpret_cast<void **>(&tmp), (4 * N + 1) * sizeof(double)), "tune buffers");
     int rc = 0;
     TuneVal best{S.LZ, S.LZi, S.Wy, S.Wx, h->ls.nbuf[1], h->ls.nbuf[2]};
     auto set_io_dev = [&]() {
@@ -933,7 +959,7 @@ int vdwgb_calculate(vdwgb_handle h, const double *rho, const double *sigma, doub
     CK(cudaSetDevice(h->device), "cudaSetDevice");
     const size_t N = (size_t)h->nx * h->ny * h->nz;
     if (!h->d_io) {
-        CK(cudaMalloc(&h->d_io, (4 * N + 1) * sizeof(double)), "staging");
+        CK(device_malloc(reinterpret_cast<void **>(&h->d_io), (4 * N + 1) * sizeof(double)), "staging");
         h->bytes += (4 * N + 1) * sizeof(double);
     }
     double *dn = h->d_io, *ds = dn + N, *odn = ds + N, *ods = odn + N, *oe = ods + N;
@@ -954,6 +980,11 @@ int vdwgb_device_status(int device) {
     if (device < 0 || device >= 64 || !g_dev[device].ready) return 0;
     int v = 0;
     CK(cudaSetDevice(device), "cudaSetDevice");
+    if (take_injection(g_inj_wait)) {
+        // as a kernel whose bounded wait ran out leaves it
+        const int one = 1;
+        CK(cudaMemcpy(g_dev[device].err, &one, sizeof(int), cudaMemcpyHostToDevice), "status injection");
+    }
     CK(cudaMemcpy(&v, g_dev[device].err, sizeof(int), cudaMemcpyDeviceToHost), "status");
     if (v) {
         CK(cudaMemset(g_dev[device].err, 0, sizeof(int)), "status");
@@ -1075,6 +1106,24 @@ int vdwgb_phi(int device, int npts, const double *d1, const double *d2, double *
 
 double vdwgb_table_build_seconds(int device) { return table_seconds(device); }
 
+int vdwgb_inject_fault(int kind, int count) {
+    if (count < 0) return fail(VDWGB_EINVAL, "negative injection count");
+    switch (kind) {
+        case VDWGB_FAULT_NONE:
+            g_inj_alloc = 0;
+            g_inj_wait = 0;
+            return 0;
+        case VDWGB_FAULT_ALLOC:
+            g_inj_alloc = count;
+            return 0;
+        case VDWGB_FAULT_WAIT:
+            g_inj_wait = count;
+            return 0;
+        default:
+            return fail(VDWGB_EINVAL, "unknown fault kind %d", kind);
+    }
+}
+
 int vdwgb_set_fused(int enable) {
     std::lock_guard<std::mutex> lk(g_fused_mu);
     g_fused = enable ? 1 : 0;
@@ -1139,7 +1188,7 @@ int vdwgb_q0(int device, int precision, int functional, int npts, const double *
     if (rc) return rc;
     CK(cudaSetDevice(device), "cudaSetDevice");
     double *b = nullptr;
-    CK(cudaMalloc(&b, 5 * (size_t)npts * sizeof(double)), "q0 buffers");
+    CK(device_malloc(reinterpret_cast<void **>(&b), 5 * (size_t)npts * sizeof(double)), "q0 buffers");
     cudaError_t e = cudaMemcpy(b, n, npts * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b + npts, sigma, npts * sizeof(double), cudaMemcpyHostToDevice);
     const double Z = functional == VDWGB_DF2 ? -1.887 : -0.8491;
@@ -1303,8 +1352,8 @@ int vdwgb_batch_new(vdwgb_handle *handles, int count, vdwgb_batch *out) {
     cudaSetDevice(b->device);
     b->host.resize(count);
     std::vector<int> pre(NKIND * (count + 1), 0);
-    cudaError_t e = cudaMalloc(&b->dsys, count * sizeof(SysDev));
-    if (e == cudaSuccess) e = cudaMalloc(&b->dprefix, pre.size() * sizeof(int));
+    cudaError_t e = device_malloc(reinterpret_cast<void **>(&b->dsys), count * sizeof(SysDev));
+    if (e == cudaSuccess) e = device_malloc(reinterpret_cast<void **>(&b->dprefix), pre.size() * sizeof(int));
     int rc = e == cudaSuccess ? batch_launchset(handles, count, b->host.data(), pre.data(), b->dsys, b->dprefix, b->ls)
                               : cuda_fail(e, "batch setup");
     if (rc == 0) {
@@ -1320,7 +1369,7 @@ int vdwgb_batch_new(vdwgb_handle *handles, int count, vdwgb_batch *out) {
         off[0] = 0;
         for (int p = 0; p < np; ++p) off[p + 1] = off[p] + (size_t)NKIND * (ps[p + 1] - ps[p] + 1);
         std::vector<int> p2(off[np], 0);
-        e = cudaMalloc(&b->dprefix2, off[np] * sizeof(int));
+        e = device_malloc(reinterpret_cast<void **>(&b->dprefix2), off[np] * sizeof(int));
         if (e != cudaSuccess) rc = cuda_fail(e, "batch setup");
         for (int p = 0; p < np && rc == 0; ++p)
             rc = batch_launchset(handles + ps[p], ps[p + 1] - ps[p], b->host.data() + ps[p], p2.data() + off[p],
@@ -1435,7 +1484,7 @@ int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double 
     const int n = (int)b->hs.size();
     CK(cudaSetDevice(b->device), "cudaSetDevice");
     if (!b->own) CK(cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking), "stream");
-    if (!b->d_energy) CK(cudaMalloc(&b->d_energy, n * sizeof(double)), "energies");
+    if (!b->d_energy) CK(device_malloc(reinterpret_cast<void **>(&b->d_energy), n * sizeof(double)), "energies");
     std::vector<const double *> dr(n), dsg(n);
     std::vector<double *> odn(n), ods(n);
     for (int i = 0; i < n; ++i) {
@@ -1443,7 +1492,7 @@ int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double 
         if (!rho[i] || !sigma[i] || !dedrho[i] || !dedsigma[i]) return fail(VDWGB_EINVAL, "null array %d", i);
         const size_t N = (size_t)h->nx * h->ny * h->nz;
         if (!h->d_io) {
-            CK(cudaMalloc(&h->d_io, (4 * N + 1) * sizeof(double)), "staging");
+            CK(device_malloc(reinterpret_cast<void **>(&h->d_io), (4 * N + 1) * sizeof(double)), "staging");
             h->bytes += (4 * N + 1) * sizeof(double);
         }
         double *d = h->d_io;

@@ -42,6 +42,9 @@ struct vdwgb_data {
 namespace vdwgb {
 
 int fail(int code, const char *fmt, ...);
+// cudaMalloc, failing with cudaErrorMemoryAllocation while an allocation
+// fault is injected (vdwgb_inject_fault)
+cudaError_t device_malloc(void **p, size_t bytes);
 int cuda_fail(cudaError_t e, const char *what);
 int device_setup(int device);
 bool device_peek(int device, int *sms, size_t *maxsmem, int **err);

@@ -403,9 +403,9 @@ int vdwgb_server_new(int device, int precision, size_t pool_bytes, int max_batch
         if (e == cudaSuccess) e = cudaMallocHost(&sl.hdesc, max_batch * sizeof(SysDev));
         if (e == cudaSuccess) e = cudaMallocHost(&sl.hpre, NKIND * (max_batch + 1) * sizeof(int));
         if (e == cudaSuccess) e = cudaMallocHost(&sl.henergy, max_batch * sizeof(double));
-        if (e == cudaSuccess) e = cudaMalloc(&sl.ddesc, max_batch * sizeof(SysDev));
-        if (e == cudaSuccess) e = cudaMalloc(&sl.dpre, NKIND * (max_batch + 1) * sizeof(int));
-        if (e == cudaSuccess) e = cudaMalloc(&sl.denergy, max_batch * sizeof(double));
+        if (e == cudaSuccess) e = device_malloc(reinterpret_cast<void **>(&sl.ddesc), max_batch * sizeof(SysDev));
+        if (e == cudaSuccess) e = device_malloc(reinterpret_cast<void **>(&sl.dpre), NKIND * (max_batch + 1) * sizeof(int));
+        if (e == cudaSuccess) e = device_malloc(reinterpret_cast<void **>(&sl.denergy), max_batch * sizeof(double));
     }
     s->plan_streams.resize(s->nplan);
     for (auto &st : s->plan_streams)

@@ -58,3 +58,13 @@ def test_host_side_validation_without_gpu():
     with pytest.raises(B.VdwgbError):
         B.vdwgb_new(3)
     assert B.vdwgb_footprint_bytes((96, 96, 96), B.FP32_MIXED) < B.vdwgb_footprint_bytes((96, 96, 96), B.FP64)
+
+
+def test_fault_injection_arguments_without_gpu():
+    from paper_1703_06999_gb300 import binding as B
+    B.vdwgb_inject_fault(B.FAULT_ALLOC, 2)
+    B.vdwgb_inject_fault(B.FAULT_NONE, 0)                # disarms
+    for kind, count in ((7, 1), (B.FAULT_WAIT, -1)):
+        with pytest.raises(B.VdwgbError) as ei:
+            B.vdwgb_inject_fault(kind, count)
+        assert ei.value.code == -1
