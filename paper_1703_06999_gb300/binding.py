@@ -13,7 +13,8 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libvdwgb.so")
+# VDWGB_CHECKED=1 loads the bounds-checked build (build.build(checked=True))
+LIB_PATH = os.path.join(HERE, "libvdwgb_checked.so" if os.environ.get("VDWGB_CHECKED") == "1" else "libvdwgb.so")
 
 DF1, DF2 = 1, 2
 FP64, FP32_MIXED = 0, 1

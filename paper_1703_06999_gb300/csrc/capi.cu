@@ -76,8 +76,8 @@ int vdwgb::device_setup(int device) {
     host_qmesh(qm);
     CK(upload_qmesh(qm), "upload q-mesh");
     CK(init_kernels(d.maxsmem - 1024), "kernel attributes");
-    CK(cudaMalloc(&d.err, sizeof(int)), "error flag");
-    CK(cudaMemset(d.err, 0, sizeof(int)), "error flag");
+    CK(cudaMalloc(&d.err, 2 * sizeof(int)), "error flag");     // status, detail
+    CK(cudaMemset(d.err, 0, 2 * sizeof(int)), "error flag");
     d.ready = true;
     return 0;
 }
@@ -779,6 +779,7 @@ static int plan(vdwgb_data *h) {
     S.spec = h->spec;
     S.rec = h->rec;
     S.epart = h->epart;
+    S.err = di.err;
     h->bytes = nspec * elem_bytes(prec) + (size_t)nx * ny * nz * rec_bytes(prec) + nepart_cap * sizeof(double) +
                (C ? 0 : nk * sizeof(unsigned)) + nchunk_cap * sizeof(int4) + kord.size() * sizeof(unsigned short);
     CK(dalloc(h, &h->dsys, sizeof(SysDev)), "descriptor");
@@ -985,10 +986,15 @@ int vdwgb_device_status(int device) {
         const int one = 1;
         CK(cudaMemcpy(g_dev[device].err, &one, sizeof(int), cudaMemcpyHostToDevice), "status injection");
     }
-    CK(cudaMemcpy(&v, g_dev[device].err, sizeof(int), cudaMemcpyDeviceToHost), "status");
+    int flag[2] = {0, 0};
+    CK(cudaMemcpy(flag, g_dev[device].err, 2 * sizeof(int), cudaMemcpyDeviceToHost), "status");
+    v = flag[0];
     if (v) {
-        CK(cudaMemset(g_dev[device].err, 0, sizeof(int)), "status");
+        CK(cudaMemset(g_dev[device].err, 0, 2 * sizeof(int)), "status");
         if (v == 2) return fail(VDWGB_ECUDA, "contraction: a k-point's table interval was outside its chunk's rows");
+        if (v == 3)
+            return fail(VDWGB_ECUDA, "checked build: an out-of-range access was skipped (check at source line %d)",
+                        flag[1]);
         return fail(VDWGB_ETIMEDOUT, "a kernel's bounded wait for its staged tile ran out");
     }
     return 0;

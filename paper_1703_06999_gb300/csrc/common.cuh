@@ -124,7 +124,25 @@ struct SysDev {
     const unsigned short *kord;   // per (kz, rank): local k-point indices sorted by table interval
     const void *tmap;    // FP32: two tensor maps of spec (y-pass tile box, x-pass tile box), else null
     double *energy;  // output (device)
+    int *err;        // device status flag (and detail word) of the device
 };
+
+// Bounds checks of the checked build (VDWGB_CHECK_BOUNDS defined): a failed
+// check sets status 3 and the source line in the flag's detail word, and the
+// caller skips the access or tile; without the define every check is the
+// constant true and compiles away.
+#ifdef VDWGB_CHECK_BOUNDS
+__device__ __forceinline__ bool vdwgb_check(bool ok, int *err, int line) {
+    if (!ok) {
+        atomicExch(err + 1, line);
+        atomicExch(err, 3);
+    }
+    return ok;
+}
+#define VDWGB_OK(cond, err) vdwgb::vdwgb_check((cond), (err), __LINE__)
+#else
+#define VDWGB_OK(cond, err) true
+#endif
 
 // Library-wide constants on the device (q-mesh and helper-spline data).
 struct QMeshDev {

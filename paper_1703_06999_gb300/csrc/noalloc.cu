@@ -258,6 +258,7 @@ extern "C" int vdwgb_calculate_noalloc(int device, int functional, int nx, int n
     S.chunks = reinterpret_cast<const int4 *>(base + OFF_CHUNK);
     S.epart = reinterpret_cast<double *>(base + OFF_EPART);
     for (int a = 0; a < 3; ++a) S.tw[a] = base + OFF_TW + (size_t)a * NA_MAX_AXIS * sizeof(cx<float>);
+    S.err = err;
     S.n = d_rho;
     S.sigma = d_sigma;
     S.dedn = d_dedrho;

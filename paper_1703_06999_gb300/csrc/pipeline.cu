@@ -418,6 +418,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zfwd(const SysD
         const int nlines_tot = S.nx * S.ny;
         const int l0 = lt * LZ;
         const int nl = min(LZ, nlines_tot - l0);
+        if (!VDWGB_OK(lt >= 0 && l0 >= 0 && nl >= 1, S.err)) continue;   // tile past the system's lines
         const int L = 10 * nl;              // complex lines in this tile
         const int ld = z_ld(nl);
         cx<T> *tw = reinterpret_cast<cx<T> *>(base);
@@ -662,6 +663,10 @@ __device__ __forceinline__ void xy_issue(const SysDev *__restrict__ sys, const i
     const XYTile g = xy_tile<XPASS>(S, si, t - (hit ? cached_base : prefix[si]));
     const cx<T> *spec = reinterpret_cast<const cx<T> *>(S.spec);
     const int lane = threadIdx.x & 31;
+    if (!VDWGB_OK(g.outer >= 0 && g.outer < (XPASS ? S.ny : S.nx) && g.kz0 >= 0 && g.wt >= 1, S.err)) {
+        if (lane == 0) mbar_expect_tx(bar, 0u);   // complete the phase without copies
+        return;
+    }
     fence_proxy_async();
     if (S.tmap) {
         // the whole tile in one tensor copy (box W 20 x rows; columns past
@@ -770,7 +775,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_xy(const SysDev
         }
         // store the rows back (16-byte vectors), walking (row, e) without division
         cx<T> *spec = reinterpret_cast<cx<T> *>(S.spec) + g.g0;
-        {
+        if (VDWGB_OK(g.outer >= 0 && g.outer < (XPASS ? S.ny : S.nx) && g.kz0 >= 0 && g.wt >= 1, S.err)) {
             constexpr int PER = 16 / (int)sizeof(cx<T>);   // complex values per vector
             const int h = g.L / PER;                         // L = 20 W: even
             const int de = blockDim.x % h, dr = blockDim.x / h;
@@ -831,7 +836,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_contract(const 
         const int si = find_sys(prefix, nsys, t);
         const SysDev &S = sys[si];
         const int lt = t - prefix[si];
-        const int4 c = S.chunks[lt];     // first, count, first interval, intervals
+        int4 c = S.chunks[lt];           // first, count, first interval, intervals
+        if (!VDWGB_OK(c.x >= 0 && c.y >= 0 && c.y <= (int)blockDim.x &&
+                          (size_t)c.x + c.y <= (size_t)S.nx * S.ny * S.nzh &&
+                          (c.w == 0 || (c.z >= 0 && c.z + min(c.w, maxspan) <= NK - 1)),
+                      S.err))
+            c = make_int4(0, 0, 0, 0);   // checked build: an empty chunk
         const int span = min(c.w, maxspan);
         if (span > 0 && threadIdx.x == 0) {
             const unsigned bytes = (unsigned)((size_t)span * NPAIR * sizeof(V));
@@ -975,7 +985,8 @@ struct __align__(16) C32Desc {
     int first;       // first kernel-table interval of the chunk
     int span;        // staged intervals (0: the chunk lies beyond the table)
     int lt;          // chunk index within its system (energy partials)
-    int pad0, pad1;
+    int nepart;      // energy partials of the system
+    int pad;
     float gf[6];
     float4 *spec;
     double *epart;
@@ -1026,6 +1037,7 @@ __device__ __forceinline__ bool c32_fetch(int i, int b, int rb, int k, int lane,
     const C32Desc &D = desc[b];
     if (k < D.count) {
         idx = sidx[b * CHUNK32 + k];
+        if (!VDWGB_OK(idx < (unsigned)(D.nx * D.ny * D.nzh), err)) idx = 0;   // checked build
         const float4 *src = D.spec + (size_t)idx * 10;
         float4 *dst = srec + ((size_t)rb * CHUNK32 + k) * C32_RSTRIDE;
 #pragma unroll
@@ -1077,8 +1089,10 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
             const int src = i & 31;
             const int s = __shfl_sync(0xffffffffu, sl, src);
             const int lt = __shfl_sync(0xffffffffu, ltl, src);
-            const int cx = __shfl_sync(0xffffffffu, cl.x, src), cy = __shfl_sync(0xffffffffu, cl.y, src);
-            const int cz = __shfl_sync(0xffffffffu, cl.z, src), cwv = __shfl_sync(0xffffffffu, cl.w, src);
+            const int cx = __shfl_sync(0xffffffffu, cl.x, src);
+            int cy = __shfl_sync(0xffffffffu, cl.y, src);
+            const int cz = __shfl_sync(0xffffffffu, cl.z, src);
+            int cwv = __shfl_sync(0xffffffffu, cl.w, src);
             if (s != psi) {                // every lane keeps the system's fields
                 const SysDev &S = sys[s];
                 d.nx = S.nx;
@@ -1091,8 +1105,18 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
                 for (int q = 0; q < 6; ++q) d.gf[q] = S.gf[q];
                 d.spec = reinterpret_cast<float4 *>(S.spec);
                 d.epart = S.epart;
+                d.nepart = S.nepart;
                 gkidx = S.kidx;
                 psi = s;
+            }
+            // checked build: a chunk record outside the system's k-points or
+            // the table is staged as an empty chunk
+            if (!VDWGB_OK(cx >= 0 && cy >= 1 && cy <= CHUNK32 &&
+                              (size_t)cx + cy <= (size_t)d.nx * d.ny * d.nzh && lt >= 0 &&
+                              (cwv == 0 || (cz >= 0 && cz + min(cwv, SPAN32) <= NK - 1)),
+                          err)) {
+                cy = 0;
+                cwv = 0;
             }
             // the chunk's indices into registers (coalesced) before its slot is free
 #pragma unroll
@@ -1124,7 +1148,7 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
                 d.first = cz;
                 d.span = span;
                 d.lt = lt;
-                d.pad0 = d.pad1 = 0;
+                d.pad = 0;
                 desc[b] = d;
             }
             __syncwarp();
@@ -1187,7 +1211,8 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
             // the warp's k-point energies widened exactly (integer pipe) and
             // summed in FP64: five FP64 additions per warp and chunk
             for (int o = 16; o > 0; o >>= 1) ed += __shfl_down_sync(0xffffffffu, ed, o);
-            if (lane == 0) D.epart[(size_t)D.lt * C32_CWARPS + cw] = ed;
+            if (lane == 0 && VDWGB_OK(D.lt * C32_CWARPS + cw < D.nepart, err))
+                D.epart[(size_t)D.lt * C32_CWARPS + cw] = ed;
             __syncwarp();                        // the warp's reads of slot b are done
             if (lane == 0) mbar_arrive_local(&empty[b]);
         }
@@ -1217,6 +1242,10 @@ __device__ __forceinline__ void zinv_issue(const SysDev *__restrict__ sys, const
     const int lt = t - (hit ? cached_base : prefix[si]);
     const int l0 = lt * S.LZi;
     const int nl = min(S.LZi, S.nx * S.ny - l0);
+    if (!VDWGB_OK(lt >= 0 && l0 >= 0 && nl >= 1, S.err)) {
+        mbar_expect_tx(bar, 0u);                 // complete the phase without copies
+        return;
+    }
     const unsigned sb = (unsigned)((size_t)nl * S.nzh * NQ * sizeof(cx<T>));
     const unsigned rb = (unsigned)((size_t)nl * S.nz * sizeof(Rec<T>));
     fence_proxy_async();
@@ -1379,6 +1408,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zinv(const SysD
             const SysDev &S = sS;
             const int l0 = (t - tbase) * S.LZi;
             const int nl = min(S.LZi, S.nx * S.ny - l0);
+            if (!VDWGB_OK(t >= tbase && nl >= 1, S.err)) continue;   // tile past the system's lines
             const int ld = z_ld(nl);
             const cx<T> *gspec = reinterpret_cast<const cx<T> *>(S.spec) + (size_t)l0 * S.nzh * NQ;
             cx<T> *R = bufA;
@@ -1422,6 +1452,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zinv(const SysD
         const int nz = S.nz, nzh = S.nzh;
         const int l0 = lt * S.LZi;
         const int nl = min(S.LZi, S.nx * S.ny - l0);
+        const bool tile_ok = VDWGB_OK(lt >= 0 && l0 >= 0 && nl >= 1, S.err);
         const int L = 10 * nl;
         const bool ok = mbar_wait(&bar[cur], ph[cur]);
         ph[cur] ^= 1u;
@@ -1431,14 +1462,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zinv(const SysD
             return;
         }
         const cx<T> *spec = ins[cur];
-        const bool even = (nz % 2) == 0;
+        if (!tile_ok) {                      // nothing staged for it (see zinv_issue)
+            __syncthreads();
+            continue;
+        }
         const int ld = z_ld(nl);
         // FP32 with a split: transformed in place, the first pass reading the
         // complex lines straight from the staged half spectrum; other axes:
-        // packed into the tile buffer first, then transformed
-        const int zs = sizeof(T) == 4 ? S.sz1 : 0, zs2 = zs ? nz / zs : 0;
-        // axes without an in-place split: the complex lines packed into the
-        // transform buffer first (zinv_pack), then transformed
+        // the complex lines packed into the transform buffer first
+        // (zinv_pack), then transformed
+        const int zs = sizeof(T) == 4 ? S.sz1 : 0;
         if (!zs) zinv_pack<T>(bufA, spec, nl, nz, nzh, ld);
         cx<T> *R;
         if (zs) {
