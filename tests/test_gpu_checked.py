@@ -45,10 +45,10 @@ B.vdwgb_batch_free(bt)
 for f in fs:
     f.close()
 sv = B.vdwgb_server_new(0, 1, pool_bytes=1 << 30, max_batch=4, max_inflight=2)
-ids = []
+ids, keep = [], []                 # the output arrays live until their requests are done
 for s in systems:
-    ids.append(B.vdwgb_server_submit(sv, s.functional, s.shape, s.cell, s.n.numpy(), s.sigma.numpy(),
-                                     np.empty(s.shape), np.empty(s.shape)))
+    keep.append((np.empty(s.shape), np.empty(s.shape)))
+    ids.append(B.vdwgb_server_submit(sv, s.functional, s.shape, s.cell, s.n.numpy(), s.sigma.numpy(), *keep[-1]))
 for i in ids:
     B.vdwgb_server_wait(sv, i, 120.0)
 B.vdwgb_server_free(sv)

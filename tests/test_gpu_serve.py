@@ -71,7 +71,8 @@ def test_server_rejects_oversized_and_bad_requests():
             B.vdwgb_server_submit(sv, 1, (192, 192, 192), np.eye(3) * 30, big, big, big, big)
         assert ei.value.code == -6      # EAGAIN: footprint exceeds the pool
         x = np.full((11, 4, 4), 0.1)
-        rid = B.vdwgb_server_submit(sv, 1, (11, 4, 4), np.eye(3) * 4, x, x, np.empty_like(x), np.empty_like(x))
+        ox, oy = np.empty_like(x), np.empty_like(x)      # alive until the request is reported
+        rid = B.vdwgb_server_submit(sv, 1, (11, 4, 4), np.eye(3) * 4, x, x, ox, oy)
         with pytest.raises(B.VdwgbError):
             B.vdwgb_server_wait(sv, rid, 30.0)   # prime factor 11: the planner fails the request
         with pytest.raises(B.VdwgbError):
@@ -127,8 +128,9 @@ def test_idle_plans_are_evicted_when_the_pool_is_full():
         for i in range(4):
             sh = g1 if i % 2 == 0 else g2
             x = np.full(sh, 0.02)
+            z = np.zeros(sh)                               # alive until the request is reported
             dn, ds = np.empty(sh), np.empty(sh)
-            rid = B.vdwgb_server_submit(sv, 1, sh, np.diag(np.array(sh) * 0.25), x, x * 0.0, dn, ds)
+            rid = B.vdwgb_server_submit(sv, 1, sh, np.diag(np.array(sh) * 0.25), x, z, dn, ds)
             e, _ = B.vdwgb_server_wait(sv, rid, 120.0)
             assert np.isfinite(e)
         st = B.vdwgb_server_stats(sv)
