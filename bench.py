@@ -276,14 +276,20 @@ CONTRACT_FMA2_PER_KPOINT = 315 + 400 + 20
 # (2 FMAs each) and 20 energy terms (2 each).
 CONTRACT_FMA64_PER_KPOINT = 630 + 800 + 40
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a
-# stage kernel, per workload: single-pass ncu captures of the benchmarked
-# launches themselves (one launch per stage, VDWGB_BATCH_SPLIT=0).  An entry
-# is removed when its kernel changes.
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of a stage over
+# the whole batch, per workload: the four part launches of one timed step of
+# a single-pass ncu capture of the benchmarked steps themselves (the launch
+# list summarised in the profiles directory).  An entry is removed when its
+# kernel changes.
 MEASURED_TRAFFIC = {
-    "dimer96_batch8": {"zfwd": 755.6e6, "yfwd": 1097.2e6, "xfwd": 1093.0e6, "xinv": 1092.8e6,
-                       "yinv": 1097.6e6, "zinv": 794.6e6},
+    "uneven64": {"zfwd": 2712e6, "zinv": 2912e6, "contract": 4092e6, "yfwd": 4004e6, "xfwd": 4004e6,
+                 "xinv": 4004e6, "yinv": 4004e6},
 }
+
+# Instruction-issue utilisation of the z-forward kernel (the q0 step in
+# double-float arithmetic makes it issue-bound): smsp__issue_active of a full
+# ncu capture of one launch on two 96^3 systems (profiles directory).
+ZFWD_ISSUE_ACTIVE = 0.718
 
 
 # ---------------------------------------------------------------------------
@@ -723,7 +729,8 @@ def main():
     roof = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": hbm,
             "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
             "peak_source": pk_kind + " (copy bandwidth, MEASURED_PEAKS.json hbm_gbs)",
-            "traffic_source": ("single-pass ncu capture of this launch" if traffic is not None
+            "traffic_source": ("single-pass ncu capture of the timed steps (four part launches per step)"
+                               if traffic is not None
                                else "no capture of the current kernel on this workload"),
             "stage_timing": "each stage launched on its own between CUDA events (one launch over the whole "
                             "batch), outside the timed steps; the timed steps replay the captured graph, where "
@@ -734,6 +741,8 @@ def main():
                        for n, m in zip(names, per_launch_ms)}}
     alu = {"peaks_gflops": {"fp32": fp32_peak, "fp32x2": fp32x2_peak, "fp64": fp64_peak,
                             "source": "vdwgb_alu_peak: FMA chains, CUDA events, timed alone"},
+           "zfwd_issue": {"bound": "alu (instruction issue)", "frac": ZFWD_ISSUE_ACTIVE,
+                          "source": "smsp__issue_active of an ncu capture (2 x 96^3 part launch)"},
            "contract_fp32": {"achieved_gflops": c_gflops, "peak_gflops": fp32x2_peak,
                              "frac": c_gflops / fp32x2_peak,
                              "flops_per_kpoint": 4 * CONTRACT_FMA2_PER_KPOINT},
