@@ -419,7 +419,7 @@ def serve_bench(B, inputs, torch, dev, local, rate=200.0, count=2000, distinct=1
     """Served form (the Poisson serving stream): arrivals with mean `rate`
     per second of evaluations with grids from 48^3 to 160x192x224 (sorted
     axes, 10-400 exponentials, spacing 0.15-0.30 bohr), FP32-mixed, admitted
-    by footprint into a 64 GiB pool where plans stay resident, continuous
+    by footprint into a 160 GiB pool where plans stay resident, continuous
     batching (up to 16 requests per batch, 3 batches in flight).  `distinct`
     different requests (density, cell, grid) are drawn from the stream's
     distribution and the `count` arrivals cycle through them in a random
@@ -460,7 +460,7 @@ def serve_bench(B, inputs, torch, dev, local, rate=200.0, count=2000, distinct=1
 
     def stream(rate_s, n_arrivals):
         log("serving: %g req/s, %d arrivals" % (rate_s, n_arrivals))
-        sv = B.vdwgb_server_new(local, B.FP32_MIXED, pool_bytes=64 << 30, max_batch=16, max_inflight=3)
+        sv = B.vdwgb_server_new(local, B.FP32_MIXED, pool_bytes=160 << 30, max_batch=16, max_inflight=3)
         try:
             for k in range(len(pool)):              # warm-up: every request once (plans built, resident)
                 sy, hn, hs, dn, ds = pool[k]

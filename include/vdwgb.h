@@ -337,6 +337,41 @@ int vdwgb_server_stats(vdwgb_server s, vdwgb_server_stats_t *out);
  * everything, set *s = NULL.  Requests not yet reported are dropped. */
 int vdwgb_server_free(vdwgb_server *s);
 
+/* ---- slab decomposition over several GPUs ----------------------------------
+ * The parallel layout of the paper (Sec. 3, parallelisation: FFTW-MPI slabs
+ * over x and the transposed, y-distributed spectrum) as GPU stages of one
+ * rank of P.  Rank r owns the real-space x-planes [r nx/P, (r+1) nx/P) (its
+ * x-slab: rho, sigma, dedrho, dedsigma as (nx/P) x ny x nz arrays, C order)
+ * and the spectrum's y positions [r ny/P, (r+1) ny/P) (its ky-slab).  One
+ * evaluation, each call enqueued on cuda_stream:
+ *   vdwgb_slab_forward   q0, theta, transforms along z and y on the x-slab
+ *   vdwgb_slab_pack      x-slab spectrum -> d_send, ordered by destination rank
+ *   (caller) all-to-all of equal parts: d_send of every rank -> d_bspec
+ *   vdwgb_slab_contract  transforms along x, kernel contraction and energy on
+ *                        the ky-slab, inverse transforms along x; d_energy
+ *                        receives this rank's part of E (sum over ranks = E)
+ *   (caller) all-to-all back: d_bspec of every rank -> d_recv
+ *   vdwgb_slab_unpack    d_recv -> x-slab spectrum
+ *   vdwgb_slab_inverse   inverse transforms along y and z and the potential
+ *   (caller) sum of the ranks' energies
+ * nx and ny must be multiples of P (EINVAL otherwise).  d_aspec and d_bspec
+ * (the x-slab and ky-slab work buffers) and the exchange buffers d_send /
+ * d_recv are device memory of vdwgb_slab_bytes bytes each, 256-byte aligned,
+ * owned by the caller (so the caller's collective library can address them)
+ * and kept until vdwgb_slab_free.  Results equal those of one handle on the
+ * whole grid: potentials bit for bit, the energy up to the order of its sum.
+ * Callers check vdwgb_device_status after synchronising. */
+typedef struct vdwgb_slab_s *vdwgb_slab;
+size_t vdwgb_slab_bytes(int nx, int ny, int nz, int P, int precision);
+int vdwgb_slab_new(int functional, int nx, int ny, int nz, const double *cell9, int P, int rank, int device,
+                   int precision, void *d_aspec, void *d_bspec, vdwgb_slab *out);
+int vdwgb_slab_forward(vdwgb_slab s, const double *d_rho, const double *d_sigma, void *cuda_stream);
+int vdwgb_slab_pack(vdwgb_slab s, void *d_send, void *cuda_stream);
+int vdwgb_slab_contract(vdwgb_slab s, double *d_energy, void *cuda_stream);
+int vdwgb_slab_unpack(vdwgb_slab s, const void *d_recv, void *cuda_stream);
+int vdwgb_slab_inverse(vdwgb_slab s, double *d_dedrho, double *d_dedsigma, void *cuda_stream);
+int vdwgb_slab_free(vdwgb_slab *s);
+
 /* ---- allocation-free evaluation ------------------------------------------
  * The paper has no counterpart of this entry point; it serves host codes that
  * must not allocate device memory where they evaluate (a code running inside

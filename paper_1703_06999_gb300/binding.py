@@ -89,6 +89,15 @@ _SIGS.update({
     "vdwgb_set_fused": (ctypes.c_int, [ctypes.c_int]),
     "vdwgb_alu_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "vdwgb_inject_fault": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+    "vdwgb_slab_bytes": (ctypes.c_size_t, [ctypes.c_int] * 5),
+    "vdwgb_slab_new": (ctypes.c_int, [ctypes.c_int] * 4 + [ctypes.c_void_p] + [ctypes.c_int] * 4
+                       + [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "vdwgb_slab_forward": (ctypes.c_int, [ctypes.c_void_p] * 4),
+    "vdwgb_slab_pack": (ctypes.c_int, [ctypes.c_void_p] * 3),
+    "vdwgb_slab_contract": (ctypes.c_int, [ctypes.c_void_p] * 3),
+    "vdwgb_slab_unpack": (ctypes.c_int, [ctypes.c_void_p] * 3),
+    "vdwgb_slab_inverse": (ctypes.c_int, [ctypes.c_void_p] * 4),
+    "vdwgb_slab_free": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p)]),
 })
 
 
@@ -210,6 +219,44 @@ def vdwgb_footprint_bytes(shape, precision):
 
 def vdwgb_device_status(device=0):
     _ck(lib().vdwgb_device_status(int(device)), "vdwgb_device_status")
+
+
+def vdwgb_slab_bytes(shape, P, precision):
+    nx, ny, nz = (int(v) for v in shape)
+    return int(lib().vdwgb_slab_bytes(nx, ny, nz, int(P), int(precision)))
+
+
+def vdwgb_slab_new(functional, shape, cell, P, rank, device, precision, aspec, bspec):
+    nx, ny, nz = (int(v) for v in shape)
+    c = np.ascontiguousarray(np.asarray(cell, dtype=np.float64).reshape(9))
+    h = ctypes.c_void_p()
+    _ck(lib().vdwgb_slab_new(int(functional), nx, ny, nz, c.ctypes.data, int(P), int(rank), int(device),
+                             int(precision), _ptr(aspec), _ptr(bspec), ctypes.byref(h)), "vdwgb_slab_new")
+    return h
+
+
+def vdwgb_slab_forward(s, rho, sigma, stream=0):
+    _ck(lib().vdwgb_slab_forward(s, _ptr(rho), _ptr(sigma), stream), "vdwgb_slab_forward")
+
+
+def vdwgb_slab_pack(s, send, stream=0):
+    _ck(lib().vdwgb_slab_pack(s, _ptr(send), stream), "vdwgb_slab_pack")
+
+
+def vdwgb_slab_contract(s, energy, stream=0):
+    _ck(lib().vdwgb_slab_contract(s, _ptr(energy), stream), "vdwgb_slab_contract")
+
+
+def vdwgb_slab_unpack(s, recv, stream=0):
+    _ck(lib().vdwgb_slab_unpack(s, _ptr(recv), stream), "vdwgb_slab_unpack")
+
+
+def vdwgb_slab_inverse(s, dedrho, dedsigma, stream=0):
+    _ck(lib().vdwgb_slab_inverse(s, _ptr(dedrho), _ptr(dedsigma), stream), "vdwgb_slab_inverse")
+
+
+def vdwgb_slab_free(s):
+    _ck(lib().vdwgb_slab_free(ctypes.byref(s)), "vdwgb_slab_free")
 
 
 FAULT_NONE, FAULT_ALLOC, FAULT_WAIT = 0, 1, 2

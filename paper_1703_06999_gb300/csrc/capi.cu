@@ -177,7 +177,8 @@ static void dfree(vdwgb_data *h, void *p) {
 static void release(vdwgb_data *h) {
     if (!h) return;
     if (h->device >= 0) cudaSetDevice(h->device);
-    dfree(h, h->spec);
+    if (!h->spec_external) dfree(h, h->spec);
+    h->spec_external = false;
     dfree(h, h->rec);
     dfree(h, h->epart);
     for (int i = 0; i < 3; ++i) dfree(h, h->tw[i]);
@@ -709,6 +710,8 @@ static int plan(vdwgb_data *h) {
     S.ny = ny;
     S.nz = nz;
     S.nzh = nzh;
+    S.yoff = 0;
+    S.nyg = ny;
     const int dims[3] = {nx, ny, nz};
     for (int a = 0; a < 3; ++a)
         if (!factor_axis(dims[a], S.ax[a]))
@@ -902,6 +905,19 @@ int vdwgb::handle_init(vdwgb_data *h, int device, int precision, cudaStream_t al
 }
 
 void vdwgb::handle_release(vdwgb_data *h) { release(h); }
+
+int vdwgb::handle_sort_kpoints(vdwgb_data *h, cudaStream_t st) { return sort_kpoints(h, st); }
+
+int vdwgb::handle_upload_plan(vdwgb_data *h) { return upload_plan(h); }
+
+void vdwgb::handle_use_spec(vdwgb_data *h, void *spec) {
+    if (!h->spec_external) dfree(h, h->spec);
+    h->spec = spec;
+    h->spec_external = true;
+    h->hsys.spec = spec;
+}
+
+int vdwgb::device_sms(int device) { return (device >= 0 && device < 64) ? g_dev[device].sms : 0; }
 
 int vdwgb::handle_replan(vdwgb_data *h, const double *cell9, int functional) {
     if (!h || !h->inited) return fail(VDWGB_ESTATE, "re-plan of an uninitialised handle");
@@ -1663,3 +1679,8 @@ int vdwgb_batch_free(vdwgb_batch *bp) {
 }
 
 }  // extern "C"
+
+int vdwgb::handle_set_io(vdwgb_data *h, const double *n, const double *s, double *dn, double *ds, double *e,
+                         cudaStream_t st) {
+    return set_io(h, n, s, dn, ds, e, st);
+}

@@ -121,6 +121,8 @@ struct SysDev {
     int sx1, sy1;    // N1 of the two-pass splits of the x and y axes
     int sz1;         // FP32: N1 of the in-place split of the z axis (0: none, out-of-place z passes)
     int kstride;     // entries per (kz, rank) list of kord
+    int yoff, nyg;   // y positions [yoff, yoff + ny) of a global y axis of length nyg (a slab of
+                     // the k-space half of a slab decomposition); 0 and ny otherwise
     const unsigned short *kord;   // per (kz, rank): local k-point indices sorted by table interval
     const void *tmap;    // FP32: two tensor maps of spec (y-pass tile box, x-pass tile box), else null
     double *energy;  // output (device)

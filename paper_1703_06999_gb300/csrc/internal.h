@@ -18,6 +18,7 @@ struct vdwgb_data {
     int prec = VDWGB_FP64;
     // device memory
     void *spec = nullptr;
+    bool spec_external = false;        // spec belongs to the caller (slab decomposition)
     void *rec = nullptr;
     double *epart = nullptr;
     void *tw[3] = {nullptr, nullptr, nullptr};
@@ -57,6 +58,16 @@ void handle_release(vdwgb_data *h);
 // descriptor; buffers, twiddles, tiles and tensor maps are kept.  Waits for
 // the handle's stream (alloc_stream for server handles).
 int handle_replan(vdwgb_data *h, const double *cell9, int functional);
+// pieces of a plan for the slab decomposition (slab.cu): I/O pointers of the
+// descriptor (uploaded on st if changed), the k-point order and chunks of the
+// current descriptor (device sort; waits for st), the descriptor, prefix sums
+// and tensor maps, a caller-owned work buffer in place of the handle's own
+int handle_set_io(vdwgb_data *h, const double *n, const double *s, double *dn, double *ds, double *e,
+                  cudaStream_t st);
+int handle_sort_kpoints(vdwgb_data *h, cudaStream_t st);
+int handle_upload_plan(vdwgb_data *h);
+void handle_use_spec(vdwgb_data *h, void *spec);
+int device_sms(int device);
 size_t handle_io_bytes(const vdwgb_data *h);
 // launch set over n handles: fills hdesc[n] (copies of the handles'
 // descriptors; the caller sets I/O pointers), hprefix[NKIND * (n + 1)] and L,

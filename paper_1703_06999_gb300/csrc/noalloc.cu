@@ -169,6 +169,7 @@ extern "C" int vdwgb_calculate_noalloc(int device, int functional, int nx, int n
     S.ny = ny;
     S.nz = nz;
     S.nzh = nz / 2 + 1;
+    S.nyg = ny;
     const int dims[3] = {nx, ny, nz};
     for (int a = 0; a < 3; ++a)
         if (!radices(dims[a], S.ax[a]))

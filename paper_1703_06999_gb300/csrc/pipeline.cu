@@ -880,13 +880,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_contract(const 
         }
         double eacc = 0.0;
         if (have) {
-            const int nx = S.nx, ny = S.ny, nz = S.nz, nzh = S.nzh;
+            const int nx = S.nx, ny = S.ny, nz = S.nz, nzh = S.nzh, nyg = S.nyg;
             const int kz = (int)(idx % (unsigned)nzh);
             const int rest = (int)(idx / (unsigned)nzh);
-            const int y = rest % ny, x = rest / ny;
-            const int mx = fold(x, nx), my = fold(y, ny);
+            const int y = S.yoff + rest % ny, x = rest / ny;
+            const int mx = fold(x, nx), my = fold(y, nyg);
             const bool nyq_x = (nx % 2 == 0) && (x == nx / 2);
-            const bool nyq_y = (ny % 2 == 0) && (y == ny / 2);
+            const bool nyq_y = (nyg % 2 == 0) && (y == nyg / 2);
             const bool nyq_z = (nz % 2 == 0) && (kz == nz / 2);
             const int mz = nyq_z ? -kz : kz;
             const T fx = (T)mx, fy = (T)my, fz = (T)mz;
@@ -986,7 +986,7 @@ struct __align__(16) C32Desc {
     int span;        // staged intervals (0: the chunk lies beyond the table)
     int lt;          // chunk index within its system (energy partials)
     int nepart;      // energy partials of the system
-    int pad;
+    int yoff, nyg;   // y positions of this system within a global y axis (slabs)
     float gf[6];
     float4 *spec;
     double *epart;
@@ -1013,10 +1013,11 @@ __device__ __forceinline__ void c32_kpoint(const C32Desc &D, unsigned idx, int &
     const int nx = D.nx, ny = D.ny, nz = D.nz, nzh = D.nzh;
     const int kz = (int)(idx % (unsigned)nzh);
     const int rest = (int)(idx / (unsigned)nzh);
-    const int y = axis_freq(rest % ny, ny, D.sy1), x = axis_freq(rest / ny, nx, D.sx1);
+    const int nyg = D.nyg;
+    const int y = axis_freq(D.yoff + rest % ny, nyg, D.sy1), x = axis_freq(rest / ny, nx, D.sx1);
     const bool nyq_z = (nz % 2 == 0) && (kz == nz / 2);
-    kpoint_interval32(D.gf, fold(x, nx), fold(y, ny), nyq_z ? -kz : kz, (nx % 2 == 0) && (x == nx / 2),
-                      (ny % 2 == 0) && (y == ny / 2), nyq_z, j, tt);
+    kpoint_interval32(D.gf, fold(x, nx), fold(y, nyg), nyq_z ? -kz : kz, (nx % 2 == 0) && (x == nx / 2),
+                      (nyg % 2 == 0) && (y == nyg / 2), nyq_z, j, tt);
     weight = (kz == 0 || nyq_z) ? 1.f : 2.f;
 }
 
@@ -1106,6 +1107,8 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
                 d.spec = reinterpret_cast<float4 *>(S.spec);
                 d.epart = S.epart;
                 d.nepart = S.nepart;
+                d.yoff = S.yoff;
+                d.nyg = S.nyg;
                 gkidx = S.kidx;
                 psi = s;
             }
@@ -1148,7 +1151,6 @@ __global__ void __launch_bounds__(C32_THREADS, 1) k_contract32(const SysDev *__r
                 d.first = cz;
                 d.span = span;
                 d.lt = lt;
-                d.pad = 0;
                 desc[b] = d;
             }
             __syncwarp();
@@ -1624,9 +1626,10 @@ __device__ __forceinline__ int ksort_bin(const SysDev &S, unsigned idx) {
     const int nx = S.nx, ny = S.ny, nz = S.nz, nzh = S.nzh;
     const int kz = (int)(idx % (unsigned)nzh);
     const int rest = (int)(idx / (unsigned)nzh);
-    const int x = axis_freq(rest / ny, nx, S.sx1), y = axis_freq(rest % ny, ny, S.sy1);
-    const int mx = fold(x, nx), my = fold(y, ny);
-    const bool qx = (nx % 2 == 0) && (x == nx / 2), qy = (ny % 2 == 0) && (y == ny / 2);
+    const int nyg = S.nyg;
+    const int x = axis_freq(rest / ny, nx, S.sx1), y = axis_freq(S.yoff + rest % ny, nyg, S.sy1);
+    const int mx = fold(x, nx), my = fold(y, nyg);
+    const bool qx = (nx % 2 == 0) && (x == nx / 2), qy = (nyg % 2 == 0) && (y == nyg / 2);
     const bool qz = (nz % 2 == 0) && (kz == nz / 2);
     const int mz = qz ? -kz : kz;
     if constexpr (F32) {
@@ -1735,6 +1738,40 @@ cudaError_t launch_ksort(const SysDev &S, bool f32, unsigned *kidx, int *scratch
     k_ksort_scan<<<1, NK, 0, st>>>(nranges, hist, counts);
     if (f32) k_ksort_scatter<true><<<blocks, 32 * KSORT_WARPS, 0, st>>>(S, nranges, hist, kidx);
     else k_ksort_scatter<false><<<blocks, 32 * KSORT_WARPS, 0, st>>>(S, nranges, hist, kidx);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Slab decomposition exchange layout: the spectrum of an x-slab, [xl][y][kz][a]
+// with the y axis cut into P ranges of run complex values per x-plane, as
+// [xl][d][run]; the send buffer of the all-to-all as [d][xl][run] (each
+// destination's part contiguous), which is exactly the layout of the
+// destination's ky-slab spectrum [x][yl][kz][a] with x = s nxl + xl.
+// ---------------------------------------------------------------------------
+__global__ void k_slab_transpose(const float4 *__restrict__ src, float4 *__restrict__ dst, int nxl, int P,
+                                 size_t run4, int to_send) {
+    const size_t total = (size_t)nxl * P * run4;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t v = i % run4, q = i / run4;
+        if (to_send) {                      // i walks the send buffer [d][xl][run]
+            const size_t xl = q % nxl, d = q / nxl;
+            dst[i] = src[(xl * P + d) * run4 + v];
+        } else {                            // i walks the x-slab spectrum [xl][d][run]
+            const size_t d = q % P, xl = q / P;
+            dst[i] = src[(d * nxl + xl) * run4 + v];
+        }
+    }
+}
+
+cudaError_t launch_slab_transpose(const void *src, void *dst, int nxl, int P, size_t run_bytes, bool to_send,
+                                  int sms, cudaStream_t st) {
+    const size_t run4 = run_bytes / 16;
+    const size_t total = (size_t)nxl * P * run4;
+    size_t blocks = (total + 255) / 256;
+    if (blocks > (size_t)sms * 8) blocks = (size_t)sms * 8;
+    if (blocks < 1) blocks = 1;
+    k_slab_transpose<<<(unsigned)blocks, 256, 0, st>>>(static_cast<const float4 *>(src), static_cast<float4 *>(dst),
+                                                       nxl, P, run4, to_send ? 1 : 0);
     return cudaGetLastError();
 }
 

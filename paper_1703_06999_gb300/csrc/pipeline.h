@@ -84,6 +84,10 @@ cudaError_t upload_qmesh(const QMeshDev &q);
 // ints of device memory; its last NK ints receive the k-points per interval.
 constexpr int KSORT_RANGE = 16384;   // k-points per warp in the sort
 size_t ksort_scratch_ints(size_t nk);
+// slab decomposition: x-slab spectrum [xl][P][run] <-> all-to-all send
+// buffer [P][xl][run] (run_bytes a multiple of 16)
+cudaError_t launch_slab_transpose(const void *src, void *dst, int nxl, int P, size_t run_bytes, bool to_send,
+                                  int sms, cudaStream_t st);
 cudaError_t launch_ksort(const SysDev &S, bool f32, unsigned *kidx, int *scratch, cudaStream_t st);
 cudaError_t launch_q0(int prec, int npts, const double *n, const double *s, double Z, double *q0, double *dqdn,
                       double *dqds);

@@ -68,7 +68,7 @@ struct Slot {
 }  // namespace
 
 struct vdwgb_server_s {
-    int device = 0, prec = 1, max_batch = 8, max_inflight = 2, nplan = 4;
+    int device = 0, prec = 1, max_batch = 8, max_inflight = 2, nplan = 8;   // nplan: planner threads
     size_t pool = 0, used = 0, peak = 0;
     std::mutex mu;
     std::condition_variable cv;
