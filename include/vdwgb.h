@@ -307,7 +307,9 @@ typedef struct {
  * the device, chunks).  max_batch (1..256): most requests per batched launch (one launch per
  * stage over all of them); max_inflight (1..8): batches on the GPU at once,
  * each on its own stream, so later requests are admitted and planned while
- * earlier ones run.  Worker threads plan requests (FFT plans, k-point order),
+ * earlier ones run.  At most max_batch (max_inflight + 1) requests are
+ * admitted and not yet launched; the rest wait on the host and hold no
+ * device memory.  Worker threads plan requests (FFT plans, k-point order),
  * upload inputs with stream-ordered allocations, launch batches and collect
  * results.  The kernel table is built and stays resident. */
 int vdwgb_server_new(int device, int precision, size_t pool_bytes, int max_batch, int max_inflight,

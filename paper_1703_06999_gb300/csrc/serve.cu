@@ -69,6 +69,10 @@ struct Slot {
 
 struct vdwgb_server_s {
     int device = 0, prec = 1, max_batch = 8, max_inflight = 2, nplan = 8;   // nplan: planner threads
+    // requests taken by a planner and not yet dispatched, and their bound:
+    // the rest wait on the host, holding no device memory, so that idle
+    // resident plans are not evicted for requests that cannot run yet
+    int staged = 0, max_staged = 0;
     size_t pool = 0, used = 0, peak = 0;
     std::mutex mu;
     std::condition_variable cv;
@@ -131,7 +135,7 @@ static void planner_loop(vdwgb_server_s *s, int k) {
             std::unique_lock<std::mutex> lk(s->mu);
             s->cv.wait(lk, [&] {
                 if (s->stop) return true;
-                if (s->pending.empty()) return false;
+                if (s->pending.empty() || s->staged >= s->max_staged) return false;
                 const Req *f = s->pending.front();
                 const auto key = std::make_tuple(f->nx, f->ny, f->nz);
                 for (const auto &x : s->idle)
@@ -141,6 +145,7 @@ static void planner_loop(vdwgb_server_s *s, int k) {
             if (s->stop) return;
             r = s->pending.front();
             s->pending.pop_front();
+            ++s->staged;
             reuse = take_idle(s, r);
             if (reuse) {
                 ++s->plans_reused;             // its footprint stays counted in used
@@ -181,6 +186,7 @@ static void planner_loop(vdwgb_server_s *s, int k) {
         if (rc) {
             if (r->h) vdwgb_finalize(&r->h);
             s->used -= r->footprint;
+            --s->staged;
             r->status = rc;
             r->t_done = now_s();
             ++s->failed;
@@ -216,6 +222,7 @@ static void dispatcher_loop(vdwgb_server_s *s) {
             while (!s->ready.empty() && (int)batch.size() < s->max_batch) {
                 batch.push_back(s->ready.front());
                 s->ready.pop_front();
+                --s->staged;
             }
             slot->busy = true;
         }
@@ -394,6 +401,7 @@ int vdwgb_server_new(int device, int precision, size_t pool_bytes, int max_batch
     s->prec = precision;
     s->pool = pool_bytes;
     s->max_batch = max_batch;
+    s->max_staged = max_batch * (max_inflight + 1);
     s->max_inflight = max_inflight;
     s->slots.resize(max_inflight);
     cudaError_t e = cudaSuccess;
