@@ -7,7 +7,11 @@ binding) never imports it, and this package never imports the product.
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py`` except where its docstring says "parity unpinned".
+
+``oracle.spin`` holds the spin-polarised form (q0 of both spins, energy and
+four potentials).
 """
+from . import spin
 from .vdw import (Params, Oracle, calculate, q_mesh, spline_basis_d2, spline_basis,
                   q0_of, pw92_eps_c, saturate, phi_dion, kernel_table, kernel_at,
                   radial_transform, kabs_grid, cell_volume, pair_list, DF1, DF2,
