@@ -549,6 +549,134 @@ def stage_breakdown(B, torch, bt, ns, ss, dn, ds, en, sp, flush, steps):
     return stage_ms / max(ncalls, 1)
 
 
+def _event_ms(torch, stream, fn, reps, flush):
+    """Mean ms of fn() over reps calls, CUDA events on `stream`, L2 flushed
+    before each call (outside the events)."""
+    tot = 0.0
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / reps
+
+
+def spin_bench(B, inputs, torch, dev, local, sp, stream, flush, reps=20):
+    """The spin-polarised form on one 96^3 dimer (FP32-mixed and FP64, device
+    form) against the plain form of the same handle; its error against the
+    spin oracle on a 48^3 dimer."""
+    s = inputs.dimer(0, shape=DIMER_SHAPE, cell_lengths=DIMER_CELL, functional=1, device=dev)
+    nu, nd, su, sd = inputs.spin_split(s, 0.6, seed=1)
+    out = {}
+    for prec, name in ((B.FP32_MIXED, "fp32_mixed"), (B.FP64, "fp64")):
+        f = B.Functional(s.shape, s.cell, s.functional, prec, device=local)
+        o = [torch.empty_like(nu) for _ in range(4)]
+        en = torch.zeros(1, dtype=torch.float64, device=dev)
+        run_spin = lambda: B.vdwgb_calculate_spin_device(f.h, nu, nd, su, sd, *o, en, sp)   # noqa: E731
+        run_plain = lambda: f.calculate_device(s.n, s.sigma, o[0], o[1], en, sp)            # noqa: E731
+        for _ in range(3):
+            run_spin()
+            run_plain()
+        torch.cuda.synchronize()
+        t_spin = _event_ms(torch, stream, run_spin, reps, flush)
+        t_plain = _event_ms(torch, stream, run_plain, reps, flush)
+        B.vdwgb_device_status(local)
+        f.close()
+        out[name] = {"ms": t_spin, "value": s.npts / (t_spin / 1000.0), "unit": "grid pts/s",
+                     "plain_ms_same_handle": t_plain}
+    # results on a smaller dimer, for the comparison with the spin oracle
+    # (made with the other oracle runs)
+    sm = inputs.dimer(0, shape=(48, 48, 48), cell_lengths=DIMER_CELL, functional=1, device=dev)
+    a = [x.cpu().numpy() for x in inputs.spin_split(sm, 0.6, seed=1)]
+    gpu48 = {}
+    for prec, name in ((B.FP32_MIXED, "fp32_mixed"), (B.FP64, "fp64")):
+        f = B.Functional(sm.shape, sm.cell, sm.functional, prec, device=local)
+        gpu48[name] = f.calculate_spin(*a)
+        f.close()
+    out["workload"] = "one 96^3 dimer (18 x 18 x 24 bohr), polarisation 0.6 sin cos texture"
+    return out, (sm.cell, sm.functional, a, gpu48)
+
+
+def spin_errors(case):
+    """Errors of the spin-polarised GPU results against the spin oracle."""
+    from oracle import spin as ospin
+    from oracle import vdw as ovdw
+    cell, functional, a, gpu48 = case
+    ref = ospin.energy_potential_spin(ovdw.Oracle(ovdw.Params()), *a, cell, functional)
+    errs = {}
+    for name, (e, dn, ds) in gpu48.items():
+        errs[name] = {"abs_dE_Ha": abs(e - ref[0]),
+                      "dedn_rel_maxnorm": max(float(np.max(np.abs(x - y)) / np.max(np.abs(y)))
+                                              for x, y in zip(dn, ref[1])),
+                      "dedsigma_rel_maxnorm": max(float(np.max(np.abs(x - y)) / np.max(np.abs(y)))
+                                                  for x, y in zip(ds, ref[2]))}
+    return errs
+
+
+def slab_bench(B, inputs, torch, dev, local, stream, flush, P=4, reps=10):
+    """The slab decomposition with P virtual ranks on this GPU (each its own
+    plans and buffers; the two all-to-alls as device copies between them, so
+    the exchange runs at device-copy speed, not at a link's): per-phase
+    times against one plan on the whole grid, 192^3 ligand shell."""
+    from paper_1703_06999_gb300.slab import LibraryStages
+    s = inputs.ligand_shell(0, device=dev)
+    st = LibraryStages(local)
+    prec = B.FP32_MIXED
+    nbytes = st.slab_bytes(s.shape, P, prec)
+    part = nbytes // P
+    nxl = s.shape[0] // P
+    R = []
+    for r in range(P):
+        a, b, x = st.buffer(nbytes), st.buffer(nbytes), st.buffer(nbytes)
+        R.append(dict(h=st.new(s.functional, s.shape, s.cell, P, r, prec, a, b), a=a, b=b, x=x,
+                      e=st.energy_buffer(), rho=s.n[r * nxl:(r + 1) * nxl].contiguous(),
+                      sig=s.sigma[r * nxl:(r + 1) * nxl].contiguous(),
+                      dn=torch.empty((nxl,) + s.shape[1:], dtype=torch.float64, device=dev),
+                      ds=torch.empty((nxl,) + s.shape[1:], dtype=torch.float64, device=dev)))
+
+    def exchange(src, dst):
+        for r, Rr in enumerate(R):
+            for q, Rq in enumerate(R):
+                Rr[dst][q * part:(q + 1) * part].copy_(Rq[src][r * part:(r + 1) * part])
+
+    phases = [("forward", lambda: [st.forward(x["h"], x["rho"], x["sig"]) for x in R]),
+              ("pack", lambda: [st.pack(x["h"], x["x"]) for x in R]),
+              ("exchange", lambda: exchange("x", "b")),
+              ("contract", lambda: [st.contract(x["h"], x["e"]) for x in R]),
+              ("exchange_back", lambda: exchange("b", "x")),
+              ("unpack", lambda: [st.unpack(x["h"], x["x"]) for x in R]),
+              ("inverse", lambda: [st.inverse(x["h"], x["dn"], x["ds"]) for x in R])]
+    for _ in range(3):
+        for _, fn in phases:
+            fn()
+    torch.cuda.synchronize()
+    per = {}
+    total = 0.0
+    for name, fn in phases:
+        per[name] = _event_ms(torch, stream, fn, reps, flush)
+        total += per[name]
+    st.status()
+    f = B.Functional(s.shape, s.cell, s.functional, prec, device=local)
+    dn1, ds1 = torch.empty_like(s.n), torch.empty_like(s.n)
+    en1 = torch.zeros(1, dtype=torch.float64, device=dev)
+    one = _event_ms(torch, stream, lambda: f.calculate_device(s.n, s.sigma, dn1, ds1, en1, stream.cuda_stream),
+                    reps, flush)
+    same = all(torch.equal(x["dn"], dn1[r * nxl:(r + 1) * nxl]) for r, x in enumerate(R))
+    f.close()
+    for x in R:
+        st.free(x["h"])
+    pack_bytes = 2 * nbytes * P                    # read and write of every rank's spectrum
+    return {"workload": "192^3 ligand shell, FP32-mixed, %d virtual ranks on one GPU" % P,
+            "phase_ms": per, "ms_all_ranks": total, "ms_one_plan_whole_grid": one,
+            "pack_GBps": pack_bytes / (per["pack"] / 1000.0) / 1e9,
+            "potentials_bitwise_equal_one_plan": bool(same),
+            "exchange": "device copies between the ranks' buffers (an all-to-all's data movement "
+                        "at device-copy speed; no link is measured)"}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -783,6 +911,13 @@ def main():
         for f in fd:
             f.close()
 
+    spin_case = None
+    if extra is not None:
+        log("spin-polarised form")
+        extra["spin_dimer96"], spin_case = spin_bench(B, inputs, torch, dev, local, sp, stream, flush)
+        log("slab decomposition, virtual ranks")
+        extra["slab_shell192_P4"] = slab_bench(B, inputs, torch, dev, local, stream, flush)
+
     if not args.no_serve:
         log("serving stream")
     serving = None if args.no_serve else serve_bench(B, inputs, torch, dev, local)
@@ -800,6 +935,9 @@ def main():
             pool.close()
         err32 = errors_vs_oracle(g32, ref)
         err64 = errors_vs_oracle(g64, ref) if g64 is not None else None
+        if spin_case is not None:
+            log("spin oracle on a 48^3 dimer")
+            extra["spin_dimer96"]["error_vs_spin_oracle_48cubed"] = spin_errors(spin_case)
         one = float(np.mean([ref[i][4] / systems[i].npts for i in ref]))    # seconds per point, one core
         cpu = {"value": pts / wall, "unit": "grid pts/s", "cores": workers, "kind": "oracle",
                "sample": "the whole %s workload (%d systems, %d grid points), one system per worker process"

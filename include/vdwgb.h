@@ -111,6 +111,30 @@ int vdwgb_calculate_device(vdwgb_handle h, const double *d_rho, const double *d_
                            double *d_dedrho, double *d_dedsigma, double *d_energy,
                            void *cuda_stream);
 
+/* Spin-polarised form (svdW-DF: announced in Sec. 1 and the outlook, defined
+ * by Thonhauser et al., PRL 115, 136402 (2015)).  Inputs: the two spin
+ * densities n_up, n_dn and the same-spin gradient products sigma_upup =
+ * |grad n_up|^2, sigma_dndn = |grad n_dn|^2 (the energy does not depend on
+ * grad n_up . grad n_dn), [nx][ny][nz] as above.  theta uses the total
+ * density n_up + n_dn with the same kernel; q0 takes spin-scaled exchange
+ * (each channel with the gradient correction of its doubled density) and
+ * PW92 correlation with its spin interpolation, formed in FP64 in either
+ * precision.  Outputs, OVERWRITTEN, per unit volume: dE/dn_up, dE/dn_dn,
+ * dE/dsigma_upup, dE/dsigma_dndn, and the energy.  n_s < 0 and sigma_ss < 0
+ * count as 0; points with n_up + n_dn <= 1e-12 give zero outputs; a channel
+ * with n_s <= 1e-12 has no exchange term.  The handle allocates 48 bytes
+ * per grid point at the first call (64 more for the host form's staging).
+ * Host form: blocking, like vdwgb_calculate.  Device form: enqueued on
+ * cuda_stream like vdwgb_calculate_device, same rules; ESTATE with the plane
+ * kernel on. */
+int vdwgb_calculate_spin(vdwgb_handle h, const double *rho_up, const double *rho_dn,
+                         const double *sigma_upup, const double *sigma_dndn, double *dedrho_up,
+                         double *dedrho_dn, double *dedsigma_upup, double *dedsigma_dndn, double *energy);
+int vdwgb_calculate_spin_device(vdwgb_handle h, const double *d_rho_up, const double *d_rho_dn,
+                                const double *d_sigma_upup, const double *d_sigma_dndn, double *d_dedrho_up,
+                                double *d_dedrho_dn, double *d_dedsigma_upup, double *d_dedsigma_dndn,
+                                double *d_energy, void *cuda_stream);
+
 /* Paper-shaped convenience: returns the energy, NaN on any error. */
 double vdwgb_calculate_simple(vdwgb_handle h, const double *rho, const double *sigma,
                               double *dedrho, double *dedsigma);

@@ -98,6 +98,8 @@ _SIGS.update({
     "vdwgb_slab_unpack": (ctypes.c_int, [ctypes.c_void_p] * 3),
     "vdwgb_slab_inverse": (ctypes.c_int, [ctypes.c_void_p] * 4),
     "vdwgb_slab_free": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p)]),
+    "vdwgb_calculate_spin": (ctypes.c_int, [ctypes.c_void_p] * 10),
+    "vdwgb_calculate_spin_device": (ctypes.c_int, [ctypes.c_void_p] * 11),
 })
 
 
@@ -172,6 +174,25 @@ def vdwgb_calculate_device(h, rho, sigma, dedrho, dedsigma, energy, stream=0):
     """Device tensors (float64, contiguous); ``stream`` is a raw cudaStream_t."""
     _ck(lib().vdwgb_calculate_device(h, _ptr(rho), _ptr(sigma), _ptr(dedrho), _ptr(dedsigma), _ptr(energy),
                                      ctypes.c_void_p(int(stream))), "vdwgb_calculate_device")
+
+
+def vdwgb_calculate_spin(h, rho_up, rho_dn, sigma_upup, sigma_dndn, dedrho_up, dedrho_dn, dedsigma_upup,
+                         dedsigma_dndn):
+    """Spin-polarised form, host arrays (float64, C order); returns the energy."""
+    e = np.zeros(1)
+    _ck(lib().vdwgb_calculate_spin(h, _ptr(rho_up), _ptr(rho_dn), _ptr(sigma_upup), _ptr(sigma_dndn),
+                                   _ptr(dedrho_up), _ptr(dedrho_dn), _ptr(dedsigma_upup), _ptr(dedsigma_dndn),
+                                   e.ctypes.data), "vdwgb_calculate_spin")
+    return float(e[0])
+
+
+def vdwgb_calculate_spin_device(h, rho_up, rho_dn, sigma_upup, sigma_dndn, dedrho_up, dedrho_dn, dedsigma_upup,
+                                dedsigma_dndn, energy, stream=0):
+    """Spin-polarised form, device tensors (float64, contiguous); ``stream`` a raw cudaStream_t."""
+    _ck(lib().vdwgb_calculate_spin_device(h, _ptr(rho_up), _ptr(rho_dn), _ptr(sigma_upup), _ptr(sigma_dndn),
+                                          _ptr(dedrho_up), _ptr(dedrho_dn), _ptr(dedsigma_upup),
+                                          _ptr(dedsigma_dndn), _ptr(energy), ctypes.c_void_p(int(stream))),
+        "vdwgb_calculate_spin_device")
 
 
 def vdwgb_set_fused(enable):
@@ -453,6 +474,14 @@ class Functional:
 
     def calculate_device(self, rho, sigma, dedrho, dedsigma, energy, stream=0):
         vdwgb_calculate_device(self.h, rho, sigma, dedrho, dedsigma, energy, stream)
+
+    def calculate_spin(self, rho_up, rho_dn, sigma_upup, sigma_dndn):
+        """Spin-polarised form, host float64 arrays in; (energy, (dE/dn_up,
+        dE/dn_dn), (dE/dsigma_upup, dE/dsigma_dndn)) out."""
+        a = [np.ascontiguousarray(x, dtype=np.float64) for x in (rho_up, rho_dn, sigma_upup, sigma_dndn)]
+        o = [np.empty_like(a[0]) for _ in range(4)]
+        e = vdwgb_calculate_spin(self.h, *a, *o)
+        return e, (o[0], o[1]), (o[2], o[3])
 
     def close(self):
         if self.h is not None and self.h.value:

@@ -21,7 +21,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvdwgb.so")
 BUILD_CHECKED = os.path.join(HERE, "_build_checked")
 LIB_CHECKED = os.path.join(HERE, "libvdwgb_checked.so")
-SOURCES = ["capi.cu", "pipeline.cu", "table.cu", "serve.cu", "noalloc.cu", "plane.cu", "probe.cu", "slab.cu"]
+SOURCES = ["capi.cu", "pipeline.cu", "table.cu", "serve.cu", "noalloc.cu", "plane.cu", "probe.cu", "slab.cu",
+           "spin.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -193,6 +193,9 @@ static void release(vdwgb_data *h) {
     dfree(h, h->dsys);
     dfree(h, h->dprefix);
     dfree(h, h->d_io);
+    dfree(h, h->d_spin);
+    dfree(h, h->d_spin_io);
+    h->d_spin = h->d_spin_io = nullptr;
     if (h->stream) cudaStreamDestroy(h->stream);
     h->spec = h->rec = nullptr;
     h->epart = nullptr;
@@ -939,6 +942,15 @@ int vdwgb_init_cuda(vdwgb_handle h, int device, int precision) {
     return handle_init(h, device, precision, nullptr);
 }
 
+// a descriptor left in the spin-polarised form (q0 given) goes back to the
+// plain form, uploaded by the next set_io
+static void plain_form(vdwgb_data *h) {
+    if (h->hsys.q0in) {
+        h->hsys.q0in = 0;
+        h->last_ptr[0] = nullptr;
+    }
+}
+
 static int set_io(vdwgb_data *h, const double *n, const double *s, double *dn, double *ds, double *e,
                   cudaStream_t st) {
     const double *p[5] = {n, s, dn, ds, e};
@@ -962,6 +974,7 @@ int vdwgb_calculate_device(vdwgb_handle h, const double *d_rho, const double *d_
         return fail(VDWGB_EINVAL, "null array");
     CK(cudaSetDevice(h->device), "cudaSetDevice");
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    plain_form(h);
     int rc = set_io(h, d_rho, d_sigma, d_dedrho, d_dedsigma, d_energy, st);
     if (rc) return rc;
     CK(launch_all(h->ls, h->prec, st), "launch");
@@ -983,6 +996,7 @@ int vdwgb_calculate(vdwgb_handle h, const double *rho, const double *sigma, doub
     cudaStream_t st = h->stream;
     CK(cudaMemcpyAsync(dn, rho, N * sizeof(double), cudaMemcpyHostToDevice, st), "copy rho");
     CK(cudaMemcpyAsync(ds, sigma, N * sizeof(double), cudaMemcpyHostToDevice, st), "copy sigma");
+    plain_form(h);
     int rc = set_io(h, dn, ds, odn, ods, oe, st);
     if (rc) return rc;
     CK(launch_all(h->ls, h->prec, st), "launch");

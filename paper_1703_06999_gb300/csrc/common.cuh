@@ -105,7 +105,8 @@ struct SysDev {
     double Z;        // Z_ab of the functional
     float zc[2];     // -Z_ab / 36 as an FP32 pair (hi, lo), for the FP32-mixed q0
     float invNf;     // 1 / N in FP32
-    int pad0;
+    int q0in;        // 1: sigma holds q0 (spin-polarised form: q0 formed beforehand) and the
+                     // z-inverse pass writes sum_a F_a p_a and n sum_a F_a p'_a as dedn / dedsigma
     const double *n;
     const double *sigma;
     double *dedn;

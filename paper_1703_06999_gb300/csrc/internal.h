@@ -35,6 +35,11 @@ struct vdwgb_data {
     size_t bytes = 0;
     // host-pointer path staging
     double *d_io = nullptr;      // n, sigma, dedn, dedsigma, energy
+    // spin-polarised form (spin.cu), allocated at its first call: n and q0
+    // (overwritten by the two potential sums), four derivatives of q0; host
+    // path staging of four inputs, four outputs and the energy
+    double *d_spin = nullptr;
+    double *d_spin_io = nullptr;
     cudaStream_t stream = nullptr;
     cudaStream_t alloc_stream = nullptr;   // set: stream-ordered allocations (server handles)
     const double *last_ptr[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};

@@ -218,6 +218,30 @@ __device__ __forceinline__ dfl df_exp_neg2(dfl S, const float2 *ex2) {
     return dfl{v.hi * sc, v.lo * sc};
 }
 
+// interval j with q_j <= q0 < q_{j+1} and B = (q0 - q_j) / h_j of a
+// double-float q0; q0 below q_min: j = 0, B = 0, q0 = q_min and false (the
+// derivatives stay zero)
+__device__ __forceinline__ bool df_interval(dfl q0, const Q0Tab *tb, Q0M &r) {
+    const dfl qmin = tb->qd[0];
+    if (df_lt(q0, qmin)) {
+        r.j = 0;
+        r.B = 0.f;
+        r.q0 = c_qm.q_min;
+        return false;
+    }
+    r.q0 = df_to(q0);
+    int lo = 0, hi = NQ - 2;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (df_lt(q0, tb->qd[mid])) hi = mid - 1;
+        else lo = mid;
+    }
+    r.j = lo;
+    const dfl qj = tb->qd[lo];
+    r.B = ((q0.hi - qj.hi) + (q0.lo - qj.lo)) * tb->invhd[lo].hi;
+    return true;
+}
+
 // zc = -Z_ab / 36 in double-float (positive)
 __device__ __forceinline__ Q0M q0_point_df(double n, double s, dfl zc, const Q0Tab *tb) {
     Q0M r;
@@ -288,23 +312,7 @@ __device__ __forceinline__ Q0M q0_point_df(double n, double s, dfl zc, const Q0T
         for (int m = 0; m < 11; ++m) dS = fmaf(dS, t.hi, 1.f);   // sum_{m=0}^{11} t^m
         dh = ex.hi * dS;
     }
-    const dfl qmin = tb->qd[0];
-    if (df_lt(q0, qmin)) {
-        r.j = 0;
-        r.B = 0.f;
-        r.q0 = c_qm.q_min;
-        return r;
-    }
-    r.q0 = df_to(q0);
-    int lo = 0, hi = NQ - 2;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (df_lt(q0, tb->qd[mid])) hi = mid - 1;
-        else lo = mid;
-    }
-    r.j = lo;
-    const dfl qj = tb->qd[lo];
-    r.B = ((q0.hi - qj.hi) + (q0.lo - qj.lo)) * tb->invhd[lo].hi;
+    if (!df_interval(q0, tb, r)) return r;
     if (dh == 0.f) return r;
     // dq_raw/dn = (k_F/3 + (4 pi/9) r_s deps/dr_s - (7/3) G) / n; the sum can
     // cancel, so it is formed in double-float; dq_raw/dsigma is a plain product
@@ -319,6 +327,38 @@ __device__ __forceinline__ Q0M q0_point_df(double n, double s, dfl zc, const Q0T
     const dfl dqn = df_mul(df_sub(t12, df_mul(DF(7.0 / 3.0), G)), df_rcp_fast(nd));
     r.dqdn = dh * dqn.hi;
     r.dqds = dh * (zc.hi * ikF.hi * in2.hi);
+    return r;
+}
+
+// q0 formed beforehand (the spin-polarised form): the interval of the given
+// q0 at live points, and the records' derivative factors set so that the
+// z-inverse pass leaves sum_a F_a p_a in dedn (dq0/dn = 0) and
+// n sum_a F_a p'_a in dedsigma (dq0/dsigma = 1)
+__device__ __forceinline__ Q0M q0_given_df(double n, double q0, const Q0Tab *tb) {
+    Q0M r;
+    r.live = __double_as_longlong(n) > __double_as_longlong(c_qm.n_min);
+    r.dqdn = 0.f;
+    r.dqds = 0.f;
+    r.nf = 0.f;
+    if (!r.live) {
+        r.j = -1;
+        r.B = 0.f;
+        r.q0 = c_qm.q_min;
+        return r;
+    }
+    const dfl nd = df_from_bits(n);
+    r.nf = nd.hi + nd.lo;
+    df_interval(df_from_bits(q0), tb, r);
+    r.dqds = 1.f;
+    return r;
+}
+
+__device__ __forceinline__ Q0 q0_given(double n, double q0) {
+    Q0 r;
+    r.live = n > c_qm.n_min;
+    r.q0 = r.live ? q0 : c_qm.q_min;
+    r.dqdn = 0.0;
+    r.dqds = r.live ? 1.0 : 0.0;
     return r;
 }
 
@@ -478,7 +518,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zfwd(const SysD
                 int j = -1;
                 T B = (T)0, ndqn = (T)0, ndqs = (T)0, nn = (T)0;
                 if (sizeof(T) == 4) {
-                    const Q0M q = q0_point_df(n, sg, zc, &qs->q0t);
+                    const Q0M q = S.q0in ? q0_given_df(n, sg, &qs->q0t) : q0_point_df(n, sg, zc, &qs->q0t);
                     j = q.j;
                     B = (T)q.B;
                     nn = (T)q.nf;
@@ -486,7 +526,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zfwd(const SysD
                     ndqs = (T)(q.nf * q.dqds);
                 } else {
                     nn = (T)n;
-                    const Q0 q = q0_point(n, sg, S.Z);
+                    const Q0 q = S.q0in ? q0_given(n, sg) : q0_point(n, sg, S.Z);
                     if (q.live) {
                         j = q_interval(q.q0, qs->q);
                         B = (T)((q.q0 - qs->q[j]) * qs->invh[j]);

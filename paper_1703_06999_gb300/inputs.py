@@ -131,6 +131,30 @@ def make_system(shape, cell, atoms, functional=1, floor=1e-10, device="cpu", nam
                   int(functional), n, s, list(atoms), name)
 
 
+def spin_split(system: System, amplitude: float = 0.6, seed: int = 0, empty_down_slab: bool = False):
+    """Spin densities of a system: n_up = n (1 + zeta) / 2, n_dn = n (1 - zeta) / 2
+    with a smooth periodic polarisation zeta(r) = amplitude sin(2 pi (u . f1))
+    cos(2 pi (u . f2)) (u the fractional coordinates, f1 and f2 small integer
+    vectors drawn from ``seed``), and sigma_ss = |grad n_s|^2 spectrally.
+    ``empty_down_slab`` makes the first quarter of the x planes fully
+    polarised (n_dn = 0 there).  Returns (n_up, n_dn, sigma_upup, sigma_dndn),
+    float64 tensors on the system's device."""
+    g = _rng(seed)
+    n = system.n
+    dev = n.device
+    fr = [torch.arange(k, dtype=torch.float64, device=dev) / k for k in system.shape]
+    u = torch.stack(torch.meshgrid(*fr, indexing="ij"), dim=-1)
+    f1 = torch.as_tensor(g.integers(-2, 3, 3), dtype=torch.float64, device=dev)
+    f2 = torch.as_tensor(g.integers(-2, 3, 3), dtype=torch.float64, device=dev)
+    f1[0] = 1.0
+    zeta = amplitude * torch.sin(2 * np.pi * (u @ f1)) * torch.cos(2 * np.pi * (u @ f2))
+    if empty_down_slab:
+        zeta[: max(1, system.shape[0] // 4)] = 1.0
+    nu = n * (1 + zeta) / 2
+    nd = n * (1 - zeta) / 2
+    return nu, nd, spectral_sigma(nu, system.cell), spectral_sigma(nd, system.cell)
+
+
 # ---------------------------------------------------------------------------
 # Workloads (sizes and structure of the paper's use cases, all synthetic).
 # ---------------------------------------------------------------------------
