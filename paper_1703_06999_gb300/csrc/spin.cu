@@ -80,7 +80,10 @@ __global__ void k_spin_q0(SpinArgs a) {
                 }
             }
             // PW92 correlation at (r_s, zeta)
-            const double zeta = (nu - nd) * inv_n;
+            // a correctly rounded division, so that a fully polarised point has
+            // zeta = +-1 exactly: (1 -+ zeta)^(1/3) has an infinite slope there
+            double zeta = (nu - nd) / n;
+            zeta = zeta > 1.0 ? 1.0 : (zeta < -1.0 ? -1.0 : zeta);
             const double rs = cbrt(3.0 / (4.0 * PI * n)), srs = sqrt(rs);
             double e0, de0, e1, de1, ga, dga;
             pw92_G(P0, rs, srs, e0, de0);
