@@ -491,7 +491,38 @@ def serve_bench(B, inputs, torch, dev, local, rate=200.0, count=2000, distinct=1
                 "failed": st["failed"], "plans_reused": st["plans_reused"] - warm["plans_reused"],
                 "plans_built": st["plans_built"] - warm["plans_built"], "pool_peak_GB": st["pool_used_peak"] / 1e9}
 
+    # the GPU alone on one batch of the stream's requests (the batch graph,
+    # device-resident inputs): what the served throughput is bounded by
+    log("serving: one 16-request batch on the GPU alone")
+    gsys = [inputs.realise(r, device=dev) for r in reqs[:16]]
+    gf = [B.Functional(sy.shape, sy.cell, sy.functional, B.FP32_MIXED, device=local) for sy in gsys]
+    gb = B.vdwgb_batch_new([f.h for f in gf])
+    gdn = [torch.empty_like(sy.n) for sy in gsys]
+    gds = [torch.empty_like(sy.n) for sy in gsys]
+    gen = torch.zeros(len(gsys), dtype=torch.float64, device=dev)
+    gsp = torch.cuda.current_stream(dev).cuda_stream
+    run = lambda: B.vdwgb_batch_calculate_device(gb, [sy.n for sy in gsys], [sy.sigma for sy in gsys],  # noqa: E731
+                                                 gdn, gds, gen, gsp)
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(5):
+        run()
+    b.record()
+    b.synchronize()
+    gpu_batch = {"requests": len(gsys), "grid_points": sum(sy.npts for sy in gsys),
+                 "value": 5 * sum(sy.npts for sy in gsys) / (a.elapsed_time(b) / 1000.0), "unit": "grid pts/s"}
+    B.vdwgb_device_status(local)
+    B.vdwgb_batch_free(gb)
+    for f in gf:
+        f.close()
+    del gsys, gdn, gds
+    torch.cuda.empty_cache()
+
     main = stream(rate, count)
+    main["gpu_alone_one_batch"] = gpu_batch
     main["fp64_one_at_a_time"] = {"value": fp64_rate, "unit": "grid pts/s", "requests": len(lat64),
                                   "p50_ms": 1000 * float(np.median(lat64)),
                                   "p99_ms": 1000 * float(np.percentile(lat64, 99))}
@@ -653,11 +684,20 @@ def slab_bench(B, inputs, torch, dev, local, stream, flush, P=4, reps=10):
         for _, fn in phases:
             fn()
     torch.cuda.synchronize()
-    per = {}
-    total = 0.0
-    for name, fn in phases:
-        per[name] = _event_ms(torch, stream, fn, reps, flush)
-        total += per[name]
+    # whole evaluations, CUDA events between the phases (every phase runs once
+    # per evaluation: the contraction works in place)
+    per = {name: 0.0 for name, _ in phases}
+    for _ in range(reps):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(phases) + 1)]
+        ev[0].record(stream)
+        for k, (_, fn) in enumerate(phases):
+            fn()
+            ev[k + 1].record(stream)
+        ev[-1].synchronize()
+        for k, (name, _) in enumerate(phases):
+            per[name] += ev[k].elapsed_time(ev[k + 1]) / reps
+    total = sum(per.values())
     st.status()
     f = B.Functional(s.shape, s.cell, s.functional, prec, device=local)
     dn1, ds1 = torch.empty_like(s.n), torch.empty_like(s.n)

@@ -281,22 +281,30 @@ static void complete_slot(vdwgb_server_s *s, Slot *slot, int dev_rc, cudaStream_
     // only under the lock (a waiting caller may free it right after)
     std::vector<int> st(reqs.size());
     std::vector<double> en(reqs.size(), 0.0);
+    std::vector<int> pend(reqs.size());
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (size_t i = 0; i < reqs.size(); ++i) pend[i] = reqs[i]->err ? reqs[i]->err : reqs[i]->status;
+    }
+    // every copy of the batch first, then one wait: the copies run back to back
+    cudaError_t ce = cudaSuccess;
+    if (dev_rc == 0) {
+        for (size_t i = 0; i < reqs.size() && ce == cudaSuccess; ++i) {
+            if (pend[i] != 1) continue;
+            Req *r = reqs[i];
+            const size_t N = r->npts;
+            ce = cudaMemcpyAsync(r->dedrho, r->h->d_io + 2 * N, N * sizeof(double), cudaMemcpyDeviceToHost, cst);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpyAsync(r->dedsigma, r->h->d_io + 3 * N, N * sizeof(double), cudaMemcpyDeviceToHost, cst);
+        }
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(cst);
+    }
     for (size_t i = 0; i < reqs.size(); ++i) {
         Req *r = reqs[i];
-        int pending_status;
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
-            pending_status = r->err ? r->err : r->status;
-        }
+        const int pending_status = pend[i];
         if (pending_status == 1 && dev_rc == 0) {
-            const size_t N = r->npts;
-            cudaError_t e = cudaMemcpyAsync(r->dedrho, r->h->d_io + 2 * N, N * sizeof(double),
-                                            cudaMemcpyDeviceToHost, cst);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(r->dedsigma, r->h->d_io + 3 * N, N * sizeof(double), cudaMemcpyDeviceToHost, cst);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(cst);
             en[i] = slot->henergy[i];
-            st[i] = e == cudaSuccess ? 0 : VDWGB_ECUDA;
+            st[i] = ce == cudaSuccess ? 0 : VDWGB_ECUDA;
         } else if (pending_status == 1) {
             st[i] = dev_rc ? dev_rc : VDWGB_ECUDA;
         } else {
