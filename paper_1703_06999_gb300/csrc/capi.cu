@@ -925,12 +925,17 @@ int vdwgb::device_sms(int device) { return (device >= 0 && device < 64) ? g_dev[
 int vdwgb::handle_replan(vdwgb_data *h, const double *cell9, int functional) {
     if (!h || !h->inited) return fail(VDWGB_ESTATE, "re-plan of an uninitialised handle");
     if (h->hsys.fused) return fail(VDWGB_ESTATE, "re-plan of a plane-kernel plan");
+    // the same cell (repeated evaluations of one system) keeps the k-point
+    // order and chunks: they depend on the metric only
+    const bool same_cell = std::memcmp(h->cell, cell9, sizeof h->cell) == 0;
     std::memcpy(h->cell, cell9, sizeof h->cell);
     h->functional = functional;
     set_metric(h);
     CK(cudaSetDevice(h->device), "cudaSetDevice");
-    int rc = sort_kpoints(h, h->alloc_stream ? h->alloc_stream : h->stream);
-    if (rc) return rc;
+    if (!same_cell) {
+        const int rc = sort_kpoints(h, h->alloc_stream ? h->alloc_stream : h->stream);
+        if (rc) return rc;
+    }
     return upload_plan(h);
 }
 

@@ -103,16 +103,23 @@ static size_t request_footprint(int nx, int ny, int nz, int prec) {
     return vdwgb_footprint_bytes(nx, ny, nz, prec) + (4 * N + 1) * sizeof(double) + (1u << 20);
 }
 
-// an idle resident plan of this grid, or nullptr (under the lock)
+// an idle resident plan of this grid, or nullptr (under the lock); one of
+// the same cell first (its re-plan skips the k-point sort)
 static vdwgb_data *take_idle(vdwgb_server_s *s, const Req *r) {
     const auto key = std::make_tuple(r->nx, r->ny, r->nz);
-    for (auto it = s->idle.begin(); it != s->idle.end(); ++it)
-        if (it->grid == key) {
-            vdwgb_data *h = it->h;
-            s->idle.erase(it);
-            return h;
+    auto pick = s->idle.end();
+    for (auto it = s->idle.begin(); it != s->idle.end(); ++it) {
+        if (it->grid != key) continue;
+        if (std::memcmp(it->h->cell, r->cell, sizeof r->cell) == 0) {
+            pick = it;
+            break;
         }
-    return nullptr;
+        if (pick == s->idle.end()) pick = it;
+    }
+    if (pick == s->idle.end()) return nullptr;
+    vdwgb_data *h = pick->h;
+    s->idle.erase(pick);
+    return h;
 }
 
 static size_t idle_bytes(const vdwgb_server_s *s) {

@@ -138,3 +138,30 @@ def test_idle_plans_are_evicted_when_the_pool_is_full():
         assert st["pool_used_peak"] <= pool
     finally:
         B.vdwgb_server_free(sv)
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_same_cell_reuse_keeps_the_kpoint_order(prec):
+    # one system evaluated repeatedly (an SCF loop) with the functional
+    # switching: one plan built, every later request re-plans without the
+    # k-point sort and equals a fresh handle bit for bit
+    s1 = _requests()[3]
+    s2 = inputs.make_system(s1.shape, s1.cell, s1.atoms, 3 - s1.functional)
+    alone = {}
+    for s in (s1, s2):
+        f = B.Functional(s.shape, s.cell, s.functional, prec)
+        alone[s.functional] = f.calculate(s.n.numpy(), s.sigma.numpy())
+        f.close()
+    sv = B.vdwgb_server_new(0, prec, pool_bytes=1 << 30, max_batch=2, max_inflight=1)
+    try:
+        for k in range(5):
+            s = s1 if k % 2 == 0 else s2
+            dn, ds = np.empty(s.shape), np.empty(s.shape)
+            rid = B.vdwgb_server_submit(sv, s.functional, s.shape, s.cell, s.n.numpy(), s.sigma.numpy(), dn, ds)
+            e, _ = B.vdwgb_server_wait(sv, rid, 120.0)
+            a = alone[s.functional]
+            assert e == a[0] and np.array_equal(dn, a[1]) and np.array_equal(ds, a[2])
+        st = B.vdwgb_server_stats(sv)
+        assert st["plans_built"] == 1 and st["plans_reused"] == 4
+    finally:
+        B.vdwgb_server_free(sv)
