@@ -56,6 +56,7 @@ struct DevInfo {
     bool ready = false;
     int sms = 0;
     size_t maxsmem = 0;
+    size_t smem_sm = 0;      // shared memory per SM
     int *err = nullptr;      // device flag written by kernels whose bounded wait ran out
 };
 static std::mutex g_dev_mu;
@@ -70,8 +71,11 @@ int vdwgb::device_setup(int device) {
     int sms = 0, optin = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device), "attr");
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device), "attr");
+    int smsm = 0;
+    CK(cudaDeviceGetAttribute(&smsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device), "attr");
     d.sms = sms;
     d.maxsmem = (size_t)optin;
+    d.smem_sm = (size_t)smsm;
     QMeshDev qm;
     host_qmesh(qm);
     CK(upload_qmesh(qm), "upload q-mesh");
@@ -216,29 +220,51 @@ static size_t rec_bytes(int prec) { return prec == VDWGB_FP32_MIXED ? 16 : 32; }
 // prefetch).  The autotuner below replaces them by measured choices.
 static const size_t TILE_BUDGET = 110 * 1024;
 
-static int best_w(int prec, int n, int nzh, int slots) {
+// Caps on one tile's shared memory, default and autotuned tiles alike.  A
+// batch launch takes the largest tile of its systems, so one system's large
+// tile would set every system's occupancy: FP32 x / y tiles are kept to two
+// blocks per SM and z tiles to three (the blocks the kernels' register
+// bounds allow), each block with its static shared memory and the 1 KB the
+// runtime reserves.  FP64 kernels run one block per SM: no cap.
+// VDWGB_XY_CAP / VDWGB_Z_CAP (bytes) override.  Measured on the 64 uneven
+// grids: x / y passes 1.31 -> 0.94 ms, z inverse 1.44 -> 1.28 ms.
+static void tile_caps(int device, int prec, size_t &xy, size_t &z) {
+    static size_t env[2] = {0, 0};
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const char *e[2] = {std::getenv("VDWGB_XY_CAP"), std::getenv("VDWGB_Z_CAP")};
+        for (int i = 0; i < 2; ++i) env[i] = e[i] ? (size_t)std::strtoull(e[i], nullptr, 10) : 0;
+    });
+    const size_t sm = g_dev[device].smem_sm;
+    const bool f32 = prec == VDWGB_FP32_MIXED && sm > 0;
+    xy = env[0] ? env[0] : (f32 ? sm / 2 - 2560 : (size_t)-1);
+    z = env[1] ? env[1] : (f32 ? sm / 3 - 1824 : (size_t)-1);
+}
+
+static int best_w(int prec, int n, int nzh, int slots, size_t budget) {
     int W = 1;
     for (int w = 8; w >= 1; --w)
-        if (stage_smem(1, prec, n, w, slots) <= TILE_BUDGET) { W = w; break; }
+        if (stage_smem(1, prec, n, w, slots) <= budget) { W = w; break; }
     return W > nzh ? nzh : W;
 }
 
 // x / y passes: two ring buffers (one tile prefetched) plus the scratch
 // buffer on axes without an in-place transform (workx / worky)
-static void choose_tiles(int prec, int nx, int ny, int nz, int nzh, size_t lim, int workx, int worky, int &LZ,
-                         int &LZi, int &Wy, int &Wx, int &nbuf) {
+static void choose_tiles(int prec, int nx, int ny, int nz, int nzh, size_t lim, size_t xycap, size_t zcap,
+                         int workx, int worky, int &LZ, int &LZi, int &Wy, int &Wx, int &nbuf) {
+    const size_t zbudget = std::min(TILE_BUDGET, zcap), xybudget = std::min(TILE_BUDGET, xycap);
     LZ = 1;
     for (int l = 16; l >= 1; --l)
-        if (stage_smem(0, prec, nz, l) <= TILE_BUDGET) { LZ = l; break; }
+        if (stage_smem(0, prec, nz, l) <= zbudget) { LZ = l; break; }
     LZi = 1;
     for (int l = 16; l >= 1; --l)
-        if (stage_smem(3, prec, nz, l) <= TILE_BUDGET) { LZi = l; break; }
+        if (stage_smem(3, prec, nz, l) <= zbudget) { LZi = l; break; }
     if (LZi > nx * ny) LZi = nx * ny;
     if (LZ > nx * ny) LZ = nx * ny;
     nbuf = 2;
     if (stage_smem(1, prec, ny, 1, 2 + worky) > lim || stage_smem(1, prec, nx, 1, 2 + workx) > lim) nbuf = 1;
-    Wy = best_w(prec, ny, nzh, nbuf + worky);
-    Wx = best_w(prec, nx, nzh, nbuf + workx);
+    Wy = best_w(prec, ny, nzh, nbuf + worky, xybudget);
+    Wx = best_w(prec, nx, nzh, nbuf + workx, xybudget);
 }
 
 // Contraction chunks of a system from the k-points per kernel-table interval
@@ -640,6 +666,9 @@ static int apply_tuned(vdwgb_data *h) {
     const int prec = h->prec;
     const size_t N = (size_t)S.nx * S.ny * S.nz;
     const size_t lim = g_dev[h->device].maxsmem - 1024;
+    size_t xycap, zcap;
+    tile_caps(h->device, prec, xycap, zcap);
+    const size_t limxy = std::min(lim, xycap), limz = std::min(lim, zcap);
     std::vector<double> host(2 * N, 0.0);
     for (size_t i = 0; i < N; ++i) host[i] = 0.01;
     double *tmp = nullptr;
@@ -667,18 +696,18 @@ static int apply_tuned(vdwgb_data *h) {
             if ((pass == 0 || pass == 3) && ci >= 8) break;
             TuneVal v = best;
             if (pass == 0) {
-                if (c > S.nx * S.ny || stage_smem(0, prec, S.nz, c) > lim) continue;
+                if (c > S.nx * S.ny || stage_smem(0, prec, S.nz, c) > limz) continue;
                 v.LZ = c;
             } else if (pass == 1) {
-                if (c > S.nzh || stage_smem(1, prec, S.ny, c, nb + (S.sy1 ? 0 : 1)) > lim) continue;
+                if (c > S.nzh || stage_smem(1, prec, S.ny, c, nb + (S.sy1 ? 0 : 1)) > limxy) continue;
                 v.Wy = c;
                 v.nby = nb;
             } else if (pass == 2) {
-                if (c > S.nzh || stage_smem(1, prec, S.nx, c, nb + (S.sx1 ? 0 : 1)) > lim) continue;
+                if (c > S.nzh || stage_smem(1, prec, S.nx, c, nb + (S.sx1 ? 0 : 1)) > limxy) continue;
                 v.Wx = c;
                 v.nbx = nb;
             } else {
-                if (c > S.nx * S.ny || stage_smem(3, prec, S.nz, c) > lim) continue;
+                if (c > S.nx * S.ny || stage_smem(3, prec, S.nz, c) > limz) continue;
                 v.LZi = c;
             }
             set_tiles(h, v.LZ, v.LZi, v.Wy, v.Wx, v.nby, v.nbx);
@@ -727,7 +756,9 @@ static int plan(vdwgb_data *h) {
     S.sz1 = prec == VDWGB_FP32_MIXED ? fft_split(nz) : 0;
     const int workx = S.sx1 ? 0 : 1, worky = S.sy1 ? 0 : 1;
     int nbuf = 2;
-    choose_tiles(prec, nx, ny, nz, nzh, lim, workx, worky, S.LZ, S.LZi, S.Wy, S.Wx, nbuf);
+    size_t xycap, zcap;
+    tile_caps(h->device, prec, xycap, zcap);
+    choose_tiles(prec, nx, ny, nz, nzh, lim, xycap, zcap, workx, worky, S.LZ, S.LZi, S.Wy, S.Wx, nbuf);
     if (stage_smem(0, prec, nz, S.LZ) > lim || stage_smem(1, prec, nx, S.Wx, nbuf + workx) > lim ||
         stage_smem(1, prec, ny, S.Wy, nbuf + worky) > lim || stage_smem(3, prec, nz, S.LZi) > lim)
         return fail(VDWGB_EINVAL, "grid %dx%dx%d too large for one block per pencil in this precision",
