@@ -282,8 +282,8 @@ CONTRACT_FMA64_PER_KPOINT = 630 + 800 + 40
 # list summarised in the profiles directory).  An entry is removed when its
 # kernel changes.
 MEASURED_TRAFFIC = {
-    "uneven64": {"zfwd": 2712e6, "zinv": 2912e6, "contract": 4092e6, "yfwd": 4004e6, "xfwd": 4004e6,
-                 "xinv": 4004e6, "yinv": 4004e6},
+    "uneven64": {"zfwd": 2732e6, "zinv": 2916e6, "contract": 4092e6, "yfwd": 4008e6, "xfwd": 4008e6,
+                 "xinv": 4008e6, "yinv": 4008e6},
 }
 
 # Instruction-issue utilisation of the z-forward kernel (the q0 step in
