@@ -1451,6 +1451,26 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_zinv(const SysD
             const int l0 = (t - tbase) * S.LZi;
             const int nl = min(S.LZi, S.nx * S.ny - l0);
             if (!VDWGB_OK(t >= tbase && nl >= 1, S.err)) continue;   // tile past the system's lines
+            {
+                // the next tile's half spectrum and point records (same system)
+                // into L2 while this tile runs
+                const int tn = t + gridDim.x;
+                if (tn < total && tn < tbase + S.tiles[3]) {
+                    const int l0n = (tn - tbase) * S.LZi;
+                    const int nln = min(S.LZi, S.nx * S.ny - l0n);
+                    if (nln > 0) {
+                        const char *ps = reinterpret_cast<const char *>(S.spec) +
+                                         (size_t)l0n * S.nzh * NQ * sizeof(cx<T>);
+                        const size_t bs = (size_t)nln * S.nzh * NQ * sizeof(cx<T>);
+                        const char *pr = reinterpret_cast<const char *>(S.rec) + (size_t)l0n * S.nz * sizeof(Rec<T>);
+                        const size_t br = (size_t)nln * S.nz * sizeof(Rec<T>);
+                        for (size_t o = (size_t)threadIdx.x * 128; o < bs; o += (size_t)blockDim.x * 128)
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(ps + o));
+                        for (size_t o = (size_t)threadIdx.x * 128; o < br; o += (size_t)blockDim.x * 128)
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(pr + o));
+                    }
+                }
+            }
             const int ld = z_ld(nl);
             const cx<T> *gspec = reinterpret_cast<const cx<T> *>(S.spec) + (size_t)l0 * S.nzh * NQ;
             cx<T> *R = bufA;

@@ -36,14 +36,17 @@ struct SpinArgs {
 };
 
 // PW92's G(r_s) = -2A (1 + a1 r_s) ln(1 + 1 / (2A (b1 r_s^1/2 + b2 r_s + b3 r_s^3/2 + b4 r_s^2)))
-// and dG/dr_s for one parameter set {A, a1, b1, b2, b3, b4}
-__device__ __forceinline__ void pw92_G(const double *P, double rs, double srs, double &g, double &dg) {
-    const double A = P[0], a1 = P[1], b1 = P[2], b2 = P[3], b3 = P[4], b4 = P[5];
-    const double D = 2.0 * A * (b1 * srs + b2 * rs + b3 * rs * srs + b4 * rs * rs);
-    const double dD = 2.0 * A * (0.5 * b1 / srs + b2 + 1.5 * b3 * srs + 2.0 * b4 * rs);
-    const double L = log1p(1.0 / D);
-    g = -2.0 * A * (1.0 + a1 * rs) * L;
-    dg = -2.0 * A * a1 * L + 2.0 * A * (1.0 + a1 * rs) * dD / (D * D + D);
+// and dG/dr_s for one parameter set {A, a1, b1, b2, b3, b4}; srs = r_s^1/2,
+// isrs = r_s^-1/2
+__device__ __forceinline__ void pw92_G(const double *P, double rs, double srs, double isrs, double &g, double &dg) {
+    const double A2 = 2.0 * P[0], a1 = P[1], b1 = P[2], b2 = P[3], b3 = P[4], b4 = P[5];
+    const double D = A2 * srs * (b1 + srs * (b2 + srs * (b3 + srs * b4)));
+    const double dD = A2 * (0.5 * b1 * isrs + b2 + srs * (1.5 * b3 + 2.0 * b4 * srs));
+    const double iD = 1.0 / D;
+    const double L = log1p(iD);
+    const double ar = 1.0 + a1 * rs;
+    g = -A2 * ar * L;
+    dg = A2 * (ar * dD * iD / (1.0 + D) - a1 * L);
 }
 
 __global__ void k_spin_q0(SpinArgs a) {
@@ -51,10 +54,11 @@ __global__ void k_spin_q0(SpinArgs a) {
     const double P0[6] = {0.031091, 0.2137, 7.5957, 3.5876, 1.6382, 0.49294};
     const double P1[6] = {0.015545, 0.20548, 14.1189, 6.1977, 3.3662, 0.62517};
     const double PA[6] = {0.016887, 0.11125, 10.357, 3.6231, 0.88026, 0.49671};
-    const double FZ20 = 1.709921;
+    const double IFZ20 = 1.0 / 1.709921;                 // 1 / f''(0)
     const double PI = 3.14159265358979323846;
-    const double FDEN = 0.51984209978974632953;   // 2^(4/3) - 2
+    const double IFDEN = 1.0 / 0.51984209978974632953;   // 1 / (2^(4/3) - 2)
     const double kc = 4.0 * PI / 3.0;
+    const double RSK = 1.9191582926775128;               // (9 pi / 4)^(1/3) = r_s k_F
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += (size_t)gridDim.x * blockDim.x) {
         const double nu = a.nu[i] > 0.0 ? a.nu[i] : 0.0, nd = a.nd[i] > 0.0 ? a.nd[i] : 0.0;
         const double su = a.su[i] > 0.0 ? a.su[i] : 0.0, sd = a.sd[i] > 0.0 ? a.sd[i] : 0.0;
@@ -62,6 +66,12 @@ __global__ void k_spin_q0(SpinArgs a) {
         double q0 = a.q_min, d[4] = {0.0, 0.0, 0.0, 0.0};
         if (n > a.n_min) {
             const double inv_n = 1.0 / n;
+            // k_F of n and of each channel: k_s = (6 pi^2 n_s)^(1/3), and
+            // (1 +- zeta)^(1/3) = (2 n_s / n)^(1/3) = k_s / k_F, r_s = RSK / k_F
+            const double kF = cbrt(3.0 * PI * PI * n);
+            const double ikF = 1.0 / kF;
+            const double kk[2] = {nu > 0.0 ? cbrt(6.0 * PI * PI * nu) : 0.0,
+                                  nd > 0.0 ? cbrt(6.0 * PI * PI * nd) : 0.0};
             // exchange of each channel (spin scaling); a channel at or below
             // n_min contributes nothing
             double x = 0.0, own[2] = {0.0, 0.0}, oth[2] = {0.0, 0.0}, sig[2] = {0.0, 0.0};
@@ -69,45 +79,46 @@ __global__ void k_spin_q0(SpinArgs a) {
             for (int s = 0; s < 2; ++s) {
                 const double ns = s ? nd : nu, ss = s ? sd : su;
                 if (ns > a.n_min) {
-                    const double k = cbrt(6.0 * PI * PI * ns);
+                    const double k = kk[s];
                     const double as = ns * k;
                     const double ia = 1.0 / as;
                     const double gr = a.c * ss * inv_n * ia;        // (Z/36) sigma_ss / (n a_s)
                     x += as * inv_n - gr;
-                    own[s] = (4.0 / 3.0) * k * inv_n - as * inv_n * inv_n + gr * (inv_n + (4.0 / 3.0) / ns);
+                    own[s] = (4.0 / 3.0) * k * inv_n - as * inv_n * inv_n + gr * (inv_n + (4.0 / 3.0) * k * ia);   // k_s / a_s = 1 / n_s
                     oth[s] = -as * inv_n * inv_n + gr * inv_n;
                     sig[s] = -a.c * inv_n * ia;
                 }
             }
-            // PW92 correlation at (r_s, zeta)
-            // a correctly rounded division, so that a fully polarised point has
-            // zeta = +-1 exactly: (1 -+ zeta)^(1/3) has an infinite slope there
+            // PW92 correlation at (r_s, zeta); zeta by a correctly rounded
+            // division, so that a fully polarised point has zeta = +-1 exactly
             double zeta = (nu - nd) / n;
             zeta = zeta > 1.0 ? 1.0 : (zeta < -1.0 ? -1.0 : zeta);
-            const double rs = cbrt(3.0 / (4.0 * PI * n)), srs = sqrt(rs);
+            const double rs = RSK * ikF, srs = sqrt(rs), isrs = 1.0 / srs;
             double e0, de0, e1, de1, ga, dga;
-            pw92_G(P0, rs, srs, e0, de0);
-            pw92_G(P1, rs, srs, e1, de1);
-            pw92_G(PA, rs, srs, ga, dga);
-            const double up = cbrt(1.0 + zeta), dn = cbrt(1.0 - zeta);
-            const double f = ((1.0 + zeta) * up + (1.0 - zeta) * dn - 2.0) / FDEN;
-            const double df = (4.0 / 3.0) * (up - dn) / FDEN;
+            pw92_G(P0, rs, srs, isrs, e0, de0);
+            pw92_G(P1, rs, srs, isrs, e1, de1);
+            pw92_G(PA, rs, srs, isrs, ga, dga);
+            const double up = kk[0] * ikF, dn = kk[1] * ikF;
+            const double f = ((1.0 + zeta) * up + (1.0 - zeta) * dn - 2.0) * IFDEN;
+            const double df = (4.0 / 3.0) * (up - dn) * IFDEN;
             const double z3 = zeta * zeta * zeta, z4 = z3 * zeta;
-            const double eps = e0 - ga * f / FZ20 * (1.0 - z4) + (e1 - e0) * f * z4;
-            const double deps_rs = de0 - dga * f / FZ20 * (1.0 - z4) + (de1 - de0) * f * z4;
-            const double deps_z = -ga / FZ20 * (df * (1.0 - z4) - 4.0 * z3 * f) + (e1 - e0) * (df * z4 + 4.0 * z3 * f);
+            const double eps = e0 - ga * f * IFZ20 * (1.0 - z4) + (e1 - e0) * f * z4;
+            const double deps_rs = de0 - dga * f * IFZ20 * (1.0 - z4) + (de1 - de0) * f * z4;
+            const double deps_z = -ga * IFZ20 * (df * (1.0 - z4) - 4.0 * z3 * f) + (e1 - e0) * (df * z4 + 4.0 * z3 * f);
             const double qraw = x - kc * eps;
-            const double common = kc * deps_rs * rs * inv_n / 3.0;
+            const double common = kc * deps_rs * rs * inv_n * (1.0 / 3.0);
             const double dq_u = own[0] + oth[1] + common - kc * deps_z * (1.0 - zeta) * inv_n;
             const double dq_d = own[1] + oth[0] + common + kc * deps_z * (1.0 + zeta) * inv_n;
             // saturation h_a(x) = a [1 - exp(-sum_{m=1}^{12} (x/a)^m / m)] (appendix)
-            const double t = qraw / a.q_cut;
+            const double t = qraw * (1.0 / a.q_cut);
+            const double IM[12] = {1.0, 1.0 / 2, 1.0 / 3, 1.0 / 4, 1.0 / 5, 1.0 / 6,
+                                   1.0 / 7, 1.0 / 8, 1.0 / 9, 1.0 / 10, 1.0 / 11, 1.0 / 12};
             double S = 0.0, dS = 0.0, tp = 1.0;
 #pragma unroll
-            for (int m = 1; m <= 12; ++m) {
+            for (int m = 0; m < 12; ++m) {
                 dS += tp;
                 tp *= t;
-                S += tp / (double)m;
+                S += tp * IM[m];
             }
             const double e = exp(-S);
             const double q = a.q_cut * (1.0 - e);
