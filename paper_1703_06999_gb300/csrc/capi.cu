@@ -1307,7 +1307,6 @@ struct vdwgb_batch_s {
     double *h_energy = nullptr;                        // pinned staging of the energies (the caller's
                                                        // array may be pageable: a copy into it would block)
     cudaEvent_t cev[2 * MAXPARTS] = {};
-    cudaEvent_t hev[2 * MAXPARTS] = {};                // host-array path: uploads / downloads of each part done
 };
 
 // Parts of a batch: K = VDWGB_BATCH_SPLIT (0 or 1: none; 2..4; default 4:
@@ -1576,15 +1575,10 @@ int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double 
     }
     if (b->nparts && !b->timing) {
         // each part on its own stream: its copies in, its stage graph, its
-        // copies out.  The parts' uploads run one after the other (part p's
-        // wait for part p - 1's), so part 0 computes while the others upload,
-        // and so do the downloads: only part 0's uploads and the last part's
-        // downloads are not hidden behind kernels
+        // copies out; the copies of one part overlap the kernels of the others
         const int np = b->nparts;
         for (int p = 1; p < np; ++p)
             if (!b->hst[p]) CK(cudaStreamCreateWithFlags(&b->hst[p], cudaStreamNonBlocking), "stream");
-        for (int e = 0; e < 2 * np; ++e)
-            if (!b->hev[e]) CK(cudaEventCreateWithFlags(&b->hev[e], cudaEventDisableTiming), "event");
         if (!b->h_energy) CK(cudaMallocHost(&b->h_energy, n * sizeof(double)), "pinned energies");
         for (int p = 0; p < np; ++p) {
             if (b->hexec[p]) continue;
@@ -1619,7 +1613,6 @@ int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double 
         for (int p = 0; p < np; ++p) {
             cudaStream_t st = p ? b->hst[p] : b->own;
             const int lo = b->pstart[p], hi = b->pstart[p + 1];
-            if (p) CK(cudaStreamWaitEvent(st, b->hev[2 * (p - 1)], 0), "upload order");
             for (int i = lo; i < hi; ++i) {
                 const size_t N = (size_t)b->hs[i]->nx * b->hs[i]->ny * b->hs[i]->nz;
                 CK(cudaMemcpyAsync(const_cast<double *>(dr[i]), rho[i], N * sizeof(double), cudaMemcpyHostToDevice, st),
@@ -1628,9 +1621,7 @@ int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double 
                                    st),
                    "copy sigma");
             }
-            CK(cudaEventRecord(b->hev[2 * p], st), "upload done");
             CK(cudaGraphLaunch(b->hexec[p], st), "graph launch");
-            if (p) CK(cudaStreamWaitEvent(st, b->hev[2 * p - 1], 0), "download order");
             for (int i = lo; i < hi; ++i) {
                 const size_t N = (size_t)b->hs[i]->nx * b->hs[i]->ny * b->hs[i]->nz;
                 CK(cudaMemcpyAsync(dedrho[i], odn[i], N * sizeof(double), cudaMemcpyDeviceToHost, st), "copy dedrho");
@@ -1640,7 +1631,6 @@ int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double 
             CK(cudaMemcpyAsync(b->h_energy + lo, b->d_energy + lo, (hi - lo) * sizeof(double), cudaMemcpyDeviceToHost,
                                st),
                "copy energy");
-            CK(cudaEventRecord(b->hev[2 * p + 1], st), "download done");
         }
         for (int p = 0; p < np; ++p) CK(cudaStreamSynchronize(p ? b->hst[p] : b->own), "synchronize");
         std::memcpy(energy, b->h_energy, n * sizeof(double));
@@ -1728,8 +1718,6 @@ int vdwgb_batch_free(vdwgb_batch *bp) {
         if (b->graph) cudaGraphDestroy(b->graph);
         if (b->cap) cudaStreamDestroy(b->cap);
         for (auto ev : b->cev)
-            if (ev) cudaEventDestroy(ev);
-        for (auto ev : b->hev)
             if (ev) cudaEventDestroy(ev);
         cudaFree(b->dsys);
         cudaFree(b->dprefix);
