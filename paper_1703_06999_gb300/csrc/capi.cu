@@ -1307,12 +1307,6 @@ struct vdwgb_batch_s {
     double *h_energy = nullptr;                        // pinned staging of the energies (the caller's
                                                        // array may be pageable: a copy into it would block)
     cudaEvent_t cev[2 * MAXPARTS] = {};
-    // host-array path: copy streams (uploads, downloads) shared by the parts in
-    // part order, and its events (uploads of part p on copy stream k; part p's
-    // graph done)
-    static constexpr int NCOPY = 4;
-    cudaStream_t ust[NCOPY] = {}, dst[NCOPY] = {};
-    cudaEvent_t uev[MAXPARTS * NCOPY] = {}, gev[MAXPARTS] = {};
 };
 
 // Parts of a batch: K = VDWGB_BATCH_SPLIT (0 or 1: none; 2..4; default 4:
@@ -1580,23 +1574,11 @@ int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double 
         ods[i] = d + 3 * N;
     }
     if (b->nparts && !b->timing) {
-        // each part's stage graph on its own stream.  Its systems' uploads go
-        // round-robin over NCOPY upload streams in part order (parallel
-        // copies, part 0 first), its graph waits for its own uploads only, and
-        // its downloads go round-robin over NCOPY download streams once its
-        // graph is done: every part's copies overlap other parts' kernels
+        // each part on its own stream: its copies in, its stage graph, its
+        // copies out; the copies of one part overlap the kernels of the others
         const int np = b->nparts;
-        const int NC = vdwgb_batch_s::NCOPY;
         for (int p = 1; p < np; ++p)
             if (!b->hst[p]) CK(cudaStreamCreateWithFlags(&b->hst[p], cudaStreamNonBlocking), "stream");
-        for (int k = 0; k < NC; ++k) {
-            if (!b->ust[k]) CK(cudaStreamCreateWithFlags(&b->ust[k], cudaStreamNonBlocking), "stream");
-            if (!b->dst[k]) CK(cudaStreamCreateWithFlags(&b->dst[k], cudaStreamNonBlocking), "stream");
-        }
-        for (int e = 0; e < np * NC; ++e)
-            if (!b->uev[e]) CK(cudaEventCreateWithFlags(&b->uev[e], cudaEventDisableTiming), "event");
-        for (int p = 0; p < np; ++p)
-            if (!b->gev[p]) CK(cudaEventCreateWithFlags(&b->gev[p], cudaEventDisableTiming), "event");
         if (!b->h_energy) CK(cudaMallocHost(&b->h_energy, n * sizeof(double)), "pinned energies");
         for (int p = 0; p < np; ++p) {
             if (b->hexec[p]) continue;
@@ -1632,33 +1614,24 @@ int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double 
             cudaStream_t st = p ? b->hst[p] : b->own;
             const int lo = b->pstart[p], hi = b->pstart[p + 1];
             for (int i = lo; i < hi; ++i) {
-                cudaStream_t us = b->ust[(i - lo) % NC];
                 const size_t N = (size_t)b->hs[i]->nx * b->hs[i]->ny * b->hs[i]->nz;
-                CK(cudaMemcpyAsync(const_cast<double *>(dr[i]), rho[i], N * sizeof(double), cudaMemcpyHostToDevice, us),
+                CK(cudaMemcpyAsync(const_cast<double *>(dr[i]), rho[i], N * sizeof(double), cudaMemcpyHostToDevice, st),
                    "copy rho");
                 CK(cudaMemcpyAsync(const_cast<double *>(dsg[i]), sigma[i], N * sizeof(double), cudaMemcpyHostToDevice,
-                                   us),
+                                   st),
                    "copy sigma");
             }
-            for (int k = 0; k < NC; ++k) {
-                CK(cudaEventRecord(b->uev[p * NC + k], b->ust[k]), "uploads done");
-                CK(cudaStreamWaitEvent(st, b->uev[p * NC + k], 0), "wait uploads");
-            }
             CK(cudaGraphLaunch(b->hexec[p], st), "graph launch");
-            CK(cudaEventRecord(b->gev[p], st), "graph done");
-            for (int k = 0; k < NC; ++k) CK(cudaStreamWaitEvent(b->dst[k], b->gev[p], 0), "wait graph");
             for (int i = lo; i < hi; ++i) {
-                cudaStream_t ds = b->dst[(i - lo) % NC];
                 const size_t N = (size_t)b->hs[i]->nx * b->hs[i]->ny * b->hs[i]->nz;
-                CK(cudaMemcpyAsync(dedrho[i], odn[i], N * sizeof(double), cudaMemcpyDeviceToHost, ds), "copy dedrho");
-                CK(cudaMemcpyAsync(dedsigma[i], ods[i], N * sizeof(double), cudaMemcpyDeviceToHost, ds),
+                CK(cudaMemcpyAsync(dedrho[i], odn[i], N * sizeof(double), cudaMemcpyDeviceToHost, st), "copy dedrho");
+                CK(cudaMemcpyAsync(dedsigma[i], ods[i], N * sizeof(double), cudaMemcpyDeviceToHost, st),
                    "copy dedsigma");
             }
             CK(cudaMemcpyAsync(b->h_energy + lo, b->d_energy + lo, (hi - lo) * sizeof(double), cudaMemcpyDeviceToHost,
-                               b->dst[0]),
+                               st),
                "copy energy");
         }
-        for (int k = 0; k < NC; ++k) CK(cudaStreamSynchronize(b->dst[k]), "synchronize");
         for (int p = 0; p < np; ++p) CK(cudaStreamSynchronize(p ? b->hst[p] : b->own), "synchronize");
         std::memcpy(energy, b->h_energy, n * sizeof(double));
         return vdwgb_device_status(b->device);
@@ -1746,14 +1719,6 @@ int vdwgb_batch_free(vdwgb_batch *bp) {
         if (b->cap) cudaStreamDestroy(b->cap);
         for (auto ev : b->cev)
             if (ev) cudaEventDestroy(ev);
-        for (auto ev : b->uev)
-            if (ev) cudaEventDestroy(ev);
-        for (auto ev : b->gev)
-            if (ev) cudaEventDestroy(ev);
-        for (int k = 0; k < vdwgb_batch_s::NCOPY; ++k) {
-            if (b->ust[k]) cudaStreamDestroy(b->ust[k]);
-            if (b->dst[k]) cudaStreamDestroy(b->dst[k]);
-        }
         cudaFree(b->dsys);
         cudaFree(b->dprefix);
         cudaFree(b->dprefix2);
