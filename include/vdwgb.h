@@ -83,6 +83,21 @@ int vdwgb_set_unit_cell(vdwgb_handle h, int nx, int ny, int nz,
                         double c10, double c11, double c12,
                         double c20, double c21, double c22);
 
+/* A caller's convolution kernel in place of the vdW-DF one, before init (the
+ * paper's outlook, Sec. 7: the spline decomposition serves any nonlocal
+ * functional expressible as a convolution; Sec. 2 end: the kernel enters
+ * only as the 20 x 20 radial functions phi_ab(k)).  phik: host array of
+ * 210 x 1024 doubles, phik[p * 1024 + j] = phi_ab(k_j) for the symmetric
+ * pairs p = (a <= b) in row-major order (a = 0: b = 0..19, then a = 1, ...)
+ * on k_j = j 2 pi / 100 bohr^-1; phi is taken as 0 beyond the last point.
+ * The q-mesh, theta = n p_a(q0) and q0 stay those of the handle's functional
+ * (the mesh values are returned by vdwgb_kernel_table).  The handle builds
+ * its own spline coefficients from phik at init (about 20 MB on the device,
+ * not counted by vdwgb_footprint_bytes); handles with different tables do
+ * not batch together.  NULL restores the vdW-DF table.  EINVAL on a
+ * non-finite entry, ESTATE after init. */
+int vdwgb_set_kernel_k(vdwgb_handle h, const double *phik);
+
 /* Choose kernel interpolation (VDWGB_INTERP_*) before init.  Default cubic. */
 int vdwgb_set_interp(vdwgb_handle h, int interp);
 

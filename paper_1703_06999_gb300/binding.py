@@ -98,6 +98,7 @@ _SIGS.update({
     "vdwgb_slab_unpack": (ctypes.c_int, [ctypes.c_void_p] * 3),
     "vdwgb_slab_inverse": (ctypes.c_int, [ctypes.c_void_p] * 4),
     "vdwgb_slab_free": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p)]),
+    "vdwgb_set_kernel_k": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "vdwgb_calculate_spin": (ctypes.c_int, [ctypes.c_void_p] * 10),
     "vdwgb_calculate_spin_device": (ctypes.c_int, [ctypes.c_void_p] * 11),
 })
@@ -193,6 +194,18 @@ def vdwgb_calculate_spin_device(h, rho_up, rho_dn, sigma_upup, sigma_dndn, dedrh
                                           _ptr(dedrho_up), _ptr(dedrho_dn), _ptr(dedsigma_upup),
                                           _ptr(dedsigma_dndn), _ptr(energy), ctypes.c_void_p(int(stream))),
         "vdwgb_calculate_spin_device")
+
+
+def vdwgb_set_kernel_k(h, phik):
+    """A caller's kernel table phi_ab(k_j) (210 x 1024 float64, pairs a <= b
+    row-major) before init; None restores the vdW-DF table."""
+    if phik is None:
+        _ck(lib().vdwgb_set_kernel_k(h, None), "vdwgb_set_kernel_k")
+        return
+    a = np.ascontiguousarray(phik, dtype=np.float64)
+    if a.size != 210 * 1024:
+        raise ValueError("kernel table must hold 210 x 1024 values")
+    _ck(lib().vdwgb_set_kernel_k(h, a.ctypes.data), "vdwgb_set_kernel_k")
 
 
 def vdwgb_set_fused(enable):
@@ -452,12 +465,14 @@ def vdwgb_server_free(sv):
 class Functional:
     """One initialised handle: ``Functional(shape, cell, functional, precision)``."""
 
-    def __init__(self, shape, cell, functional=DF1, precision=FP64, device=0, interp=INTERP_CUBIC):
+    def __init__(self, shape, cell, functional=DF1, precision=FP64, device=0, interp=INTERP_CUBIC, kernel_k=None):
         self.shape = tuple(int(v) for v in shape)
         self.h = vdwgb_new(functional)
         try:
             vdwgb_set_unit_cell(self.h, self.shape, cell)
             vdwgb_set_interp(self.h, interp)
+            if kernel_k is not None:
+                vdwgb_set_kernel_k(self.h, kernel_k)
             vdwgb_init_cuda(self.h, device, precision)
         except Exception:
             vdwgb_finalize(self.h)

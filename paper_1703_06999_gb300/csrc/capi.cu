@@ -197,6 +197,7 @@ static void release(vdwgb_data *h) {
     dfree(h, h->dsys);
     dfree(h, h->dprefix);
     dfree(h, h->d_io);
+    table_custom_free(h->ktab);
     dfree(h, h->d_spin);
     dfree(h, h->d_spin_io);
     h->d_spin = h->d_spin_io = nullptr;
@@ -841,6 +842,14 @@ static int plan(vdwgb_data *h) {
     set_tiles(h, S.LZ, S.LZi, S.Wy, S.Wx, nbuf, nbuf);
     TableRefs tr;
     CK(table_get(h->device, tr), "kernel table");
+    if (!h->kernel_k.empty()) {
+        // the caller's kernel: its own spline coefficients in place of the resident table's
+        CK(table_custom(h->kernel_k.data(), h->ktab, h->alloc_stream ? h->alloc_stream : 0), "caller's kernel table");
+        tr.cub64 = h->ktab.cub64;
+        tr.lin64 = h->ktab.lin64;
+        tr.cub32 = h->ktab.cub32;
+        tr.lin32 = h->ktab.lin32;
+    }
     if (prec == VDWGB_FP32_MIXED)
         L.table = h->interp == VDWGB_INTERP_LINEAR ? (const void *)tr.lin32 : (const void *)tr.cub32;
     else
@@ -895,6 +904,19 @@ int vdwgb_set_unit_cell(vdwgb_handle h, int nx, int ny, int nz, double c00, doub
     h->nz = nz;
     std::memcpy(h->cell, c, sizeof c);
     h->cell_set = true;
+    return 0;
+}
+
+int vdwgb_set_kernel_k(vdwgb_handle h, const double *phik) {
+    if (!h) return fail(VDWGB_EINVAL, "null handle");
+    if (h->inited) return fail(VDWGB_ESTATE, "set the kernel table before init");
+    if (!phik) {
+        h->kernel_k.clear();                 // back to the resident vdW-DF table
+        return 0;
+    }
+    for (size_t i = 0; i < (size_t)NPAIR * NK; ++i)
+        if (!std::isfinite(phik[i])) return fail(VDWGB_EINVAL, "kernel table entry %zu is not finite", i);
+    h->kernel_k.assign(phik, phik + (size_t)NPAIR * NK);
     return 0;
 }
 

@@ -2,10 +2,12 @@
 // (serve.cu).  Not part of the public header.
 #pragma once
 #include <cstddef>
+#include <vector>
 #include <cuda_runtime.h>
 #include "../../include/vdwgb.h"
 #include "common.cuh"
 #include "pipeline.h"
+#include "table.h"
 
 struct vdwgb_data {
     int functional = 1;
@@ -40,6 +42,11 @@ struct vdwgb_data {
     // path staging of four inputs, four outputs and the energy
     double *d_spin = nullptr;
     double *d_spin_io = nullptr;
+    // a caller's kernel table (vdwgb_set_kernel_k): its k-space values, and
+    // the spline coefficients built from them at init (the resident table
+    // otherwise)
+    std::vector<double> kernel_k;
+    vdwgb::CustomTable ktab;
     cudaStream_t stream = nullptr;
     cudaStream_t alloc_stream = nullptr;   // set: stream-ordered allocations (server handles)
     const double *last_ptr[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};

@@ -421,6 +421,40 @@ double table_seconds(int device) {
     return g_tab[device].built ? g_tab[device].seconds : 0.0;
 }
 
+// Spline coefficients (the same construction as the resident table's) of a
+// caller's k-space table, phik[pair * NK + j] on the host; the four arrays
+// are allocated here, on the current device.
+cudaError_t table_custom(const double *h_phik, CustomTable &out, cudaStream_t st) {
+    out = CustomTable{};
+    double *phik = nullptr, *scratch = nullptr;
+    const size_t ncoef = (size_t)NPAIR * (NK - 1);
+    cudaError_t e = cudaMalloc(&phik, (size_t)NPAIR * NK * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&scratch, (size_t)NPAIR * 2 * NK * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&out.cub64, ncoef * sizeof(dvec4));
+    if (e == cudaSuccess) e = cudaMalloc(&out.lin64, ncoef * sizeof(dvec4));
+    if (e == cudaSuccess) e = cudaMalloc(&out.cub32, ncoef * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc(&out.lin32, ncoef * sizeof(float4));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(phik, h_phik, (size_t)NPAIR * NK * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        k_kspline<<<(NPAIR + 63) / 64, 64, 0, st>>>(phik, scratch, out.cub64, out.cub32, out.lin64, out.lin32);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(phik);
+    cudaFree(scratch);
+    if (e != cudaSuccess) table_custom_free(out);
+    return e;
+}
+
+void table_custom_free(CustomTable &t) {
+    cudaFree(t.cub64);
+    cudaFree(t.lin64);
+    cudaFree(t.cub32);
+    cudaFree(t.lin32);
+    t = CustomTable{};
+}
+
 cudaError_t table_phi(int device, int npts, const double *d1, const double *d2, double *out) {
     TableRefs r;
     cudaError_t e = table_get(device, r);

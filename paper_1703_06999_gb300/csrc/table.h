@@ -22,4 +22,14 @@ bool table_peek(int device, TableRefs &out);
 cudaError_t table_phi(int device, int npts, const double *d1, const double *d2, double *out);
 void host_qmesh(QMeshDev &q);
 
+// A caller's kernel table: spline coefficients built like the resident
+// table's from its k-space values (NPAIR x NK FP64, host), on the current
+// device; freed with table_custom_free.
+struct CustomTable {
+    dvec4 *cub64 = nullptr, *lin64 = nullptr;
+    float4 *cub32 = nullptr, *lin32 = nullptr;
+};
+cudaError_t table_custom(const double *h_phik, CustomTable &out, cudaStream_t st);
+void table_custom_free(CustomTable &t);
+
 }  // namespace vdwgb

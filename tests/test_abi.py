@@ -68,3 +68,21 @@ def test_fault_injection_arguments_without_gpu():
         with pytest.raises(B.VdwgbError) as ei:
             B.vdwgb_inject_fault(kind, count)
         assert ei.value.code == -1
+
+
+def test_kernel_table_argument_checks_without_gpu():
+    import numpy as np
+    from paper_1703_06999_gb300 import binding as B
+    h = B.vdwgb_new(B.DF1)
+    try:
+        tab = np.zeros((210, 1024))
+        B.vdwgb_set_kernel_k(h, tab)                   # accepted before init
+        tab[3, 7] = np.nan
+        with pytest.raises(B.VdwgbError) as ei:
+            B.vdwgb_set_kernel_k(h, tab)
+        assert ei.value.code == -1
+        B.vdwgb_set_kernel_k(h, None)                  # back to the vdW-DF table
+        with pytest.raises(ValueError):
+            B.vdwgb_set_kernel_k(h, np.zeros(10))
+    finally:
+        B.vdwgb_finalize(h)
