@@ -70,9 +70,10 @@ def test_caller_kernel_matches_oracle(name, prec, oracle_default):
     assert res[0] == again[0]
     ref = vdw.Oracle(vdw.Params(), phik=tab).energy_potential(s.n.numpy(), s.sigma.numpy(), s.cell, s.functional)
     _check(res, ref, prec)
-    if name == "gaussian":
-        # partition of unity: every F_a is the same convolution, so dE/dsigma vanishes
-        assert np.max(np.abs(res[2])) <= 1e-5 * np.max(np.abs(res[1])) + 1e-12
+    if name == "gaussian" and prec == 0:
+        # partition of unity: every F_a is the same convolution, so dE/dsigma
+        # vanishes (in FP32 its rounding residual scales with dq0/dsigma)
+        assert np.max(np.abs(res[2])) <= 1e-10 * np.max(np.abs(res[1]))
 
 
 def test_kernel_table_rules(oracle_default):
