@@ -545,18 +545,36 @@ static EncodeTiledFn encode_tiled() {
     return fn;
 }
 
+// Rows per tensor copy of a tile of n rows and W kz-columns: n itself up to
+// 256 (one copy), else the largest divisor of n <= 256 whose copies land at
+// 128-byte aligned offsets of the tile buffer (rows x W x 20 x 8 bytes), at
+// most 16 copies; 0: none (row-by-row copies).
+static int tile_box_rows(int n, int W) {
+    if (n <= 256) return n;
+    for (int k = 2; k <= 16; ++k) {
+        if (n % k) continue;
+        const int b = n / k;
+        if (b <= 256 && (b * W) % 4 == 0) return b;
+    }
+    return 0;
+}
+
 // both maps of a handle's current plan; false if a box does not fit the
-// tensor-copy limits (each box side <= 256) or no encoder is available
-static bool encode_xy_maps(const SysDev &S, CUtensorMap maps[2]) {
+// tensor-copy limits (each box side <= 256) or no encoder is available.
+// by / bx: rows per copy of a y / x tile
+static bool encode_xy_maps(const SysDev &S, CUtensorMap maps[2], int &by, int &bx) {
     EncodeTiledFn enc = encode_tiled();
     if (!enc || !S.spec) return false;
     const int nzh = S.nzh;
-    if (S.nx > 256 || S.ny > 256 || S.Wy * NQ > 256 || S.Wx * NQ > 256) return false;
+    if (S.Wy * NQ > 256 || S.Wx * NQ > 256) return false;
+    by = tile_box_rows(S.ny, S.Wy);
+    bx = tile_box_rows(S.nx, S.Wx);
+    if (!by || !bx) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)nzh * NQ, (cuuint64_t)S.ny, (cuuint64_t)S.nx};
     const cuuint64_t strides[2] = {(cuuint64_t)nzh * NQ * 8, (cuuint64_t)S.ny * nzh * NQ * 8};
     const cuuint32_t one[3] = {1, 1, 1};
-    const cuuint32_t box_y[3] = {(cuuint32_t)(S.Wy * NQ), (cuuint32_t)S.ny, 1};
-    const cuuint32_t box_x[3] = {(cuuint32_t)(S.Wx * NQ), 1, (cuuint32_t)S.nx};
+    const cuuint32_t box_y[3] = {(cuuint32_t)(S.Wy * NQ), (cuuint32_t)by, 1};
+    const cuuint32_t box_x[3] = {(cuuint32_t)(S.Wx * NQ), 1, (cuuint32_t)bx};
     for (int m = 0; m < 2; ++m) {
         const CUresult r = enc(&maps[m], CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, S.spec, dims, strides,
                                m == 0 ? box_y : box_x, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -572,12 +590,16 @@ static bool encode_xy_maps(const SysDev &S, CUtensorMap maps[2]) {
 static int upload_maps(vdwgb_data *h, bool sync) {
     SysDev &S = h->hsys;
     S.tmap = nullptr;
+    S.tby = S.tbx = 0;
     if (!h->tmap) return 0;
     alignas(64) CUtensorMap maps[2];
-    if (!encode_xy_maps(S, maps)) return 0;
+    int by = 0, bx = 0;
+    if (!encode_xy_maps(S, maps, by, bx)) return 0;
     if (sync) CK(cudaMemcpy(h->tmap, maps, sizeof maps, cudaMemcpyHostToDevice), "tensor maps");
     else CK(dupload(h, h->tmap, maps, sizeof maps), "tensor maps");
     S.tmap = h->tmap;
+    S.tby = by;
+    S.tbx = bx;
     return 0;
 }
 

@@ -126,6 +126,7 @@ struct SysDev {
                      // the k-space half of a slab decomposition); 0 and ny otherwise
     const unsigned short *kord;   // per (kz, rank): local k-point indices sorted by table interval
     const void *tmap;    // FP32: two tensor maps of spec (y-pass tile box, x-pass tile box), else null
+    int tby, tbx;        // rows per tensor copy of a y / x tile (a divisor of ny / nx, <= 256)
     double *energy;  // output (device)
     int *err;        // device status flag (and detail word) of the device
 };

@@ -709,13 +709,18 @@ __device__ __forceinline__ void xy_issue(const SysDev *__restrict__ sys, const i
     }
     fence_proxy_async();
     if (S.tmap) {
-        // the whole tile in one tensor copy (box W 20 x rows; columns past
-        // the last kz are filled with zeros and never stored back)
+        // the tile in tensor copies of `nb` rows each (box W 20 x nb; one copy
+        // up to 256 rows; columns past the last kz are filled with zeros and
+        // never stored back)
         if (lane == 0) {
             const void *map = static_cast<const unsigned char *>(S.tmap) + (XPASS ? 128 : 0);
+            int nb = XPASS ? S.tbx : S.tby;
+            if (nb < 1 || g.nrows % nb) nb = g.nrows;   // never: the plan divides the rows
             fence_tensormap(map);
             mbar_expect_tx(bar, (unsigned)((size_t)g.ldr * g.nrows * sizeof(cx<T>)));
-            tma_load_3d(buf, map, g.kz0 * NQ, XPASS ? g.outer : 0, XPASS ? 0 : g.outer, bar);
+            for (int r0 = 0; r0 < g.nrows; r0 += nb)
+                tma_load_3d(buf + (size_t)r0 * g.ldr, map, g.kz0 * NQ, XPASS ? g.outer : r0, XPASS ? r0 : g.outer,
+                            bar);
         }
         return;
     }

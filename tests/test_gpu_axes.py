@@ -157,6 +157,22 @@ def test_axis_640_fp32_and_fp64_limit(oracle_default, axis):
     assert ei.value.code == -1
 
 
+@pytest.mark.parametrize("axis", [0, 1])
+@pytest.mark.parametrize("n", [300, 448])
+def test_axes_above_256_points_in_several_tensor_copies(oracle_default, n, axis):
+    # x / y tiles longer than the 256 rows of one tensor copy go in several
+    # copies of a divisor of the axis (300: 100 or 150 rows, 448: 224), each
+    # landing at an aligned offset of the tile buffer
+    s = _thin(n, axis)
+    sn, sg = s.n.numpy(), s.sigma.numpy()
+    ref = oracle_default.energy_potential(sn, sg, s.cell, s.functional)
+    f = B.Functional(s.shape, s.cell, s.functional, B.FP32_MIXED)
+    try:
+        _check(f.calculate(sn, sg), ref, B.FP32_MIXED)
+    finally:
+        f.close()
+
+
 def _shell160():
     """A ligand-shell-like density on 160^3 points in a 27.4 bohr cell (one
     quarter of the paper's (58 Angstrom)^3 box along each axis)."""
