@@ -242,6 +242,15 @@ static void tile_caps(int device, int prec, size_t &xy, size_t &z) {
     z = env[1] ? env[1] : (f32 ? sm / 3 - 1824 : (size_t)-1);
 }
 
+// The z cap for one z stage (0 forward, 3 inverse) of an axis of nz points:
+// where it would leave tiles of a single line (long axes: 640 points take
+// about 100 KB per two lines), tiles of one line cost more than the lost
+// occupancy, and the stage keeps the uncapped limit.
+static size_t z_stage_cap(int stage, int prec, int nz, size_t zcap, size_t lim) {
+    return stage_smem(stage, prec, nz, 2) <= zcap ? std::min(zcap, lim) : lim;
+}
+
+
 static int best_w(int prec, int n, int nzh, int slots, size_t budget) {
     int W = 1;
     for (int w = 8; w >= 1; --w)
@@ -253,13 +262,15 @@ static int best_w(int prec, int n, int nzh, int slots, size_t budget) {
 // buffer on axes without an in-place transform (workx / worky)
 static void choose_tiles(int prec, int nx, int ny, int nz, int nzh, size_t lim, size_t xycap, size_t zcap,
                          int workx, int worky, int &LZ, int &LZi, int &Wy, int &Wx, int &nbuf) {
-    const size_t zbudget = std::min(TILE_BUDGET, zcap), xybudget = std::min(TILE_BUDGET, xycap);
+    const size_t xybudget = std::min(TILE_BUDGET, xycap);
+    const size_t zb0 = std::min(TILE_BUDGET, z_stage_cap(0, prec, nz, zcap, lim));
+    const size_t zb3 = std::min(TILE_BUDGET, z_stage_cap(3, prec, nz, zcap, lim));
     LZ = 1;
     for (int l = 16; l >= 1; --l)
-        if (stage_smem(0, prec, nz, l) <= zbudget) { LZ = l; break; }
+        if (stage_smem(0, prec, nz, l) <= zb0) { LZ = l; break; }
     LZi = 1;
     for (int l = 16; l >= 1; --l)
-        if (stage_smem(3, prec, nz, l) <= zbudget) { LZi = l; break; }
+        if (stage_smem(3, prec, nz, l) <= zb3) { LZi = l; break; }
     if (LZi > nx * ny) LZi = nx * ny;
     if (LZ > nx * ny) LZ = nx * ny;
     nbuf = 2;
@@ -691,7 +702,8 @@ static int apply_tuned(vdwgb_data *h) {
     const size_t lim = g_dev[h->device].maxsmem - 1024;
     size_t xycap, zcap;
     tile_caps(h->device, prec, xycap, zcap);
-    const size_t limxy = std::min(lim, xycap), limz = std::min(lim, zcap);
+    const size_t limxy = std::min(lim, xycap);
+    const size_t limz0 = z_stage_cap(0, prec, S.nz, zcap, lim), limz3 = z_stage_cap(3, prec, S.nz, zcap, lim);
     std::vector<double> host(2 * N, 0.0);
     for (size_t i = 0; i < N; ++i) host[i] = 0.01;
     double *tmp = nullptr;
@@ -719,7 +731,7 @@ static int apply_tuned(vdwgb_data *h) {
             if ((pass == 0 || pass == 3) && ci >= 8) break;
             TuneVal v = best;
             if (pass == 0) {
-                if (c > S.nx * S.ny || stage_smem(0, prec, S.nz, c) > limz) continue;
+                if (c > S.nx * S.ny || stage_smem(0, prec, S.nz, c) > limz0) continue;
                 v.LZ = c;
             } else if (pass == 1) {
                 if (c > S.nzh || stage_smem(1, prec, S.ny, c, nb + (S.sy1 ? 0 : 1)) > limxy) continue;
@@ -730,7 +742,7 @@ static int apply_tuned(vdwgb_data *h) {
                 v.Wx = c;
                 v.nbx = nb;
             } else {
-                if (c > S.nx * S.ny || stage_smem(3, prec, S.nz, c) > limz) continue;
+                if (c > S.nx * S.ny || stage_smem(3, prec, S.nz, c) > limz3) continue;
                 v.LZi = c;
             }
             set_tiles(h, v.LZ, v.LZi, v.Wy, v.Wx, v.nby, v.nbx);
