@@ -1397,7 +1397,7 @@ static int batch_parts(vdwgb_data *const *hs, int count, int *start) {
 }  // extern "C"
 
 int vdwgb::batch_launchset(vdwgb_data *const *hs, int count, SysDev *hdesc, int *pre, const SysDev *ddesc,
-                           const int *dprefix, LaunchSet &L, bool shared) {
+                           const int *dprefix, LaunchSet &L) {
     std::memset(&L, 0, sizeof L);
     for (int s = 0; s < NKIND; ++s) pre[s * (count + 1)] = 0;   // the caller's array may hold an older launch
     const int device = hs[0]->device;
@@ -1439,14 +1439,7 @@ int vdwgb::batch_launchset(vdwgb_data *const *hs, int count, SysDev *hdesc, int 
     for (int s = 0; s < NKIND; ++s) {
         L.prefix[s] = dprefix + s * (count + 1);
         L.total[s] = pre[s * (count + 1) + count];
-        int bps = stage_blocks_per_sm(s, prec, L.smem[s]);
-        // shared: z passes (instruction- and latency-bound) at two thirds of
-        // their blocks per SM, x / y passes (bandwidth-bound) at half, so that
-        // launches of concurrent parts mix on an SM (64 uneven grids: 8.04 ->
-        // 7.78 ms per step); the contraction fills its SM alone either way
-        if (shared && (s == 0 || s == 3)) bps = std::max(1, (2 * bps + 1) / 3);
-        if (shared && (s == 1 || s == 2)) bps = std::max(1, (bps + 1) / 2);
-        const int cap = di.sms * bps;
+        const int cap = di.sms * stage_blocks_per_sm(s, prec, L.smem[s]);
         L.grid[s] = L.total[s] < cap ? L.total[s] : cap;
     }
     // plane kernel: one cluster size per launch; grid in clusters
@@ -1508,7 +1501,7 @@ int vdwgb_batch_new(vdwgb_handle *handles, int count, vdwgb_batch *out) {
         if (e != cudaSuccess) rc = cuda_fail(e, "batch setup");
         for (int p = 0; p < np && rc == 0; ++p)
             rc = batch_launchset(handles + ps[p], ps[p + 1] - ps[p], b->host.data() + ps[p], p2.data() + off[p],
-                                 b->dsys + ps[p], b->dprefix2 + off[p], b->part[p], true);
+                                 b->dsys + ps[p], b->dprefix2 + off[p], b->part[p]);
         if (rc == 0) {
             e = cudaMemcpy(b->dprefix2, p2.data(), off[np] * sizeof(int), cudaMemcpyHostToDevice);
             if (e != cudaSuccess) rc = cuda_fail(e, "batch setup");

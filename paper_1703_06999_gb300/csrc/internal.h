@@ -83,11 +83,8 @@ int device_sms(int device);
 size_t handle_io_bytes(const vdwgb_data *h);
 // launch set over n handles: fills hdesc[n] (copies of the handles'
 // descriptors; the caller sets I/O pointers), hprefix[NKIND * (n + 1)] and L,
-// whose device pointers are ddesc / dprefix (filled by the caller's copy).
-// shared: the launches run beside other launch sets' (batch parts as graph
-// branches, server batches in flight), and their persistent grids leave
-// room on each SM for a block of another launch
+// whose device pointers are ddesc / dprefix (filled by the caller's copy)
 int batch_launchset(vdwgb_data *const *hs, int n, SysDev *hdesc, int *hprefix, const SysDev *ddesc,
-                    const int *dprefix, LaunchSet &L, bool shared = false);
+                    const int *dprefix, LaunchSet &L);
 
 }  // namespace vdwgb

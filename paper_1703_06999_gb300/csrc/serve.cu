@@ -237,8 +237,7 @@ static void dispatcher_loop(vdwgb_server_s *s) {
         std::vector<vdwgb_data *> hs(n);
         for (int i = 0; i < n; ++i) hs[i] = batch[i]->h;
         LaunchSet L;
-        int rc = batch_launchset(hs.data(), n, slot->hdesc, slot->hpre, slot->ddesc, slot->dpre, L,
-                                 s->max_inflight > 1);
+        int rc = batch_launchset(hs.data(), n, slot->hdesc, slot->hpre, slot->ddesc, slot->dpre, L);
         cudaError_t e = cudaSuccess;
         if (!rc) {
             for (int i = 0; i < n; ++i) {
