@@ -1,9 +1,11 @@
 """GPU: the bounds-checked build (VDWGB_CHECK_BOUNDS) runs the parity cases
 clean.  The checked library is built here (a minute or two) and exercised in
 a child process with VDWGB_CHECKED=1: single evaluations on split, unsplit,
-odd and triclinic grids in both precisions, a batch in parts, the server and
-the allocation-free entry point, each compared with the oracle and followed
-by a clean device status (no access was skipped)."""
+odd and triclinic grids in both precisions, a batch in parts, the server,
+the allocation-free entry point, the spin-polarised form, two slab ranks, a
+caller's kernel table and a 300-point axis, each compared with the oracle
+(or one plan) and followed by a clean device status (no access was
+skipped)."""
 import os
 import subprocess
 import sys
@@ -58,6 +60,69 @@ out = torch.empty_like(n)
 en = torch.zeros(1, dtype=torch.float64, device="cuda")
 B.vdwgb_calculate_noalloc(0, s.functional, s.shape, s.cell, n, sg, out, torch.empty_like(n), en, 0)
 torch.cuda.synchronize()
+B.vdwgb_device_status(0)
+# spin-polarised form, both precisions, against the spin oracle
+from oracle import spin as ospin
+s = systems[1]
+arrs = [x.numpy() for x in inputs.spin_split(s, 0.6, seed=2, empty_down_slab=True)]
+sref = ospin.energy_potential_spin(o, *arrs, s.cell, s.functional)
+for prec in (0, 1):
+    f = B.Functional(s.shape, s.cell, s.functional, prec)
+    e, dn, ds = f.calculate_spin(*arrs)
+    f.close()
+    assert abs(e - sref[0]) <= tol[prec][0] * max(1.0, abs(sref[0])), (prec, e, sref[0])
+    B.vdwgb_device_status(0)
+# slab decomposition over two virtual ranks: potentials equal one plan
+from paper_1703_06999_gb300.slab import LibraryStages
+s = systems[0]
+st = LibraryStages(0)
+P, nxl = 2, s.shape[0] // 2
+nb = st.slab_bytes(s.shape, P, 1)
+part = nb // P
+R = []
+for r in range(P):
+    a, b, x = st.buffer(nb), st.buffer(nb), st.buffer(nb)
+    R.append(dict(h=st.new(s.functional, s.shape, s.cell, P, r, 1, a, b), a=a, b=b, x=x, e=st.energy_buffer(),
+                  dn=torch.empty((nxl,) + s.shape[1:], dtype=torch.float64, device="cuda"),
+                  ds=torch.empty((nxl,) + s.shape[1:], dtype=torch.float64, device="cuda")))
+for r, Rr in enumerate(R):
+    st.forward(Rr["h"], n[r * nxl:(r + 1) * nxl].contiguous(), sg[r * nxl:(r + 1) * nxl].contiguous())
+    st.pack(Rr["h"], Rr["x"])
+for r, Rr in enumerate(R):
+    for q, Rq in enumerate(R):
+        Rr["b"][q * part:(q + 1) * part].copy_(Rq["x"][r * part:(r + 1) * part])
+for Rr in R:
+    st.contract(Rr["h"], Rr["e"])
+for r, Rr in enumerate(R):
+    for q, Rq in enumerate(R):
+        Rr["x"][q * part:(q + 1) * part].copy_(Rq["b"][r * part:(r + 1) * part])
+for Rr in R:
+    st.unpack(Rr["h"], Rr["x"])
+    st.inverse(Rr["h"], Rr["dn"], Rr["ds"])
+torch.cuda.synchronize()
+B.vdwgb_device_status(0)
+f = B.Functional(s.shape, s.cell, s.functional, 1)
+e1, dn1, ds1 = f.calculate(s.n.numpy(), s.sigma.numpy())
+f.close()
+assert np.array_equal(torch.cat([Rr["dn"] for Rr in R]).cpu().numpy(), dn1)
+for Rr in R:
+    st.free(Rr["h"])
+# a caller's kernel table and a 300-point axis (several tensor copies per tile)
+k = vdw.k_grid(vdw.Params())
+gauss = np.tile(np.exp(-0.5 * k * k), (210, 1))
+s = systems[2]
+f = B.Functional(s.shape, s.cell, s.functional, 1, kernel_k=gauss)
+e, dn, ds = f.calculate(s.n.numpy(), s.sigma.numpy())
+f.close()
+gref = vdw.Oracle(vdw.Params(), phik=gauss).energy_potential(s.n.numpy(), s.sigma.numpy(), s.cell, s.functional)
+assert abs(e - gref.energy) <= 1e-6 * max(1.0, abs(gref.energy))
+B.vdwgb_device_status(0)
+s = inputs.make_system((300, 6, 8), np.diag([60.0, 3.0, 4.0]), [(3.0, 1.5, (20.0, 1.5, 2.0))], 1)
+lref = o.energy_potential(s.n.numpy(), s.sigma.numpy(), s.cell, s.functional)
+f = B.Functional(s.shape, s.cell, s.functional, 1)
+e, dn, ds = f.calculate(s.n.numpy(), s.sigma.numpy())
+f.close()
+assert abs(e - lref.energy) <= 1e-6 * max(1.0, abs(lref.energy))
 B.vdwgb_device_status(0)
 print("checked build clean")
 '''
