@@ -211,8 +211,9 @@ int vdwgb_phi(int device, int npts, const double *d1, const double *d2, double *
 /* q0(n, sigma) and its partial derivatives (appendix, q0 with PW92
  * correlation and the saturation h_5) exactly as the given precision form
  * evaluates them inside vdwgb_calculate (FP64 values either way; the
- * FP32-mixed form evaluates q0 in double-float arithmetic, pairs of FP32
- * with about 46 significant bits, and forms the derivatives in FP32).  Host
+ * FP32-mixed form evaluates q0 and its derivatives in double-float
+ * arithmetic, pairs of FP32 with about 46 significant bits, and rounds the
+ * derivatives to FP32).  Host
  * arrays of npts doubles. */
 int vdwgb_q0(int device, int precision, int functional, int npts, const double *n, const double *sigma,
              double *q0, double *dq0dn, double *dq0dsigma);
