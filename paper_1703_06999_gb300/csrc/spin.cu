@@ -22,6 +22,7 @@
 
 #include "internal.h"
 #include "table.h"
+#include "dfmath.cuh"
 
 using namespace vdwgb;
 
@@ -138,6 +139,126 @@ __global__ void k_spin_q0(SpinArgs a) {
     }
 }
 
+// PW92's G for one parameter set in double-float: gp = -G > 0 and dG/dr_s
+__device__ __forceinline__ void pw92_G_df(const double *P, dfl rs, dfl srs, dfl isrs, const float4 *lnt, dfl &gp,
+                                          dfl &dg) {
+    const double A2 = 2.0 * P[0], a1 = P[1], b1 = P[2], b2 = P[3], b3 = P[4], b4 = P[5];
+    dfl poly = df_add_pos(df_mul(DF(b4), srs), DF(b3));
+    poly = df_add_pos(df_mul(poly, srs), DF(b2));
+    poly = df_add_pos(df_mul(poly, srs), DF(b1));
+    const dfl D = df_mul(df_mul(poly, srs), DF(A2));       // 2A (b1 rs^1/2 + b2 rs + b3 rs^3/2 + b4 rs^2)
+    dfl dD = df_add_pos(df_mul(DF(0.5 * b1), isrs), DF(b2));
+    dD = df_add_pos(dD, df_mul(srs, df_add_pos(DF(1.5 * b3), df_mul(DF(2.0 * b4), srs))));
+    dD = df_mul(dD, DF(A2));
+    const dfl iD = df_rcp_fast(D);
+    const dfl L = df_log1p(iD, lnt);
+    const dfl ar = df_add_pos(DF(1.0), df_mul(DF(a1), rs));
+    gp = df_mul(df_mul(DF(A2), ar), L);
+    dg = df_sub(df_mul(df_mul(DF(A2), ar), df_mul(dD, df_rcp_fast(df_add_pos(D, df_mul(D, D))))),
+                df_mul(DF(A2 * a1), L));
+}
+
+// The same q0 and derivatives in double-float arithmetic (about 46 bits),
+// the FP32-mixed form's counterpart of the FP64 kernel above (the FP64 pipe
+// runs at 1/64 of the FP32 rate); the derivatives are rounded to FP32 by
+// the saturation slope h'(x), as in the plain form
+__global__ void k_spin_q0_df(SpinArgs a) {
+    __shared__ float4 lnt[64];
+    __shared__ float2 ex2[64];
+    load_df_tables(lnt, ex2);
+    __syncthreads();
+    const double P0[6] = {0.031091, 0.2137, 7.5957, 3.5876, 1.6382, 0.49294};
+    const double P1[6] = {0.015545, 0.20548, 14.1189, 6.1977, 3.3662, 0.62517};
+    const double PA[6] = {0.016887, 0.11125, 10.357, 3.6231, 0.88026, 0.49671};
+    const double PI = 3.14159265358979323846;
+    const dfl IFZ20 = DF(1.0 / 1.709921), IFDEN = DF(1.0 / 0.51984209978974632953);
+    const dfl KC = DF(4.0 * PI / 3.0);
+    const dfl zc = df_from(-a.c);                          // -Z_ab / 36 > 0
+    const float qcut = (float)a.q_cut;
+    const dfl iqcut = df_from(1.0 / a.q_cut);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += (size_t)gridDim.x * blockDim.x) {
+        const double nu = a.nu[i] > 0.0 ? a.nu[i] : 0.0, nd = a.nd[i] > 0.0 ? a.nd[i] : 0.0;
+        const double su = a.su[i] > 0.0 ? a.su[i] : 0.0, sd = a.sd[i] > 0.0 ? a.sd[i] : 0.0;
+        const double n = nu + nd;
+        double q0 = a.q_min, d[4] = {0.0, 0.0, 0.0, 0.0};
+        if (n > a.n_min) {
+            const dfl nD = df_from_bits(n);
+            const dfl inv_n = df_rcp_fast(nD);
+            const dfl kF = df_cbrt(df_mul(nD, DF(3.0 * PI * PI)));
+            const dfl ikF = df_rcp_fast(kF);
+            const double ns2[2] = {nu, nd}, ss2[2] = {su, sd};
+            dfl kk[2] = {DF(0.0), DF(0.0)};
+            // exchange of each channel (spin scaling); a channel at or below
+            // n_min contributes nothing
+            dfl x = DF(0.0), own[2] = {DF(0.0), DF(0.0)}, oth[2] = {DF(0.0), DF(0.0)}, sig[2] = {DF(0.0), DF(0.0)};
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const double ns = ns2[s];
+                if (ns > 0.0) kk[s] = df_cbrt(df_mul(df_from_bits(ns), DF(6.0 * PI * PI)));
+                if (ns > a.n_min) {
+                    const dfl nsD = df_from_bits(ns);
+                    const dfl as = df_mul(nsD, kk[s]);
+                    const dfl ia = df_rcp_fast(as);
+                    const dfl gp = df_mul(df_mul(df_mul(zc, df_from_bits(ss2[s])), inv_n), ia);   // -(Z/36) s / (n a)
+                    const dfl asn = df_mul(as, inv_n);
+                    x = df_add_pos(x, df_add_pos(asn, gp));
+                    const dfl asn2 = df_mul(asn, inv_n);
+                    const dfl t1 = df_mul(DF(4.0 / 3.0), df_mul(kk[s], inv_n));
+                    const dfl t3 = df_mul(gp, df_add_pos(inv_n, df_mul(DF(4.0 / 3.0), df_mul(kk[s], ia))));
+                    own[s] = df_sub(df_sub(t1, asn2), t3);
+                    oth[s] = df_neg(df_add_pos(asn2, df_mul(gp, inv_n)));
+                    sig[s] = df_mul(df_mul(zc, inv_n), ia);
+                }
+            }
+            dfl zeta = df_mul(df_sub(df_from_bits(nu), df_from_bits(nd)), inv_n);
+            if (zeta.hi >= 1.f) zeta = DF(1.0);
+            if (zeta.hi <= -1.f) zeta = DF(-1.0);
+            const dfl rs = df_mul(ikF, DF(1.9191582926775128));   // (9 pi / 4)^(1/3) / k_F
+            const dfl srs = df_sqrt(rs);
+            const dfl isrs = df_rcp_fast(srs);
+            dfl g0, dg0, g1, dg1, gA, dgA;                         // g = -G
+            pw92_G_df(P0, rs, srs, isrs, lnt, g0, dg0);
+            pw92_G_df(P1, rs, srs, isrs, lnt, g1, dg1);
+            pw92_G_df(PA, rs, srs, isrs, lnt, gA, dgA);
+            const dfl up = df_mul(kk[0], ikF), dn = df_mul(kk[1], ikF);   // (1 +- zeta)^(1/3)
+            const dfl one_p = df_add(DF(1.0), zeta), one_m = df_sub(DF(1.0), zeta);
+            const dfl f = df_mul(df_sub(df_add(df_mul(one_p, up), df_mul(one_m, dn)), DF(2.0)), IFDEN);
+            const dfl fd = df_mul(df_mul(DF(4.0 / 3.0), df_sub(up, dn)), IFDEN);
+            const dfl z3 = df_mul(df_mul(zeta, zeta), zeta), z4 = df_mul(z3, zeta);
+            const dfl w1 = df_mul(df_mul(f, IFZ20), df_sub(DF(1.0), z4));   // f (1 - z^4) / f''(0)
+            const dfl w2 = df_mul(f, z4);
+            // -eps = g0 - gA w1 - (g0 - g1) w2   (G = -g; alpha_c = g_A)
+            const dfl g01 = df_sub(g0, g1);
+            const dfl meps = df_sub(df_sub(g0, df_mul(gA, w1)), df_mul(g01, w2));
+            const dfl deps_rs = df_add(df_sub(dg0, df_mul(dgA, w1)), df_mul(df_sub(dg1, dg0), w2));
+            const dfl four_z3f = df_mul(DF(4.0), df_mul(z3, f));
+            // deps/dzeta = g_A (fd (1 - z^4) - 4 z^3 f) / f''(0) - (g1 - g0) ... with G = -g:
+            // -G_A (...) / f''(0) + (G1 - G0)(fd z^4 + 4 z^3 f) = g_A (...) / f''(0) + (g0 - g1)(...)
+            const dfl deps_z = df_add(df_mul(df_mul(gA, IFZ20), df_sub(df_mul(fd, df_sub(DF(1.0), z4)), four_z3f)),
+                                      df_mul(g01, df_add(df_mul(fd, z4), four_z3f)));
+            const dfl qraw = df_add_pos(x, df_mul(KC, meps));
+            const dfl common = df_mul(df_mul(df_mul(KC, deps_rs), rs), df_mul(inv_n, DF(1.0 / 3.0)));
+            const dfl zt = df_mul(df_mul(KC, deps_z), inv_n);
+            const dfl dq_u = df_sub(df_add(df_add(own[0], oth[1]), common), df_mul(zt, one_m));
+            const dfl dq_d = df_add(df_add(df_add(own[1], oth[0]), common), df_mul(zt, one_p));
+            float dh = 0.f;
+            const dfl q = df_saturate(df_mul(qraw, iqcut), qcut, ex2, dh);
+            const double qd = df_to(q);
+            if (qd >= a.q_min) {
+                q0 = qd;
+                d[0] = (double)dh * df_to(dq_u);
+                d[1] = (double)dh * df_to(dq_d);
+                d[2] = (double)dh * df_to(sig[0]);
+                d[3] = (double)dh * df_to(sig[1]);
+            }
+        }
+        a.ntot[i] = n;
+        a.q0[i] = q0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) a.dq[c * a.N + i] = d[c];
+    }
+}
+
 __global__ void k_spin_finish(const double *__restrict__ S0, const double *__restrict__ S1,
                               const double *__restrict__ dq, size_t N, double *__restrict__ onu,
                               double *__restrict__ ond, double *__restrict__ osu, double *__restrict__ osd) {
@@ -191,7 +312,8 @@ int vdwgb_calculate_spin_device(vdwgb_handle h, const double *d_rho_up, const do
     SpinArgs a{d_rho_up, d_rho_dn, d_sigma_upup, d_sigma_dndn, ntot, q0, dq, N, h->hsys.Z / 36.0,
                qm.n_min, qm.q_min, qm.q_cut};
     const unsigned grid = spin_grid(h->device, N);
-    k_spin_q0<<<grid, 256, 0, st>>>(a);
+    if (h->prec == VDWGB_FP32_MIXED) k_spin_q0_df<<<grid, 256, 0, st>>>(a);
+    else k_spin_q0<<<grid, 256, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "spin q0");
     // the pipeline reads n and q0 and leaves S0 in n's array, S1 in q0's
     h->hsys.q0in = 1;
