@@ -133,9 +133,10 @@ int vdwgb_calculate_device(vdwgb_handle h, const double *d_rho, const double *d_
  * grad n_up . grad n_dn), [nx][ny][nz] as above.  theta uses the total
  * density n_up + n_dn with the same kernel; q0 takes spin-scaled exchange
  * (each channel with the gradient correction of its doubled density) and
- * PW92 correlation with its spin interpolation, formed in FP64 in either
- * precision.  Outputs, OVERWRITTEN, per unit volume: dE/dn_up, dE/dn_dn,
- * dE/dsigma_upup, dE/dsigma_dndn, and the energy.  n_s < 0 and sigma_ss < 0
+ * PW92 correlation with its spin interpolation, formed in FP64 (FP64 form)
+ * or double-float, about 46 bits (FP32-mixed form).  Outputs, OVERWRITTEN,
+ * per unit volume: dE/dn_up, dE/dn_dn, dE/dsigma_upup, dE/dsigma_dndn, and
+ * the energy.  n_s < 0 and sigma_ss < 0
  * count as 0; points with n_up + n_dn <= 1e-12 give zero outputs; a channel
  * with n_s <= 1e-12 has no exchange term.  The handle allocates 48 bytes
  * per grid point at the first call (64 more for the host form's staging).

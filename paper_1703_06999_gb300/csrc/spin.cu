@@ -10,7 +10,9 @@
 //     eps_c = eps_0 + alpha_c f(zeta) / f''(0) (1 - zeta^4) + (eps_1 - eps_0) f(zeta) zeta^4.
 //
 // On the device:
-//   k_spin_q0      (FP64) n, q0 and dq0/d{n_up, n_dn, sigma_upup, sigma_dndn}
+//   k_spin_q0      n, q0 and dq0/d{n_up, n_dn, sigma_upup, sigma_dndn} in FP64
+//                  (FP64 form); k_spin_q0_df the same in double-float
+//                  (FP32-mixed form)
 //   the pipeline   with the descriptor's q0in set: the z-forward pass takes
 //                  q0 as given, the z-inverse pass leaves the two potential
 //                  sums S0 = sum_a F_a p_a and S1 = n sum_a F_a p'_a in place
