@@ -1357,7 +1357,7 @@ struct vdwgb_batch_s {
     LaunchSet part[MAXPARTS];
     int *dprefix2 = nullptr;
     cudaStream_t capp[MAXPARTS] = {};                  // capture streams of parts 1.. (part 0: cap)
-    cudaStream_t hst[MAXPARTS] = {};                   // host-pointer path streams of parts 1.. (part 0: own)
+    cudaStream_t hst[MAXPARTS] = {};                   // host-pointer path: one stream per part
     cudaGraph_t hgraph[MAXPARTS] = {};                 // host-pointer path: one stage chain per part
     cudaGraphExec_t hexec[MAXPARTS] = {};
     double *h_energy = nullptr;                        // pinned staging of the energies (the caller's
@@ -1633,8 +1633,17 @@ int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double 
         // each part on its own stream: its copies in, its stage graph, its
         // copies out; the copies of one part overlap the kernels of the others
         const int np = b->nparts;
-        for (int p = 1; p < np; ++p)
-            if (!b->hst[p]) CK(cudaStreamCreateWithFlags(&b->hst[p], cudaStreamNonBlocking), "stream");
+        if (!b->hst[np - 1]) {
+            // part p at the p-th highest priority: earlier parts get their
+            // blocks first and finish first, so their downloads overlap the
+            // kernels of the later parts
+            int least = 0, greatest = 0;
+            CK(cudaDeviceGetStreamPriorityRange(&least, &greatest), "priority range");
+            for (int p = 0; p < np; ++p) {
+                const int pr = std::max(greatest, std::min(least, greatest + p));
+                if (!b->hst[p]) CK(cudaStreamCreateWithPriority(&b->hst[p], cudaStreamNonBlocking, pr), "stream");
+            }
+        }
         if (!b->h_energy) CK(cudaMallocHost(&b->h_energy, n * sizeof(double)), "pinned energies");
         for (int p = 0; p < np; ++p) {
             if (b->hexec[p]) continue;
@@ -1667,7 +1676,7 @@ int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double 
             for (auto &q : b->last) q = nullptr;   // the graph path re-uploads its own pointers
         }
         for (int p = 0; p < np; ++p) {
-            cudaStream_t st = p ? b->hst[p] : b->own;
+            cudaStream_t st = b->hst[p];
             const int lo = b->pstart[p], hi = b->pstart[p + 1];
             for (int i = lo; i < hi; ++i) {
                 const size_t N = (size_t)b->hs[i]->nx * b->hs[i]->ny * b->hs[i]->nz;
@@ -1688,7 +1697,7 @@ int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double 
                                st),
                "copy energy");
         }
-        for (int p = 0; p < np; ++p) CK(cudaStreamSynchronize(p ? b->hst[p] : b->own), "synchronize");
+        for (int p = 0; p < np; ++p) CK(cudaStreamSynchronize(b->hst[p]), "synchronize");
         std::memcpy(energy, b->h_energy, n * sizeof(double));
         return vdwgb_device_status(b->device);
     }
