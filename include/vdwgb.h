@@ -298,8 +298,10 @@ int vdwgb_batch_calculate_device(vdwgb_batch b, const double *const *d_rho,
  * evaluates, copies dedrho, dedsigma and the `count` energies back, and waits.
  * Blocking.  A split batch (see vdwgb_batch_launches) runs each part as its
  * own copy-in / stages / copy-out chain on its own stream, so one part's
- * copies overlap the other parts' kernels; pinned host arrays let the copies
- * run asynchronously (pageable ones work, at the speed of staged copies). */
+ * copies overlap the other parts' kernels; the streams' priorities fall with
+ * the part index, so earlier parts finish first and their copies out overlap
+ * the later parts' kernels.  Pinned host arrays let the copies run
+ * asynchronously (pageable ones work, at the speed of staged copies). */
 int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double *const *sigma,
                           double *const *dedrho, double *const *dedsigma, double *energy);
 
@@ -308,7 +310,7 @@ int vdwgb_batch_calculate(vdwgb_batch b, const double *const *rho, const double 
  * whose stage chains are independent branches of the captured graph, so
  * their stages overlap; each part launches its own stages.  K comes from
  * VDWGB_BATCH_SPLIT in the environment when the batch is created (0 or 1:
- * one launch per stage for the whole batch; 2..4; default 4), capped by the
+ * one launch per stage for the whole batch; 2..8; default 6), capped by the
  * number of systems.  Results are the same either way. */
 int vdwgb_batch_launches(vdwgb_batch b);
 

@@ -1351,7 +1351,7 @@ struct vdwgb_batch_s {
     cudaStream_t own = nullptr;
     // the batch as parts (systems [pstart[p], pstart[p + 1])) whose stage
     // chains are independent branches (nparts = 0: one launch set for all)
-    static constexpr int MAXPARTS = 4;
+    static constexpr int MAXPARTS = 8;
     int nparts = 0;
     int pstart[MAXPARTS + 1] = {};
     LaunchSet part[MAXPARTS];
@@ -1365,14 +1365,15 @@ struct vdwgb_batch_s {
     cudaEvent_t cev[2 * MAXPARTS] = {};
 };
 
-// Parts of a batch: K = VDWGB_BATCH_SPLIT (0 or 1: none; 2..4; default 4:
-// measured on 8 x 96^3 systems, the kernels alone run alike with 2-4 parts,
-// and 4 parts leave the least copy time exposed in the host-array call)
+// Parts of a batch: K = VDWGB_BATCH_SPLIT (0 or 1: none; 2..8; default 6:
+// measured on 64 uneven grids, the captured graph runs alike with 4, 6 and 8
+// parts, and the host-array call leaves the least copy time exposed with 6,
+// one part per stream priority level of the GPU)
 // capped by the system count; boundary p at the system prefix whose grid
 // points come closest to p/K of the total (boundaries strictly increasing).
 // Returns the number of parts (0: no split) and fills start[0..parts].
 static int batch_parts(vdwgb_data *const *hs, int count, int *start) {
-    int K = vdwgb_batch_s::MAXPARTS;
+    int K = 6;
     {
         const char *e = std::getenv("VDWGB_BATCH_SPLIT");
         if (e && e[0] >= '0' && e[0] <= '9') K = e[0] - '0';
