@@ -277,13 +277,13 @@ CONTRACT_FMA2_PER_KPOINT = 315 + 400 + 20
 CONTRACT_FMA64_PER_KPOINT = 630 + 800 + 40
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of a stage over
-# the whole batch, per workload: the four part launches of one timed step of
+# the whole batch, per workload: the six part launches of one timed step of
 # a single-pass ncu capture of the benchmarked steps themselves (the launch
 # list summarised in the profiles directory).  An entry is removed when its
 # kernel changes.
 MEASURED_TRAFFIC = {
-    "uneven64": {"zfwd": 2732e6, "zinv": 2916e6, "contract": 4092e6, "yfwd": 4008e6, "xfwd": 4008e6,
-                 "xinv": 4008e6, "yinv": 4008e6},
+    "uneven64": {"zfwd": 2616e6, "zinv": 2904e6, "contract": 3979e6, "yfwd": 3880e6, "xfwd": 3880e6,
+                 "xinv": 3879e6, "yinv": 3880e6},
 }
 
 # Instruction-issue utilisation of the z-forward kernel (the q0 step in
@@ -897,7 +897,7 @@ def main():
     roof = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": hbm,
             "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
             "peak_source": pk_kind + " (copy bandwidth, MEASURED_PEAKS.json hbm_gbs)",
-            "traffic_source": ("single-pass ncu capture of the timed steps (four part launches per step)"
+            "traffic_source": ("single-pass ncu capture of the timed steps (six part launches per step)"
                                if traffic is not None
                                else "no capture of the current kernel on this workload"),
             "stage_timing": "each stage launched on its own between CUDA events (one launch over the whole "

@@ -5,7 +5,8 @@ host-array batch call (vdwgb_batch_calculate, parts pipelined on their own
 streams), the device-pointer call (captured graph, independent parts)
 and the unsplit batch (VDWGB_BATCH_SPLIT=0) must all reproduce each system's
 single evaluation exactly, in both precisions, on repeated calls and when
-the two paths alternate on one batch; with 2 and 4 parts."""
+the two paths alternate on one batch; with 2 and 4 parts, and with the
+default split (six parts of one or two systems)."""
 import os
 
 import numpy as np
@@ -30,14 +31,25 @@ def table():
     return B.vdwgb_kernel_table(0)
 
 
-@pytest.mark.parametrize("split", ["2", "4", "0"])
+def _seven_systems():
+    """Seven small systems: the default split cuts them into six parts of one
+    or two systems."""
+    return [inputs.small_cubic(10 + i, ngrid=(16, 20, 24)[i % 3], functional=1 + i % 2) for i in range(7)]
+
+
+@pytest.mark.parametrize("split,systems_of,parts", [("2", _systems, 2), ("4", _systems, 4), ("0", _systems, 1),
+                                                    (None, _seven_systems, 6)],
+                         ids=["split2", "split4", "unsplit", "default_split"])
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
-def test_batch_paths_match_single_evaluations(table, prec, split):
+def test_batch_paths_match_single_evaluations(table, prec, split, systems_of, parts):
     import torch
-    systems = _systems()
+    systems = systems_of()
     fs = [B.Functional(s.shape, s.cell, s.functional, prec) for s in systems]
     old = os.environ.get("VDWGB_BATCH_SPLIT")
-    os.environ["VDWGB_BATCH_SPLIT"] = split
+    if split is None:
+        os.environ.pop("VDWGB_BATCH_SPLIT", None)
+    else:
+        os.environ["VDWGB_BATCH_SPLIT"] = split
     bt = None
     try:
         alone = [f.calculate(s.n.numpy(), s.sigma.numpy()) for f, s in zip(fs, systems)]
@@ -70,7 +82,7 @@ def test_batch_paths_match_single_evaluations(table, prec, split):
         e = B.vdwgb_batch_calculate(bt, hn, hs, hdn, hds)
         assert all(e[i] == alone[i][0] for i in range(len(fs)))
         assert all(np.array_equal(hdn[i], alone[i][1]) for i in range(len(fs)))
-        assert B.vdwgb_batch_launches(bt) == 8 * max(int(split), 1)
+        assert B.vdwgb_batch_launches(bt) == 8 * parts
     finally:
         if bt is not None:
             B.vdwgb_batch_free(bt)
