@@ -786,8 +786,8 @@ static int plan(vdwgb_data *h) {
     const size_t lim = di.maxsmem - 1024;
     // in-place x / y transforms (permuted spectrum between the passes) where a
     // two-pass split is compiled (FP32); 0: out of place through the scratch buffer
-    S.sx1 = prec == VDWGB_FP32_MIXED ? fft_split(nx) : 0;
-    S.sy1 = prec == VDWGB_FP32_MIXED ? fft_split(ny) : 0;
+    S.sx1 = prec == VDWGB_FP32_MIXED ? xy_split(nx) : 0;
+    S.sy1 = prec == VDWGB_FP32_MIXED ? xy_split(ny) : 0;
     S.sz1 = prec == VDWGB_FP32_MIXED ? fft_split(nz) : 0;
     const int workx = S.sx1 ? 0 : 1, worky = S.sy1 ? 0 : 1;
     int nbuf = 2;

@@ -314,6 +314,18 @@ __device__ __forceinline__ void fft_ip_auto(cx<T> *a, int n, int nlines, int ld,
     }
 }
 
+// The x / y passes also split 640-point axes (the paper's density grid), as
+// 32 x 20: their blocks hold the registers of a 32-point codelet (two blocks
+// per SM), which the z passes, at three blocks per SM, do not.
+__host__ __device__ constexpr int xy_split(int n) { return n == 640 ? 32 : fft_split(n); }
+
+// In-place permuted transform of the x / y passes (an xy_split length).
+template <bool INV, typename T>
+__device__ __forceinline__ void fft_ip_xy_auto(cx<T> *a, int n, int nlines, int ld, const cx<T> *tw) {
+    if (n == 640) fft_ip<32, 20, INV>(a, nlines, ld, tw);
+    else fft_ip_auto<INV>(a, n, nlines, ld, tw);
+}
+
 // Inverse in-place permuted transform of a z tile whose input is the staged
 // half spectrum of the 20 real fields, packed into complex lines on the fly:
 // line l = 10 li + c holds Z(f) = X_2c(f) + i X_2c+1(f) for f < nzh (the

@@ -213,8 +213,8 @@ extern "C" int vdwgb_calculate_noalloc(int device, int functional, int nx, int n
     const int nzh = S.nzh;
     S.LZ = tile_lines(0, nz, nx * ny);
     S.LZi = tile_lines(3, nz, nx * ny);
-    S.sx1 = fft_split(nx);                   // in-place x / y transforms where compiled
-    S.sy1 = fft_split(ny);
+    S.sx1 = xy_split(nx);                    // in-place x / y transforms where compiled
+    S.sy1 = xy_split(ny);
     S.sz1 = fft_split(nz);
     const int workx = S.sx1 ? 0 : 1, worky = S.sy1 ? 0 : 1;
     S.Wy = tile_cols(ny, nzh, 2 + worky);

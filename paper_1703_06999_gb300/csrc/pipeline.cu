@@ -677,7 +677,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_xy(const SysDev
         const int split = sizeof(T) == 4 ? (XPASS ? S.sx1 : S.sy1) : 0;
         cx<T> *R;
         if (split) {
-            fft_ip_auto<INV>(in, ap.n, g.L, g.ldr, tw);
+            fft_ip_xy_auto<INV>(in, ap.n, g.L, g.ldr, tw);
             R = in;
         } else {
             R = fft_auto<INV>(in, work, ap, g.L, g.ldr, tw);

@@ -114,7 +114,7 @@ int vdwgb_slab_new(int functional, int nx, int ny, int nz, const double *cell9, 
         LaunchSet &L = s->B->ls;
         S.yoff = rank * s->nyl;
         S.nyg = ny;
-        S.sy1 = precision == VDWGB_FP32_MIXED ? fft_split(ny) : 0;   // the y pass's output order
+        S.sy1 = precision == VDWGB_FP32_MIXED ? xy_split(ny) : 0;    // the y pass's output order
         S.invN = 1.0 / N;
         S.invNf = (float)S.invN;
         S.escale = 0.5 * std::fabs(det) / (N * N);
