@@ -282,8 +282,7 @@ CONTRACT_FMA64_PER_KPOINT = 630 + 800 + 40
 # list summarised in the profiles directory).  An entry is removed when its
 # kernel changes.
 MEASURED_TRAFFIC = {
-    "uneven64": {"zfwd": 2616e6, "zinv": 2904e6, "contract": 3979e6, "yfwd": 3880e6, "xfwd": 3880e6,
-                 "xinv": 3879e6, "yinv": 3880e6},
+    "uneven64": {"zfwd": 2616e6, "zinv": 2904e6, "contract": 3979e6},
 }
 
 # Instruction-issue utilisation of the z-forward kernel (the q0 step in
