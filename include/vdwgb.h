@@ -249,7 +249,13 @@ int vdwgb_set_fused(int enable);
  * kz-columns with 1 to 4 ring buffers, z-inverse lines) on the handle's
  * own buffers and keeps the
  * fastest; the choice is cached per (grid, precision) for the process and
- * reused by later handles, batches and the server.  Default off. */
+ * reused by later handles, batches and the server.  Default off.  Candidates
+ * (and the untuned default) of the FP32-mixed form are capped in shared
+ * memory per block: y / x tiles at half of an SM's shared memory less 2.5 KB
+ * (two blocks per SM), z tiles at a third less 1.8 KB (three blocks) unless
+ * that leaves tiles of a single line.  The environment variables
+ * VDWGB_XY_CAP and VDWGB_Z_CAP (bytes), read once per process, replace the
+ * two caps. */
 int vdwgb_set_autotune(int enable);
 
 /* Replace the tile shapes of an initialised handle's plan (as the autotuner
