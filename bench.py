@@ -70,6 +70,17 @@ def rank_seeds(rank, nb):
     return [rank * 1000 + i // 2 for i in range(nb)]
 
 
+def job_points(pts, world, device):
+    """Grid points of one step over all ranks (each rank its own systems)."""
+    if world <= 1:
+        return pts
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(pts)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def reduce_max(x, device):
     """Max of a float over the ranks of the default process group."""
     import torch
@@ -108,7 +119,7 @@ def make_workload(name, rank, device):
         return [inputs.ligand_shell(rank, device=device)]
     if name == "shell640":
         return [shell640(rank, device)]
-    return inputs.uneven_batch(rank, count=64, device=device)
+    return inputs.uneven_batch(rank, count=64, device=device, shape_seed=0)
 
 
 def shell160(seed, device):
@@ -765,7 +776,8 @@ def main():
     log("timed batched steps")
     step_ms, tot_ms, clocks = timed_batch(B, torch, bt, ns, ss, dn, ds, en, sp, stream, args.steps, args.warmup,
                                           flush, world, dev, local)
-    value = pts * world * args.steps / (tot_ms / 1000.0)
+    job_pts = job_points(pts, world, dev)
+    value = job_pts * args.steps / (tot_ms / 1000.0)
     per_launch_ms = stage_breakdown(B, torch, bt, ns, ss, dn, ds, en, sp, flush, args.steps)
     if args.only_timed:
         if rank == 0:
@@ -808,7 +820,7 @@ def main():
     e2e_s = time.perf_counter() - t0
     e2e_val = pts * ke / e2e_s
     if world > 1:
-        e2e_val = pts * world * ke / reduce_max(e2e_s, dev)
+        e2e_val = job_pts * ke / reduce_max(e2e_s, dev)
     h2d = sum(2 * s.npts * 8 for s in systems)
     d2h = sum(2 * s.npts * 8 for s in systems) + 8 * nb
     launches_per_step = B.vdwgb_batch_launches(bt)
@@ -942,7 +954,7 @@ def main():
         if not any(B.vdwgb_plan_info(f.h)["cluster"] for f in fd):
             sbd["plane"] = 0
         extra = {"dimer96_batch8": {
-            "value": ptsd * world * args.steps / (totd / 1000.0), "unit": "grid pts/s",
+            "value": job_points(ptsd, world, dev) * args.steps / (totd / 1000.0), "unit": "grid pts/s",
             "ms_per_step": totd / args.steps, "clocks": clkd,
             "stages": {n: {"ms_per_launch": float(m), "frac_hbm": (sbd[n] / (m / 1000.0) / 1e9 / hbm)
                            if m > 0 else None} for n, m in zip(names, pld)}}}

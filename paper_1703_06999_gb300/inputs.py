@@ -214,10 +214,16 @@ def ligand_shell(seed=0, ngrid=192, L=36.0, functional=1, device="cpu") -> Syste
 
 
 def uneven_batch(seed=0, count=64, sizes=(32, 48, 64, 80, 96, 128), functional_mix=True,
-                 device="cpu") -> List[System]:
+                 device="cpu", shape_seed=None) -> List[System]:
     """Independent systems with grids drawn per axis from ``sizes`` (non-cubic
-    mixes), spacing h in [0.15, 0.30] bohr and 4-60 exponentials each."""
-    g = _rng(seed)
+    mixes), spacing h in [0.15, 0.30] bohr and 4-60 exponentials each.
+
+    shape_seed: grids, spacings, exponential counts and functionals come from
+    this seed and the exponentials themselves from ``seed`` (ranks of a
+    weak-scaling run: the same work per rank, independent densities).  None,
+    or equal to ``seed``: everything from ``seed``."""
+    g = _rng(seed if shape_seed is None else shape_seed)
+    ga = _rng(seed) if shape_seed is not None and shape_seed != seed else None
     out = []
     for i in range(count):
         shape = tuple(int(v) for v in g.choice(sizes, 3))
@@ -226,6 +232,9 @@ def uneven_batch(seed=0, count=64, sizes=(32, 48, 64, 80, 96, 128), functional_m
         na = int(g.integers(4, 61))
         atoms = [(float(g.uniform(1, 8)), float(g.uniform(1, 3)),
                   tuple(g.uniform(0, 1, 3) * lengths)) for _ in range(na)]
+        if ga is not None:      # g drew its atoms all the same, so its stream is seed-independent
+            atoms = [(float(ga.uniform(1, 8)), float(ga.uniform(1, 3)),
+                      tuple(ga.uniform(0, 1, 3) * lengths)) for _ in range(na)]
         fn = int(g.integers(1, 3)) if functional_mix else 1
         out.append(make_system(shape, np.diag(lengths), atoms, fn, 1e-10, device,
                                "batch%d_%dx%dx%d" % ((i,) + shape)))
